@@ -1,0 +1,453 @@
+/*
+ * sw_oracle.c -- plain FP64 CPU oracle for rigid alignment in sliced
+ * 2-Wasserstein distance (arXiv 2503.13756).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  It shares no code,
+ * header, table or constant generator with the CUDA library: every quantity
+ * here is computed from its definition, in double precision, with plain
+ * loops and no blocking, fusion or reordering.
+ *
+ * Conventions (readings of the paper, each restated where it is used):
+ *   image    F[r][c], r = row, c = column, L x L cells on [-1,1]^2, pitch
+ *            h = 2/L, cell centre x = -1 + (c+1/2)h, y = -1 + (r+1/2)h
+ *            (App. A.1.2 "Pixel Grid and Discrete Image").
+ *   angles   theta_k = 2*pi*k/n, k = 0..n-1 (App. A.1.2, "Discretization
+ *            Parameters"); direction e_k = (cos theta_k, sin theta_k).
+ *   bins     B bins of width h with centres s_b = (b - (B-1)/2) h; CDF
+ *            nodes e_j = (j - B/2) h, j = 0..B.
+ *   levels   z_p = (p + 1/2)/M (level_rule 0) or z_p = p/M (level_rule 1,
+ *            the left Riemann points of Theorem E3 in App. A).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    int32_t best_l;   /* argmin over the rotation grid, lowest index on ties */
+    int32_t status;   /* 0 ok, 1 image f unusable, 2 image g unusable        */
+    double angle;     /* 2*pi*best_l/n                                        */
+    double shift[2];  /* optimal translation at best_l (0 if translation=0)   */
+    double d2;        /* squared sliced-W2 distance at best_l                 */
+} orc_result;
+
+/* Number of bins that holds every pixel-centre projection of an L x L
+ * image with at least half a bin to spare on each side:
+ * B = 2*ceil((L-1)/sqrt(2)) + 2.  The paper samples L points on [-1,1]
+ * (Sec. 2.3 "Computation"); its images live on the unit disk, ours may fill
+ * the square, so the projection range is widened to the square's diagonal.
+ * Empty bins never change a quantile. */
+int orc_default_bins(int L)
+{
+    return 2 * (int)ceil((double)(L - 1) / sqrt(2.0)) + 2;
+}
+
+/* Image preparation, Sec. 5.4 (noisy images are split g = g+ + g- and the
+ * positive part is renormalised) and App. A.1.2 (cell averages normalised
+ * to sum 1).  Writes out = max(img,0)/mass and returns mass = sum max(img,0);
+ * returns 0 if the mass is not positive or any pixel is not finite. */
+double orc_prepare(const double *img, int L, double *out)
+{
+    double mass = 0.0;
+    for (int i = 0; i < L * L; ++i) {
+        if (!isfinite(img[i])) return 0.0;
+        double v = img[i] > 0.0 ? img[i] : 0.0;
+        out[i] = v;
+        mass += v;
+    }
+    if (!(mass > 0.0)) return 0.0;
+    for (int i = 0; i < L * L; ++i) out[i] /= mass;
+    return mass;
+}
+
+/* Radon projection (Eq. radon_transform, Sec. 2.1; the appendix form
+ * P_theta g(s) = integral of g(s theta + t theta_perp) dt), discretised as a
+ * pixel-driven linear splat.  The paper computes projections with a NUFFT
+ * and is silent on a direct discretisation; this reading sends each cell's
+ * mass to the two bins around s = <(x,y), e_k>, split linearly, which keeps
+ * the mass and the first moment of every projection exact.
+ * U is [n][B], row k = projection at theta_k. */
+void orc_project(const double *F, int L, int n, int B, double *U)
+{
+    const double h = 2.0 / L;
+    memset(U, 0, sizeof(double) * (size_t)n * B);
+    for (int k = 0; k < n; ++k) {
+        const double th = 2.0 * ORC_PI * k / n;
+        const double ct = cos(th), st = sin(th);
+        double *Uk = U + (size_t)k * B;
+        for (int r = 0; r < L; ++r) {
+            const double y = -1.0 + (r + 0.5) * h;
+            for (int c = 0; c < L; ++c) {
+                const double x = -1.0 + (c + 0.5) * h;
+                const double f = F[r * L + c];
+                if (f == 0.0) continue;
+                const double s = x * ct + y * st;
+                const double u = s / h + 0.5 * (B - 1);
+                const double fl = floor(u);
+                const int b0 = (int)fl;
+                const double t = u - fl;
+                Uk[b0] += f * (1.0 - t);
+                if (t > 0.0) Uk[b0 + 1] += f * t;
+            }
+        }
+    }
+}
+
+/* Quantile function of one histogram (Sec. 2.3 "Computation": CDF by
+ * cumulative sum, ICDF by linear interpolation; Eq. inv_cdf with the
+ * appendix's ">=" reading, App. A.1.1).  The histogram U[0..B) has a
+ * piecewise-constant density on bins [e_j, e_{j+1}], so its CDF is the
+ * piecewise-linear function through (e_j, F_j), F_0 = 0, F_j = sum_{b<j} U_b.
+ * For tau = z_p * F_B the quantile is Q = e_{j-1} + h (tau - F_{j-1}) / U_{j-1}
+ * with j = min{ j >= 1 : F_j >= tau }; for tau = 0 (level p = 0 under
+ * level_rule 1) it is the left edge of the first bin with positive mass,
+ * the limit of Q(z) as z -> 0+.
+ * The levels are walked in increasing order against the cumulative mass
+ * (a merge of the two sorted sequences).  Returns 0 if the histogram has no
+ * positive mass. */
+static int orc_quantiles_1d(const double *U, int B, double h, int M,
+                            int level_rule, double *Fbuf, double *Q)
+{
+    Fbuf[0] = 0.0;
+    for (int j = 1; j <= B; ++j) Fbuf[j] = Fbuf[j - 1] + U[j - 1];
+    const double total = Fbuf[B];
+    if (!(total > 0.0)) return 0;
+    int j = 1;
+    for (int p = 0; p < M; ++p) {
+        const double z = level_rule == 0 ? (p + 0.5) / M : (double)p / M;
+        const double tau = z * total;
+        if (tau == 0.0) {
+            int jj = 1;
+            while (jj < B && !(Fbuf[jj] > 0.0)) ++jj;
+            Q[p] = (jj - 1 - 0.5 * B) * h;
+            continue;
+        }
+        while (j < B && Fbuf[j] < tau) ++j;
+        const double mass = Fbuf[j] - Fbuf[j - 1];
+        double frac = mass > 0.0 ? (tau - Fbuf[j - 1]) / mass : 0.0;
+        if (frac < 0.0) frac = 0.0;
+        if (frac > 1.0) frac = 1.0;
+        Q[p] = (j - 1 - 0.5 * B) * h + h * frac;
+    }
+    return 1;
+}
+
+/* Quantiles of every projection: Q is [n][M], row k = U_I column k of the
+ * paper (Sec. 2.3).  Returns 0 if some projection has no mass. */
+int orc_quantiles(const double *U, int n, int B, double h, int M,
+                  int level_rule, double *Q)
+{
+    double *Fbuf = (double *)malloc(sizeof(double) * (B + 1));
+    int ok = 1;
+    for (int k = 0; k < n; ++k)
+        ok &= orc_quantiles_1d(U + (size_t)k * B, B, h, M, level_rule, Fbuf,
+                               Q + (size_t)k * M);
+    free(Fbuf);
+    return ok;
+}
+
+/* Squared 1-D W2 distance between two histograms on the same bin grid,
+ * computed exactly (App. A.1.1: W2^2 = integral over z in [0,1] of
+ * (Q_u(z) - Q_v(z))^2).  Both quantile functions are piecewise linear in z
+ * with breakpoints at the normalised cumulative masses; on each interval of
+ * the merged breakpoints the integrand is the square of a linear function
+ * and is integrated in closed form.  Used only to check the sampled-level
+ * sums against the bound of Theorem E3 (App. A). */
+double orc_w2_hist_exact(const double *Ua, const double *Ub, int B, double h)
+{
+    double ta = 0.0, tb = 0.0;
+    for (int b = 0; b < B; ++b) { ta += Ua[b]; tb += Ub[b]; }
+    if (!(ta > 0.0) || !(tb > 0.0)) return NAN;
+    int ia = 0, ib = 0;
+    while (ia < B && Ua[ia] <= 0.0) ++ia;
+    while (ib < B && Ub[ib] <= 0.0) ++ib;
+    double Fa = 0.0, Fb = 0.0;   /* cumulative mass before bin ia / ib  */
+    double z = 0.0, acc = 0.0;
+    while (ia < B && ib < B && z < 1.0) {
+        const double za1 = (Fa + Ua[ia]) / ta;  /* end of bin ia in z     */
+        const double zb1 = (Fb + Ub[ib]) / tb;
+        double z1 = za1 < zb1 ? za1 : zb1;
+        if (z1 > 1.0) z1 = 1.0;
+        const double dz = z1 - z;
+        if (dz > 0.0) {
+            /* Q_a(z) = e_ia + h (z*ta - Fa)/Ua[ia], same for b. */
+            const double sa = h * ta / Ua[ia], sb = h * tb / Ub[ib];
+            const double qa0 = (ia - 0.5 * B) * h + sa * (z - Fa / ta);
+            const double qb0 = (ib - 0.5 * B) * h + sb * (z - Fb / tb);
+            const double d0 = qa0 - qb0, slope = sa - sb;
+            acc += dz * (d0 * d0 + d0 * slope * dz + slope * slope * dz * dz / 3.0);
+        }
+        z = z1;
+        if (za1 <= z1) {
+            Fa += Ua[ia];
+            ++ia;
+            while (ia < B && Ua[ia] <= 0.0) ++ia;
+        }
+        if (zb1 <= z1) {
+            Fb += Ub[ib];
+            ++ib;
+            while (ib < B && Ub[ib] <= 0.0) ++ib;
+        }
+    }
+    return acc;
+}
+
+/* Translation centring (closed-form optimal translation; derived from the
+ * shift lemma in the proof of the translation theorem, App. B, where
+ * P_theta(T_s f)(t) = P_theta f(t - <s, theta>)): a translation by s adds
+ * <s, e_k> to every quantile of column k.  With ubar_k = mean_p Q[k][p],
+ * a = (2/n) sum_k ubar_k e_k and Qc[k][p] = Q[k][p] - <a, e_k>.
+ * For n >= 3, sum_k e_k e_k^T = (n/2) I, which makes a the least-squares
+ * optimum. */
+void orc_center(const double *Q, int n, int M, double *a, double *Qc)
+{
+    double ax = 0.0, ay = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double ub = 0.0;
+        for (int p = 0; p < M; ++p) ub += Q[(size_t)k * M + p];
+        ub /= M;
+        const double th = 2.0 * ORC_PI * k / n;
+        ax += ub * cos(th);
+        ay += ub * sin(th);
+    }
+    ax *= 2.0 / n;
+    ay *= 2.0 / n;
+    a[0] = ax;
+    a[1] = ay;
+    if (Qc) {
+        for (int k = 0; k < n; ++k) {
+            const double th = 2.0 * ORC_PI * k / n;
+            const double off = ax * cos(th) + ay * sin(th);
+            for (int p = 0; p < M; ++p)
+                Qc[(size_t)k * M + p] = Q[(size_t)k * M + p] - off;
+        }
+    }
+}
+
+/* Squared distance over the rotation grid, computed directly from its
+ * definition (Eq. discrete_sw2 and Eq. discrete_rot_sw2, Sec. 2.3):
+ *   D[l] = 1/(n M) * sum_k sum_p (Qf[k][p] - Qg[(k-l) mod n][p])^2,
+ * which compares f with R_{alpha_l} g, alpha_l = 2 pi l / n, because
+ * P_theta(R_alpha g) = P_{theta - alpha} g.  O(n^2 M), no FFT. */
+void orc_rotation_curve(const double *Qf, const double *Qg, int n, int M,
+                        double *D)
+{
+    const double inv = 1.0 / ((double)n * M);
+    for (int l = 0; l < n; ++l) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const int kg = ((k - l) % n + n) % n;
+            const double *u = Qf + (size_t)k * M;
+            const double *v = Qg + (size_t)kg * M;
+            for (int p = 0; p < M; ++p) {
+                const double d = u[p] - v[p];
+                acc += d * d;
+            }
+        }
+        D[l] = acc * inv;
+    }
+}
+
+/* Per-image transform: prepare, project, quantiles and (if translation)
+ * centring.  Q receives the quantiles used in the distance (centred when
+ * translation != 0), a the centring vector.  Returns 0 for an unusable
+ * image. */
+typedef struct {
+    int L, n, M, B, level_rule, translation;
+} orc_cfg;
+
+static int orc_transform(const orc_cfg *cfg, const double *img, double *Q,
+                         double *a)
+{
+    const int L = cfg->L, n = cfg->n, M = cfg->M, B = cfg->B;
+    double *F = (double *)malloc(sizeof(double) * (size_t)L * L);
+    double *U = (double *)malloc(sizeof(double) * (size_t)n * B);
+    double *Qraw = (double *)malloc(sizeof(double) * (size_t)n * M);
+    int ok = orc_prepare(img, L, F) > 0.0;
+    if (ok) {
+        orc_project(F, L, n, B, U);
+        ok = orc_quantiles(U, n, B, 2.0 / L, M, cfg->level_rule, Qraw);
+    }
+    if (ok) {
+        orc_center(Qraw, n, M, a, cfg->translation ? Q : NULL);
+        if (!cfg->translation) memcpy(Q, Qraw, sizeof(double) * (size_t)n * M);
+    }
+    free(F);
+    free(U);
+    free(Qraw);
+    return ok;
+}
+
+/* Decision (Eq. optimal_rotation and Eq. discrete_rot_sw2): l* = argmin D,
+ * lowest index on exact ties; shift s*(l) = a_f - R_{alpha_l} a_g when the
+ * translation is optimised, 0 otherwise. */
+static void orc_decide(const double *D, int n, const double *af,
+                       const double *ag, int translation, double *shifts,
+                       orc_result *res)
+{
+    int best = 0;
+    for (int l = 1; l < n; ++l)
+        if (D[l] < D[best]) best = l;
+    for (int l = 0; l < n; ++l) {
+        if (!shifts) break;
+        const double al = 2.0 * ORC_PI * l / n;
+        const double rx = cos(al) * ag[0] - sin(al) * ag[1];
+        const double ry = sin(al) * ag[0] + cos(al) * ag[1];
+        shifts[2 * l] = translation ? af[0] - rx : 0.0;
+        shifts[2 * l + 1] = translation ? af[1] - ry : 0.0;
+    }
+    const double ab = 2.0 * ORC_PI * best / n;
+    res->best_l = best;
+    res->status = 0;
+    res->angle = ab;
+    if (translation) {
+        res->shift[0] = af[0] - (cos(ab) * ag[0] - sin(ab) * ag[1]);
+        res->shift[1] = af[1] - (sin(ab) * ag[0] + cos(ab) * ag[1]);
+    } else {
+        res->shift[0] = res->shift[1] = 0.0;
+    }
+    res->d2 = D[best];
+}
+
+static void orc_bad(orc_result *res, int status)
+{
+    res->best_l = -1;
+    res->status = status;
+    res->angle = NAN;
+    res->shift[0] = res->shift[1] = NAN;
+    res->d2 = NAN;
+}
+
+/* One pair, full curve: f is the reference, g is rotated (and translated
+ * when translation != 0) onto f.  D (may be NULL) receives the n distances,
+ * shifts (may be NULL) the n optimal translations. */
+void orc_align_pair(const double *f, const double *g, int L, int n, int M,
+                    int B, int level_rule, int translation, double *D,
+                    double *shifts, orc_result *res)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    double *Qf = (double *)malloc(sizeof(double) * (size_t)n * M);
+    double *Qg = (double *)malloc(sizeof(double) * (size_t)n * M);
+    double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
+    double af[2] = {0, 0}, ag[2] = {0, 0};
+    const int okf = orc_transform(&cfg, f, Qf, af);
+    const int okg = orc_transform(&cfg, g, Qg, ag);
+    if (!okf || !okg) {
+        orc_bad(res, okf ? 2 : 1);
+        if (D) for (int l = 0; l < n; ++l) D[l] = NAN;
+        if (shifts) for (int l = 0; l < 2 * n; ++l) shifts[l] = NAN;
+    } else {
+        orc_rotation_curve(Qf, Qg, n, M, Dl);
+        orc_decide(Dl, n, af, ag, translation, shifts, res);
+        if (D) memcpy(D, Dl, sizeof(double) * (size_t)n);
+    }
+    free(Qf);
+    free(Qg);
+    free(Dl);
+}
+
+/* ---- many pairs, parallel over independent work items ------------------ */
+
+typedef struct {
+    const orc_cfg *cfg;
+    const double *imgs;    /* [nimg][L][L] */
+    double *Q;             /* [nimg][n][M] */
+    double *A;             /* [nimg][2]    */
+    int *ok;               /* [nimg]       */
+    int nimg;
+    /* pair stage */
+    int Nq, Nt;
+    orc_result *out;       /* [Nq][Nt]     */
+    int next;              /* shared work counter (guarded by mu) */
+    pthread_mutex_t mu;
+} orc_job;
+
+static int orc_take(orc_job *job, int limit)
+{
+    pthread_mutex_lock(&job->mu);
+    const int i = job->next < limit ? job->next++ : -1;
+    pthread_mutex_unlock(&job->mu);
+    return i;
+}
+
+static void *orc_image_worker(void *arg)
+{
+    orc_job *job = (orc_job *)arg;
+    const orc_cfg *c = job->cfg;
+    for (int i; (i = orc_take(job, job->nimg)) >= 0;)
+        job->ok[i] = orc_transform(c, job->imgs + (size_t)i * c->L * c->L,
+                                   job->Q + (size_t)i * c->n * c->M,
+                                   job->A + 2 * (size_t)i);
+    return NULL;
+}
+
+static void *orc_pair_worker(void *arg)
+{
+    orc_job *job = (orc_job *)arg;
+    const orc_cfg *c = job->cfg;
+    double *D = (double *)malloc(sizeof(double) * c->n);
+    for (int w; (w = orc_take(job, job->Nq * job->Nt)) >= 0;) {
+        const int i = w / job->Nt, j = job->Nq + w % job->Nt;
+        orc_result *res = job->out + w;
+        if (!job->ok[w / job->Nt]) { orc_bad(res, 1); continue; }
+        if (!job->ok[j]) { orc_bad(res, 2); continue; }
+        orc_rotation_curve(job->Q + (size_t)i * c->n * c->M,
+                           job->Q + (size_t)j * c->n * c->M, c->n, c->M, D);
+        orc_decide(D, c->n, job->A + 2 * (size_t)i, job->A + 2 * (size_t)j,
+                   c->translation, NULL, res);
+    }
+    free(D);
+    return NULL;
+}
+
+static void orc_run(orc_job *job, void *(*fn)(void *), int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    job->next = 0;
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, fn, job);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+}
+
+/* All pairs (query i, template j): out[i*Nt + j] aligns template j onto
+ * query i (query = reference f, template = g).  Queries are [Nq][L][L],
+ * templates [Nt][L][L], both double.  Returns 0 on allocation failure. */
+int orc_align_all_pairs(const double *queries, int Nq, const double *templates,
+                        int Nt, int L, int n, int M, int B, int level_rule,
+                        int translation, int nthreads, orc_result *out)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    const int nimg = Nq + Nt;
+    double *imgs = (double *)malloc(sizeof(double) * (size_t)nimg * L * L);
+    double *Q = (double *)malloc(sizeof(double) * (size_t)nimg * n * M);
+    double *A = (double *)malloc(sizeof(double) * 2 * (size_t)nimg);
+    int *ok = (int *)malloc(sizeof(int) * (size_t)nimg);
+    if (!imgs || !Q || !A || !ok) {
+        free(imgs); free(Q); free(A); free(ok);
+        return 0;
+    }
+    memcpy(imgs, queries, sizeof(double) * (size_t)Nq * L * L);
+    memcpy(imgs + (size_t)Nq * L * L, templates, sizeof(double) * (size_t)Nt * L * L);
+    orc_job job;
+    memset(&job, 0, sizeof(job));
+    job.cfg = &cfg;
+    job.imgs = imgs;
+    job.Q = Q;
+    job.A = A;
+    job.ok = ok;
+    job.nimg = nimg;
+    job.Nq = Nq;
+    job.Nt = Nt;
+    job.out = out;
+    pthread_mutex_init(&job.mu, NULL);
+    orc_run(&job, orc_image_worker, nthreads);
+    orc_run(&job, orc_pair_worker, nthreads);
+    pthread_mutex_destroy(&job.mu);
+    free(imgs); free(Q); free(A); free(ok);
+    return 1;
+}
