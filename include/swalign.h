@@ -1,0 +1,184 @@
+/*
+ * swalign.h -- C ABI of the GB300 library for rigid image alignment in
+ * sliced 2-Wasserstein distance (arXiv 2503.13756, "Fast rigid alignment of
+ * heterogeneous images in sliced Wasserstein distance").
+ *
+ * The library scores a reference image f against a moving image g at every
+ * rotation on the grid alpha_l = 2 pi l / n (Eq. optimal_rotation, Sec. 1.1;
+ * Eq. discrete_rot_sw2, Sec. 2.3) and, optionally, at the closed-form optimal
+ * translation (derived from the shift lemma in the proof of Theorem 3.2,
+ * App. B: a translation by s adds <s, theta_k> to every quantile of
+ * projection k).  It returns the best rotation, the translation and the
+ * squared distance d^2 = 1/(nM) ||U_I - T_l V_I||_F^2 (Eq. discrete_sw2).
+ *
+ * Conventions shared by every call
+ *  - Images are L x L float32, row-major [row][column]; cell centres at
+ *    x = -1 + (c + 1/2) h, y = -1 + (r + 1/2) h with h = 2/L (App. A.1.2),
+ *    so y grows with the row index.  Rotations are counter-clockwise in
+ *    (x, y).  Negative pixels are clipped to 0 (the g+ rule of Sec. 5.4);
+ *    images need not be normalised (quantiles do not depend on the mass).
+ *  - Projection angles theta_k = 2 pi k / n, k = 0..n-1; B bins of width h
+ *    centred at s_b = (b - (B-1)/2) h; M quantile levels z_p = (p + 1/2)/M
+ *    (or p/M with level_rule = 1).
+ *  - Every pointer named d_* is DEVICE memory owned by the caller; the
+ *    library never frees it.  Image, projection and quantile pointers must be
+ *    16-byte aligned.  The library owns only its workspace, held in the
+ *    context (grown on demand by cudaMalloc, or sized up front by
+ *    sw_reserve).
+ *  - Every call is asynchronous on the given stream (NULL = legacy default
+ *    stream).  The return value reports argument validation and launch errors
+ *    synchronously; sw_last_error() gives a message.  A call that returns an
+ *    error has launched nothing.
+ *  - Per-item failures (an image with no positive mass or a non-finite
+ *    pixel) are reported in sw_result.status; such results hold NaN.
+ *  - A context is used by one host thread at a time.  No C++ exception
+ *    crosses this interface.
+ */
+#ifndef SWALIGN_H
+#define SWALIGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, declared without the CUDA headers. */
+typedef struct CUstream_st *sw_stream_t;
+
+typedef enum {
+    SW_OK = 0,
+    SW_ERR_INVALID_ARG = 1, /* bad size, NULL or misaligned pointer       */
+    SW_ERR_UNSUPPORTED = 2, /* valid but not built (e.g. precision)       */
+    SW_ERR_OOM = 3,         /* workspace does not fit the memory limit    */
+    SW_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed       */
+    SW_ERR_TIMEOUT = 5      /* a bounded device wait gave up              */
+} sw_status;
+
+typedef enum {
+    SW_PREC_FP32 = 0, /* correlation in FP32 on the CUDA cores                  */
+    SW_PREC_BF16 = 1, /* correlation GEMM on tcgen05, BF16 in, FP32 accumulate  */
+    SW_PREC_FP16 = 2  /* correlation GEMM on tcgen05, FP16 in, FP32 accumulate  */
+} sw_precision;
+
+typedef struct {
+    int32_t L;              /* image side, 2..512                                   */
+    int32_t n_theta;        /* n: even, 4..1024, factors 2, 3, 5 only               */
+    int32_t n_levels;       /* M: 1..1024                                           */
+    int32_t n_bins;         /* 0 = default B = 2 ceil((L-1)/sqrt 2) + 2; else even, */
+                            /* >= the default (fewer bins would lose mass)          */
+    int32_t translation;    /* 1 = closed-form optimal translation, 0 = rotation    */
+                            /* only (the paper's Eq. discrete_rot_sw2)              */
+    int32_t level_rule;     /* 0 = midpoints (p+1/2)/M, 1 = p/M (App. A, Thm. E3)   */
+    int32_t gemm_precision; /* sw_precision, used by sw_align_batch / sw_bank_align */
+} sw_params;
+
+typedef struct {
+    int32_t best_l;   /* l*: g is turned by alpha* = 2 pi l* / n onto f         */
+    int32_t status;   /* 0 ok, 1 reference/query unusable, 2 template unusable  */
+    float angle_rad;  /* alpha* = 2 pi l* / n                                   */
+    float reserved;
+    double shift[2];  /* s*: f ~ T_{s*} R_{alpha*} g; 0 when translation == 0   */
+    double d2;        /* squared distance at (l*, s*), Eq. discrete_sw2         */
+} sw_result;          /* 40 bytes */
+
+typedef struct sw_ctx sw_ctx;
+typedef struct sw_bank sw_bank;
+
+/* Context on CUDA device `device`.  *out receives the context. */
+sw_status sw_create(int device, sw_ctx **out);
+/* Frees the workspace; waits for the device. NULL is ignored. */
+void sw_destroy(sw_ctx *ctx);
+/* Message for the last failing call on ctx ("" if none).  Owned by ctx. */
+const char *sw_last_error(const sw_ctx *ctx);
+/* Default bin count for side L: 2 ceil((L-1)/sqrt 2) + 2. */
+int sw_default_bins(int L);
+/* Caps the workspace (bytes; 0 = no cap).  A call whose workspace would
+ * exceed the cap returns SW_ERR_OOM without launching anything. */
+sw_status sw_set_workspace_limit(sw_ctx *ctx, size_t bytes);
+/* Workspace bytes that sw_align_batch needs for Nq x Nt pairs. */
+size_t sw_batch_workspace_bytes(const sw_params *p, int Nq, int Nt);
+/* Allocates the workspace for batches up to Nq x Nt now, so that later
+ * calls of that size allocate nothing (and can be stream-captured). */
+sw_status sw_reserve(sw_ctx *ctx, const sw_params *p, int Nq, int Nt);
+
+/* Stages of the alignment, for sw_profile_read. */
+typedef enum {
+    SW_STAGE_PROJECT = 0,   /* Radon projection                         */
+    SW_STAGE_QUANTILE = 1,  /* CDF + quantiles                          */
+    SW_STAGE_SPECTRUM = 2,  /* centring + FFT over angle                */
+    SW_STAGE_CORR = 3,      /* per-frequency correlation GEMM           */
+    SW_STAGE_DECIDE = 4,    /* inverse FFT + argmin + FP64 distance     */
+    SW_STAGE_BEST = 5,      /* best template per query                  */
+    SW_STAGE_COUNT = 8
+} sw_stage;
+
+/* Kernel timing (not part of the method; used by the benchmark).  With
+ * enable = 1 every kernel launched through ctx is bracketed by CUDA events on
+ * its stream; sw_profile_read waits for the recorded events, writes the
+ * summed milliseconds and launch counts per stage (arrays of SW_STAGE_COUNT)
+ * and clears the record.  enable = 0 stops recording. */
+sw_status sw_profile(sw_ctx *ctx, int enable);
+sw_status sw_profile_read(sw_ctx *ctx, double *ms, int64_t *launches);
+/* Kernels launched through ctx since its creation. */
+int64_t sw_launch_count(const sw_ctx *ctx);
+
+/* Radon projections (Eq. radon_transform, Sec. 2.1; Sec. 2.3 "Computation")
+ * of nb images, discretised as a pixel-driven linear splat: the mass of each
+ * cell goes to the two bins around s = <(x, y), theta_k>, split linearly.
+ *   d_img  [nb][L][L] float32 (input)
+ *   d_proj [nb][n][B] float32 (output); row k is the projection at theta_k,
+ *          holding the clipped (not renormalised) mass of the image. */
+sw_status sw_project(sw_ctx *ctx, const sw_params *p, const float *d_img, int nb,
+                     float *d_proj, sw_stream_t stream);
+
+/* Quantile functions of projections (Sec. 2.3: CDF by cumulative sum, ICDF
+ * by linear interpolation; Eq. inv_cdf with the ">=" of App. A.1.1).
+ *   d_proj   [nb][n][B] float32 (input, as written by sw_project)
+ *   d_q      [nb][n][M] float32 (output): d_q[i][k][p] = Q_k(z_p), uncentred
+ *   d_center [nb][2] double (output, may be NULL): a = (2/n) sum_k ubar_k theta_k,
+ *            the centring vector (= the translation-optimal offset)
+ *   d_norm   [nb] double (output, may be NULL): sum_k sum_p (Q_k(z_p) - <a, theta_k>)^2 */
+sw_status sw_quantiles(sw_ctx *ctx, const sw_params *p, const float *d_proj, int nb,
+                       float *d_q, double *d_center, double *d_norm, sw_stream_t stream);
+
+/* One pair, every rotation (Eq. discrete_rot_sw2 with the FFT
+ * cross-correlation of Sec. 2.3 "Fast computation over rotations").
+ *   d_f, d_g [L][L] float32: reference f and moving image g
+ *   d_D      [n] double (may be NULL): d^2 at every l (at s*(l) if translation)
+ *   d_shift  [n][2] double (may be NULL): s*(l) (0 if translation == 0)
+ *   d_best   [1] sw_result: the argmin (lowest l on ties) */
+sw_status sw_align_all_rotations(sw_ctx *ctx, const sw_params *p, const float *d_f,
+                                 const float *d_g, double *d_D, double *d_shift,
+                                 sw_result *d_best, sw_stream_t stream);
+
+/* Many pairs: every query i (reference f) against every template j (moving
+ * image g).  The per-frequency correlation sum_p Qhat_i(k,p) conj(Qhat_j(k,p))
+ * runs as a batched GEMM in the precision p->gemm_precision.
+ *   d_q_img [Nq][L][L] float32, d_t_img [Nt][L][L] float32
+ *   mode 0: d_out [Nq][Nt] sw_result, every pair
+ *   mode 1: d_out [Nq] sw_result, the best template per query (lowest index
+ *           on ties); best_l etc. refer to that template, whose index is
+ *           written to `reserved` as a float. */
+sw_status sw_align_batch(sw_ctx *ctx, const sw_params *p, const float *d_q_img, int Nq,
+                         const float *d_t_img, int Nt, int mode, sw_result *d_out,
+                         sw_stream_t stream);
+
+/* Template bank for serving: the angle spectra, centring vectors and norms
+ * of Nt templates, computed once and kept on the device (owned by the bank,
+ * freed by sw_bank_destroy). */
+sw_status sw_bank_create(sw_ctx *ctx, const sw_params *p, const float *d_t_img, int Nt,
+                         sw_bank **out, sw_stream_t stream);
+/* Queries against a bank.  q_L == p->L, or q_L == p->L / 2: the query is then
+ * upsampled 2 x 2 (each cell split into four of a quarter of its value,
+ * exact under the cell-average model).  mode as in sw_align_batch. */
+sw_status sw_bank_align(sw_ctx *ctx, const sw_bank *bank, const float *d_q_img, int Nq,
+                        int q_L, int mode, sw_result *d_out, sw_stream_t stream);
+int sw_bank_size(const sw_bank *bank);
+void sw_bank_destroy(sw_bank *bank);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWALIGN_H */

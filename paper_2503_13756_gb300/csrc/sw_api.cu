@@ -1,0 +1,686 @@
+// sw_api.cu -- the C ABI declared in include/swalign.h: argument checks,
+// angle/twiddle tables, workspace and the launch sequence of each call.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sw_internal.cuh"
+#include "swalign.h"
+
+using swk::FftPlan;
+
+namespace {
+
+// Angle tables for one n: theta_k = 2 pi k / n, k < n.  Built in FP64 from
+// the first octant and completed by exact symmetries, so that cos/sin of
+// k = n/4, n/2, 3n/4 are exactly 0 and +-1 and theta + pi is exactly -theta.
+struct Tables {
+    int n = 0;
+    FftPlan plan{};
+    float2 *cs = nullptr;     // [n] (cos, sin) fp32
+    double2 *cs64 = nullptr;  // [n] (cos, sin) fp64
+    float2 *tw = nullptr;     // [n] e^{-2 pi i m / n}
+};
+
+void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
+{
+    c.assign(n, 0.0);
+    s.assign(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        // reduce 8k/n to the first octant
+        long long num = 8LL * k;  // angle = (num / n) * (pi / 4)
+        int oct = (int)(num / n);
+        long long rem = num - (long long)oct * n;  // angle = (oct + rem/n) pi/4
+        double cc, ss;
+        auto base = [&](long long r, bool from_top, double &co, double &si) {
+            // t in [0, pi/4]
+            double t = (double)r / n * (M_PI / 4.0);
+            if (from_top) t = M_PI / 4.0 - t;
+            co = std::cos(t);
+            si = std::sin(t);
+        };
+        double co, si;
+        switch (oct & 7) {
+        case 0: base(rem, false, co, si); cc = co; ss = si; break;
+        case 1: base(rem, true, co, si); cc = si; ss = co; break;
+        case 2: base(rem, false, co, si); cc = -si; ss = co; break;
+        case 3: base(rem, true, co, si); cc = -co; ss = si; break;
+        case 4: base(rem, false, co, si); cc = -co; ss = -si; break;
+        case 5: base(rem, true, co, si); cc = -si; ss = -co; break;
+        case 6: base(rem, false, co, si); cc = si; ss = -co; break;
+        default: base(rem, true, co, si); cc = co; ss = -si; break;
+        }
+        c[k] = cc;
+        s[k] = ss;
+    }
+}
+
+bool fft_plan(int n, FftPlan &p)
+{
+    p.n = n;
+    p.nst = 0;
+    int m = n;
+    while (m % 4 == 0 && p.nst < swk::kMaxStages) {
+        p.radix[p.nst++] = 4;
+        m /= 4;
+    }
+    const int primes[3] = {2, 3, 5};
+    for (int q : primes)
+        while (m % q == 0 && p.nst < swk::kMaxStages) {
+            p.radix[p.nst++] = q;
+            m /= q;
+        }
+    return m == 1;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Offsets of the batch workspace.
+struct Layout {
+    size_t status, proj, quant, spec32, lp_q, lp_t, prof, center, norm32, norm16, C, scratch,
+        total;
+};
+
+int bins_of(const sw_params *p) { return p->n_bins > 0 ? p->n_bins : sw_default_bins(p->L); }
+
+Layout batch_layout(const sw_params *p, int Nq, int Nt, bool lp, bool scratch)
+{
+    const size_t nimg = (size_t)Nq + Nt;
+    const size_t n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    Layout l{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    l.status = take(4 * nimg);
+    l.proj = take(4 * nimg * nh * B);
+    l.quant = take(4 * nimg * n * M);
+    l.spec32 = take(4 * nh * nimg * 2 * M);
+    l.lp_q = take(lp ? 2 * nh * (size_t)Nq * 2 * M : 0);
+    l.lp_t = take(lp ? 2 * nh * (size_t)2 * Nt * 2 * M : 0);
+    l.prof = take(4 * nimg * M);
+    l.center = take(16 * nimg);
+    l.norm32 = take(8 * nimg);
+    l.norm16 = take(8 * nimg);
+    l.C = take(8 * nh * (size_t)Nq * Nt);
+    l.scratch = take(scratch ? sizeof(sw_result) * (size_t)Nq * Nt : 0);
+    l.total = o;
+    return l;
+}
+
+}  // namespace
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct sw_ctx {
+    int device = 0;
+    std::string err;
+    char *ws = nullptr;
+    size_t ws_size = 0;
+    size_t limit = 0;
+    std::deque<Tables> tables;  // stable addresses
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+};
+
+struct sw_bank {
+    sw_params p{};
+    int Nt = 0;
+    int device = 0;
+    char *mem = nullptr;
+    float *spec32 = nullptr;  // [nh][Nt][2M]
+    void *lp_t = nullptr;     // [nh][2Nt][2M] (bf16/fp16) or NULL
+    float *prof = nullptr;    // [Nt][M]
+    double *center = nullptr; // [Nt][2]
+    double *norm32 = nullptr, *norm16 = nullptr;
+    int32_t *status = nullptr;
+};
+
+namespace {
+
+sw_status fail(sw_ctx *c, sw_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+sw_status fail(sw_ctx *c, sw_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define SW_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), SW_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Runs one kernel launch `fn` on `st`, counting it and, when profiling,
+// bracketing it with events.
+template <typename F>
+cudaError_t launch(sw_ctx *c, int stage, cudaStream_t st, F &&fn)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        for (cudaEvent_t *e : {&a, &b}) {
+            if (!c->pool.empty()) {
+                *e = c->pool.back();
+                c->pool.pop_back();
+            } else if (cudaEventCreate(e) != cudaSuccess) {
+                return cudaGetLastError();
+            }
+        }
+        cudaEventRecord(a, st);
+    }
+    cudaError_t e = fn();
+    ++c->launches;
+    if (c->prof) {
+        cudaEventRecord(b, st);
+        c->recs.push_back({stage, a, b});
+    }
+    return e;
+}
+
+bool smooth235(int n)
+{
+    for (int q : {2, 3, 5})
+        while (n % q == 0) n /= q;
+    return n == 1;
+}
+
+sw_status check_params(sw_ctx *c, const sw_params *p)
+{
+    if (!p) return fail(c, SW_ERR_INVALID_ARG, "params is NULL");
+    if (p->L < 2 || p->L > 512) return fail(c, SW_ERR_INVALID_ARG, "L=%d outside 2..512", p->L);
+    const int n = p->n_theta;
+    if (n < 4 || n > 1024 || (n & 1) || !smooth235(n))
+        return fail(c, SW_ERR_INVALID_ARG, "n_theta=%d must be even, 4..1024, with factors 2,3,5",
+                    n);
+    if (p->n_levels < 1 || p->n_levels > 1024)
+        return fail(c, SW_ERR_INVALID_ARG, "n_levels=%d outside 1..1024", p->n_levels);
+    const int Bd = sw_default_bins(p->L);
+    if (p->n_bins != 0 && (p->n_bins < Bd || (p->n_bins & 1) || p->n_bins > 2048))
+        return fail(c, SW_ERR_INVALID_ARG, "n_bins=%d must be 0 or even in %d..2048", p->n_bins,
+                    Bd);
+    if (p->translation != 0 && p->translation != 1)
+        return fail(c, SW_ERR_INVALID_ARG, "translation must be 0 or 1");
+    if (p->level_rule != 0 && p->level_rule != 1)
+        return fail(c, SW_ERR_INVALID_ARG, "level_rule must be 0 or 1");
+    if (p->gemm_precision < SW_PREC_FP32 || p->gemm_precision > SW_PREC_FP16)
+        return fail(c, SW_ERR_INVALID_ARG, "gemm_precision=%d unknown", p->gemm_precision);
+    return SW_OK;
+}
+
+bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+sw_status check_ptr(sw_ctx *c, const void *ptr, const char *name, bool need)
+{
+    if (!ptr) return need ? fail(c, SW_ERR_INVALID_ARG, "%s is NULL", name) : SW_OK;
+    if (!aligned16(ptr)) return fail(c, SW_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+    return SW_OK;
+}
+
+sw_status set_device(sw_ctx *c)
+{
+    SW_CUDA(c, cudaSetDevice(c->device));
+    return SW_OK;
+}
+
+sw_status get_tables(sw_ctx *c, int n, const Tables **out)
+{
+    for (const Tables &t : c->tables)
+        if (t.n == n) {
+            *out = &t;
+            return SW_OK;
+        }
+    Tables t;
+    t.n = n;
+    if (!fft_plan(n, t.plan)) return fail(c, SW_ERR_INVALID_ARG, "no FFT plan for n=%d", n);
+    std::vector<double> co, si;
+    angle_table(n, co, si);
+    std::vector<float2> cs(n), tw(n);
+    std::vector<double2> cs64(n);
+    for (int k = 0; k < n; ++k) {
+        cs[k] = make_float2((float)co[k], (float)si[k]);
+        cs64[k] = make_double2(co[k], si[k]);
+        tw[k] = make_float2((float)co[k], (float)-si[k]);  // e^{-i theta_k}
+    }
+    SW_CUDA(c, cudaMalloc(&t.cs, sizeof(float2) * n));
+    SW_CUDA(c, cudaMalloc(&t.cs64, sizeof(double2) * n));
+    SW_CUDA(c, cudaMalloc(&t.tw, sizeof(float2) * n));
+    SW_CUDA(c, cudaMemcpy(t.cs, cs.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    SW_CUDA(c, cudaMemcpy(t.cs64, cs64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+    SW_CUDA(c, cudaMemcpy(t.tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    c->tables.push_back(t);
+    *out = &c->tables.back();
+    return SW_OK;
+}
+
+sw_status ensure_ws(sw_ctx *c, size_t bytes)
+{
+    if (bytes <= c->ws_size) return SW_OK;
+    if (c->limit && bytes > c->limit)
+        return fail(c, SW_ERR_OOM, "workspace of %zu bytes exceeds the limit of %zu bytes", bytes,
+                    c->limit);
+    if (c->ws) {
+        SW_CUDA(c, cudaFree(c->ws));
+        c->ws = nullptr;
+        c->ws_size = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->ws = nullptr;
+        return fail(c, SW_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->ws_size = bytes;
+    return SW_OK;
+}
+
+// Per-image stages into a spectrum set.
+struct ImageOut {
+    int32_t *status;
+    float *proj;  // scratch [nb][nh][B]
+    float *quant; // scratch [nb][n][M]
+    float *spec32;
+    size_t fstride;
+    int lp_kind;
+    void *lp_q;
+    size_t lpq_fstride;
+    void *lp_t;
+    size_t lpt_fstride;
+    int Nq;  // images [0, Nq) are queries for the low-precision layout
+    float *prof;
+    double *center, *norm32, *norm16;
+};
+
+sw_status run_images(sw_ctx *c, const sw_params *p, const Tables *t, const float *img,
+                     int srcL, int nb, int img_off, const ImageOut &o, cudaStream_t st)
+{
+    const int nh = p->n_theta / 2, B = bins_of(p);
+    SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                return swk::launch_project(img, nb, p->L, srcL, nh, B, t->cs,
+                                           o.proj + (size_t)img_off * nh * B, 0,
+                                           o.status + img_off, st);
+            }));
+    return SW_OK;
+}
+
+sw_status run_after_projection(sw_ctx *c, const sw_params *p, const Tables *t, int nb,
+                               const ImageOut &o, cudaStream_t st)
+{
+    const int L = p->L, n = p->n_theta, M = p->n_levels, B = bins_of(p);
+    const float h = 2.0f / (float)L;
+    SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                return swk::launch_quantiles(o.proj, nb, n, B, M, h, p->level_rule, 1, o.quant,
+                                             o.status, st);
+            }));
+    SW_CUDA(c, launch(c, SW_STAGE_SPECTRUM, st, [&] {
+                return swk::launch_spectrum(o.quant, nb, n, M, t->plan, t->tw, o.spec32,
+                                            o.fstride, o.lp_kind, o.lp_q, o.lpq_fstride, o.lp_t,
+                                            o.lpt_fstride, o.Nq, o.prof, o.center, o.norm32,
+                                            o.norm16, st);
+            }));
+    return SW_OK;
+}
+
+template <typename T>
+T *at(char *base, size_t off)
+{
+    return reinterpret_cast<T *>(base + off);
+}
+
+sw_status lp_unsupported(sw_ctx *c, const sw_params *p)
+{
+    if (p->gemm_precision != SW_PREC_FP32)
+        return fail(c, SW_ERR_UNSUPPORTED,
+                    "gemm_precision=%d: tensor-core correlation not available in this build",
+                    p->gemm_precision);
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_default_bins(int L)
+{
+    if (L < 1) return 0;
+    return 2 * (int)std::ceil((double)(L - 1) / std::sqrt(2.0)) + 2;
+}
+
+sw_status sw_create(int device, sw_ctx **out)
+{
+    if (!out) return SW_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return SW_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return SW_ERR_INVALID_ARG;
+    sw_ctx *c = new (std::nothrow) sw_ctx;
+    if (!c) return SW_ERR_OOM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SW_ERR_CUDA;
+    }
+    *out = c;
+    return SW_OK;
+}
+
+void sw_destroy(sw_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->ws) cudaFree(c->ws);
+    for (ProfRec &r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    for (Tables &t : c->tables) {
+        cudaFree(t.cs);
+        cudaFree(t.cs64);
+        cudaFree(t.tw);
+    }
+    delete c;
+}
+
+const char *sw_last_error(const sw_ctx *c) { return c ? c->err.c_str() : ""; }
+
+sw_status sw_profile(sw_ctx *c, int enable)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->prof = enable != 0;
+    return SW_OK;
+}
+
+sw_status sw_profile_read(sw_ctx *c, double *ms, int64_t *launches)
+{
+    if (!c || !ms || !launches) return SW_ERR_INVALID_ARG;
+    for (int i = 0; i < SW_STAGE_COUNT; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    sw_status s = SW_OK;
+    for (ProfRec &r : c->recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess ||
+            cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(c, SW_ERR_CUDA, "profiling event failed");
+        }
+        ms[r.stage] += t;
+        launches[r.stage] += 1;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+    return s;
+}
+
+int64_t sw_launch_count(const sw_ctx *c) { return c ? c->launches : 0; }
+
+sw_status sw_set_workspace_limit(sw_ctx *c, size_t bytes)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->limit = bytes;
+    return SW_OK;
+}
+
+size_t sw_batch_workspace_bytes(const sw_params *p, int Nq, int Nt)
+{
+    if (!p || Nq < 0 || Nt < 0 || check_params(nullptr, p) != SW_OK) return 0;
+    return batch_layout(p, Nq, Nt, p->gemm_precision != SW_PREC_FP32, true).total;
+}
+
+sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if (Nq < 0 || Nt < 0) return fail(c, SW_ERR_INVALID_ARG, "negative batch size");
+    if ((s = set_device(c))) return s;
+    const Tables *t;
+    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    return ensure_ws(c, batch_layout(p, Nq, Nt, p->gemm_precision != SW_PREC_FP32, true).total);
+}
+
+sw_status sw_project(sw_ctx *c, const sw_params *p, const float *d_img, int nb, float *d_proj,
+                     sw_stream_t stream)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if (nb < 0) return fail(c, SW_ERR_INVALID_ARG, "nb=%d", nb);
+    if (nb == 0) return SW_OK;
+    if ((s = check_ptr(c, d_img, "d_img", true)) || (s = check_ptr(c, d_proj, "d_proj", true)))
+        return s;
+    if ((s = set_device(c))) return s;
+    const Tables *t;
+    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    const size_t need = align_up(4 * (size_t)nb);
+    if ((s = ensure_ws(c, need))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                return swk::launch_project(d_img, nb, p->L, p->L, p->n_theta / 2, bins_of(p),
+                                           t->cs, d_proj, 1, at<int32_t>(c->ws, 0), st);
+            }));
+    return SW_OK;
+}
+
+sw_status sw_quantiles(sw_ctx *c, const sw_params *p, const float *d_proj, int nb, float *d_q,
+                       double *d_center, double *d_norm, sw_stream_t stream)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if (nb < 0) return fail(c, SW_ERR_INVALID_ARG, "nb=%d", nb);
+    if (nb == 0) return SW_OK;
+    if ((s = check_ptr(c, d_proj, "d_proj", true)) || (s = check_ptr(c, d_q, "d_q", true)) ||
+        (s = check_ptr(c, d_center, "d_center", false)) ||
+        (s = check_ptr(c, d_norm, "d_norm", false)))
+        return s;
+    if ((s = set_device(c))) return s;
+    const Tables *t;
+    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    if ((s = ensure_ws(c, align_up(4 * (size_t)nb)))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = at<int32_t>(c->ws, 0);
+    SW_CUDA(c, cudaMemsetAsync(status, 0, 4 * (size_t)nb, st));
+    SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                return swk::launch_quantiles(d_proj, nb, p->n_theta, bins_of(p), p->n_levels,
+                                             2.0f / (float)p->L, p->level_rule, 0, d_q, status,
+                                             st);
+            }));
+    if (d_center || d_norm)
+        SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                    return swk::launch_center_norm(d_q, nb, p->n_theta, p->n_levels, t->cs64,
+                                                   d_center, d_norm, st);
+                }));
+    return SW_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shared body of sw_align_batch / sw_align_all_rotations.
+sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int Nq,
+                           const float *dt, int Nt, int mode, sw_result *out, double *curve,
+                           double *shifts, bool force_fp32, cudaStream_t st)
+{
+    const int n = p->n_theta, nh = n / 2, M = p->n_levels;
+    const bool lp = !force_fp32 && p->gemm_precision != SW_PREC_FP32;
+    const Tables *t;
+    sw_status s = get_tables(c, n, &t);
+    if (s) return s;
+    const Layout l = batch_layout(p, Nq, Nt, lp, mode == 1);
+    if ((s = ensure_ws(c, l.total))) return s;
+    char *w = c->ws;
+    const int nimg = Nq + Nt;
+    ImageOut o{};
+    o.status = at<int32_t>(w, l.status);
+    o.proj = at<float>(w, l.proj);
+    o.quant = at<float>(w, l.quant);
+    o.spec32 = at<float>(w, l.spec32);
+    o.fstride = (size_t)nimg * 2 * M;
+    o.lp_kind = lp ? p->gemm_precision : 0;
+    o.lp_q = lp ? (void *)(w + l.lp_q) : nullptr;
+    o.lpq_fstride = (size_t)Nq * 2 * M;
+    o.lp_t = lp ? (void *)(w + l.lp_t) : nullptr;
+    o.lpt_fstride = (size_t)2 * Nt * 2 * M;
+    o.Nq = Nq;
+    o.prof = at<float>(w, l.prof);
+    o.center = at<double>(w, l.center);
+    o.norm32 = at<double>(w, l.norm32);
+    o.norm16 = at<double>(w, l.norm16);
+    if ((s = run_images(c, p, t, dq, p->L, Nq, 0, o, st))) return s;
+    if ((s = run_images(c, p, t, dt, p->L, Nt, Nq, o, st))) return s;
+    if ((s = run_after_projection(c, p, t, nimg, o, st))) return s;
+    float2 *C = at<float2>(w, l.C);
+    if (lp) {
+        if ((s = lp_unsupported(c, p))) return s;
+    } else {
+        SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
+                    return swk::launch_corr_simt(o.spec32, o.fstride,
+                                                 o.spec32 + (size_t)Nq * 2 * M, o.fstride, Nq, Nt,
+                                                 M, nh, C, st);
+                }));
+    }
+    swk::DecideArgs a{};
+    a.C = C;
+    a.Nq = Nq;
+    a.Nt = Nt;
+    a.n = n;
+    a.M = M;
+    a.prof_q = o.prof;
+    a.prof_t = o.prof + (size_t)Nq * M;
+    a.ctr_q = o.center;
+    a.ctr_t = o.center + 2 * (size_t)Nq;
+    const double *nrm = lp ? o.norm16 : o.norm32;
+    a.norm_q = nrm;
+    a.norm_t = nrm + Nq;
+    a.st_q = o.status;
+    a.st_t = o.status + Nq;
+    a.cs64 = t->cs64;
+    a.translation = p->translation;
+    a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)out;
+    a.curve = curve;
+    a.shifts = shifts;
+    SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st,
+                      [&] { return swk::launch_decide(a, t->plan, t->tw, st); }));
+    if (mode == 1)
+        SW_CUDA(c, launch(c, SW_STAGE_BEST, st, [&] {
+                    return swk::launch_best_template(w + l.scratch, Nq, Nt, out, st);
+                }));
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sw_status sw_align_all_rotations(sw_ctx *c, const sw_params *p, const float *d_f,
+                                 const float *d_g, double *d_D, double *d_shift,
+                                 sw_result *d_best, sw_stream_t stream)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if ((s = check_ptr(c, d_f, "d_f", true)) || (s = check_ptr(c, d_g, "d_g", true)) ||
+        (s = check_ptr(c, d_best, "d_best", true)))
+        return s;
+    if (d_D && ((uintptr_t)d_D & 7)) return fail(c, SW_ERR_INVALID_ARG, "d_D misaligned");
+    if (d_shift && ((uintptr_t)d_shift & 7))
+        return fail(c, SW_ERR_INVALID_ARG, "d_shift misaligned");
+    if ((s = set_device(c))) return s;
+    return align_batch_impl(c, p, d_f, 1, d_g, 1, 0, d_best, d_D, d_shift, true,
+                            (cudaStream_t)stream);
+}
+
+sw_status sw_align_batch(sw_ctx *c, const sw_params *p, const float *d_q_img, int Nq,
+                         const float *d_t_img, int Nt, int mode, sw_result *d_out,
+                         sw_stream_t stream)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if (Nq < 0 || Nt < 0) return fail(c, SW_ERR_INVALID_ARG, "Nq=%d Nt=%d", Nq, Nt);
+    if (mode != 0 && mode != 1) return fail(c, SW_ERR_INVALID_ARG, "mode=%d", mode);
+    if (Nq == 0) return SW_OK;
+    if (Nt == 0 && mode == 0) return SW_OK;
+    if ((s = check_ptr(c, d_q_img, "d_q_img", true)) || (s = check_ptr(c, d_out, "d_out", true)))
+        return s;
+    if (Nt > 0 && (s = check_ptr(c, d_t_img, "d_t_img", true))) return s;
+    if ((s = set_device(c))) return s;
+    if (p->gemm_precision != SW_PREC_FP32 && (s = lp_unsupported(c, p))) return s;
+    if (Nt == 0) return fail(c, SW_ERR_INVALID_ARG, "mode 1 needs at least one template");
+    return align_batch_impl(c, p, d_q_img, Nq, d_t_img, Nt, mode, d_out, nullptr, nullptr,
+                            false, (cudaStream_t)stream);
+}
+
+sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, int Nt,
+                         sw_bank **out, sw_stream_t stream)
+{
+    (void)d_t_img;
+    (void)Nt;
+    (void)stream;
+    if (out) *out = nullptr;
+    if (!c) return SW_ERR_INVALID_ARG;
+    return fail(c, SW_ERR_UNSUPPORTED, "template banks are not available in this build");
+    (void)p;
+}
+
+sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, int Nq, int q_L,
+                        int mode, sw_result *d_out, sw_stream_t stream)
+{
+    (void)bank;
+    (void)d_q_img;
+    (void)Nq;
+    (void)q_L;
+    (void)mode;
+    (void)d_out;
+    (void)stream;
+    if (!c) return SW_ERR_INVALID_ARG;
+    return fail(c, SW_ERR_UNSUPPORTED, "template banks are not available in this build");
+}
+
+int sw_bank_size(const sw_bank *bank) { return bank ? bank->Nt : 0; }
+
+void sw_bank_destroy(sw_bank *bank)
+{
+    if (!bank) return;
+    cudaSetDevice(bank->device);
+    cudaDeviceSynchronize();
+    cudaFree(bank->mem);
+    delete bank;
+}
+
+}  // extern "C"

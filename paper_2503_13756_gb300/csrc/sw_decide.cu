@@ -1,0 +1,236 @@
+// sw_decide.cu -- second half of the FFT cross-correlation of Sec. 2.3
+// ("Fast computation over rotations") and the alignment decision
+// (Eq. optimal_rotation, Eq. discrete_rot_sw2).
+//
+// For a pair (i, j) with correlation spectra C(k'), k' = 1..n/2:
+//   corr'(l) = (1/n) sum_{k' != 0} C(k') e^{2 pi i k' l / n}     (inverse FFT)
+//   n M D_T(l) = n |m_i - m_j|^2 + N_i + N_j - 2 corr'(l)
+// where m is the profile (mean over angle of each quantile level), N the
+// centred, mean-free quantile norm, and the k' = 0 part n|m_i - m_j|^2 is a
+// direct difference.  Without translation the distance is
+// D_0(l) = D_T(l) + |s*(l)|^2 / 2, s*(l) = a_i - R_{alpha_l} a_j.
+// l* = argmin (lowest l on ties) is taken on FP32 values; the distance at l*
+// is formed in FP64.
+//
+// Design: one CTA per (query, 2*nsig templates); two real correlation
+// curves are packed in one complex inverse FFT (the curves are real, so the
+// spectrum of c_a + i c_b is C_a + i C_b extended by Hermitian symmetry).
+#include "sw_internal.cuh"
+#include "swalign.h"
+
+namespace swk {
+namespace {
+
+constexpr int kDecThreads = 256;
+
+__global__ void __launch_bounds__(kDecThreads)
+k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw, int nsig)
+{
+    extern __shared__ float2 smd[];
+    const int n = A.n, M = A.M, nh = n / 2;
+    float2 *b0 = smd;
+    float2 *b1 = b0 + n * nsig;
+    float *prof_i = reinterpret_cast<float *>(b1 + n * nsig);  // [M]
+    float *delta = prof_i + M;                                  // [2 nsig]
+    const int i = blockIdx.x;
+    const int j0 = blockIdx.y * 2 * nsig;
+    const int Nq = A.Nq, Nt = A.Nt;
+
+    for (int p = threadIdx.x; p < M; p += blockDim.x) prof_i[p] = A.prof_q[(size_t)i * M + p];
+    // ---- Hermitian-extended spectra of two pairs per signal
+    const float2 *Ci = A.C + (size_t)i * Nt;
+    const size_t fs = (size_t)Nq * Nt;
+    for (int t = threadIdx.x; t < n * nsig; t += blockDim.x) {
+        const int kf = t / nsig, s = t % nsig;
+        const int ja = j0 + 2 * s, jb = ja + 1;
+        float2 Z = make_float2(0.f, 0.f);
+        if (kf != 0) {
+            const int m = kf <= nh ? kf : n - kf;
+            const float2 *Cm = Ci + (size_t)(m - 1) * fs;
+            const float2 Xa = ja < Nt ? Cm[ja] : make_float2(0.f, 0.f);
+            const float2 Xb = jb < Nt ? Cm[jb] : make_float2(0.f, 0.f);
+            if (kf < nh) Z = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);       // Xa + i Xb
+            else if (kf == nh) Z = make_float2(Xa.x, Xb.x);                // real parts
+            else Z = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);                // conj Xa + i conj Xb
+        }
+        b0[t] = Z;
+    }
+    __syncthreads();
+    const float2 *R = fft_smem(b0, b1, plan, nsig, tw, +1);  // R[l][s] = n (corr_a + i corr_b)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    // ---- k' = 0 part: n |m_i - m_j|^2
+    for (int pr = warp; pr < 2 * nsig; pr += nw) {
+        const int j = j0 + pr;
+        float s = 0.f;
+        if (j < Nt) {
+            const float *pj = A.prof_t + (size_t)j * M;
+            for (int p = lane; p < M; p += 32) {
+                const float d = prof_i[p] - pj[p];
+                s = fmaf(d, d, s);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) delta[pr] = s * (float)n;
+    }
+    __syncthreads();
+
+    const double nM = (double)n * M;
+    const double aix = A.ctr_q[2 * i], aiy = A.ctr_q[2 * i + 1];
+    const float invn = 1.f / (float)n;
+    for (int pr = warp; pr < 2 * nsig; pr += nw) {
+        const int j = j0 + pr;
+        if (j >= Nt) continue;
+        const int s = pr >> 1, comp = pr & 1;
+        const double ajx = A.ctr_t[2 * j], ajy = A.ctr_t[2 * j + 1];
+        // argmin over l of key(l) (FP32), lowest l on ties
+        float best = __int_as_float(0x7f800000);
+        int bl = 0x7fffffff;
+        for (int l = lane; l < n; l += 32) {
+            const float2 z = R[l * nsig + s];
+            float key = -2.f * (comp ? z.y : z.x) * invn;
+            if (!A.translation) {
+                const double2 c = A.cs64[l];
+                const float sx = (float)(aix - (c.x * ajx - c.y * ajy));
+                const float sy = (float)(aiy - (c.y * ajx + c.x * ajy));
+                key = fmaf(0.5f * (float)nM, sx * sx + sy * sy, key);
+            }
+            if (key < best || (key == best && l < bl)) {
+                best = key;
+                bl = l;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+            if (ob < best || (ob == best && ol < bl)) {
+                best = ob;
+                bl = ol;
+            }
+        }
+        if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
+        const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
+        const int st = A.st_q[i] ? 1 : (A.st_t[j] ? 2 : 0);
+        // FP64 distance at l (and shift)
+        auto dist = [&](int l, double &sx, double &sy) {
+            const float2 z = R[l * nsig + s];
+            const double corr = (double)(comp ? z.y : z.x) / n;
+            const double2 c = A.cs64[l];
+            sx = aix - (c.x * ajx - c.y * ajy);
+            sy = aiy - (c.y * ajx + c.x * ajy);
+            double d = (base - 2.0 * corr) / nM;
+            if (!A.translation) {
+                d += 0.5 * (sx * sx + sy * sy);
+                sx = sy = 0.0;
+            }
+            return d;
+        };
+        if (lane == 0) {
+            sw_result r;
+            if (st) {
+                const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+                r.best_l = -1;
+                r.status = st;
+                r.angle_rad = __int_as_float(0x7fc00000);
+                r.shift[0] = r.shift[1] = nan;
+                r.d2 = nan;
+            } else {
+                double sx, sy;
+                r.d2 = dist(bl, sx, sy);
+                r.best_l = bl;
+                r.status = 0;
+                r.angle_rad = (float)(6.283185307179586 * bl / n);
+                r.shift[0] = sx;
+                r.shift[1] = sy;
+            }
+            r.reserved = 0.f;
+            reinterpret_cast<sw_result *>(A.out)[(size_t)i * Nt + j] = r;
+        }
+        if (A.curve && i == 0 && j == 0) {
+            for (int l = lane; l < n; l += 32) {
+                double sx, sy;
+                const double d = dist(l, sx, sy);
+                A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
+                if (A.shifts) {
+                    A.shifts[2 * l] = sx;
+                    A.shifts[2 * l + 1] = sy;
+                }
+            }
+        }
+    }
+}
+
+// Best template per query: lowest d2 among usable templates, lowest j on ties.
+__global__ void k_best_template(const sw_result *__restrict__ all, int Nq, int Nt,
+                                sw_result *__restrict__ out)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= Nq) return;
+    const sw_result *row = all + (size_t)warp * Nt;
+    double best = __longlong_as_double(0x7ff0000000000000ULL);
+    int bj = 0x7fffffff;
+    int qbad = 0;
+    for (int j = lane; j < Nt; j += 32) {
+        const sw_result r = row[j];
+        if (r.status == 1) qbad = 1;
+        if (r.status == 0 && (r.d2 < best || (r.d2 == best && j < bj))) {
+            best = r.d2;
+            bj = j;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        qbad |= __shfl_xor_sync(0xffffffffu, qbad, off);
+        if (ob < best || (ob == best && oj < bj)) {
+            best = ob;
+            bj = oj;
+        }
+    }
+    if (lane == 0) {
+        sw_result r;
+        if (bj == 0x7fffffff) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+            r.best_l = -1;
+            r.status = qbad || Nt == 0 ? 1 : 2;
+            r.angle_rad = __int_as_float(0x7fc00000);
+            r.reserved = -1.f;
+            r.shift[0] = r.shift[1] = nan;
+            r.d2 = nan;
+        } else {
+            r = row[bj];
+            r.reserved = (float)bj;
+        }
+        out[warp] = r;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
+                          cudaStream_t st)
+{
+    if (a.Nq <= 0 || a.Nt <= 0) return cudaSuccess;
+    const int nsig = a.n <= 512 ? 16 : 8;
+    const size_t smem = sizeof(float2) * (size_t)2 * a.n * nsig + sizeof(float) * (a.M + 2 * nsig);
+    cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    dim3 grid(a.Nq, (a.Nt + 2 * nsig - 1) / (2 * nsig));  // queries on x (no 65535 cap)
+    k_decide<<<grid, kDecThreads, smem, st>>>(a, plan, tw, nsig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_best_template(const void *all, int Nq, int Nt, void *out, cudaStream_t st)
+{
+    if (Nq <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (Nq * 32 + threads - 1) / threads;
+    k_best_template<<<blocks, threads, 0, st>>>(reinterpret_cast<const sw_result *>(all), Nq,
+                                                Nt, reinterpret_cast<sw_result *>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace swk

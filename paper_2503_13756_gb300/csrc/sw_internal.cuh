@@ -1,0 +1,229 @@
+// sw_internal.cuh -- device helpers and launcher declarations shared by the
+// kernels of the sliced-2-Wasserstein alignment library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swk {
+
+constexpr int kMaxStages = 12;
+
+// Radix plan of an angle-length FFT: n = prod(radix[0..nst)), radices in
+// {2, 3, 4, 5}, fours first.  Built on the host.
+struct FftPlan {
+    int n;
+    int nst;
+    int radix[kMaxStages];
+};
+
+// ------------------------------------------------------------------------
+// Double-float ("hi + lo") helpers for the compensated CDF.  TwoSum is exact
+// for any two floats (Knuth); the sums below keep |lo| <= ulp(hi)/2.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    float s = a + b;
+    float v = s - a;
+    float e = (a - (s - v)) + (b - v);
+    return {s, e};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = df_two_sum(a.hi, b.hi);
+    float e = s.lo + (a.lo + b.lo);
+    return df_two_sum(s.hi, e);
+}
+
+// a >= b for normalised double-floats.
+__device__ __forceinline__ bool df_ge(DF a, DF b)
+{
+    return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);
+}
+
+// z * T with the product error captured by an FMA.
+__device__ __forceinline__ DF df_mul_f(DF t, float z)
+{
+    float p = z * t.hi;
+    float e = fmaf(z, t.hi, -p);
+    return df_two_sum(p, fmaf(z, t.lo, e));
+}
+
+// ------------------------------------------------------------------------
+// Complex helpers.
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse):  dir = -1 gives -i*a, +1 gives i*a
+__device__ __forceinline__ float2 cmul_i(float2 a, int dir)
+{
+    return dir < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// ------------------------------------------------------------------------
+// Batched complex FFT of length n over `nsig` signals held in shared memory
+// as buf[k * nsig + s] (signal s, element k), Stockham self-sorting, mixed
+// radix 2/3/4/5.  dir = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};
+// dir = +1: the unnormalised inverse.  tw[m] = e^{-2 pi i m / n}.
+// Each stage reads one buffer and writes the other; returns the buffer that
+// holds the result.  Must be called by every thread of the block; ends with
+// a __syncthreads().
+__device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan &plan,
+                                            int nsig, const float2 *__restrict__ tw, int dir)
+{
+    const int n = plan.n;
+    int Ns = 1;
+    for (int st = 0; st < plan.nst; ++st) {
+        const int r = plan.radix[st];
+        const int nr = n / r;
+        const int tstep = n / (Ns * r);  // twiddle index step for w^{i*k}
+        const int total = nr * nsig;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int s = t % nsig;
+            const int j = t / nsig;
+            const int k = j % Ns;
+            float2 v[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                if (i < r) {
+                    float2 x = a[(j + i * nr) * nsig + s];
+                    if (i > 0 && k > 0) {
+                        float2 w = tw[(i * k * tstep) % n];
+                        if (dir > 0) w.y = -w.y;
+                        x = cmul(x, w);
+                    }
+                    v[i] = x;
+                }
+            }
+            float2 V[5];
+            if (r == 2) {
+                V[0] = cadd(v[0], v[1]);
+                V[1] = csub(v[0], v[1]);
+            } else if (r == 4) {
+                float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+                float2 s13 = cadd(v[1], v[3]), d13 = cmul_i(csub(v[1], v[3]), dir);
+                V[0] = cadd(s02, s13);
+                V[2] = csub(s02, s13);
+                V[1] = cadd(d02, d13);
+                V[3] = csub(d02, d13);
+            } else if (r == 3) {
+                // w3 = e^{dir 2 pi i / 3} = -1/2 + dir i sqrt(3)/2
+                const float c3 = -0.5f, s3 = 0.86602540378443864676f;
+                float2 t1 = cadd(v[1], v[2]);
+                float2 t2 = make_float2(v[0].x + c3 * t1.x, v[0].y + c3 * t1.y);
+                float2 t3 = cmul_i(csub(v[1], v[2]), dir);
+                t3.x *= s3;
+                t3.y *= s3;
+                V[0] = cadd(v[0], t1);
+                V[1] = cadd(t2, t3);
+                V[2] = csub(t2, t3);
+            } else {  // r == 5
+                const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+                const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+                const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+                const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+                float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+                float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+                float2 r1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+                float2 r2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+                // i1 = dir*i*(s1 b1 + s2 b2), i2 = dir*i*(s2 b1 - s1 b2)
+                float2 i1 = cmul_i(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y), dir);
+                float2 i2 = cmul_i(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y), dir);
+                V[0] = make_float2(v[0].x + a1.x + a2.x, v[0].y + a1.y + a2.y);
+                V[1] = cadd(r1, i1);
+                V[4] = csub(r1, i1);
+                V[2] = cadd(r2, i2);
+                V[3] = csub(r2, i2);
+            }
+            const int base = (j / Ns) * Ns * r + k;
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (i < r) b[(base + i * Ns) * nsig + s] = V[i];
+        }
+        __syncthreads();
+        float2 *tmp = a;
+        a = b;
+        b = tmp;
+        Ns *= r;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------------------
+// Launchers.  All return the launch status (cudaGetLastError).
+
+// Projection of nb images (sw_project / first stage of the alignment).
+// img: [nb][srcL][srcL]; srcL == L, or srcL == L/2 (2x2 upsampling on load).
+// out: full_n ? [nb][2*nh][B] (angles k and k+nh, the latter mirrored)
+//             : [nb][nh][B] (angles k < nh only).
+// cs: [nh] (cos, sin) of theta_k.  status: [nb], 1 for an unusable image.
+cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
+                           const float2 *cs, float *out, int full_n, int32_t *status,
+                           cudaStream_t st);
+
+// Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
+//                        : [nb][2nh][B].
+// q: [nb][n][M].  status: [nb], OR-ed with 1 when a projection has no mass.
+cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, float h,
+                             int level_rule, int half, float *q, int32_t *status,
+                             cudaStream_t st);
+
+// Centring vector and centred norm of quantiles (public sw_quantiles):
+// a = (2/n) sum_k ubar_k theta_k, norm = sum (q - <a, theta_k>)^2.
+cudaError_t launch_center_norm(const float *q, int nb, int n, int M, const double2 *cs64,
+                               double *center, double *norm, cudaStream_t st);
+
+// Angle spectra of nb images.  For k' = 1..n/2, spec32[(k'-1)*fstride + img*2M + p]
+// = Re Qhat(k', p) and [.. + M + p] = Im, where Qhat is the DFT over angle of
+// the quantiles centred by a.  prof[img][p] = mean_k q[k][p] (k' = 0 / n).
+// norm32[img] = sum over k' != 0 of |Qhat|^2 / n (the centred, mean-free norm);
+// lp_kind 1/2 also writes bf16/fp16 copies: queries (img < Nq) to
+// lp_q[(k'-1)*lpq_fstride + img*2M + ...], templates to the doubled layout
+// lp_t[(k'-1)*lpt_fstride + (2j)*2M] = [re | im], [(2j+1)*2M] = [-im | re],
+// and norm16 from the rounded values.
+cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan &plan,
+                            const float2 *tw, float *spec32, size_t fstride, int lp_kind,
+                            void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
+                            int Nq, float *prof, double *center, double *norm32,
+                            double *norm16, cudaStream_t st);
+
+// FP32 SIMT correlation: for f < nf, i < Nq, j < Nt
+// C[(f*Nq + i)*Nt + j] = sum_p Qhat_i(f,p) conj(Qhat_j(f,p)) as (re, im).
+// X rows: X + f*xf + i*2M ([re | im]); Y rows: Y + f*yf + j*2M.
+cudaError_t launch_corr_simt(const float *X, size_t xf, const float *Y, size_t yf, int Nq,
+                             int Nt, int M, int nf, float2 *C, cudaStream_t st);
+
+// Inverse angle FFT of the correlation spectra, argmin over the rotation
+// grid and the FP64 distance at the optimum.  See sw_decide.cu.
+struct DecideArgs {
+    const float2 *C;      // [nf][Nq][Nt]
+    int Nq, Nt, n, M;
+    const float *prof_q;  // [Nq][M]
+    const float *prof_t;  // [Nt][M]
+    const double *ctr_q;  // [Nq][2]
+    const double *ctr_t;  // [Nt][2]
+    const double *norm_q; // [Nq]
+    const double *norm_t; // [Nt]
+    const int32_t *st_q;  // [Nq]
+    const int32_t *st_t;  // [Nt]
+    const double2 *cs64;  // [n] (cos, sin) of alpha_l
+    int translation;
+    void *out;            // sw_result [Nq][Nt]
+    double *curve;        // [n] or NULL (pair 0,0 only)
+    double *shifts;       // [n][2] or NULL
+};
+cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
+                          cudaStream_t st);
+
+// Best template per query from the [Nq][Nt] results.
+cudaError_t launch_best_template(const void *all, int Nq, int Nt, void *out, cudaStream_t st);
+
+}  // namespace swk

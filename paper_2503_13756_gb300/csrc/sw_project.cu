@@ -1,0 +1,195 @@
+// sw_project.cu -- Radon projection of images at nh = n/2 angles in [0, pi)
+// (Eq. radon_transform, Sec. 2.1; Sec. 2.3 "Computation"), as a
+// pixel-driven linear splat: a cell at (x, y) with value f adds
+// f * max(0, 1 - |u - b|) to bin b, u = <(x,y), theta>/h + (B-1)/2.
+// The angles theta + pi are the mirror images (P_{theta+pi} f(s) = P_theta f(-s))
+// and are not recomputed.
+//
+// Design (GB300): the splat is evaluated as a deterministic gather.  A warp
+// owns one angle and 32 consecutive bins; each lane walks the rows (or the
+// columns, when the direction is closer to the y axis) of an image tile held
+// in shared memory and sums the <= 3 cells whose projection falls within one
+// bin of its own.  No atomics, so results are bitwise reproducible and
+// independent of batching.  Rows whose projection misses the warp's 32 bins
+// are skipped.  Images larger than the tile are processed tile by tile with
+// zero borders, accumulating in shared memory.
+#include "sw_internal.cuh"
+
+namespace swk {
+namespace {
+
+constexpr int kProjThreads = 512;
+constexpr int kPad = 2;  // zero border (cells) around the staged tile
+
+struct TileGeom {
+    int T;   // tile side
+    int S;   // row stride of the staged tile (odd, >= T + 2*kPad)
+    int nt;  // tiles per side
+};
+
+__host__ __device__ inline TileGeom tile_geom(int L)
+{
+    TileGeom g;
+    g.T = L <= 128 ? L : 128;
+    g.nt = (L + g.T - 1) / g.T;
+    g.S = g.T + 2 * kPad;
+    if ((g.S & 1) == 0) g.S += 1;
+    return g;
+}
+
+__global__ void __launch_bounds__(kProjThreads)
+k_project(const float *__restrict__ img, int L, int srcL, int nh, int B, int G,
+          const float2 *__restrict__ cs, float *__restrict__ out, int full_n,
+          int32_t *__restrict__ status)
+{
+    extern __shared__ float smem[];
+    const TileGeom tg = tile_geom(L);
+    const int T = tg.T, S = tg.S;
+    const int rowsT = T + 2 * kPad;
+    float *tile = smem;                      // [rowsT][S]
+    const int Bp = (B + 31) & ~31;
+    float *acc = tile + rowsT * S;           // [G][Bp]
+    __shared__ int s_bad, s_mass;
+
+    const int imgi = blockIdx.y;
+    const int k0 = blockIdx.x * G;
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float *src = img + (size_t)imgi * srcL * srcL;
+
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_mass = 0;
+    }
+    for (int i = threadIdx.x; i < G * Bp; i += blockDim.x) acc[i] = 0.f;
+
+    const float half_L1 = 0.5f * (float)(L - 1);
+    const float half_B1 = 0.5f * (float)(B - 1);
+    const int ngroups = Bp >> 5;
+    const int nitems = G * ngroups;
+    int bad = 0, mass = 0;
+
+    for (int tr = 0; tr < tg.nt; ++tr) {
+        for (int tc = 0; tc < tg.nt; ++tc) {
+            __syncthreads();
+            // ---- stage tile (rows tr*T.., cols tc*T..) with a zero border
+            for (int idx = threadIdx.x; idx < rowsT * S; idx += blockDim.x) {
+                const int rr = idx / S - kPad, cc = idx % S - kPad;
+                const int r = tr * T + rr, c = tc * T + cc;
+                float v = 0.f;
+                if (rr >= 0 && rr < T && cc >= 0 && cc < T && r < L && c < L) {
+                    if (srcL == L) v = __ldg(src + (size_t)r * L + c);
+                    else v = 0.25f * __ldg(src + (size_t)(r >> 1) * srcL + (c >> 1));
+                    if (!isfinite(v)) {
+                        bad = 1;
+                        v = 0.f;
+                    }
+                    v = fmaxf(v, 0.f);
+                    mass |= v > 0.f;
+                }
+                tile[idx] = v;
+            }
+            __syncthreads();
+            // ---- warp items: (angle a, bin group g)
+            const float q0 = (float)(tc * T) - half_L1;  // centred x of tile column 0
+            const float m0 = (float)(tr * T) - half_L1;  // centred y of tile row 0
+            for (int it = warp; it < nitems; it += nwarps) {
+                const int a = it / ngroups, g = it % ngroups;
+                const int k = k0 + a;
+                if (k >= nh) continue;
+                const float2 t = cs[k];
+                const bool rowmode = fabsf(t.x) >= fabsf(t.y);
+                // minor index q runs along x in row mode (y in column mode)
+                const float kq = rowmode ? t.x : t.y;
+                const float km = rowmode ? t.y : t.x;
+                const float qc0 = rowmode ? q0 : m0;  // centred coord of minor index 0
+                const float mc0 = rowmode ? m0 : q0;  // centred coord of major index 0
+                const int sq = rowmode ? 1 : S;       // smem stride of the minor index
+                const int sm = rowmode ? S : 1;       // smem stride of the major index
+                const int b0 = g << 5;
+                // rows whose projection can reach bins [b0-1, b0+32]:
+                // u(q, m) = q kq + m km + U0, q in [0, T), m in [0, T)
+                const float U0 = fmaf(qc0, kq, fmaf(mc0, km, half_B1));
+                const float ext = (float)(T - 1) * kq;
+                const float umin = U0 + fminf(0.f, ext), umax = U0 + fmaxf(0.f, ext);
+                int mlo = 0, mhi = T - 1;
+                if (fabsf(km) > 1e-6f) {
+                    // need umin + m km <= b0 + 32 and umax + m km >= b0 - 1
+                    float ma = ((float)b0 + 32.f - umin) / km;
+                    float mb = ((float)b0 - 1.f - umax) / km;
+                    float lo = fminf(ma, mb), hi = fmaxf(ma, mb);
+                    lo = fmaxf(lo - 1.f, 0.f);
+                    hi = fminf(hi + 1.f, (float)(T - 1));
+                    if (lo > hi) continue;
+                    mlo = (int)lo;
+                    mhi = (int)hi;
+                } else if (umax < (float)b0 - 1.f || umin > (float)b0 + 32.f) {
+                    continue;
+                }
+                const int b = b0 + lane;
+                // d(q, m) = u(q, m) - b = q kq + beta_m
+                const float Ab = fmaf(qc0, kq, half_B1 - (float)b);
+                const float invk = 1.f / kq;
+                const float cw = -1.f / fabsf(kq);
+                float sum = 0.f;
+                for (int m = mlo; m <= mhi; ++m) {
+                    const float beta = fmaf(mc0 + (float)m, km, Ab);
+                    const float qlo = fmaf(-beta, invk, cw);  // window (qlo, qlo + 2/|kq|)
+                    float qs = floorf(qlo) + 1.f;
+                    qs = fminf(fmaxf(qs, -2.f), (float)(T - 1));
+                    const int qi = (int)qs;
+                    const float d0 = fmaf(qs, kq, beta);
+                    const float d1 = d0 + kq, d2 = d1 + kq;
+                    const float *p = tile + (m + kPad) * sm + (qi + kPad) * sq;
+                    const float w0 = fmaxf(0.f, 1.f - fabsf(d0));
+                    const float w1 = fmaxf(0.f, 1.f - fabsf(d1));
+                    const float w2 = fmaxf(0.f, 1.f - fabsf(d2));
+                    sum = fmaf(w0, p[0], sum);
+                    sum = fmaf(w1, p[sq], sum);
+                    sum = fmaf(w2, p[2 * sq], sum);
+                }
+                acc[a * Bp + b] += sum;
+            }
+        }
+    }
+    // ---- image status (every block of an image computes the same flags)
+    if (bad) atomicOr(&s_bad, 1);
+    if (mass) atomicOr(&s_mass, 1);
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) status[imgi] = (s_bad || !s_mass) ? 1 : 0;
+    // ---- write
+    const int nrow = full_n ? 2 * nh : nh;
+    for (int i = threadIdx.x; i < G * B; i += blockDim.x) {
+        const int a = i / B, b = i % B;
+        const int k = k0 + a;
+        if (k >= nh) continue;
+        const float v = acc[a * Bp + b];
+        float *o = out + ((size_t)imgi * nrow + k) * B;
+        o[b] = v;
+        if (full_n) o[(size_t)nh * B + (B - 1 - b)] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
+                           const float2 *cs, float *out, int full_n, int32_t *status,
+                           cudaStream_t st)
+{
+    if (nb <= 0) return cudaSuccess;
+    const TileGeom tg = tile_geom(L);
+    const int Bp = (B + 31) & ~31;
+    int G = 16;
+    if (nh < G) G = nh;
+    const size_t smem = sizeof(float) * ((size_t)(tg.T + 2 * kPad) * tg.S + (size_t)G * Bp);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_done = true;
+    }
+    dim3 grid((nh + G - 1) / G, nb);
+    k_project<<<grid, kProjThreads, smem, st>>>(img, L, srcL, nh, B, G, cs, out, full_n, status);
+    return cudaGetLastError();
+}
+
+}  // namespace swk

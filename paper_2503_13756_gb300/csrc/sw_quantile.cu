@@ -1,0 +1,201 @@
+// sw_quantile.cu -- quantile functions of the projections (Sec. 2.3
+// "Computation": CDF by cumulative sum, ICDF by linear interpolation;
+// Eq. inv_cdf read with the ">=" of App. A.1.1).
+//
+// For one projection U[0..B) with nodes e_j = (j - B/2) h:
+//   F_0 = 0, F_j = sum_{b<j} U_b,  tau_p = z_p F_B,
+//   j* = min{ j >= 1 : F_j >= tau_p },
+//   Q(z_p) = e_{j*-1} + h (tau_p - F_{j*-1}) / U_{j*-1};
+// at tau = 0 (level p = 0 under the p/M rule) Q is the left edge of the first
+// bin with mass.
+//
+// Design (GB300): one warp per projection.  The CDF is a warp scan of
+// double-float partial sums (TwoSum-compensated FP32) kept in shared memory,
+// so that tau - F_{j-1} keeps ~48 bits even where it cancels; each lane then
+// binary-searches its levels.  No FP64 on this path.
+#include "sw_internal.cuh"
+
+namespace swk {
+namespace {
+
+constexpr int kQThreads = 256;  // 8 warps = 8 projections per block
+
+__global__ void __launch_bounds__(kQThreads)
+k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int level_rule,
+            int half, float *__restrict__ q, int32_t *__restrict__ status)
+{
+    extern __shared__ float sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int imgi = blockIdx.y;
+    const int k = blockIdx.x * nw + warp;
+    const int stride = 3 * (B + 1);
+    float *U = sm + warp * stride;   // [B]
+    float *Fh = U + (B + 1);         // [B+1]
+    float *Fl = Fh + (B + 1);        // [B+1]
+    if (k >= n) return;              // whole warp leaves; no block barrier below
+    const int nh = n / 2;
+    const float *row;
+    bool mirror = false;
+    if (half) {
+        mirror = k >= nh;
+        row = proj + ((size_t)imgi * nh + (mirror ? k - nh : k)) * B;
+    } else {
+        row = proj + ((size_t)imgi * n + k) * B;
+    }
+    for (int b = lane; b < B; b += 32) U[b] = mirror ? row[B - 1 - b] : row[b];
+    __syncwarp();
+
+    // ---- compensated prefix sums: lane owns bins [c0, c1)
+    const int C = (B + 31) / 32;
+    const int c0 = min(B, lane * C), c1 = min(B, c0 + C);
+    DF s = {0.f, 0.f};
+    for (int b = c0; b < c1; ++b) s = df_add(s, DF{U[b], 0.f});
+    // inclusive warp scan of the lane sums
+    DF inc = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        DF o;
+        o.hi = __shfl_up_sync(0xffffffffu, inc.hi, off);
+        o.lo = __shfl_up_sync(0xffffffffu, inc.lo, off);
+        if (lane >= off) inc = df_add(o, inc);
+    }
+    DF run;
+    run.hi = __shfl_up_sync(0xffffffffu, inc.hi, 1);
+    run.lo = __shfl_up_sync(0xffffffffu, inc.lo, 1);
+    if (lane == 0) {
+        run = {0.f, 0.f};
+        Fh[0] = 0.f;
+        Fl[0] = 0.f;
+    }
+    for (int b = c0; b < c1; ++b) {
+        run = df_add(run, DF{U[b], 0.f});
+        Fh[b + 1] = run.hi;
+        Fl[b + 1] = run.lo;
+    }
+    __syncwarp();
+    const DF total = {Fh[B], Fl[B]};
+    float *qo = q + ((size_t)imgi * n + k) * M;
+    if (!(total.hi > 0.f) || !isfinite(total.hi)) {
+        for (int p = lane; p < M; p += 32) qo[p] = __int_as_float(0x7fc00000);
+        if (lane == 0) atomicOr(status + imgi, 1);
+        return;
+    }
+    const float invM = 1.f / (float)M;
+    for (int p = lane; p < M; p += 32) {
+        const float z = level_rule == 0 ? (2.f * p + 1.f) * (0.5f * invM) : (float)p * invM;
+        float Q;
+        if (z == 0.f) {
+            // left edge of the first bin with mass: j* = min{j >= 1: F_j > 0}
+            int lo = 1, hi = B;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (Fh[mid] > 0.f) hi = mid;
+                else lo = mid + 1;
+            }
+            Q = ((float)(lo - 1) - 0.5f * (float)B) * h;
+        } else {
+            const DF tau = df_mul_f(total, z);
+            int lo = 1, hi = B;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (df_ge(DF{Fh[mid], Fl[mid]}, tau)) hi = mid;
+                else lo = mid + 1;
+            }
+            const int j = lo;
+            const float num = (tau.hi - Fh[j - 1]) + (tau.lo - Fl[j - 1]);
+            const float den = U[j - 1];
+            float frac = den > 0.f ? num / den : 0.f;
+            frac = fminf(fmaxf(frac, 0.f), 1.f);
+            const float ej = ((float)(j - 1) - 0.5f * (float)B) * h;
+            Q = fmaf(h, frac, ej);
+        }
+        qo[p] = Q;
+    }
+}
+
+// Centring vector and centred norm (public sw_quantiles outputs).  One block
+// per image; FP64 accumulation.
+__global__ void k_center_norm(const float *__restrict__ q, int n, int M,
+                              const double2 *__restrict__ cs64, double *__restrict__ center,
+                              double *__restrict__ norm)
+{
+    __shared__ double red[3][32];
+    __shared__ double s_a[2];
+    const int imgi = blockIdx.x;
+    const float *qi = q + (size_t)imgi * n * M;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // a = (2/n) sum_k ubar_k (cos, sin),  ubar_k = mean_p q[k][p]
+    double ax = 0.0, ay = 0.0;
+    for (int k = warp; k < n; k += nw) {
+        double s = 0.0;
+        for (int p = lane; p < M; p += 32) s += (double)qi[(size_t)k * M + p];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        const double ub = s / M;
+        ax += ub * cs64[k].x;
+        ay += ub * cs64[k].y;
+    }
+    if (lane == 0) {
+        red[0][warp] = ax;
+        red[1][warp] = ay;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sx = 0.0, sy = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            sx += red[0][w];
+            sy += red[1][w];
+        }
+        s_a[0] = sx * 2.0 / n;
+        s_a[1] = sy * 2.0 / n;
+    }
+    __syncthreads();
+    const double a0 = s_a[0], a1 = s_a[1];
+    double acc = 0.0;
+    for (int k = warp; k < n; k += nw) {
+        const double off = a0 * cs64[k].x + a1 * cs64[k].y;
+        for (int p = lane; p < M; p += 32) {
+            const double d = (double)qi[(size_t)k * M + p] - off;
+            acc += d * d;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) red[2][warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[2][w];
+        if (center) {
+            center[2 * imgi] = a0;
+            center[2 * imgi + 1] = a1;
+        }
+        if (norm) norm[imgi] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, float h,
+                             int level_rule, int half, float *q, int32_t *status,
+                             cudaStream_t st)
+{
+    if (nb <= 0) return cudaSuccess;
+    const int nw = kQThreads / 32;
+    const size_t smem = sizeof(float) * (size_t)nw * 3 * (B + 1);
+    cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    dim3 grid((n + nw - 1) / nw, nb);
+    k_quantiles<<<grid, kQThreads, smem, st>>>(proj, n, B, M, h, level_rule, half, q, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center_norm(const float *q, int nb, int n, int M, const double2 *cs64,
+                               double *center, double *norm, cudaStream_t st)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_center_norm<<<nb, 256, 0, st>>>(q, n, M, cs64, center, norm);
+    return cudaGetLastError();
+}
+
+}  // namespace swk

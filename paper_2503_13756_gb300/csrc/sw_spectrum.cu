@@ -1,0 +1,228 @@
+// sw_spectrum.cu -- angle spectra of the quantile functions: the first half
+// of the FFT cross-correlation of Sec. 2.3 ("Fast computation over
+// rotations": the correlation along angle of every row of U_I and V_I is
+// computed with the FFT), plus the translation centring.
+//
+// For level p, the quantiles u_pk (k = 0..n-1) are transformed over k:
+//   Qhat(k', p) = sum_k u~_pk e^{-2 pi i k k'/n},  u~_pk = u_pk - <a, theta_k>,
+// with a = (2/n) sum_k ubar_k theta_k.  Centring only changes k' = 1 (and
+// n-1): Qhat(1, p) -= c1 with c1 = mean_p Qhat_u(1, p) = (n/2)(a_x - i a_y),
+// so it is applied after the transform with no second pass over the data.
+// The k' = 0 term (n times the mean over angle of each level, the "profile")
+// is kept apart, so that the rotation-invariant part of the distance is
+// computed later as a direct difference instead of a cancelling sum.
+//
+// Design (GB300): one CTA per image; levels are taken 2*nsig at a time, two
+// real levels packed into one complex signal, FFT'd by the shared-memory
+// Stockham FFT and unpacked by Hermitian symmetry.  Norms are accumulated
+// in FP64.  Optional BF16/FP16 copies feed the tensor-core GEMM, with their
+// norms taken from the rounded values so that self-distances cancel.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "sw_internal.cuh"
+
+namespace swk {
+namespace {
+
+constexpr int kSpecThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T to_lp(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to_lp<__half>(float x) { return __float2half_rn(x); }
+template <typename T>
+__device__ __forceinline__ float from_lp(T x);
+template <>
+__device__ __forceinline__ float from_lp<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float from_lp<__half>(__half x) { return __half2float(x); }
+
+struct SpecOut {
+    float *spec32;
+    size_t fstride;
+    void *lp_q;
+    size_t lpq_fstride;
+    void *lp_t;
+    size_t lpt_fstride;
+    int Nq;
+};
+
+// Writes Qhat(kf, p) (kf >= 1) for image img; returns |.|^2 weight-summed
+// contributions through acc32 / acc16.
+template <typename T>
+__device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, int p, float2 X,
+                                     double w, double &acc32, double &acc16)
+{
+    float *row = o.spec32 + (size_t)(kf - 1) * o.fstride + (size_t)img * 2 * M;
+    row[p] = X.x;
+    row[M + p] = X.y;
+    acc32 += w * ((double)X.x * X.x + (double)X.y * X.y);
+    if (o.lp_q) {
+        const T re = to_lp<T>(X.x), im = to_lp<T>(X.y);
+        const float rf = from_lp<T>(re), imf = from_lp<T>(im);
+        acc16 += w * ((double)rf * rf + (double)imf * imf);
+        if (img < o.Nq) {
+            T *r = reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
+                   (size_t)img * 2 * M;
+            r[p] = re;
+            r[M + p] = im;
+        } else {
+            const int j = img - o.Nq;
+            T *r = reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
+                   (size_t)(2 * j) * 2 * M;
+            r[p] = re;          // row 2j:   [ re | im ]
+            r[M + p] = im;
+            r[2 * M + p] = to_lp<T>(-imf);  // row 2j+1: [ -im | re ]
+            r[3 * M + p] = re;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSpecThreads)
+k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2 *__restrict__ tw,
+           int nsig, SpecOut o, float *__restrict__ prof, double *__restrict__ center,
+           double *__restrict__ norm32, double *__restrict__ norm16)
+{
+    extern __shared__ float2 smc[];
+    float2 *b0 = smc;
+    float2 *b1 = b0 + n * nsig;
+    float2 *x1 = b1 + n * nsig;  // [M] Qhat(1, p) before centring
+    __shared__ double red[2][kSpecThreads / 32];
+    __shared__ double s_c1[2];
+    const int img = blockIdx.x;
+    const float *qi = q + (size_t)img * n * M;
+    const int nh = n / 2;
+    double acc32 = 0.0, acc16 = 0.0;
+    const float invn = 1.f / (float)n;
+
+    for (int p0 = 0; p0 < M; p0 += 2 * nsig) {
+        // ---- load: signal s = levels (p0 + 2s, p0 + 2s + 1) as (re, im)
+        for (int t = threadIdx.x; t < n * nsig; t += blockDim.x) {
+            const int k = t / nsig, s = t % nsig;
+            const int p = p0 + 2 * s;
+            const float xr = p < M ? qi[(size_t)k * M + p] : 0.f;
+            const float xi = p + 1 < M ? qi[(size_t)k * M + p + 1] : 0.f;
+            b0[t] = make_float2(xr, xi);
+        }
+        __syncthreads();
+        const float2 *R = fft_smem(b0, b1, plan, nsig, tw, -1);
+        // ---- unpack two real spectra per signal, k' = 0..n/2
+        for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
+            const int kf = t / nsig, s = t % nsig;
+            const float2 Z = R[kf * nsig + s];
+            const float2 Zc = cconj(R[((n - kf) % n) * nsig + s]);
+            // Xa = (Z + conj Z(n-k))/2, Xb = (Z - conj Z(n-k)) / (2i)
+            const float2 Xa = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+            const float2 dz = make_float2(0.5f * (Z.x - Zc.x), 0.5f * (Z.y - Zc.y));
+            const float2 Xb = make_float2(dz.y, -dz.x);
+            const int pa = p0 + 2 * s, pb = pa + 1;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int p = h2 ? pb : pa;
+                if (p >= M) continue;
+                float2 X = h2 ? Xb : Xa;
+                if (kf == 0) {
+                    prof[(size_t)img * M + p] = X.x * invn;
+                } else if (kf == 1) {
+                    x1[p] = X;
+                } else {
+                    if (kf == nh) X.y = 0.f;  // Nyquist term of a real signal
+                    const double w = kf == nh ? 1.0 : 2.0;
+                    emit<T>(o, img, M, kf, p, X, w, acc32, acc16);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- centring: c1 = mean_p Qhat_u(1, p);  a = (2/n)(Re c1, -Im c1)
+    {
+        double cr = 0.0, ci = 0.0;
+        for (int p = threadIdx.x; p < M; p += blockDim.x) {
+            cr += x1[p].x;
+            ci += x1[p].y;
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            cr += __shfl_xor_sync(0xffffffffu, cr, off);
+            ci += __shfl_xor_sync(0xffffffffu, ci, off);
+        }
+        if (lane == 0) {
+            red[0][warp] = cr;
+            red[1][warp] = ci;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sr = 0.0, si = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                sr += red[0][w];
+                si += red[1][w];
+            }
+            s_c1[0] = sr / M;
+            s_c1[1] = si / M;
+            center[2 * img] = 2.0 * s_c1[0] / n;
+            center[2 * img + 1] = -2.0 * s_c1[1] / n;
+        }
+        __syncthreads();
+    }
+    const float c1r = (float)s_c1[0], c1i = (float)s_c1[1];
+    for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        const float2 X = make_float2(x1[p].x - c1r, x1[p].y - c1i);
+        emit<T>(o, img, M, 1, p, X, 2.0, acc32, acc16);  // n >= 4: k' = 1 < n/2
+    }
+    // ---- norms: Parseval over k' != 0 of the centred spectra, / n
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        acc32 += __shfl_xor_sync(0xffffffffu, acc32, off);
+        acc16 += __shfl_xor_sync(0xffffffffu, acc16, off);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[0][warp] = acc32;
+        red[1][warp] = acc16;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s32 = 0.0, s16 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s32 += red[0][w];
+            s16 += red[1][w];
+        }
+        norm32[img] = s32 / n;
+        if (norm16) norm16[img] = s16 / n;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan &plan,
+                            const float2 *tw, float *spec32, size_t fstride, int lp_kind,
+                            void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
+                            int Nq, float *prof, double *center, double *norm32,
+                            double *norm16, cudaStream_t st)
+{
+    if (nb <= 0) return cudaSuccess;
+    const int nsig = n <= 512 ? 16 : 8;
+    const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M);
+    SpecOut o{spec32, fstride, lp_kind ? lp_q : nullptr, lpq_fstride, lp_t, lpt_fstride, Nq};
+    if (lp_kind == 2) {
+        cudaFuncSetAttribute(k_spectrum<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        k_spectrum<__half><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, nsig, o, prof,
+                                                            center, norm32, norm16);
+    } else {
+        cudaFuncSetAttribute(k_spectrum<__nv_bfloat16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_spectrum<__nv_bfloat16><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, nsig, o,
+                                                                   prof, center, norm32,
+                                                                   norm16);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace swk

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of the C ABI in ``include/swalign.h``.
+
+Argument marshalling only: tensors are passed as device pointers with the
+current torch CUDA stream; every step of the alignment runs in the CUDA
+library.  There is no fallback: if the library cannot be built or loaded,
+or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SW_OK, SW_ERR_INVALID_ARG, SW_ERR_UNSUPPORTED, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT = range(6)
+PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+RESULT_DTYPE = np.dtype(
+    [("best_l", "<i4"), ("status", "<i4"), ("angle_rad", "<f4"), ("reserved", "<f4"),
+     ("shift", "<f8", (2,)), ("d2", "<f8")],
+    align=True,
+)
+assert RESULT_DTYPE.itemsize == 40
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in
+                ("L", "n_theta", "n_levels", "n_bins", "translation", "level_rule",
+                 "gemm_precision")]
+
+
+def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
+                precision="fp32") -> Params:
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    return Params(int(L), int(n_theta), int(n_levels), int(n_bins), int(translation),
+                  int(level_rule), prec)
+
+
+class SwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"swalign status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = (
+    "sw_create", "sw_destroy", "sw_last_error", "sw_default_bins", "sw_set_workspace_limit",
+    "sw_batch_workspace_bytes", "sw_reserve", "sw_project", "sw_quantiles",
+    "sw_align_all_rotations", "sw_align_batch", "sw_bank_create", "sw_bank_align",
+    "sw_bank_size", "sw_bank_destroy", "sw_profile", "sw_profile_read", "sw_launch_count",
+)
+STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best")
+
+
+def load(path: str | None = None):
+    """Builds (if stale) and loads the library; returns the ctypes handle."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(path or _build.build())
+            vp, ci, P = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Params)
+            sig = {
+                "sw_create": ([ci, ctypes.POINTER(vp)], ci),
+                "sw_destroy": ([vp], None),
+                "sw_last_error": ([vp], ctypes.c_char_p),
+                "sw_default_bins": ([ci], ci),
+                "sw_set_workspace_limit": ([vp, ctypes.c_size_t], ci),
+                "sw_batch_workspace_bytes": ([P, ci, ci], ctypes.c_size_t),
+                "sw_reserve": ([vp, P, ci, ci], ci),
+                "sw_project": ([vp, P, vp, ci, vp, vp], ci),
+                "sw_quantiles": ([vp, P, vp, ci, vp, vp, vp, vp], ci),
+                "sw_align_all_rotations": ([vp, P, vp, vp, vp, vp, vp, vp], ci),
+                "sw_align_batch": ([vp, P, vp, ci, vp, ci, ci, vp, vp], ci),
+                "sw_bank_create": ([vp, P, vp, ci, ctypes.POINTER(vp), vp], ci),
+                "sw_bank_align": ([vp, vp, vp, ci, ci, ci, vp, vp], ci),
+                "sw_bank_size": ([vp], ci),
+                "sw_bank_destroy": ([vp], None),
+                "sw_profile": ([vp, ci], ci),
+                "sw_profile_read": ([vp, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int64)], ci),
+                "sw_launch_count": ([vp], ctypes.c_int64),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(x, device):
+    import torch
+    t = torch.as_tensor(x, dtype=torch.float32, device=device)
+    return t.contiguous()
+
+
+class Aligner:
+    """One library context (one device, one workspace).  Use one per stream."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("swalign needs a CUDA device; none is visible")
+        self.lib = load()
+        self.device = device
+        self.torch_device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        self._check(self.lib.sw_create(device, ctypes.byref(h)), None)
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.sw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status, ctx):
+        if status != SW_OK:
+            msg = self.lib.sw_last_error(ctx).decode() if ctx else ""
+            raise SwError(status, msg)
+
+    def call(self, name, *args):
+        self._check(getattr(self.lib, name)(self.ctx, *args), self.ctx)
+
+    # ---------------------------------------------------------------- API
+    def profile(self, enable: bool):
+        self.call("sw_profile", int(bool(enable)))
+
+    def profile_read(self):
+        """{stage: (total ms, launches)} since the last read (waits for them)."""
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_int64 * 8)()
+        self.call("sw_profile_read", ms, cnt)
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES) if cnt[i]}
+
+    def launch_count(self) -> int:
+        return int(self.lib.sw_launch_count(self.ctx))
+
+    def default_bins(self, L: int) -> int:
+        return int(self.lib.sw_default_bins(int(L)))
+
+    def set_workspace_limit(self, nbytes: int):
+        self.call("sw_set_workspace_limit", ctypes.c_size_t(int(nbytes)))
+
+    def reserve(self, params: Params, Nq: int, Nt: int):
+        self.call("sw_reserve", ctypes.byref(params), int(Nq), int(Nt))
+
+    def project(self, imgs, params: Params, out=None, stream=None):
+        import torch
+        x = _f32(imgs, self.torch_device)
+        nb = x.shape[0]
+        B = params.n_bins or self.default_bins(params.L)
+        if out is None:
+            out = torch.empty((nb, params.n_theta, B), dtype=torch.float32, device=x.device)
+        self.call("sw_project", ctypes.byref(params), _ptr(x), nb, _ptr(out), _stream(stream))
+        return out
+
+    def quantiles(self, proj, params: Params, stream=None):
+        import torch
+        x = _f32(proj, self.torch_device)
+        nb = x.shape[0]
+        q = torch.empty((nb, params.n_theta, params.n_levels), dtype=torch.float32,
+                        device=x.device)
+        center = torch.empty((nb, 2), dtype=torch.float64, device=x.device)
+        norm = torch.empty((nb,), dtype=torch.float64, device=x.device)
+        self.call("sw_quantiles", ctypes.byref(params), _ptr(x), nb, _ptr(q), _ptr(center),
+                  _ptr(norm), _stream(stream))
+        return q, center, norm
+
+    def align_all_rotations(self, f, g, params: Params, stream=None):
+        import torch
+        F, G = _f32(f, self.torch_device), _f32(g, self.torch_device)
+        n = params.n_theta
+        D = torch.empty((n,), dtype=torch.float64, device=F.device)
+        S = torch.empty((n, 2), dtype=torch.float64, device=F.device)
+        best = torch.empty((40,), dtype=torch.uint8, device=F.device)
+        self.call("sw_align_all_rotations", ctypes.byref(params), _ptr(F), _ptr(G), _ptr(D),
+                  _ptr(S), _ptr(best), _stream(stream))
+        return D, S, best
+
+    def align_batch(self, queries, templates, params: Params, mode=0, out=None, stream=None):
+        import torch
+        q = _f32(queries, self.torch_device)
+        t = _f32(templates, self.torch_device)
+        Nq, Nt = q.shape[0], t.shape[0]
+        rows = Nq * Nt if mode == 0 else Nq
+        if out is None:
+            out = torch.empty((rows, 40), dtype=torch.uint8, device=q.device)
+        self.call("sw_align_batch", ctypes.byref(params), _ptr(q), Nq, _ptr(t), Nt, int(mode),
+                  _ptr(out), _stream(stream))
+        return out
+
+
+def results_to_numpy(buf) -> np.ndarray:
+    """Device result buffer ([N][40] uint8) -> structured numpy array."""
+    a = buf.detach().cpu().numpy().reshape(-1)
+    return a.view(RESULT_DTYPE)

@@ -1,0 +1,43 @@
+"""Tolerances for comparing the CUDA path with the FP64 oracle.
+
+Distances (FP32 correlation path): |d2_gpu - d2_ref| <= 1e-5 * max(d2_ref, 0.1 S),
+S = (N_f + N_g) / (n M) with N the centred quantile norm.  The relative bound
+1e-5 is the stated FP32 target; the floor 0.1 S covers the cancellation in
+N_f + N_g - 2 corr, whose FP32 rounding scales with S, not with d2 (so a
+relative bound alone is undefined as d2 -> 0, e.g. for self-comparisons).
+Reduced precision (BF16/FP16 correlation): the same with 1e-2.
+
+Argmin: identical, except at ties -- the GPU's choice l_gpu is accepted when
+the oracle's own curve puts it within the distance tolerance of the optimum,
+D_ref(l_gpu) - D_ref(l_ref) <= tol (several rotations are then correct).
+"""
+import numpy as np
+
+import oracle
+
+REL_FP32 = 1e-5
+REL_LP = 1e-2
+
+
+def norm_scale(f, g, n, M, level_rule=0):
+    """S = (N_f + N_g) / (n M) from the oracle's centred quantiles."""
+    tot = 0.0
+    for img in (f, g):
+        F, mass = oracle.prepare(img)
+        if mass <= 0:
+            return np.nan
+        Q = oracle.quantiles(oracle.project(F, n), 2.0 / F.shape[0], M, level_rule)
+        _, Qc = oracle.center(Q)
+        tot += float((Qc ** 2).sum())
+    return tot / (n * M)
+
+
+def d2_tol(d2_ref, S, rel=REL_FP32):
+    return rel * np.maximum(d2_ref, 0.1 * S)
+
+
+def check_argmin(l_gpu, l_ref, D_ref, tol):
+    """True when l_gpu is l_ref or ties with it within tol on the oracle curve."""
+    if l_gpu == l_ref:
+        return True
+    return D_ref[l_gpu] - D_ref[l_ref] <= tol

@@ -1,0 +1,55 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point that include/swalign.h declares.  No GPU call."""
+import ctypes
+import os
+import re
+
+import oracle
+from paper_2503_13756_gb300 import swalign
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "swalign.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sw_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("sw_project", "sw_quantiles", "sw_align_all_rotations", "sw_align_batch",
+                 "sw_create", "sw_destroy", "sw_last_error", "sw_bank_create",
+                 "sw_bank_align", "sw_bank_destroy"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol():
+    lib = swalign.load()
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(swalign.EXPORTS) <= set(declared_symbols())
+
+
+def test_result_struct_layout():
+    # sw_result: int32 best_l, int32 status, float angle, float reserved,
+    # double shift[2], double d2 -> 40 bytes, d2 at offset 32
+    assert swalign.RESULT_DTYPE.itemsize == 40
+    assert swalign.RESULT_DTYPE.fields["d2"][1] == 32
+    assert ctypes.sizeof(swalign.Params) == 28
+
+
+def test_default_bins_agree_with_oracle():
+    lib = swalign.load()
+    for L in [2, 3, 16, 39, 64, 85, 96, 128, 192, 256, 512]:
+        assert lib.sw_default_bins(L) == oracle.default_bins(L)
+
+
+def test_workspace_size_is_host_computable():
+    lib = swalign.load()
+    p = swalign.make_params(128, 256, 128)
+    small = lib.sw_batch_workspace_bytes(ctypes.byref(p), 16, 8)
+    big = lib.sw_batch_workspace_bytes(ctypes.byref(p), 4096, 256)
+    assert 0 < small < big
+    bad = swalign.make_params(128, 257, 128)  # odd n is rejected
+    assert lib.sw_batch_workspace_bytes(ctypes.byref(bad), 16, 8) == 0
