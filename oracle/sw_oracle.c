@@ -35,6 +35,28 @@ typedef struct {
     double d2;        /* squared sliced-W2 distance at best_l                 */
 } orc_result;
 
+/* Direction e_k = (cos theta_k, sin theta_k), theta_k = 2 pi k / n
+ * (App. A.1.2).  At quarter turns (4k divisible by n) the direction is the
+ * exact axis vector: cos(2 pi k / n) evaluated at the rounded pi would put
+ * 1e-16 of mass into bins that the exact direction leaves empty, and the
+ * z = 0 quantile (the left edge of the first bin with mass) depends on
+ * exactly that. */
+static void orc_direction(int k, int n, double *c, double *s)
+{
+    k %= n;
+    if (k < 0) k += n;
+    if ((4 * k) % n == 0) {
+        static const double cq[4] = {1.0, 0.0, -1.0, 0.0};
+        static const double sq[4] = {0.0, 1.0, 0.0, -1.0};
+        *c = cq[4 * k / n];
+        *s = sq[4 * k / n];
+        return;
+    }
+    const double th = 2.0 * ORC_PI * k / n;
+    *c = cos(th);
+    *s = sin(th);
+}
+
 /* Number of bins that holds every pixel-centre projection of an L x L
  * image with at least half a bin to spare on each side:
  * B = 2*ceil((L-1)/sqrt(2)) + 2.  The paper samples L points on [-1,1]
@@ -76,8 +98,8 @@ void orc_project(const double *F, int L, int n, int B, double *U)
     const double h = 2.0 / L;
     memset(U, 0, sizeof(double) * (size_t)n * B);
     for (int k = 0; k < n; ++k) {
-        const double th = 2.0 * ORC_PI * k / n;
-        const double ct = cos(th), st = sin(th);
+        double ct, st;
+        orc_direction(k, n, &ct, &st);
         double *Uk = U + (size_t)k * B;
         for (int r = 0; r < L; ++r) {
             const double y = -1.0 + (r + 0.5) * h;
@@ -210,9 +232,10 @@ void orc_center(const double *Q, int n, int M, double *a, double *Qc)
         double ub = 0.0;
         for (int p = 0; p < M; ++p) ub += Q[(size_t)k * M + p];
         ub /= M;
-        const double th = 2.0 * ORC_PI * k / n;
-        ax += ub * cos(th);
-        ay += ub * sin(th);
+        double ct, st;
+        orc_direction(k, n, &ct, &st);
+        ax += ub * ct;
+        ay += ub * st;
     }
     ax *= 2.0 / n;
     ay *= 2.0 / n;
@@ -220,8 +243,9 @@ void orc_center(const double *Q, int n, int M, double *a, double *Qc)
     a[1] = ay;
     if (Qc) {
         for (int k = 0; k < n; ++k) {
-            const double th = 2.0 * ORC_PI * k / n;
-            const double off = ax * cos(th) + ay * sin(th);
+            double ct, st;
+            orc_direction(k, n, &ct, &st);
+            const double off = ax * ct + ay * st;
             for (int p = 0; p < M; ++p)
                 Qc[(size_t)k * M + p] = Q[(size_t)k * M + p] - off;
         }
@@ -294,19 +318,21 @@ static void orc_decide(const double *D, int n, const double *af,
         if (D[l] < D[best]) best = l;
     for (int l = 0; l < n; ++l) {
         if (!shifts) break;
-        const double al = 2.0 * ORC_PI * l / n;
-        const double rx = cos(al) * ag[0] - sin(al) * ag[1];
-        const double ry = sin(al) * ag[0] + cos(al) * ag[1];
+        double ca, sa;
+        orc_direction(l, n, &ca, &sa);
+        const double rx = ca * ag[0] - sa * ag[1];
+        const double ry = sa * ag[0] + ca * ag[1];
         shifts[2 * l] = translation ? af[0] - rx : 0.0;
         shifts[2 * l + 1] = translation ? af[1] - ry : 0.0;
     }
-    const double ab = 2.0 * ORC_PI * best / n;
+    double cb, sb;
+    orc_direction(best, n, &cb, &sb);
     res->best_l = best;
     res->status = 0;
-    res->angle = ab;
+    res->angle = 2.0 * ORC_PI * best / n;
     if (translation) {
-        res->shift[0] = af[0] - (cos(ab) * ag[0] - sin(ab) * ag[1]);
-        res->shift[1] = af[1] - (sin(ab) * ag[0] + cos(ab) * ag[1]);
+        res->shift[0] = af[0] - (cb * ag[0] - sb * ag[1]);
+        res->shift[1] = af[1] - (sb * ag[0] + cb * ag[1]);
     } else {
         res->shift[0] = res->shift[1] = 0.0;
     }
