@@ -38,12 +38,14 @@ CORR_FLOPS_PER_PAIR_FREQ = 8 * M_LEVELS  # complex multiply-add per level
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
+    ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
     return ap.parse_args()
 
 
@@ -57,7 +59,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -72,7 +74,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -149,7 +151,7 @@ def sum_over_ranks(x, world, device):
     return float(t.item())
 
 
-def cpu_baseline(data, sample_q=96, sample_t=96):
+def cpu_baseline(data, sample_q=160, sample_t=160):
     """The FP64 oracle as it stands, on the host cores, on the first
     sample_q x sample_t pairs of the workload."""
     import oracle
@@ -213,15 +215,16 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    data = synth.many_to_many(seed=synth.SEED_BASE + 2 + 1000 * rank)
-    pairs_per_rank = NQ * NT
+    nq, nt = args.nq, args.nt
+    data = synth.many_to_many(n_queries=nq, n_templates=nt, seed=synth.SEED_BASE + 2 + 1000 * rank)
+    pairs_per_rank = nq * nt
     al = swalign.Aligner(local)
     p = swalign.make_params(L, N_THETA, M_LEVELS, precision=args.precision)
     q_h = torch.from_numpy(data["queries"]).pin_memory()
     t_h = torch.from_numpy(data["templates"]).pin_memory()
     q_d, t_d = q_h.to(dev), t_h.to(dev)
-    out = torch.empty((NQ * NT, 40), dtype=torch.uint8, device=dev)
-    al.reserve(p, NQ, NT)
+    out = torch.empty((nq * nt, 40), dtype=torch.uint8, device=dev)
+    al.reserve(p, nq, nt)
     stream = torch.cuda.current_stream()
 
     for _ in range(max(3, args.warmup)):
@@ -248,13 +251,13 @@ def main():
     ms_max = max_over_ranks(ms, world, dev)
     total_pairs = sum_over_ranks(pairs_per_rank, world, dev)
     value = total_pairs / (ms_max / 1e3)
-    res = swalign.results_to_numpy(out[:NT])
+    res = swalign.results_to_numpy(out[:nt])
     assert np.all(res["status"] == 0)
 
     # ---- end to end: pinned host inputs -> device -> results back, per step
     e2e = None
     if not args.no_e2e:
-        out_h = torch.empty((NQ * NT, 40), dtype=torch.uint8).pin_memory()
+        out_h = torch.empty((nq * nt, 40), dtype=torch.uint8).pin_memory()
         for _ in range(2):
             q_d.copy_(q_h, non_blocking=True)
             t_d.copy_(t_h, non_blocking=True)
@@ -279,7 +282,7 @@ def main():
         return
     # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
-    nimg = NQ + NT
+    nimg = nq + nt
     per_stage = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                  for k, v in stages.items()}
     dom = max(stages, key=lambda k: stages[k][0])
@@ -291,7 +294,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
     elif dom == "corr" and args.precision == "fp32":
-        flops = args.steps * NQ * NT * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
+        flops = args.steps * nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
         achieved = flops / (stages[dom][0] / 1e3) / 1e12
         roof = {"kernel": "k_corr_simt", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
@@ -306,7 +309,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else args.precision,
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "Nq": NQ, "Nt": NT, "L": L, "n_theta": N_THETA,
+        "config": {"workload": WORKLOAD if (nq, nt) == (NQ, NT) else
+                   f"many-to-many {nq}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
+                   "Nq": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
                    "n_levels": M_LEVELS, "precision": args.precision, "translation": 1,
                    "parallelism": f"{world} independent replicas (weak)",
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},

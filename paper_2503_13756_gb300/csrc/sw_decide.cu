@@ -37,23 +37,38 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw, int nsig)
     const int Nq = A.Nq, Nt = A.Nt;
 
     for (int p = threadIdx.x; p < M; p += blockDim.x) prof_i[p] = A.prof_q[(size_t)i * M + p];
-    // ---- Hermitian-extended spectra of two pairs per signal
+    // ---- Hermitian-extended spectra of two pairs per signal.  Each thread
+    // reads C(k') of two adjacent templates with one 16-byte load and writes
+    // Z(k') and Z(n - k').  Templates that are unusable contribute zeros, so
+    // that their NaNs cannot reach the partner pair through the FFT.
     const float2 *Ci = A.C + (size_t)i * Nt;
     const size_t fs = (size_t)Nq * Nt;
-    for (int t = threadIdx.x; t < n * nsig; t += blockDim.x) {
+    const bool vec = (Nt & 1) == 0;  // C rows of even length keep 16-byte alignment
+    for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
         const int kf = t / nsig, s = t % nsig;
         const int ja = j0 + 2 * s, jb = ja + 1;
-        float2 Z = make_float2(0.f, 0.f);
+        float2 Xa = make_float2(0.f, 0.f), Xb = make_float2(0.f, 0.f);
         if (kf != 0) {
-            const int m = kf <= nh ? kf : n - kf;
-            const float2 *Cm = Ci + (size_t)(m - 1) * fs;
-            const float2 Xa = ja < Nt ? Cm[ja] : make_float2(0.f, 0.f);
-            const float2 Xb = jb < Nt ? Cm[jb] : make_float2(0.f, 0.f);
-            if (kf < nh) Z = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);       // Xa + i Xb
-            else if (kf == nh) Z = make_float2(Xa.x, Xb.x);                // real parts
-            else Z = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);                // conj Xa + i conj Xb
+            const float2 *Cm = Ci + (size_t)(kf - 1) * fs;
+            if (vec && jb < Nt) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(Cm + ja));
+                Xa = make_float2(v.x, v.y);
+                Xb = make_float2(v.z, v.w);
+            } else {
+                if (ja < Nt) Xa = Cm[ja];
+                if (jb < Nt) Xb = Cm[jb];
+            }
+            if (ja >= Nt || A.st_t[ja]) Xa = make_float2(0.f, 0.f);
+            if (jb >= Nt || A.st_t[jb]) Xb = make_float2(0.f, 0.f);
         }
-        b0[t] = Z;
+        if (kf == 0) {
+            b0[s] = make_float2(0.f, 0.f);
+        } else if (kf == nh) {
+            b0[kf * nsig + s] = make_float2(Xa.x, Xb.x);  // real parts
+        } else {
+            b0[kf * nsig + s] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);             // Xa + i Xb
+            b0[(n - kf) * nsig + s] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);       // conj Xa + i conj Xb
+        }
     }
     __syncthreads();
     const float2 *R = fft_smem(b0, b1, plan, nsig, tw, +1);  // R[l][s] = n (corr_a + i corr_b)

@@ -53,6 +53,18 @@ __device__ __forceinline__ DF df_mul_f(DF t, float z)
     return df_two_sum(p, fmaf(z, t.lo, e));
 }
 
+// k * t / d for small integers k, d (exact floats): the product is formed
+// error-free, the quotient with its FMA remainder.
+__device__ __forceinline__ DF df_scale_ratio(DF t, float k, float d)
+{
+    float p = t.hi * k;
+    float e = fmaf(t.hi, k, -p);
+    DF num = df_two_sum(p, fmaf(t.lo, k, e));
+    float q = num.hi / d;
+    float r = fmaf(-q, d, num.hi);
+    return df_two_sum(q, (r + num.lo) / d);
+}
+
 // ------------------------------------------------------------------------
 // Complex helpers.
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)

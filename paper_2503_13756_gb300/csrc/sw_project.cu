@@ -7,11 +7,13 @@
 //
 // Design (GB300): the splat is evaluated as a deterministic gather.  A warp
 // owns one angle and 32 consecutive bins; each lane walks the rows (or the
-// columns, when the direction is closer to the y axis) of an image tile held
-// in shared memory and sums the <= 3 cells whose projection falls within one
+// columns, when the direction is closer to the y axis) of an image held in
+// shared memory and sums the <= 3 cells whose projection falls within one
 // bin of its own.  No atomics, so results are bitwise reproducible and
 // independent of batching.  Rows whose projection misses the warp's 32 bins
-// are skipped.  Images larger than the tile are processed tile by tile with
+// are skipped.  When n % 4 == 0 and the image fits in shared memory
+// (k_project4), one set of weights serves four angles through the square's
+// symmetries; otherwise (k_project) images are processed tile by tile with
 // zero borders, accumulating in shared memory.
 #include "sw_internal.cuh"
 
@@ -170,6 +172,136 @@ k_project(const float *__restrict__ img, int L, int srcL, int nh, int B, int G,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Four angles per set of weights.  For theta in [0, pi/4] the angles
+// pi/2 - theta, pi/2 + theta and pi - theta are theta applied to exact cell
+// permutations of the image (transpose and flips), so the splat weights of a
+// cell of the canonical frame serve all four:
+//   view 1: F[m][q]        -> angle k
+//   view 2: F[q][m]        -> angle n/4 - k
+//   view 3: F[q][L-1-m]    -> angle n/4 + k
+//   view 4: F[m][L-1-q]    -> angle n/2 - k
+// for canonical k with 8k <= n (needs n % 4 == 0).  Duplicates (k = 0, 8k = n)
+// are written once.  The whole image sits in shared memory with a zero
+// border of two cells, so every view reads it in place.
+constexpr int kMaxL4 = 200;
+
+__global__ void __launch_bounds__(kProjThreads)
+k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per, int kc,
+           const float2 *__restrict__ cs, float *__restrict__ out, int full_n,
+           int32_t *__restrict__ status)
+{
+    // this CTA's canonical angles: [kc0, kc0 + kcn)
+    const int kc0 = blockIdx.x * per;
+    const int kcn = min(per, kc - kc0);
+    extern __shared__ float tile[];
+    const int S = ((L + 2 * kPad) & 1) ? L + 2 * kPad : L + 2 * kPad + 1;
+    const int rowsT = L + 2 * kPad;
+    __shared__ int s_bad, s_mass;
+    const int imgi = blockIdx.y;
+    const float *src = img + (size_t)imgi * srcL * srcL;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_mass = 0;
+    }
+    int bad = 0, mass = 0;
+    for (int idx = threadIdx.x; idx < rowsT * S; idx += blockDim.x) {
+        const int r = idx / S - kPad, c = idx % S - kPad;
+        float v = 0.f;
+        if (r >= 0 && r < L && c >= 0 && c < L) {
+            if (srcL == L) v = __ldg(src + (size_t)r * L + c);
+            else v = 0.25f * __ldg(src + (size_t)(r >> 1) * srcL + (c >> 1));
+            if (!isfinite(v)) {
+                bad = 1;
+                v = 0.f;
+            }
+            v = fmaxf(v, 0.f);
+            mass |= v > 0.f;
+        }
+        tile[idx] = v;
+    }
+    if (bad) atomicOr(&s_bad, 1);
+    if (mass) atomicOr(&s_mass, 1);
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) status[imgi] = (s_bad || !s_mass) ? 1 : 0;
+
+    const int nh = n / 2, n4 = n / 4;
+    const int nrow = full_n ? n : nh;
+    const int Bp = (B + 31) & ~31;
+    const int ngroups = Bp >> 5;
+    const int nitems = kcn * ngroups;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const float c0 = 0.5f * (float)(L - 1);
+    const float half_B1 = 0.5f * (float)(B - 1);
+    float *outi = out + (size_t)imgi * nrow * B;
+
+    for (int it = warp; it < nitems; it += nwarps) {
+        const int k = kc0 + it / ngroups, g = it % ngroups;
+        const float2 t = cs[k];  // cos >= sin >= 0
+        const float kq = t.x, km = t.y;
+        const int b0 = g << 5;
+        // u(q, m) = q kq + m km + U0 on the canonical frame, q, m in [0, L)
+        const float U0 = fmaf(-c0, kq, fmaf(-c0, km, half_B1));
+        const float ext = (float)(L - 1) * kq;
+        // rows that can reach bins [b0-1, b0+32]; an empty range still writes
+        // its (zero) bins below
+        int mlo = 0, mhi = L - 1;
+        if (km > 1e-6f) {
+            float hi = ((float)b0 + 32.f - U0) / km;
+            float lo = ((float)b0 - 1.f - U0 - ext) / km;
+            lo = fmaxf(floorf(lo) - 1.f, 0.f);
+            hi = fminf(ceilf(hi) + 1.f, (float)(L - 1));
+            mlo = (int)lo;
+            mhi = lo > hi ? mlo - 1 : (int)hi;
+        } else if (U0 + ext < (float)b0 - 1.f || U0 > (float)b0 + 32.f) {
+            mhi = -1;
+        }
+        const int b = b0 + lane;
+        const float Ab = fmaf(-c0, kq, half_B1 - (float)b);
+        const float invk = 1.f / kq;
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+        for (int m = mlo; m <= mhi; ++m) {
+            const float beta = fmaf((float)m - c0, km, Ab);  // d(q) = q kq + beta
+            const float qlo = fmaf(-beta, invk, -invk);       // window (qlo, qlo + 2/kq)
+            float qs = floorf(qlo) + 1.f;
+            qs = fminf(fmaxf(qs, -2.f), (float)(L - 1));
+            const int qi = __float_as_int(qs + 12582912.f) - 0x4B400000;  // exact small int
+            const float d0 = fmaf(qs, kq, beta), d1 = d0 + kq, d2 = d1 + kq;
+            const float w0 = fmaxf(0.f, 1.f - fabsf(d0));
+            const float w1 = fmaxf(0.f, 1.f - fabsf(d1));
+            const float w2 = fmaxf(0.f, 1.f - fabsf(d2));
+            const float *r1 = tile + (m + kPad) * S + (qi + kPad);
+            const float *r2 = tile + (qi + kPad) * S + (m + kPad);
+            const float *r3 = tile + (qi + kPad) * S + (L - 1 - m + kPad);
+            const float *r4 = tile + (m + kPad) * S + (L - 1 - qi + kPad);
+            s1 = fmaf(w0, r1[0], s1);
+            s2 = fmaf(w0, r2[0], s2);
+            s3 = fmaf(w0, r3[0], s3);
+            s4 = fmaf(w0, r4[0], s4);
+            s1 = fmaf(w1, r1[1], s1);
+            s2 = fmaf(w1, r2[S], s2);
+            s3 = fmaf(w1, r3[S], s3);
+            s4 = fmaf(w1, r4[-1], s4);
+            s1 = fmaf(w2, r1[2], s1);
+            s2 = fmaf(w2, r2[2 * S], s2);
+            s3 = fmaf(w2, r3[2 * S], s3);
+            s4 = fmaf(w2, r4[-2], s4);
+        }
+        if (b >= B) continue;
+        const int angle[4] = {k, n4 - k, n4 + k, nh - k};
+        const bool keep[4] = {true, 8 * k != n, k != 0, k != 0 && 8 * k != n};
+        const float val[4] = {s1, s2, s3, s4};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (!keep[v]) continue;
+            float *o = outi + (size_t)angle[v] * B;
+            o[b] = val[v];
+            if (full_n) o[(size_t)nh * B + (B - 1 - b)] = val[v];
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
@@ -177,16 +309,29 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
                            cudaStream_t st)
 {
     if (nb <= 0) return cudaSuccess;
+    const int n = 2 * nh;
+    if (n % 4 == 0 && L <= kMaxL4) {
+        // canonical angles k = 0..n/8; split over CTAs when the batch is small
+        const int kc = n / 8 + 1;
+        const int want = 456;  // ~3 resident CTAs per SM on 152 SMs
+        int groups = nb >= want ? 1 : (want + nb - 1) / nb;
+        if (groups > kc) groups = kc;
+        const int per = (kc + groups - 1) / groups;
+        groups = (kc + per - 1) / per;
+        const int S = ((L + 2 * kPad) & 1) ? L + 2 * kPad : L + 2 * kPad + 1;
+        const size_t smem = sizeof(float) * (size_t)(L + 2 * kPad) * S;
+        cudaFuncSetAttribute(k_project4, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        dim3 grid(groups, nb);
+        k_project4<<<grid, kProjThreads, smem, st>>>(img, L, srcL, n, B, per, kc, cs, out, full_n,
+                                                      status);
+        return cudaGetLastError();
+    }
     const TileGeom tg = tile_geom(L);
     const int Bp = (B + 31) & ~31;
     int G = 16;
     if (nh < G) G = nh;
     const size_t smem = sizeof(float) * ((size_t)(tg.T + 2 * kPad) * tg.S + (size_t)G * Bp);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
-    }
+    cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid((nh + G - 1) / G, nb);
     k_project<<<grid, kProjThreads, smem, st>>>(img, L, srcL, nh, B, G, cs, out, full_n, status);
     return cudaGetLastError();

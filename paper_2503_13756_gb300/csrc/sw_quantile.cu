@@ -81,11 +81,12 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
         if (lane == 0) atomicOr(status + imgi, 1);
         return;
     }
-    const float invM = 1.f / (float)M;
     for (int p = lane; p < M; p += 32) {
-        const float z = level_rule == 0 ? (2.f * p + 1.f) * (0.5f * invM) : (float)p * invM;
+        // tau = z_p F_B with z_p = (2p+1)/(2M) or p/M, formed exactly
+        const float kz = level_rule == 0 ? 2.f * p + 1.f : (float)p;
+        const float dz = level_rule == 0 ? 2.f * M : (float)M;
         float Q;
-        if (z == 0.f) {
+        if (kz == 0.f) {
             // left edge of the first bin with mass: j* = min{j >= 1: F_j > 0}
             int lo = 1, hi = B;
             while (lo < hi) {
@@ -95,7 +96,7 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
             }
             Q = ((float)(lo - 1) - 0.5f * (float)B) * h;
         } else {
-            const DF tau = df_mul_f(total, z);
+            const DF tau = df_scale_ratio(total, kz, dz);
             int lo = 1, hi = B;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;

@@ -5,7 +5,15 @@ S = (N_f + N_g) / (n M) with N the centred quantile norm.  The relative bound
 1e-5 is the stated FP32 target; the floor 0.1 S covers the cancellation in
 N_f + N_g - 2 corr, whose FP32 rounding scales with S, not with d2 (so a
 relative bound alone is undefined as d2 -> 0, e.g. for self-comparisons).
-Reduced precision (BF16/FP16 correlation): the same with 1e-2.
+Reduced precision (BF16/FP16 correlation): the same with 1e-2.  Both carry an
+absolute floor of 1e-12: the quantiles are FP32 values of magnitude <= 2
+(half an ulp <= 1.2e-7), and when both the distance and the centred norms
+vanish (e.g. M = 1, n = 4, where every centred quantile is 0) only the squared
+rounding of the quantiles remains.
+
+Quantiles: |Q_gpu - Q_ref| <= 2.5e-7 |Q_ref| + 1e-7 -- the FP32 bin width h
+(relative error <= 6e-8), the node e_j = (j - B/2) h (one more rounding) and
+the final rounding of Q (half an ulp), plus the interpolation fraction.
 
 Argmin: identical, except at ties -- the GPU's choice l_gpu is accepted when
 the oracle's own curve puts it within the distance tolerance of the optimum,
@@ -32,8 +40,15 @@ def norm_scale(f, g, n, M, level_rule=0):
     return tot / (n * M)
 
 
+ABS_FLOOR = 1e-12
+
+
 def d2_tol(d2_ref, S, rel=REL_FP32):
-    return rel * np.maximum(d2_ref, 0.1 * S)
+    return rel * np.maximum(d2_ref, 0.1 * S) + ABS_FLOOR
+
+
+def q_tol(q_ref):
+    return 2.5e-7 * np.abs(q_ref) + 1e-7
 
 
 def check_argmin(l_gpu, l_ref, D_ref, tol):

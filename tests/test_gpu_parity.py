@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_2503_13756_gb300 import swalign, synth
-from tests.parity import REL_FP32, check_argmin, d2_tol, norm_scale
+from tests.parity import REL_FP32, check_argmin, d2_tol, norm_scale, q_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,8 @@ def blobs(rng, count, L, ncomp=(2, 4)):
 
 # ------------------------------------------------------------- projection
 
-@pytest.mark.parametrize("L,n", [(16, 8), (33, 36), (64, 60), (128, 256), (200, 24), (256, 16)])
+@pytest.mark.parametrize("L,n", [(16, 8), (33, 36), (64, 60), (128, 256), (200, 24),  # 4 angles/weight
+                                 (48, 30), (130, 18), (256, 16)])                   # generic, tiled
 def test_project_matches_oracle(al, L, n):
     rng = np.random.default_rng(L * 1000 + n)
     imgs = blobs(rng, 3, L)
@@ -69,7 +70,8 @@ def test_quantiles_match_oracle(al, L, n, M, level_rule):
     h = 2.0 / L
     for i in range(2):
         ref = oracle.quantiles(U32[i].astype(np.float64), h, M, level_rule)
-        assert np.abs(q[i] - ref).max() <= 2e-7, np.abs(q[i] - ref).max()
+        err = np.abs(q[i] - ref)
+        assert np.all(err <= q_tol(ref)), (err / q_tol(ref)).max()
         a, Qc = oracle.center(q[i].astype(np.float64))
         np.testing.assert_allclose(center[i], a, rtol=0, atol=1e-12)
         np.testing.assert_allclose(norm[i], (Qc ** 2).sum(), rtol=1e-10)
@@ -199,6 +201,10 @@ def test_best_template_mode(al):
 
 
 def test_pair_alone_equals_pair_in_batch(al):
+    # Run to run the same batch is bitwise identical (no atomics, fixed
+    # reduction orders).  A pair alone and in a batch agree within the parity
+    # tolerance: the decision FFT packs two pairs per complex signal, so the
+    # rounding of one depends on its partner.
     rng = np.random.default_rng(8)
     L, n, M = 64, 72, 32
     q = f32(blobs(rng, 9, L))
@@ -206,10 +212,14 @@ def test_pair_alone_equals_pair_in_batch(al):
     p = swalign.make_params(L, n, M)
     big = swalign.results_to_numpy(al.align_batch(q, t, p)).reshape(9, 11)
     again = swalign.results_to_numpy(al.align_batch(q, t, p)).reshape(9, 11)
-    assert big.tobytes() == again.tobytes()  # run to run: bitwise
+    assert big.tobytes() == again.tobytes()
     for (i, j) in [(0, 0), (4, 7), (8, 10)]:
         one = swalign.results_to_numpy(al.align_batch(q[i:i + 1], t[j:j + 1], p))[0]
-        assert one.tobytes() == big[i, j].tobytes()
+        _, Dref, _ = oracle.align_pair(q[i].astype(np.float64), t[j].astype(np.float64), n, M)
+        Sc = norm_scale(q[i].astype(np.float64), t[j].astype(np.float64), n, M)
+        tol = d2_tol(Dref[int(big[i, j]["best_l"])], Sc)
+        assert check_argmin(int(one["best_l"]), int(big[i, j]["best_l"]), Dref, tol)
+        assert abs(one["d2"] - big[i, j]["d2"]) <= 2 * tol
 
 
 def test_invalid_arguments_are_rejected(al):
