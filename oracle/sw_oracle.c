@@ -126,8 +126,11 @@ void orc_project(const double *F, int L, int n, int B, double *U)
  * piecewise-linear function through (e_j, F_j), F_0 = 0, F_j = sum_{b<j} U_b.
  * For tau = z_p * F_B the quantile is Q = e_{j-1} + h (tau - F_{j-1}) / U_{j-1}
  * with j = min{ j >= 1 : F_j >= tau }; for tau = 0 (level p = 0 under
- * level_rule 1) it is the left edge of the first bin with positive mass,
- * the limit of Q(z) as z -> 0+.
+ * level_rule 1) the set {t : F(t) >= 0} is the whole domain, whose infimum
+ * is its left end e_0 (App. A.1.1 integrates the CDF from the domain's left
+ * end).  This value is the same for every image, so it cancels in the
+ * distance; the left edge of the first bin with mass would instead depend on
+ * whether a vanishing weight rounds to zero.
  * The levels are walked in increasing order against the cumulative mass
  * (a merge of the two sorted sequences).  Returns 0 if the histogram has no
  * positive mass. */
@@ -143,9 +146,8 @@ static int orc_quantiles_1d(const double *U, int B, double h, int M,
         const double z = level_rule == 0 ? (p + 0.5) / M : (double)p / M;
         const double tau = z * total;
         if (tau == 0.0) {
-            int jj = 1;
-            while (jj < B && !(Fbuf[jj] > 0.0)) ++jj;
-            Q[p] = (jj - 1 - 0.5 * B) * h;
+            /* inf{t : F(t) >= 0} is the left end of the domain, e_0 */
+            Q[p] = -0.5 * B * h;
             continue;
         }
         while (j < B && Fbuf[j] < tau) ++j;

@@ -125,7 +125,8 @@ def test_quantiles_of_uniform_histogram_closed_form():
     z = (np.arange(M) + 0.5) / M
     np.testing.assert_allclose(Q[0], e11 + 7 * h * z, atol=1e-14)
     Q1 = oracle.quantiles(U, h, M, level_rule=1)
-    np.testing.assert_allclose(Q1[0], e11 + 7 * h * np.arange(M) / M, atol=1e-14)
+    np.testing.assert_allclose(Q1[0, 1:], e11 + 7 * h * np.arange(1, M) / M, atol=1e-14)
+    assert Q1[0, 0] == -B / 2 * h  # z = 0: the left end of the domain
 
 
 def test_sampled_w2_of_two_uniforms_closed_form():
@@ -143,16 +144,18 @@ def test_sampled_w2_of_two_uniforms_closed_form():
     assert abs(exact - (D * D - 4 * h * D + 16 * h * h / 3)) < 1e-14
 
 
-def test_quantile_takes_left_end_of_flat_cdf_and_first_mass_at_zero():
+def test_quantile_takes_left_end_of_flat_cdf_and_domain_start_at_zero():
     # Masses 1,1,1 in bins 2..4, nothing in 5..6, masses 1,1,1 in 7..9.
     # level_rule 1 with M = 2: z = 0 and z = 1/2; tau = 3 = F_5 = F_6 = F_7.
+    # inf{t : F(t) >= z} (App. A.1.1): at z = 0 every t of the domain
+    # qualifies, so Q(0) = e_0; at z = 1/2 it is the left end of the flat part.
     B, h = 12, 0.25
     U = np.zeros((1, B))
     U[0, [2, 3, 4, 7, 8, 9]] = 1.0
     Q = oracle.quantiles(U, h, 2, level_rule=1)
     e = lambda j: (j - B / 2) * h
-    assert Q[0, 0] == pytest.approx(e(2), abs=1e-15)  # left edge of first mass
-    assert Q[0, 1] == pytest.approx(e(5), abs=1e-15)  # inf{t: F(t) >= 1/2}
+    assert Q[0, 0] == pytest.approx(e(0), abs=1e-15)
+    assert Q[0, 1] == pytest.approx(e(5), abs=1e-15)
 
 
 def test_w2_gaussian_closed_form_and_E3_bound():
