@@ -6,8 +6,8 @@
 //   F_0 = 0, F_j = sum_{b<j} U_b,  tau_p = z_p F_B,
 //   j* = min{ j >= 1 : F_j >= tau_p },
 //   Q(z_p) = e_{j*-1} + h (tau_p - F_{j*-1}) / U_{j*-1};
-// at tau = 0 (level p = 0 under the p/M rule) Q is the left edge of the first
-// bin with mass.
+// at tau = 0 (level p = 0 under the p/M rule) every t qualifies and Q is the
+// left end of the domain, e_0.
 //
 // Design (GB300): one warp per projection.  The CDF is a warp scan of
 // double-float partial sums (TwoSum-compensated FP32) kept in shared memory,
@@ -87,14 +87,7 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
         const float dz = level_rule == 0 ? 2.f * M : (float)M;
         float Q;
         if (kz == 0.f) {
-            // left edge of the first bin with mass: j* = min{j >= 1: F_j > 0}
-            int lo = 1, hi = B;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (Fh[mid] > 0.f) hi = mid;
-                else lo = mid + 1;
-            }
-            Q = ((float)(lo - 1) - 0.5f * (float)B) * h;
+            Q = -0.5f * (float)B * h;  // inf{t : F(t) >= 0}: the domain's left end e_0
         } else {
             const DF tau = df_scale_ratio(total, kz, dz);
             int lo = 1, hi = B;
