@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
     return ap.parse_args()
@@ -254,6 +255,41 @@ def main():
     res = swalign.results_to_numpy(out[:nt])
     assert np.all(res["status"] == 0)
 
+    # ---- the same workload with the tensor-core correlation (BF16 / FP16)
+    variants = {}
+    if args.precision == "fp32" and not args.no_variants:
+        for prec in ("bf16", "fp16"):
+            pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec)
+            al.reserve(pv, nq, nt)
+            for _ in range(3):
+                al.align_batch(q_d, t_d, pv, out=out)
+            torch.cuda.synchronize()
+            al.profile(True)
+            al.profile_read()
+            e0.record(stream)
+            for _ in range(args.steps):
+                al.align_batch(q_d, t_d, pv, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            st_v = al.profile_read()
+            al.profile(False)
+            ms_v = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+            rv = swalign.results_to_numpy(out[:nt])
+            corr_ms = st_v.get("corr", (0.0, 1))[0] / args.steps
+            flops = nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
+            peaks_v, _ = measured_peaks()
+            tf = flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else None
+            variants[prec] = {
+                "value": sum_over_ranks(nq * nt, world, dev) / (ms_v / 1e3), "unit": "pairs/s",
+                "ms_per_step": ms_v, "status_ok": bool(np.all(rv["status"] == 0)),
+                "stages": {k: v[0] / args.steps for k, v in st_v.items()},
+                "corr_tensor": {"achieved": tf, "unit": "TFLOP/s",
+                                "peak": peaks_v.get("bf16_tflops"),
+                                "frac": tf / peaks_v["bf16_tflops"] if tf else None,
+                                "flops_per_launch": flops},
+            }
+        al.reserve(p, nq, nt)
+
     # ---- end to end: pinned host inputs -> device -> results back, per step
     e2e = None
     if not args.no_e2e:
@@ -317,6 +353,7 @@ def main():
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},
         "roofline": roof, "peaks": peak_src, "stages": per_stage, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
 

@@ -76,7 +76,8 @@ typedef struct {
 
 typedef struct {
     int32_t best_l;   /* l*: g is turned by alpha* = 2 pi l* / n onto f         */
-    int32_t status;   /* 0 ok, 1 reference/query unusable, 2 template unusable  */
+    int32_t status;   /* 0 ok, 1 reference/query unusable, 2 template unusable, */
+                      /* 3 a bounded device wait gave up (results NaN)           */
     float angle_rad;  /* alpha* = 2 pi l* / n                                   */
     float reserved;
     double shift[2];  /* s*: f ~ T_{s*} R_{alpha*} g; 0 when translation == 0   */

@@ -86,7 +86,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // Offsets of the batch workspace.
 struct Layout {
     size_t status, proj, quant, spec32, lp_q, lp_t, prof, center, norm32, norm16, C, scratch,
-        total;
+        err, total;
 };
 
 int bins_of(const sw_params *p) { return p->n_bins > 0 ? p->n_bins : sw_default_bins(p->L); }
@@ -106,14 +106,16 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, bool lp, bool scratch)
     l.proj = take(4 * nimg * nh * B);
     l.quant = take(4 * nimg * n * M);
     l.spec32 = take(4 * nh * nimg * 2 * M);
-    l.lp_q = take(lp ? 2 * nh * (size_t)Nq * 2 * M : 0);
-    l.lp_t = take(lp ? 2 * nh * (size_t)2 * Nt * 2 * M : 0);
+    const size_t ldk = swk::tc_ldk((int)M);
+    l.lp_q = take(lp ? 2 * nh * (size_t)Nq * ldk : 0);
+    l.lp_t = take(lp ? 2 * nh * (size_t)2 * Nt * ldk : 0);
     l.prof = take(4 * nimg * M);
     l.center = take(16 * nimg);
     l.norm32 = take(8 * nimg);
     l.norm16 = take(8 * nimg);
     l.C = take(8 * nh * (size_t)Nq * Nt);
     l.scratch = take(scratch ? sizeof(sw_result) * (size_t)Nq * Nt : 0);
+    l.err = take(sizeof(int));
     l.total = o;
     return l;
 }
@@ -127,6 +129,7 @@ struct ProfRec {
 
 struct sw_ctx {
     int device = 0;
+    int num_sms = 0;
     std::string err;
     char *ws = nullptr;
     size_t ws_size = 0;
@@ -347,15 +350,6 @@ T *at(char *base, size_t off)
     return reinterpret_cast<T *>(base + off);
 }
 
-sw_status lp_unsupported(sw_ctx *c, const sw_params *p)
-{
-    if (p->gemm_precision != SW_PREC_FP32)
-        return fail(c, SW_ERR_UNSUPPORTED,
-                    "gemm_precision=%d: tensor-core correlation not available in this build",
-                    p->gemm_precision);
-    return SW_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -379,7 +373,8 @@ sw_status sw_create(int device, sw_ctx **out)
     sw_ctx *c = new (std::nothrow) sw_ctx;
     if (!c) return SW_ERR_OOM;
     c->device = device;
-    if (cudaSetDevice(device) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SW_ERR_CUDA;
@@ -551,9 +546,10 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     o.fstride = (size_t)nimg * 2 * M;
     o.lp_kind = lp ? p->gemm_precision : 0;
     o.lp_q = lp ? (void *)(w + l.lp_q) : nullptr;
-    o.lpq_fstride = (size_t)Nq * 2 * M;
+    const int ldk = swk::tc_ldk(M);
+    o.lpq_fstride = (size_t)Nq * ldk;
     o.lp_t = lp ? (void *)(w + l.lp_t) : nullptr;
-    o.lpt_fstride = (size_t)2 * Nt * 2 * M;
+    o.lpt_fstride = (size_t)2 * Nt * ldk;
     o.Nq = Nq;
     o.prof = at<float>(w, l.prof);
     o.center = at<double>(w, l.center);
@@ -563,8 +559,13 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     if ((s = run_images(c, p, t, dt, p->L, Nt, Nq, o, st))) return s;
     if ((s = run_after_projection(c, p, t, nimg, o, st))) return s;
     float2 *C = at<float2>(w, l.C);
+    int *err = at<int>(w, l.err);
+    SW_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), st));
     if (lp) {
-        if ((s = lp_unsupported(c, p))) return s;
+        SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
+                    return swk::launch_corr_tc(o.lp_q, o.lp_t, Nq, Nt, M, nh, p->gemm_precision,
+                                               C, err, c->num_sms, st);
+                }));
     } else {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
                     return swk::launch_corr_simt(o.spec32, o.fstride,
@@ -589,6 +590,7 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     a.st_t = o.status + Nq;
     a.cs64 = t->cs64;
     a.translation = p->translation;
+    a.dev_err = err;
     a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)out;
     a.curve = curve;
     a.shifts = shifts;
@@ -640,7 +642,6 @@ sw_status sw_align_batch(sw_ctx *c, const sw_params *p, const float *d_q_img, in
         return s;
     if (Nt > 0 && (s = check_ptr(c, d_t_img, "d_t_img", true))) return s;
     if ((s = set_device(c))) return s;
-    if (p->gemm_precision != SW_PREC_FP32 && (s = lp_unsupported(c, p))) return s;
     if (Nt == 0) return fail(c, SW_ERR_INVALID_ARG, "mode 1 needs at least one template");
     return align_batch_impl(c, p, d_q_img, Nq, d_t_img, Nt, mode, d_out, nullptr, nullptr,
                             false, (cudaStream_t)stream);

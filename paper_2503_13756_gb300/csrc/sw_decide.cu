@@ -128,7 +128,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw, int nsig)
         }
         if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
         const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
-        const int st = A.st_q[i] ? 1 : (A.st_t[j] ? 2 : 0);
+        const int st = A.st_q[i] ? 1 : (A.st_t[j] ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
         // FP64 distance at l (and shift)
         auto dist = [&](int l, double &sx, double &sy) {
             const float2 z = R[l * nsig + s];

@@ -197,10 +197,11 @@ cudaError_t launch_center_norm(const float *q, int nb, int n, int M, const doubl
 // = Re Qhat(k', p) and [.. + M + p] = Im, where Qhat is the DFT over angle of
 // the quantiles centred by a.  prof[img][p] = mean_k q[k][p] (k' = 0 / n).
 // norm32[img] = sum over k' != 0 of |Qhat|^2 / n (the centred, mean-free norm);
-// lp_kind 1/2 also writes bf16/fp16 copies: queries (img < Nq) to
-// lp_q[(k'-1)*lpq_fstride + img*2M + ...], templates to the doubled layout
-// lp_t[(k'-1)*lpt_fstride + (2j)*2M] = [re | im], [(2j+1)*2M] = [-im | re],
-// and norm16 from the rounded values.
+// lp_kind 1/2 also writes bf16/fp16 copies in rows of ldk = tc_ldk(M)
+// elements, zero padded after 2M: queries (img < Nq) to
+// lp_q[(k'-1)*lpq_fstride + img*ldk] = [re | im | 0], templates to the doubled
+// layout lp_t[(k'-1)*lpt_fstride + (2j)*ldk] = [re | im | 0] and
+// [(2j+1)*ldk] = [-im | re | 0], and norm16 from the rounded values.
 cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan &plan,
                             const float2 *tw, float *spec32, size_t fstride, int lp_kind,
                             void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
@@ -212,6 +213,14 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
 // X rows: X + f*xf + i*2M ([re | im]); Y rows: Y + f*yf + j*2M.
 cudaError_t launch_corr_simt(const float *X, size_t xf, const float *Y, size_t yf, int Nq,
                              int Nt, int M, int nf, float2 *C, cudaStream_t st);
+
+// Tensor-core correlation (tcgen05): the same product as launch_corr_simt for
+// BF16 (kind 1) or FP16 (kind 2) spectra in the padded K-major layout of
+// launch_spectrum: Xq [nf][Nq][ldk], Yt [nf][2Nt][ldk] (doubled template rows).
+// *err is set to 1 if a bounded wait gave up.
+int tc_ldk(int M);  // K row length: 2M rounded up to 64
+cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
+                           int kind, float2 *C, int *err, int num_sms, cudaStream_t st);
 
 // Inverse angle FFT of the correlation spectra, argmin over the rotation
 // grid and the FP64 distance at the optimum.  See sw_decide.cu.
@@ -228,6 +237,7 @@ struct DecideArgs {
     const int32_t *st_t;  // [Nt]
     const double2 *cs64;  // [n] (cos, sin) of alpha_l
     int translation;
+    const int *dev_err;   // nonzero: the correlation gave up (status 3), or NULL
     void *out;            // sw_result [Nq][Nt]
     double *curve;        // [n] or NULL (pair 0,0 only)
     double *shifts;       // [n][2] or NULL

@@ -48,6 +48,7 @@ struct SpecOut {
     void *lp_t;
     size_t lpt_fstride;
     int Nq;
+    int ldk;  // low-precision row length (>= 2M, zero padded)
 };
 
 // Writes Qhat(kf, p) (kf >= 1) for image img; returns |.|^2 weight-summed
@@ -66,17 +67,17 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
         acc16 += w * ((double)rf * rf + (double)imf * imf);
         if (img < o.Nq) {
             T *r = reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
-                   (size_t)img * 2 * M;
+                   (size_t)img * o.ldk;
             r[p] = re;
             r[M + p] = im;
         } else {
             const int j = img - o.Nq;
             T *r = reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
-                   (size_t)(2 * j) * 2 * M;
-            r[p] = re;          // row 2j:   [ re | im ]
+                   (size_t)(2 * j) * o.ldk;
+            r[p] = re;                        // row 2j:   [ re | im | 0 ]
             r[M + p] = im;
-            r[2 * M + p] = to_lp<T>(-imf);  // row 2j+1: [ -im | re ]
-            r[3 * M + p] = re;
+            r[o.ldk + p] = to_lp<T>(-imf);    // row 2j+1: [ -im | re | 0 ]
+            r[o.ldk + M + p] = re;
         }
     }
 }
@@ -174,6 +175,20 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
         const float2 X = make_float2(x1[p].x - c1r, x1[p].y - c1i);
         emit<T>(o, img, M, 1, p, X, 2.0, acc32, acc16);  // n >= 4: k' = 1 < n/2
     }
+    // ---- zero padding of the low-precision rows, [2M, ldk)
+    if (o.lp_q && o.ldk > 2 * M) {
+        const int pad = o.ldk - 2 * M;
+        const bool tmpl = img >= o.Nq;
+        const int rows = tmpl ? 2 : 1;
+        for (int t = threadIdx.x; t < nh * rows * pad; t += blockDim.x) {
+            const int kf = 1 + t / (rows * pad), rr = (t / pad) % rows, e = 2 * M + t % pad;
+            T *r = tmpl ? reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
+                              (size_t)(2 * (img - o.Nq) + rr) * o.ldk
+                        : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
+                              (size_t)img * o.ldk;
+            r[e] = to_lp<T>(0.f);
+        }
+    }
     // ---- norms: Parseval over k' != 0 of the centred spectra, / n
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -209,7 +224,8 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
     if (nb <= 0) return cudaSuccess;
     const int nsig = n <= 512 ? 16 : 8;
     const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M);
-    SpecOut o{spec32, fstride, lp_kind ? lp_q : nullptr, lpq_fstride, lp_t, lpt_fstride, Nq};
+    SpecOut o{spec32, fstride, lp_kind ? lp_q : nullptr, lpq_fstride, lp_t, lpt_fstride, Nq,
+              tc_ldk(M)};
     if (lp_kind == 2) {
         cudaFuncSetAttribute(k_spectrum<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
