@@ -78,6 +78,13 @@ bool fft_plan(int n, FftPlan &p)
             p.radix[p.nst++] = q;
             m /= q;
         }
+    int Ns = 1;
+    for (int st = 0; st < p.nst; ++st) {
+        p.ns[st] = Ns;
+        p.ns_rcp[st] = (unsigned)((((unsigned long long)1 << 32) + Ns - 1) / Ns);
+        p.tstep[st] = n / (Ns * p.radix[st]);
+        Ns *= p.radix[st];
+    }
     return m == 1;
 }
 

@@ -277,13 +277,20 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * BN + c0, r);
                 if (i < args.Nq && c0 < ncols) {
-                    if (c0 + 32 <= ncols) {
+                    // rows are 2 Nt floats: 16-byte aligned only when Nt is even,
+                    // always 8-byte aligned (float2 per template)
+                    if (c0 + 32 <= ncols && (args.Nt2 & 3) == 0) {
                         float4 *dst = reinterpret_cast<float4 *>(crow + c0);
 #pragma unroll
                         for (int v = 0; v < 8; ++v)
                             dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
                                                  __uint_as_float(r[4 * v + 2]),
                                                  __uint_as_float(r[4 * v + 3]));
+                    } else if (c0 + 32 <= ncols) {
+                        float2 *dst = reinterpret_cast<float2 *>(crow + c0);
+#pragma unroll
+                        for (int v = 0; v < 16; ++v)
+                            dst[v] = make_float2(__uint_as_float(r[2 * v]), __uint_as_float(r[2 * v + 1]));
                     } else {
 #pragma unroll
                         for (int v = 0; v < 32; ++v)

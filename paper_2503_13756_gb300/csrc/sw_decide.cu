@@ -23,15 +23,18 @@ namespace {
 
 constexpr int kDecThreads = 256;
 
+template <int nsig>
 __global__ void __launch_bounds__(kDecThreads)
-k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw, int nsig)
+k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 smd[];
     const int n = A.n, M = A.M, nh = n / 2;
     float2 *b0 = smd;
     float2 *b1 = b0 + n * nsig;
-    float *prof_i = reinterpret_cast<float *>(b1 + n * nsig);  // [M]
-    float *delta = prof_i + M;                                  // [2 nsig]
+    float2 *tws = b1 + n * nsig;                              // [n] twiddles
+    float *prof_i = reinterpret_cast<float *>(tws + n);       // [M]
+    float *delta = prof_i + M;                                // [2 nsig]
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tws[t] = tw[t];
     const int i = blockIdx.x;
     const int j0 = blockIdx.y * 2 * nsig;
     const int Nq = A.Nq, Nt = A.Nt;
@@ -44,6 +47,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw, int nsig)
     const float2 *Ci = A.C + (size_t)i * Nt;
     const size_t fs = (size_t)Nq * Nt;
     const bool vec = (Nt & 1) == 0;  // C rows of even length keep 16-byte alignment
+#pragma unroll 4
     for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
         const int kf = t / nsig, s = t % nsig;
         const int ja = j0 + 2 * s, jb = ja + 1;
@@ -71,7 +75,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw, int nsig)
         }
     }
     __syncthreads();
-    const float2 *R = fft_smem(b0, b1, plan, nsig, tw, +1);  // R[l][s] = n (corr_a + i corr_b)
+    const float2 *R = fft_smem<nsig>(b0, b1, plan, tws, +1);  // R[l][s] = n (corr_a + i corr_b)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
@@ -230,11 +234,19 @@ cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2
                           cudaStream_t st)
 {
     if (a.Nq <= 0 || a.Nt <= 0) return cudaSuccess;
-    const int nsig = a.n <= 512 ? 16 : 8;
-    const size_t smem = sizeof(float2) * (size_t)2 * a.n * nsig + sizeof(float) * (a.M + 2 * nsig);
-    cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // 8 signals (16 pairs) per CTA keeps the shared footprint small enough
+    // for several CTAs per SM; 4 at n = 1024
+    const int nsig = a.n <= 512 ? 8 : 4;
+    const size_t smem = sizeof(float2) * ((size_t)2 * a.n * nsig + a.n) +
+                        sizeof(float) * (a.M + 2 * nsig);
     dim3 grid(a.Nq, (a.Nt + 2 * nsig - 1) / (2 * nsig));  // queries on x (no 65535 cap)
-    k_decide<<<grid, kDecThreads, smem, st>>>(a, plan, tw, nsig);
+    if (nsig == 8) {
+        cudaFuncSetAttribute(k_decide<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_decide<8><<<grid, kDecThreads, smem, st>>>(a, plan, tw);
+    } else {
+        cudaFuncSetAttribute(k_decide<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_decide<4><<<grid, kDecThreads, smem, st>>>(a, plan, tw);
+    }
     return cudaGetLastError();
 }
 

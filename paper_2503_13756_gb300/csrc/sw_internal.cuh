@@ -10,11 +10,17 @@ namespace swk {
 constexpr int kMaxStages = 12;
 
 // Radix plan of an angle-length FFT: n = prod(radix[0..nst)), radices in
-// {2, 3, 4, 5}, fours first.  Built on the host.
+// {2, 3, 4, 5}, fours first.  Built on the host with, per stage, the span
+// Ns of the sub-transforms already done (product of earlier radices), a
+// multiply-high reciprocal of Ns (exact for dividends < 2^16) and the
+// twiddle index step n / (Ns r).
 struct FftPlan {
     int n;
     int nst;
     int radix[kMaxStages];
+    int ns[kMaxStages];
+    unsigned ns_rcp[kMaxStages];  // ceil(2^32 / Ns)
+    int tstep[kMaxStages];
 };
 
 // ------------------------------------------------------------------------
@@ -53,16 +59,17 @@ __device__ __forceinline__ DF df_mul_f(DF t, float z)
     return df_two_sum(p, fmaf(z, t.lo, e));
 }
 
-// k * t / d for small integers k, d (exact floats): the product is formed
-// error-free, the quotient with its FMA remainder.
-__device__ __forceinline__ DF df_scale_ratio(DF t, float k, float d)
+// k * t / d for small integers k, d (exact floats), inv_d ~ 1/d: the product
+// is formed error-free; the quotient estimate q carries its exact FMA
+// remainder, so the result is accurate whatever the rounding of q.
+__device__ __forceinline__ DF df_scale_ratio(DF t, float k, float d, float inv_d)
 {
     float p = t.hi * k;
     float e = fmaf(t.hi, k, -p);
     DF num = df_two_sum(p, fmaf(t.lo, k, e));
-    float q = num.hi / d;
+    float q = num.hi * inv_d;
     float r = fmaf(-q, d, num.hi);
-    return df_two_sum(q, (r + num.lo) / d);
+    return df_two_sum(q, (r + num.lo) * inv_d);
 }
 
 // ------------------------------------------------------------------------
@@ -81,34 +88,37 @@ __device__ __forceinline__ float2 cmul_i(float2 a, int dir)
 }
 
 // ------------------------------------------------------------------------
-// Batched complex FFT of length n over `nsig` signals held in shared memory
-// as buf[k * nsig + s] (signal s, element k), Stockham self-sorting, mixed
+// Batched complex FFT of length n over NSIG signals held in shared memory
+// as buf[k * NSIG + s] (signal s, element k), Stockham self-sorting, mixed
 // radix 2/3/4/5.  dir = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};
-// dir = +1: the unnormalised inverse.  tw[m] = e^{-2 pi i m / n}.
-// Each stage reads one buffer and writes the other; returns the buffer that
-// holds the result.  Must be called by every thread of the block; ends with
-// a __syncthreads().
+// dir = +1: the unnormalised inverse.  tw[m] = e^{-2 pi i m / n} (shared
+// memory).  Each stage reads one buffer and writes the other; returns the
+// buffer that holds the result.  Must be called by every thread of the block;
+// ends with a __syncthreads().
+template <int NSIG>
 __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan &plan,
-                                            int nsig, const float2 *__restrict__ tw, int dir)
+                                            const float2 *tw, int dir)
 {
     const int n = plan.n;
-    int Ns = 1;
     for (int st = 0; st < plan.nst; ++st) {
         const int r = plan.radix[st];
+        const int Ns = plan.ns[st];
+        const unsigned rcp = plan.ns_rcp[st];
         const int nr = n / r;
-        const int tstep = n / (Ns * r);  // twiddle index step for w^{i*k}
-        const int total = nr * nsig;
+        const int tstep = plan.tstep[st];
+        const int total = nr * NSIG;
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int s = t % nsig;
-            const int j = t / nsig;
-            const int k = j % Ns;
+            const int s = t % NSIG;
+            const int j = t / NSIG;
+            const int jq = Ns == 1 ? j : (int)__umulhi((unsigned)j, rcp);  // j / Ns
+            const int k = j - jq * Ns;
             float2 v[5];
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
                 if (i < r) {
-                    float2 x = a[(j + i * nr) * nsig + s];
+                    float2 x = a[(j + i * nr) * NSIG + s];
                     if (i > 0 && k > 0) {
-                        float2 w = tw[(i * k * tstep) % n];
+                        float2 w = tw[i * k * tstep];  // i k < r Ns, so the index is < n
                         if (dir > 0) w.y = -w.y;
                         x = cmul(x, w);
                     }
@@ -155,16 +165,15 @@ __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan 
                 V[2] = cadd(r2, i2);
                 V[3] = csub(r2, i2);
             }
-            const int base = (j / Ns) * Ns * r + k;
+            const int base = jq * Ns * r + k;
 #pragma unroll
             for (int i = 0; i < 5; ++i)
-                if (i < r) b[(base + i * Ns) * nsig + s] = V[i];
+                if (i < r) b[(base + i * Ns) * NSIG + s] = V[i];
         }
         __syncthreads();
         float2 *tmp = a;
         a = b;
         b = tmp;
-        Ns *= r;
     }
     return a;
 }

@@ -29,10 +29,12 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
     const int nw = blockDim.x >> 5;
     const int imgi = blockIdx.y;
     const int k = blockIdx.x * nw + warp;
-    const int stride = 3 * (B + 1);
-    float *U = sm + warp * stride;   // [B]
-    float *Fh = U + (B + 1);         // [B+1]
-    float *Fl = Fh + (B + 1);        // [B+1]
+    // per warp: U (B+1 floats, padded to even) then F (B+1 float2): every
+    // region and every F starts 8-byte aligned
+    const int ue = (B + 1) + ((B + 1) & 1);
+    const int stride = ue + 2 * (B + 1);
+    float *U = sm + warp * stride;                          // [B]
+    float2 *F = reinterpret_cast<float2 *>(U + ue);         // [B+1] (hi, lo)
     if (k >= n) return;              // whole warp leaves; no block barrier below
     const int nh = n / 2;
     const float *row;
@@ -65,41 +67,43 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
     run.lo = __shfl_up_sync(0xffffffffu, inc.lo, 1);
     if (lane == 0) {
         run = {0.f, 0.f};
-        Fh[0] = 0.f;
-        Fl[0] = 0.f;
+        F[0] = make_float2(0.f, 0.f);
     }
     for (int b = c0; b < c1; ++b) {
         run = df_add(run, DF{U[b], 0.f});
-        Fh[b + 1] = run.hi;
-        Fl[b + 1] = run.lo;
+        F[b + 1] = make_float2(run.hi, run.lo);
     }
     __syncwarp();
-    const DF total = {Fh[B], Fl[B]};
+    const DF total = {F[B].x, F[B].y};
     float *qo = q + ((size_t)imgi * n + k) * M;
     if (!(total.hi > 0.f) || !isfinite(total.hi)) {
         for (int p = lane; p < M; p += 32) qo[p] = __int_as_float(0x7fc00000);
         if (lane == 0) atomicOr(status + imgi, 1);
         return;
     }
+    const float dz = level_rule == 0 ? 2.f * M : (float)M;
+    const float inv_dz = 1.f / dz;
     for (int p = lane; p < M; p += 32) {
         // tau = z_p F_B with z_p = (2p+1)/(2M) or p/M, formed exactly
         const float kz = level_rule == 0 ? 2.f * p + 1.f : (float)p;
-        const float dz = level_rule == 0 ? 2.f * M : (float)M;
         float Q;
         if (kz == 0.f) {
             Q = -0.5f * (float)B * h;  // inf{t : F(t) >= 0}: the domain's left end e_0
         } else {
-            const DF tau = df_scale_ratio(total, kz, dz);
+            const DF tau = df_scale_ratio(total, kz, dz, inv_dz);
             int lo = 1, hi = B;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (df_ge(DF{Fh[mid], Fl[mid]}, tau)) hi = mid;
+                const float2 f = F[mid];
+                if (df_ge(DF{f.x, f.y}, tau)) hi = mid;
                 else lo = mid + 1;
             }
             const int j = lo;
-            const float num = (tau.hi - Fh[j - 1]) + (tau.lo - Fl[j - 1]);
+            const float2 fj = F[j - 1];
+            const float num = (tau.hi - fj.x) + (tau.lo - fj.y);
             const float den = U[j - 1];
-            float frac = den > 0.f ? num / den : 0.f;
+            // the fraction only scales h: a fast divide (error ~2 ulp) is ample
+            float frac = den > 0.f ? __fdividef(num, den) : 0.f;
             frac = fminf(fmaxf(frac, 0.f), 1.f);
             const float ej = ((float)(j - 1) - 0.5f * (float)B) * h;
             Q = fmaf(h, frac, ej);
@@ -177,7 +181,8 @@ cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, flo
 {
     if (nb <= 0) return cudaSuccess;
     const int nw = kQThreads / 32;
-    const size_t smem = sizeof(float) * (size_t)nw * 3 * (B + 1);
+    const int ue = (B + 1) + ((B + 1) & 1);
+    const size_t smem = sizeof(float) * (size_t)nw * (ue + 2 * (B + 1));
     cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid((n + nw - 1) / nw, nb);
     k_quantiles<<<grid, kQThreads, smem, st>>>(proj, n, B, M, h, level_rule, half, q, status);

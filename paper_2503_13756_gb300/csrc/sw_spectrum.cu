@@ -82,16 +82,18 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
     }
 }
 
-template <typename T>
+template <typename T, int nsig>
 __global__ void __launch_bounds__(kSpecThreads)
 k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2 *__restrict__ tw,
-           int nsig, SpecOut o, float *__restrict__ prof, double *__restrict__ center,
+           SpecOut o, float *__restrict__ prof, double *__restrict__ center,
            double *__restrict__ norm32, double *__restrict__ norm16)
 {
     extern __shared__ float2 smc[];
     float2 *b0 = smc;
     float2 *b1 = b0 + n * nsig;
     float2 *x1 = b1 + n * nsig;  // [M] Qhat(1, p) before centring
+    float2 *tws = x1 + M;        // [n] twiddles
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __shared__ double red[2][kSpecThreads / 32];
     __shared__ double s_c1[2];
     const int img = blockIdx.x;
@@ -110,7 +112,7 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
             b0[t] = make_float2(xr, xi);
         }
         __syncthreads();
-        const float2 *R = fft_smem(b0, b1, plan, nsig, tw, -1);
+        const float2 *R = fft_smem<nsig>(b0, b1, plan, tws, -1);
         // ---- unpack two real spectra per signal, k' = 0..n/2
         for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
             const int kf = t / nsig, s = t % nsig;
@@ -223,21 +225,24 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
 {
     if (nb <= 0) return cudaSuccess;
     const int nsig = n <= 512 ? 16 : 8;
-    const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M);
+    const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M + n);
     SpecOut o{spec32, fstride, lp_kind ? lp_q : nullptr, lpq_fstride, lp_t, lpt_fstride, Nq,
               tc_ldk(M)};
+#define SW_SPEC_LAUNCH(T, NS)                                                                    \
+    do {                                                                                        \
+        cudaFuncSetAttribute(k_spectrum<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             200 * 1024);                                                       \
+        k_spectrum<T, NS><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, o, prof, center,  \
+                                                          norm32, norm16);                      \
+    } while (0)
     if (lp_kind == 2) {
-        cudaFuncSetAttribute(k_spectrum<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        k_spectrum<__half><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, nsig, o, prof,
-                                                            center, norm32, norm16);
+        if (nsig == 16) SW_SPEC_LAUNCH(__half, 16);
+        else SW_SPEC_LAUNCH(__half, 8);
     } else {
-        cudaFuncSetAttribute(k_spectrum<__nv_bfloat16>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_spectrum<__nv_bfloat16><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, nsig, o,
-                                                                   prof, center, norm32,
-                                                                   norm16);
+        if (nsig == 16) SW_SPEC_LAUNCH(__nv_bfloat16, 16);
+        else SW_SPEC_LAUNCH(__nv_bfloat16, 8);
     }
+#undef SW_SPEC_LAUNCH
     return cudaGetLastError();
 }
 
