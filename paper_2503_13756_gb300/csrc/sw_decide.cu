@@ -27,23 +27,33 @@ template <int nsig>
 __global__ void __launch_bounds__(kDecThreads)
 k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
 {
+    constexpr int NP = 2 * nsig;                               // pairs per CTA
+    constexpr int NW = kDecThreads / 32;
     extern __shared__ float2 smd[];
     const int n = A.n, M = A.M, nh = n / 2;
     float2 *b0 = smd;
     float2 *b1 = b0 + n * nsig;
     float2 *tws = b1 + n * nsig;                              // [n] twiddles
     float *prof_i = reinterpret_cast<float *>(tws + n);       // [M]
-    float *delta = prof_i + M;                                // [2 nsig]
-    for (int t = threadIdx.x; t < n; t += blockDim.x) tws[t] = tw[t];
+    __shared__ float delta[NP];
+    __shared__ int stt[NP];
+    __shared__ float red_key[NW][NP];
+    __shared__ int red_l[NW][NP];
     const int i = blockIdx.x;
-    const int j0 = blockIdx.y * 2 * nsig;
+    const int j0 = blockIdx.y * NP;
     const int Nq = A.Nq, Nt = A.Nt;
 
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tws[t] = tw[t];
     for (int p = threadIdx.x; p < M; p += blockDim.x) prof_i[p] = A.prof_q[(size_t)i * M + p];
+    if (threadIdx.x < NP) {
+        const int j = j0 + threadIdx.x;
+        stt[threadIdx.x] = j < Nt ? A.st_t[j] : 1;
+    }
+    __syncthreads();
     // ---- Hermitian-extended spectra of two pairs per signal.  Each thread
     // reads C(k') of two adjacent templates with one 16-byte load and writes
-    // Z(k') and Z(n - k').  Templates that are unusable contribute zeros, so
-    // that their NaNs cannot reach the partner pair through the FFT.
+    // Z(k') and Z(n - k').  Unusable templates contribute zeros, so that their
+    // NaNs cannot reach the partner pair through the FFT.
     const float2 *Ci = A.C + (size_t)i * Nt;
     const size_t fs = (size_t)Nq * Nt;
     const bool vec = (Nt & 1) == 0;  // C rows of even length keep 16-byte alignment
@@ -62,92 +72,107 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 if (ja < Nt) Xa = Cm[ja];
                 if (jb < Nt) Xb = Cm[jb];
             }
-            if (ja >= Nt || A.st_t[ja]) Xa = make_float2(0.f, 0.f);
-            if (jb >= Nt || A.st_t[jb]) Xb = make_float2(0.f, 0.f);
+            if (stt[2 * s]) Xa = make_float2(0.f, 0.f);
+            if (stt[2 * s + 1]) Xb = make_float2(0.f, 0.f);
         }
         if (kf == 0) {
             b0[s] = make_float2(0.f, 0.f);
         } else if (kf == nh) {
             b0[kf * nsig + s] = make_float2(Xa.x, Xb.x);  // real parts
         } else {
-            b0[kf * nsig + s] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);             // Xa + i Xb
-            b0[(n - kf) * nsig + s] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);       // conj Xa + i conj Xb
+            b0[kf * nsig + s] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);        // Xa + i Xb
+            b0[(n - kf) * nsig + s] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);  // conj Xa + i conj Xb
         }
     }
     __syncthreads();
     const float2 *R = fft_smem<nsig>(b0, b1, plan, tws, +1);  // R[l][s] = n (corr_a + i corr_b)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = blockDim.x >> 5;
     // ---- k' = 0 part: n |m_i - m_j|^2
-    for (int pr = warp; pr < 2 * nsig; pr += nw) {
+    for (int pr = warp; pr < NP; pr += NW) {
         const int j = j0 + pr;
-        float s = 0.f;
+        float sacc = 0.f;
         if (j < Nt) {
             const float *pj = A.prof_t + (size_t)j * M;
             for (int p = lane; p < M; p += 32) {
                 const float d = prof_i[p] - pj[p];
-                s = fmaf(d, d, s);
+                sacc = fmaf(d, d, sacc);
             }
         }
 #pragma unroll
-        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) delta[pr] = s * (float)n;
+        for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+        if (lane == 0) delta[pr] = sacc * (float)n;
     }
-    __syncthreads();
 
+    // ---- argmin over l (FP32 keys, lowest l on ties).  Thread (s, lq) scans
+    // l = lq, lq + LQ, ... for both pairs of signal s: a warp then reads 32
+    // consecutive complex values (conflict-free).
     const double nM = (double)n * M;
     const double aix = A.ctr_q[2 * i], aiy = A.ctr_q[2 * i + 1];
     const float invn = 1.f / (float)n;
-    for (int pr = warp; pr < 2 * nsig; pr += nw) {
-        const int j = j0 + pr;
-        if (j >= Nt) continue;
-        const int s = pr >> 1, comp = pr & 1;
-        const double ajx = A.ctr_t[2 * j], ajy = A.ctr_t[2 * j + 1];
-        // argmin over l of key(l) (FP32), lowest l on ties
-        float best = __int_as_float(0x7f800000);
-        int bl = 0x7fffffff;
-        for (int l = lane; l < n; l += 32) {
-            const float2 z = R[l * nsig + s];
-            float key = -2.f * (comp ? z.y : z.x) * invn;
-            if (!A.translation) {
-                const double2 c = A.cs64[l];
-                const float sx = (float)(aix - (c.x * ajx - c.y * ajy));
-                const float sy = (float)(aiy - (c.y * ajx + c.x * ajy));
-                key = fmaf(0.5f * (float)nM, sx * sx + sy * sy, key);
-            }
-            if (key < best || (key == best && l < bl)) {
-                best = key;
-                bl = l;
-            }
+    constexpr int LQ = kDecThreads / nsig;
+    const int s = threadIdx.x % nsig, lq = threadIdx.x / nsig;
+    float best0 = __int_as_float(0x7f800000), best1 = best0;
+    int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
+    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;  // a_j of the two pairs (rotation only)
+    if (!A.translation) {
+        const int ja = min(j0 + 2 * s, Nt - 1), jb = min(j0 + 2 * s + 1, Nt - 1);
+        ax0 = (float)A.ctr_t[2 * ja];
+        ay0 = (float)A.ctr_t[2 * ja + 1];
+        ax1 = (float)A.ctr_t[2 * jb];
+        ay1 = (float)A.ctr_t[2 * jb + 1];
+    }
+    const float hnm = 0.5f * (float)nM;
+    for (int l = lq; l < n; l += LQ) {
+        const float2 z = R[l * nsig + s];
+        float k0 = -2.f * z.x * invn, k1 = -2.f * z.y * invn;
+        if (!A.translation) {
+            const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
+            const float c = w.x, sn = -w.y;
+            float sx = (float)aix - (c * ax0 - sn * ay0), sy = (float)aiy - (sn * ax0 + c * ay0);
+            k0 = fmaf(hnm, sx * sx + sy * sy, k0);
+            sx = (float)aix - (c * ax1 - sn * ay1);
+            sy = (float)aiy - (sn * ax1 + c * ay1);
+            k1 = fmaf(hnm, sx * sx + sy * sy, k1);
         }
+        if (k0 < best0) { best0 = k0; bl0 = l; }   // l increases: ties keep the lowest
+        if (k1 < best1) { best1 = k1; bl1 = l; }
+    }
+    // reduce over the lanes of this warp that share s (lane bits above log2 nsig)
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
-            if (ob < best || (ob == best && ol < bl)) {
-                best = ob;
-                bl = ol;
+    for (int off = nsig; off < 32; off <<= 1) {
+        const float o0 = __shfl_xor_sync(0xffffffffu, best0, off);
+        const int q0 = __shfl_xor_sync(0xffffffffu, bl0, off);
+        const float o1 = __shfl_xor_sync(0xffffffffu, best1, off);
+        const int q1 = __shfl_xor_sync(0xffffffffu, bl1, off);
+        if (o0 < best0 || (o0 == best0 && q0 < bl0)) { best0 = o0; bl0 = q0; }
+        if (o1 < best1 || (o1 == best1 && q1 < bl1)) { best1 = o1; bl1 = q1; }
+    }
+    if (lane < nsig) {
+        red_key[warp][2 * s] = best0;
+        red_l[warp][2 * s] = bl0;
+        red_key[warp][2 * s + 1] = best1;
+        red_l[warp][2 * s + 1] = bl1;
+    }
+    __syncthreads();
+
+    // ---- one thread per pair: combine warps, FP64 distance at l*
+    if (threadIdx.x < NP) {
+        const int pr = threadIdx.x;
+        const int j = j0 + pr;
+        if (j < Nt) {
+            float bk = red_key[0][pr];
+            int bl = red_l[0][pr];
+            for (int w = 1; w < NW; ++w) {
+                const float k = red_key[w][pr];
+                const int l = red_l[w][pr];
+                if (k < bk || (k == bk && l < bl)) { bk = k; bl = l; }
             }
-        }
-        if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
-        const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
-        const int st = A.st_q[i] ? 1 : (A.st_t[j] ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
-        // FP64 distance at l (and shift)
-        auto dist = [&](int l, double &sx, double &sy) {
-            const float2 z = R[l * nsig + s];
-            const double corr = (double)(comp ? z.y : z.x) / n;
-            const double2 c = A.cs64[l];
-            sx = aix - (c.x * ajx - c.y * ajy);
-            sy = aiy - (c.y * ajx + c.x * ajy);
-            double d = (base - 2.0 * corr) / nM;
-            if (!A.translation) {
-                d += 0.5 * (sx * sx + sy * sy);
-                sx = sy = 0.0;
-            }
-            return d;
-        };
-        if (lane == 0) {
+            if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
+            const int sg = pr >> 1, comp = pr & 1;
+            const double ajx = A.ctr_t[2 * j], ajy = A.ctr_t[2 * j + 1];
+            const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
+            const int st = A.st_q[i] ? 1 : (stt[pr] ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
             sw_result r;
             if (st) {
                 const double nan = __longlong_as_double(0x7ff8000000000000ULL);
@@ -157,26 +182,46 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 r.shift[0] = r.shift[1] = nan;
                 r.d2 = nan;
             } else {
-                double sx, sy;
-                r.d2 = dist(bl, sx, sy);
+                const float2 z = R[bl * nsig + sg];
+                const double corr = (double)(comp ? z.y : z.x) / n;
+                const double2 c = A.cs64[bl];
+                double sx = aix - (c.x * ajx - c.y * ajy);
+                double sy = aiy - (c.y * ajx + c.x * ajy);
+                double d = (base - 2.0 * corr) / nM;
+                if (!A.translation) {
+                    d += 0.5 * (sx * sx + sy * sy);
+                    sx = sy = 0.0;
+                }
                 r.best_l = bl;
                 r.status = 0;
                 r.angle_rad = (float)(6.283185307179586 * bl / n);
                 r.shift[0] = sx;
                 r.shift[1] = sy;
+                r.d2 = d;
             }
             r.reserved = 0.f;
             reinterpret_cast<sw_result *>(A.out)[(size_t)i * Nt + j] = r;
         }
-        if (A.curve && i == 0 && j == 0) {
-            for (int l = lane; l < n; l += 32) {
-                double sx, sy;
-                const double d = dist(l, sx, sy);
-                A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
-                if (A.shifts) {
-                    A.shifts[2 * l] = sx;
-                    A.shifts[2 * l + 1] = sy;
-                }
+    }
+    // ---- full curve of pair (0, 0) (single-pair call)
+    if (A.curve && i == 0 && j0 == 0) {
+        const double ajx = A.ctr_t[0], ajy = A.ctr_t[1];
+        const double base = (double)delta[0] + A.norm_q[0] + A.norm_t[0];
+        const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
+        for (int l = threadIdx.x; l < n; l += blockDim.x) {
+            const double corr = (double)R[l * nsig].x / n;
+            const double2 c = A.cs64[l];
+            double sx = aix - (c.x * ajx - c.y * ajy);
+            double sy = aiy - (c.y * ajx + c.x * ajy);
+            double d = (base - 2.0 * corr) / nM;
+            if (!A.translation) {
+                d += 0.5 * (sx * sx + sy * sy);
+                sx = sy = 0.0;
+            }
+            A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
+            if (A.shifts) {
+                A.shifts[2 * l] = sx;
+                A.shifts[2 * l + 1] = sy;
             }
         }
     }
@@ -237,8 +282,7 @@ cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2
     // 8 signals (16 pairs) per CTA keeps the shared footprint small enough
     // for several CTAs per SM; 4 at n = 1024
     const int nsig = a.n <= 512 ? 8 : 4;
-    const size_t smem = sizeof(float2) * ((size_t)2 * a.n * nsig + a.n) +
-                        sizeof(float) * (a.M + 2 * nsig);
+    const size_t smem = sizeof(float2) * ((size_t)2 * a.n * nsig + a.n) + sizeof(float) * a.M;
     dim3 grid(a.Nq, (a.Nt + 2 * nsig - 1) / (2 * nsig));  // queries on x (no 65535 cap)
     if (nsig == 8) {
         cudaFuncSetAttribute(k_decide<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
