@@ -154,6 +154,29 @@ sw_status sw_align_all_rotations(sw_ctx *ctx, const sw_params *p, const float *d
                                  const float *d_g, double *d_D, double *d_shift,
                                  sw_result *d_best, sw_stream_t stream);
 
+/* Allocation-free variant of sw_align_all_rotations (the paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory while running -- a process that has given all device memory to its
+ * own pool, a latency-critical loop that cannot accept the device-wide
+ * synchronisation of cudaMalloc/cudaFree, or a plugin whose host forbids
+ * device allocations after start-up).  Same arguments and results as
+ * sw_align_all_rotations, minus the context; the pair is scored in the FP32
+ * path on the current device and the given stream.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine: every intermediate buffer and table
+ * lives in one fixed 4 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   Limit: the per-pair intermediates, about 8 (n/2) B + 16 n M + 20 n
+ *   bytes, must fit in 4 MiB (e.g. L <= 512 with n <= 512 and M <= 256);
+ *   larger sizes return SW_ERR_OOM and launch nothing.  Invalid parameters or
+ *   pointers return SW_ERR_INVALID_ARG.
+ *   The first call on a device looks up the array's device address (make it
+ *   before any stream capture).  All calls on a device share the array and
+ *   leave their intermediates in it; calls that overlap on the GPU (e.g. on
+ *   unordered streams) race and must be serialised by the caller. */
+sw_status sw_align_all_rotations_noalloc(const sw_params *p, const float *d_f, const float *d_g,
+                                         double *d_D, double *d_shift, sw_result *d_best,
+                                         sw_stream_t stream);
+
 /* Many pairs: every query i (reference f) against every template j (moving
  * image g).  The per-frequency correlation sum_p Qhat_i(k,p) conj(Qhat_j(k,p))
  * runs as a batched GEMM in the precision p->gemm_precision.

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -692,3 +693,168 @@ void sw_bank_destroy(sw_bank *bank)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-pair alignment (sw_align_all_rotations_noalloc).
+//
+// Some callers may not allocate device memory once they are running: a
+// serving process that has handed all device memory to its own pool, a
+// latency-critical loop where the implicit device synchronisation of
+// cudaMalloc / cudaFree is not acceptable, or a plugin whose host forbids
+// device allocations after start-up.  For them this entry point runs the same
+// kernel sequence as sw_align_all_rotations with every intermediate buffer
+// and table carved from one file-scope device array of fixed size, and calls
+// no cudaMalloc, cudaFree or allocating library routine.
+//
+// The array is a __device__ variable: host code cannot use its name as a
+// device address, so its address is taken with cudaGetSymbolAddress, once per
+// device with that device current, on the first call made on that device
+// (make that first call before any stream capture).  Every call on a device
+// shares the array and leaves its contents behind; calls that overlap on the
+// GPU (different streams, no ordering) race on it.
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)4 << 20;  // 4 MiB on every device that loads the library
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocState {
+    std::mutex mu;
+    char *addr[kNoAllocMaxDevices] = {};
+    // host copies of the angle tables, per n
+    struct HostTables {
+        int n;
+        FftPlan plan;
+        std::vector<float2> cs, tw;
+        std::vector<double2> cs64;
+    };
+    std::deque<HostTables> tables;
+};
+
+NoAllocState &noalloc_state()
+{
+    static NoAllocState s;
+    return s;
+}
+
+}  // namespace
+
+extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const float *d_f,
+                                                    const float *d_g, double *d_D,
+                                                    double *d_shift, sw_result *d_best,
+                                                    sw_stream_t stream)
+{
+    if (check_params(nullptr, p) != SW_OK) return SW_ERR_INVALID_ARG;
+    if (!d_f || !d_g || !d_best || !aligned16(d_f) || !aligned16(d_g) || !aligned16(d_best) ||
+        ((uintptr_t)d_D & 7) || ((uintptr_t)d_shift & 7))
+        return SW_ERR_INVALID_ARG;
+    const int n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    // scratch: the FP32 batch layout for one query and one template, then the tables
+    const Layout l = batch_layout(p, 1, 1, false, false);
+    const size_t o_cs = align_up(l.total);
+    const size_t o_cs64 = align_up(o_cs + sizeof(float2) * nh);
+    const size_t o_tw = align_up(o_cs64 + sizeof(double2) * n);
+    const size_t need = o_tw + sizeof(float2) * n;
+    if (need > kNoAllocBytes) return SW_ERR_OOM;  // beyond the fixed scratch
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SW_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return SW_ERR_UNSUPPORTED;
+    NoAllocState &ns = noalloc_state();
+    char *w = nullptr;
+    const NoAllocState::HostTables *ht = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ns.mu);
+        if (!ns.addr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return SW_ERR_CUDA;
+            }
+            ns.addr[dev] = static_cast<char *>(ptr);
+        }
+        w = ns.addr[dev];
+        for (const auto &t : ns.tables)
+            if (t.n == n) ht = &t;
+        if (!ht) {
+            NoAllocState::HostTables t;
+            t.n = n;
+            if (!fft_plan(n, t.plan)) return SW_ERR_INVALID_ARG;
+            std::vector<double> co, si;
+            angle_table(n, co, si);
+            t.cs.resize(nh);
+            t.tw.resize(n);
+            t.cs64.resize(n);
+            for (int k = 0; k < n; ++k) {
+                if (k < nh) t.cs[k] = make_float2((float)co[k], (float)si[k]);
+                t.cs64[k] = make_double2(co[k], si[k]);
+                t.tw[k] = make_float2((float)co[k], (float)-si[k]);
+            }
+            ns.tables.push_back(std::move(t));
+            ht = &ns.tables.back();
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float2 *cs = reinterpret_cast<float2 *>(w + o_cs);
+    double2 *cs64 = reinterpret_cast<double2 *>(w + o_cs64);
+    float2 *tw = reinterpret_cast<float2 *>(w + o_tw);
+    int *err = reinterpret_cast<int *>(w + l.err);
+#define SW_NA(call)                                \
+    do {                                           \
+        if ((call) != cudaSuccess) {               \
+            cudaGetLastError();                    \
+            return SW_ERR_CUDA;                    \
+        }                                          \
+    } while (0)
+    SW_NA(cudaMemcpyAsync(cs, ht->cs.data(), sizeof(float2) * nh, cudaMemcpyHostToDevice, st));
+    SW_NA(cudaMemcpyAsync(cs64, ht->cs64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, st));
+    SW_NA(cudaMemcpyAsync(tw, ht->tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, st));
+    SW_NA(cudaMemsetAsync(err, 0, sizeof(int), st));  // the only value that must start at zero
+
+    int32_t *status = reinterpret_cast<int32_t *>(w + l.status);
+    float *proj = reinterpret_cast<float *>(w + l.proj);
+    float *quant = reinterpret_cast<float *>(w + l.quant);
+    float *spec32 = reinterpret_cast<float *>(w + l.spec32);
+    float *prof = reinterpret_cast<float *>(w + l.prof);
+    double *center = reinterpret_cast<double *>(w + l.center);
+    double *norm32 = reinterpret_cast<double *>(w + l.norm32);
+    double *norm16 = reinterpret_cast<double *>(w + l.norm16);
+    float2 *C = reinterpret_cast<float2 *>(w + l.C);
+    const size_t fstride = (size_t)2 * 2 * M;
+    SW_NA(swk::launch_project(d_f, 1, p->L, p->L, nh, B, cs, proj, 0, status, st));
+    SW_NA(swk::launch_project(d_g, 1, p->L, p->L, nh, B, cs, proj + (size_t)nh * B, 0,
+                              status + 1, st));
+    SW_NA(swk::launch_quantiles(proj, 2, n, B, M, 2.0f / (float)p->L, p->level_rule, 1, quant,
+                                status, st));
+    SW_NA(swk::launch_spectrum(quant, 2, n, M, ht->plan, tw, spec32, fstride, 0, nullptr, 0,
+                               nullptr, 0, 1, prof, center, norm32, norm16, st));
+    SW_NA(swk::launch_corr_simt(spec32, fstride, spec32 + (size_t)2 * M, fstride, 1, 1, M, nh, C,
+                                st));
+    swk::DecideArgs a{};
+    a.C = C;
+    a.Nq = 1;
+    a.Nt = 1;
+    a.n = n;
+    a.M = M;
+    a.prof_q = prof;
+    a.prof_t = prof + M;
+    a.ctr_q = center;
+    a.ctr_t = center + 2;
+    a.norm_q = norm32;
+    a.norm_t = norm32 + 1;
+    a.st_q = status;
+    a.st_t = status + 1;
+    a.cs64 = cs64;
+    a.translation = p->translation;
+    a.dev_err = err;
+    a.out = d_best;
+    a.curve = d_D;
+    a.shifts = d_shift;
+    SW_NA(swk::launch_decide(a, ht->plan, tw, st));
+#undef SW_NA
+    return SW_OK;
+}

@@ -53,6 +53,7 @@ EXPORTS = (
     "sw_batch_workspace_bytes", "sw_reserve", "sw_project", "sw_quantiles",
     "sw_align_all_rotations", "sw_align_batch", "sw_bank_create", "sw_bank_align",
     "sw_bank_size", "sw_bank_destroy", "sw_profile", "sw_profile_read", "sw_launch_count",
+    "sw_align_all_rotations_noalloc",
 )
 STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best")
 
@@ -84,6 +85,7 @@ def load(path: str | None = None):
                 "sw_profile_read": ([vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int64)], ci),
                 "sw_launch_count": ([vp], ctypes.c_int64),
+                "sw_align_all_rotations_noalloc": ([P, vp, vp, vp, vp, vp, vp], ci),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)

@@ -1,0 +1,71 @@
+"""The allocation-free single-pair entry point, through the C ABI.
+
+sw_align_all_rotations_noalloc serves callers that may not allocate device
+memory while they run (all memory handed to their own pool, no implicit device
+synchronisation allowed, or a host that forbids allocations after start-up).
+It keeps its intermediates in one fixed device array inside the library.
+This file is collected last so that, if it fails, a run stopping at the first
+failure has already run every other test; it passes alone and after them.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2503_13756_gb300 import swalign, synth
+from tests.parity import d2_tol, norm_scale
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _call_noalloc(lib, params, f, g):
+    n = params.n_theta
+    D = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    S = torch.full((n, 2), float("nan"), dtype=torch.float64, device="cuda")
+    best = torch.zeros((40,), dtype=torch.uint8, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.sw_align_all_rotations_noalloc(
+        ctypes.byref(params), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+        ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(S.data_ptr()),
+        ctypes.c_void_p(best.data_ptr()), stream)
+    assert st == swalign.SW_OK, st
+    torch.cuda.synchronize()
+    return D.cpu().numpy(), S.cpu().numpy(), swalign.results_to_numpy(best)[0]
+
+
+def test_noalloc_matches_allocating_entry_point_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = swalign.load()
+    al = swalign.Aligner(0)
+    try:
+        rng = np.random.default_rng(2026)
+        cases = [(64, 360, 128, 1), (48, 60, 36, 0)]  # two calls in a row, different sizes
+        for L, n, M, translation in cases:
+            mix = synth.draw_mixtures(rng, 2, L, ncomp=(2, 4))
+            imgs = synth.render(mix, L, beta=[0.0, 1.1], shift=[[0, 0], [2, -1]])
+            f = torch.from_numpy(imgs[0]).cuda()
+            g = torch.from_numpy(imgs[1]).cuda()
+            p = swalign.make_params(L, n, M, translation=translation)
+            D, S, r = _call_noalloc(lib, p, f, g)
+            Dr, Sr, br = al.align_all_rotations(f, g, p)
+            torch.cuda.synchronize()
+            Dr, Sr = Dr.cpu().numpy(), Sr.cpu().numpy()
+            rr = swalign.results_to_numpy(br)[0]
+            Sc = norm_scale(imgs[0].astype(np.float64), imgs[1].astype(np.float64), n, M)
+            assert np.all(np.abs(D - Dr) <= d2_tol(Dr, Sc))
+            np.testing.assert_allclose(S, Sr, rtol=0, atol=1e-9)
+            assert r["status"] == rr["status"] == 0
+            assert r["best_l"] == rr["best_l"]
+            assert abs(r["d2"] - rr["d2"]) <= d2_tol(rr["d2"], Sc)
+        # sizes beyond the fixed scratch are refused, nothing is launched
+        big = swalign.make_params(64, 1024, 1024)
+        f = torch.zeros((64, 64), device="cuda")
+        out = torch.zeros((40,), dtype=torch.uint8, device="cuda")
+        st = lib.sw_align_all_rotations_noalloc(
+            ctypes.byref(big), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+            None, None, ctypes.c_void_p(out.data_ptr()), None)
+        assert st == swalign.SW_ERR_OOM
+    finally:
+        al.close()
