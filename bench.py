@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
     return ap.parse_args()
@@ -166,6 +168,36 @@ def cpu_baseline(data, sample_q=160, sample_t=160):
     return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"first {sample_q} queries x {sample_t} templates of the workload "
                       f"({pairs} pairs, {dt:.1f} s)"}
+
+
+def serving_block(args, device):
+    """Continuous-batching serving of Poisson requests against a 1000-template
+    bank at 256 x 256 (n = 360, M = 256): latency percentiles and throughput."""
+    from paper_2503_13756_gb300 import serving, swalign, synth
+    bank = synth.serving_bank(n_templates=1000, L=256)
+    pool = synth.serving_pool(bank, pool_size=256)
+    sched = synth.serving_schedule(args.serve_requests, rate_hz=200.0, max_images=512, Lb=256)
+    out = {"workload": "Poisson 200 req/s, 1-512 images per request (log-uniform), L=128 "
+                       "(upsampled) or 256, bank of 1000 templates at 256x256, n=360, M=256, "
+                       "best template per query",
+           "requests": args.serve_requests}
+    for prec in ("bf16", "fp32"):
+        p = swalign.make_params(256, 360, 256, precision=prec)
+        eng = serving.ServingEngine(bank["templates"], p, n_slots=3, max_batch_images=512,
+                                    device=device)
+        try:
+            warm = serving.make_requests(pool, synth.serving_schedule(8, 1000.0, 64, Lb=256))
+            eng.run(warm, realtime=False)
+            eng.batches, eng.batch_sizes = 0, []
+            reqs = serving.make_requests(pool, sched)
+            st = eng.run(reqs, realtime=True)
+            hits = float(np.mean(np.concatenate(
+                [r.results["reserved"].astype(int) == r.source for r in reqs])))
+            st["source_template_found"] = hits
+            out[prec] = st
+        finally:
+            eng.close()
+    return out
 
 
 def run_reference(args, world, rank):
@@ -339,6 +371,7 @@ def main():
         roof = {"kernel": dom, "bound": "unknown", "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(data)
+    serve = None if (args.no_serving or world > 1) else serving_block(args, local)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -353,7 +386,7 @@ def main():
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},
         "roofline": roof, "peaks": peak_src, "stages": per_stage, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-        "variants": variants,
+        "variants": variants, "serving": serve,
     }
     print(json.dumps(line), flush=True)
 

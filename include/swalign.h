@@ -200,6 +200,9 @@ sw_status sw_bank_create(sw_ctx *ctx, const sw_params *p, const float *d_t_img, 
 sw_status sw_bank_align(sw_ctx *ctx, const sw_bank *bank, const float *d_q_img, int Nq,
                         int q_L, int mode, sw_result *d_out, sw_stream_t stream);
 int sw_bank_size(const sw_bank *bank);
+/* Context workspace bytes that sw_bank_align needs for Nq queries (the
+ * basis of memory-based admission in a serving loop). */
+size_t sw_bank_workspace_bytes(const sw_bank *bank, int Nq, int mode);
 void sw_bank_destroy(sw_bank *bank);
 
 #ifdef __cplusplus

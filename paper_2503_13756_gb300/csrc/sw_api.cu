@@ -128,6 +128,37 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, bool lp, bool scratch)
     return l;
 }
 
+// Workspace of sw_bank_align: query-side buffers only, the correlation of
+// Nq queries against Nt bank templates.
+Layout bank_layout(const sw_params *p, int Nq, int Nt, bool scratch)
+{
+    const size_t n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    const bool lp = p->gemm_precision != SW_PREC_FP32;
+    const size_t ldk = swk::tc_ldk((int)M);
+    Layout l{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at_ = o;
+        o = align_up(o + bytes);
+        return at_;
+    };
+    l.status = take(4 * (size_t)Nq);
+    l.proj = take(4 * (size_t)Nq * nh * B);
+    l.quant = take(4 * (size_t)Nq * n * M);
+    l.spec32 = take(4 * nh * (size_t)Nq * 2 * M);
+    l.lp_q = take(lp ? 2 * nh * (size_t)Nq * ldk : 0);
+    l.lp_t = take(0);
+    l.prof = take(4 * (size_t)Nq * M);
+    l.center = take(16 * (size_t)Nq);
+    l.norm32 = take(8 * (size_t)Nq);
+    l.norm16 = take(8 * (size_t)Nq);
+    l.C = take(8 * nh * (size_t)Nq * Nt);
+    l.scratch = take(scratch ? sizeof(sw_result) * (size_t)Nq * Nt : 0);
+    l.err = take(sizeof(int));
+    l.total = o;
+    return l;
+}
+
 }  // namespace
 
 struct ProfRec {
@@ -658,27 +689,177 @@ sw_status sw_align_batch(sw_ctx *c, const sw_params *p, const float *d_q_img, in
 sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, int Nt,
                          sw_bank **out, sw_stream_t stream)
 {
-    (void)d_t_img;
-    (void)Nt;
-    (void)stream;
-    if (out) *out = nullptr;
     if (!c) return SW_ERR_INVALID_ARG;
-    return fail(c, SW_ERR_UNSUPPORTED, "template banks are not available in this build");
-    (void)p;
+    c->err.clear();
+    if (!out) return fail(c, SW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if (Nt <= 0) return fail(c, SW_ERR_INVALID_ARG, "Nt=%d", Nt);
+    if ((s = check_ptr(c, d_t_img, "d_t_img", true))) return s;
+    if ((s = set_device(c))) return s;
+    const Tables *t;
+    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    const bool lp = p->gemm_precision != SW_PREC_FP32;
+    const int ldk = swk::tc_ldk(M);
+    // bank memory (owned by the bank)
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at_ = o;
+        o = align_up(o + bytes);
+        return at_;
+    };
+    const size_t o_spec = take(4 * (size_t)nh * Nt * 2 * M);
+    const size_t o_lp = take(lp ? 2 * (size_t)nh * 2 * Nt * ldk : 0);
+    const size_t o_prof = take(4 * (size_t)Nt * M);
+    const size_t o_ctr = take(16 * (size_t)Nt);
+    const size_t o_n32 = take(8 * (size_t)Nt);
+    const size_t o_n16 = take(8 * (size_t)Nt);
+    const size_t o_st = take(4 * (size_t)Nt);
+    sw_bank *b = new (std::nothrow) sw_bank;
+    if (!b) return fail(c, SW_ERR_OOM, "bank descriptor");
+    b->p = *p;
+    b->Nt = Nt;
+    b->device = c->device;
+    if (cudaMalloc(&b->mem, o) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(c, SW_ERR_OOM, "bank of %zu bytes does not fit", o);
+    }
+    b->spec32 = at<float>(b->mem, o_spec);
+    b->lp_t = lp ? (void *)(b->mem + o_lp) : nullptr;
+    b->prof = at<float>(b->mem, o_prof);
+    b->center = at<double>(b->mem, o_ctr);
+    b->norm32 = at<double>(b->mem, o_n32);
+    b->norm16 = at<double>(b->mem, o_n16);
+    b->status = at<int32_t>(b->mem, o_st);
+    // projections and quantiles pass through the context workspace
+    const size_t need = align_up(4 * (size_t)Nt * nh * B) + align_up(4 * (size_t)Nt * n * M);
+    if ((s = ensure_ws(c, need))) {
+        cudaFree(b->mem);
+        delete b;
+        return s;
+    }
+    ImageOut io{};
+    io.status = b->status;
+    io.proj = at<float>(c->ws, 0);
+    io.quant = at<float>(c->ws, align_up(4 * (size_t)Nt * nh * B));
+    io.spec32 = b->spec32;
+    io.fstride = (size_t)Nt * 2 * M;
+    io.lp_kind = lp ? p->gemm_precision : 0;
+    io.lp_q = nullptr;
+    io.lpq_fstride = 0;
+    io.lp_t = b->lp_t;
+    io.lpt_fstride = (size_t)2 * Nt * ldk;
+    io.Nq = 0;  // every image is a template (doubled low-precision rows)
+    io.prof = b->prof;
+    io.center = b->center;
+    io.norm32 = b->norm32;
+    io.norm16 = b->norm16;
+    if ((s = run_images(c, p, t, d_t_img, p->L, Nt, 0, io, st)) ||
+        (s = run_after_projection(c, p, t, Nt, io, st))) {
+        cudaStreamSynchronize(st);
+        cudaFree(b->mem);
+        delete b;
+        return s;
+    }
+    *out = b;
+    return SW_OK;
+}
+
+size_t sw_bank_workspace_bytes(const sw_bank *bank, int Nq, int mode)
+{
+    if (!bank || Nq < 0) return 0;
+    return bank_layout(&bank->p, Nq, bank->Nt, mode == 1).total;
 }
 
 sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, int Nq, int q_L,
                         int mode, sw_result *d_out, sw_stream_t stream)
 {
-    (void)bank;
-    (void)d_q_img;
-    (void)Nq;
-    (void)q_L;
-    (void)mode;
-    (void)d_out;
-    (void)stream;
     if (!c) return SW_ERR_INVALID_ARG;
-    return fail(c, SW_ERR_UNSUPPORTED, "template banks are not available in this build");
+    c->err.clear();
+    if (!bank) return fail(c, SW_ERR_INVALID_ARG, "bank is NULL");
+    const sw_params *p = &bank->p;
+    if (Nq < 0) return fail(c, SW_ERR_INVALID_ARG, "Nq=%d", Nq);
+    if (mode != 0 && mode != 1) return fail(c, SW_ERR_INVALID_ARG, "mode=%d", mode);
+    if (q_L != p->L && !(2 * q_L == p->L))
+        return fail(c, SW_ERR_INVALID_ARG, "q_L=%d must be L=%d or L/2", q_L, p->L);
+    if (Nq == 0) return SW_OK;
+    sw_status s;
+    if ((s = check_ptr(c, d_q_img, "d_q_img", true)) || (s = check_ptr(c, d_out, "d_out", true)))
+        return s;
+    if (bank->device != c->device)
+        return fail(c, SW_ERR_INVALID_ARG, "bank lives on device %d, context on %d", bank->device,
+                    c->device);
+    if ((s = set_device(c))) return s;
+    const Tables *t;
+    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p->n_theta, nh = n / 2, M = p->n_levels, Nt = bank->Nt;
+    const bool lp = p->gemm_precision != SW_PREC_FP32;
+    const Layout l = bank_layout(p, Nq, Nt, mode == 1);
+    if ((s = ensure_ws(c, l.total))) return s;
+    char *w = c->ws;
+    const int ldk = swk::tc_ldk(M);
+    ImageOut o{};
+    o.status = at<int32_t>(w, l.status);
+    o.proj = at<float>(w, l.proj);
+    o.quant = at<float>(w, l.quant);
+    o.spec32 = at<float>(w, l.spec32);
+    o.fstride = (size_t)Nq * 2 * M;
+    o.lp_kind = lp ? p->gemm_precision : 0;
+    o.lp_q = lp ? (void *)(w + l.lp_q) : nullptr;
+    o.lpq_fstride = (size_t)Nq * ldk;
+    o.lp_t = nullptr;
+    o.lpt_fstride = 0;
+    o.Nq = Nq;  // every image is a query
+    o.prof = at<float>(w, l.prof);
+    o.center = at<double>(w, l.center);
+    o.norm32 = at<double>(w, l.norm32);
+    o.norm16 = at<double>(w, l.norm16);
+    if ((s = run_images(c, p, t, d_q_img, q_L, Nq, 0, o, st))) return s;
+    if ((s = run_after_projection(c, p, t, Nq, o, st))) return s;
+    float2 *C = at<float2>(w, l.C);
+    int *err = at<int>(w, l.err);
+    SW_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (lp) {
+        SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
+                    return swk::launch_corr_tc(o.lp_q, bank->lp_t, Nq, Nt, M, nh,
+                                               p->gemm_precision, C, err, c->num_sms, st);
+                }));
+    } else {
+        SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
+                    return swk::launch_corr_simt(o.spec32, o.fstride, bank->spec32,
+                                                 (size_t)Nt * 2 * M, Nq, Nt, M, nh, C, st);
+                }));
+    }
+    swk::DecideArgs a{};
+    a.C = C;
+    a.Nq = Nq;
+    a.Nt = Nt;
+    a.n = n;
+    a.M = M;
+    a.prof_q = o.prof;
+    a.prof_t = bank->prof;
+    a.ctr_q = o.center;
+    a.ctr_t = bank->center;
+    a.norm_q = lp ? o.norm16 : o.norm32;
+    a.norm_t = lp ? bank->norm16 : bank->norm32;
+    a.st_q = o.status;
+    a.st_t = bank->status;
+    a.cs64 = t->cs64;
+    a.translation = p->translation;
+    a.dev_err = err;
+    a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)d_out;
+    SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st,
+                      [&] { return swk::launch_decide(a, t->plan, t->tw, st); }));
+    if (mode == 1)
+        SW_CUDA(c, launch(c, SW_STAGE_BEST, st, [&] {
+                    return swk::launch_best_template(w + l.scratch, Nq, Nt, d_out, st);
+                }));
+    return SW_OK;
 }
 
 int sw_bank_size(const sw_bank *bank) { return bank ? bank->Nt : 0; }

@@ -53,7 +53,7 @@ EXPORTS = (
     "sw_batch_workspace_bytes", "sw_reserve", "sw_project", "sw_quantiles",
     "sw_align_all_rotations", "sw_align_batch", "sw_bank_create", "sw_bank_align",
     "sw_bank_size", "sw_bank_destroy", "sw_profile", "sw_profile_read", "sw_launch_count",
-    "sw_align_all_rotations_noalloc",
+    "sw_align_all_rotations_noalloc", "sw_bank_workspace_bytes",
 )
 STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best")
 
@@ -86,6 +86,7 @@ def load(path: str | None = None):
                                      ctypes.POINTER(ctypes.c_int64)], ci),
                 "sw_launch_count": ([vp], ctypes.c_int64),
                 "sw_align_all_rotations_noalloc": ([P, vp, vp, vp, vp, vp, vp], ci),
+                "sw_bank_workspace_bytes": ([vp, ci, ci], ctypes.c_size_t),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -211,6 +212,47 @@ class Aligner:
         self.call("sw_align_batch", ctypes.byref(params), _ptr(q), Nq, _ptr(t), Nt, int(mode),
                   _ptr(out), _stream(stream))
         return out
+
+
+class Bank:
+    """Device-resident angle spectra of a template set (sw_bank_create)."""
+
+    def __init__(self, aligner: "Aligner", templates, params: Params, stream=None):
+        self.al = aligner
+        self.params = params
+        t = _f32(templates, aligner.torch_device)
+        self.Nt = t.shape[0]
+        h = ctypes.c_void_p()
+        aligner.call("sw_bank_create", ctypes.byref(params), _ptr(t), self.Nt, ctypes.byref(h),
+                     _stream(stream))
+        self.handle = h
+
+    def workspace_bytes(self, Nq: int, mode: int = 0) -> int:
+        return int(self.al.lib.sw_bank_workspace_bytes(self.handle, int(Nq), int(mode)))
+
+    def align(self, queries, q_L=None, mode=0, out=None, stream=None, aligner=None):
+        import torch
+        al = aligner or self.al
+        q = _f32(queries, al.torch_device)
+        Nq = q.shape[0]
+        q_L = q.shape[-1] if q_L is None else q_L
+        rows = Nq * self.Nt if mode == 0 else Nq
+        if out is None:
+            out = torch.empty((rows, 40), dtype=torch.uint8, device=q.device)
+        al.call("sw_bank_align", self.handle, _ptr(q), Nq, int(q_L), int(mode), _ptr(out),
+                _stream(stream))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.al.lib.sw_bank_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def results_to_numpy(buf) -> np.ndarray:

@@ -223,40 +223,39 @@ def serving_bank(n_templates=1000, L=256, seed=SEED_BASE + 4, dtype=np.float32):
     return {"templates": render(p, L, dtype=dtype), "params": p, "rng": rng}
 
 
-def serving_requests(bank, n_requests, rate_hz=200.0, max_images=512, seed=None,
-                     dtype=np.float32):
-    """Poisson arrivals at ``rate_hz``; each request holds a log-uniform count
-    in [1, max_images] of perturbed bank templates at L = 256 or L = 128 (the
-    latter rendered at half resolution), with equal odds."""
-    rng = _rng(SEED_BASE + 5 if seed is None else seed)
+def serving_pool(bank, pool_size=256, seed=SEED_BASE + 5, max_shift_px=8, warp_amp_px=3.0):
+    """Perturbed copies of bank templates (random rotation, shift, warp) at
+    the bank's side L and at L/2 (rendered at L and block-averaged 2 x 2),
+    from which serving requests draw their images."""
+    rng = _rng(seed)
     p = bank["params"]
     Lb = bank["templates"].shape[-1]
     nt = bank["templates"].shape[0]
+    out = {}
+    for L in (Lb, Lb // 2):
+        src = rng.integers(0, nt, size=pool_size)
+        beta = rng.uniform(0, 2 * np.pi, size=pool_size)
+        shift = rng.integers(-max_shift_px, max_shift_px + 1, size=(pool_size, 2)).astype(float)
+        warp = _smooth_field(rng, pool_size, Lb, 6.0 * Lb / 64, warp_amp_px)
+        fine = render(p, Lb, idx=src, beta=beta, shift=shift, warp=warp, dtype=np.float32)
+        if L != Lb:
+            k = Lb // L
+            fine = fine.reshape(pool_size, L, k, L, k).sum(axis=(2, 4), dtype=np.float64)
+            fine = fine.astype(np.float32)
+        out[L] = {"images": fine, "source": src, "beta": beta}
+    return out
+
+
+def serving_schedule(n_requests, rate_hz=200.0, max_images=512, Lb=256, seed=SEED_BASE + 6):
+    """Poisson arrivals at rate_hz; per request a count log-uniform on
+    [1, max_images] and L = Lb or Lb/2 with equal odds."""
+    rng = _rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_requests))
-    reqs = []
-    for r in range(n_requests):
-        count = int(np.clip(np.round(np.exp(rng.uniform(0, np.log(max_images)))), 1,
-                            max_images))
-        L = Lb if rng.random() < 0.5 else Lb // 2
-        src = rng.integers(0, nt, size=count)
-        beta = rng.uniform(0, 2 * np.pi, size=count)
-        scale = L / Lb
-        shift = rng.integers(-8, 9, size=(count, 2)) * scale
-        # the mixture lives in bank pixels; render on a grid of L cells
-        q = _render_scaled(p, Lb, L, src, beta, shift / scale, dtype)
-        reqs.append({"t_arrive": float(t[r]), "L": L, "images": q, "source": src,
-                     "beta": beta})
-    return reqs
-
-
-def _render_scaled(params, Lb, L, idx, beta, shift_bank_px, dtype):
-    """Render bank mixtures (defined in Lb-pixel units) on an L-cell grid."""
-    if L == Lb:
-        return render(params, Lb, idx=idx, beta=beta, shift=shift_bank_px, dtype=dtype)
-    fine = render(params, Lb, idx=idx, beta=beta, shift=shift_bank_px, dtype=np.float64)
-    k = Lb // L
-    coarse = fine.reshape(len(idx), L, k, L, k).sum(axis=(2, 4))
-    return coarse.astype(dtype)
+    counts = np.clip(np.round(np.exp(rng.uniform(0, np.log(max_images), n_requests))), 1,
+                     max_images).astype(int)
+    Ls = np.where(rng.random(n_requests) < 0.5, Lb, Lb // 2)
+    picks = [rng.integers(0, 1 << 30, size=c) for c in counts]
+    return t, counts, Ls, picks
 
 
 def random_dense(L, count=2, seed=SEED_BASE + 9, dtype=np.float32):
