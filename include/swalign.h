@@ -22,7 +22,7 @@
  *    (or p/M with level_rule = 1).
  *  - Every pointer named d_* is DEVICE memory owned by the caller; the
  *    library never frees it.  Image, projection and quantile pointers must be
- *    16-byte aligned.  The library owns only its workspace, held in the
+ *    16-byte aligned, sw_result pointers 8-byte aligned.  The library owns only its workspace, held in the
  *    context (grown on demand by cudaMalloc, or sized up front by
  *    sw_reserve).
  *  - Every call is asynchronous on the given stream (NULL = legacy default

@@ -272,6 +272,14 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
 
 bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
+// sw_result holds doubles: an array of them (at any index) is 8-byte aligned.
+sw_status check_result_ptr(sw_ctx *c, const void *ptr, const char *name)
+{
+    if (!ptr) return fail(c, SW_ERR_INVALID_ARG, "%s is NULL", name);
+    if ((uintptr_t)ptr & 7u) return fail(c, SW_ERR_INVALID_ARG, "%s is not 8-byte aligned", name);
+    return SW_OK;
+}
+
 sw_status check_ptr(sw_ctx *c, const void *ptr, const char *name, bool need)
 {
     if (!ptr) return need ? fail(c, SW_ERR_INVALID_ARG, "%s is NULL", name) : SW_OK;
@@ -655,7 +663,7 @@ sw_status sw_align_all_rotations(sw_ctx *c, const sw_params *p, const float *d_f
     sw_status s = check_params(c, p);
     if (s) return s;
     if ((s = check_ptr(c, d_f, "d_f", true)) || (s = check_ptr(c, d_g, "d_g", true)) ||
-        (s = check_ptr(c, d_best, "d_best", true)))
+        (s = check_result_ptr(c, d_best, "d_best")))
         return s;
     if (d_D && ((uintptr_t)d_D & 7)) return fail(c, SW_ERR_INVALID_ARG, "d_D misaligned");
     if (d_shift && ((uintptr_t)d_shift & 7))
@@ -677,7 +685,7 @@ sw_status sw_align_batch(sw_ctx *c, const sw_params *p, const float *d_q_img, in
     if (mode != 0 && mode != 1) return fail(c, SW_ERR_INVALID_ARG, "mode=%d", mode);
     if (Nq == 0) return SW_OK;
     if (Nt == 0 && mode == 0) return SW_OK;
-    if ((s = check_ptr(c, d_q_img, "d_q_img", true)) || (s = check_ptr(c, d_out, "d_out", true)))
+    if ((s = check_ptr(c, d_q_img, "d_q_img", true)) || (s = check_result_ptr(c, d_out, "d_out")))
         return s;
     if (Nt > 0 && (s = check_ptr(c, d_t_img, "d_t_img", true))) return s;
     if ((s = set_device(c))) return s;
@@ -788,7 +796,7 @@ sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, in
         return fail(c, SW_ERR_INVALID_ARG, "q_L=%d must be L=%d or L/2", q_L, p->L);
     if (Nq == 0) return SW_OK;
     sw_status s;
-    if ((s = check_ptr(c, d_q_img, "d_q_img", true)) || (s = check_ptr(c, d_out, "d_out", true)))
+    if ((s = check_ptr(c, d_q_img, "d_q_img", true)) || (s = check_result_ptr(c, d_out, "d_out")))
         return s;
     if (bank->device != c->device)
         return fail(c, SW_ERR_INVALID_ARG, "bank lives on device %d, context on %d", bank->device,

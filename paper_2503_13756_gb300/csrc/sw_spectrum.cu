@@ -49,6 +49,7 @@ struct SpecOut {
     size_t lpt_fstride;
     int Nq;
     int ldk;  // low-precision row length (>= 2M, zero padded)
+    int lp;   // write low-precision copies (queries to lp_q, templates to lp_t)
 };
 
 // Writes Qhat(kf, p) (kf >= 1) for image img; returns |.|^2 weight-summed
@@ -61,7 +62,7 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
     row[p] = X.x;
     row[M + p] = X.y;
     acc32 += w * ((double)X.x * X.x + (double)X.y * X.y);
-    if (o.lp_q) {
+    if (o.lp) {
         const T re = to_lp<T>(X.x), im = to_lp<T>(X.y);
         const float rf = from_lp<T>(re), imf = from_lp<T>(im);
         acc16 += w * ((double)rf * rf + (double)imf * imf);
@@ -178,7 +179,7 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
         emit<T>(o, img, M, 1, p, X, 2.0, acc32, acc16);  // n >= 4: k' = 1 < n/2
     }
     // ---- zero padding of the low-precision rows, [2M, ldk)
-    if (o.lp_q && o.ldk > 2 * M) {
+    if (o.lp && o.ldk > 2 * M) {
         const int pad = o.ldk - 2 * M;
         const bool tmpl = img >= o.Nq;
         const int rows = tmpl ? 2 : 1;
@@ -226,8 +227,8 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
     if (nb <= 0) return cudaSuccess;
     const int nsig = n <= 512 ? 16 : 8;
     const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M + n);
-    SpecOut o{spec32, fstride, lp_kind ? lp_q : nullptr, lpq_fstride, lp_t, lpt_fstride, Nq,
-              tc_ldk(M)};
+    SpecOut o{spec32, fstride, lp_q, lpq_fstride, lp_t, lpt_fstride, Nq, tc_ldk(M),
+              lp_kind != 0};
 #define SW_SPEC_LAUNCH(T, NS)                                                                    \
     do {                                                                                        \
         cudaFuncSetAttribute(k_spectrum<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \

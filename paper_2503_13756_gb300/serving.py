@@ -126,7 +126,11 @@ class ServingEngine:
             while self.queue and used < self.max_batch:
                 req, start = self.queue[0]
                 take = min(len(req.images) - start, self.max_batch - used)
-                if self.bank.workspace_bytes(used + take, 1) > self.slot_budget:
+                # shrink to the budget; an empty batch always takes one image,
+                # so that the queue drains even under a budget below one image
+                while take > 1 and self.bank.workspace_bytes(used + take, 1) > self.slot_budget:
+                    take //= 2
+                if used and self.bank.workspace_bytes(used + take, 1) > self.slot_budget:
                     break
                 batch.append((req, start, take))
                 used += take
