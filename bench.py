@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -29,9 +30,14 @@ sys.path.insert(0, ROOT)
 METRIC = "aligned image pairs/s (128x128, 256 angles) FP32 vs BF16; p99 request latency"
 NQ, NT, L, N_THETA, M_LEVELS = 4096, 256, 128, 256, 128
 SM_COUNT, FP32_LANES, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
+B_BINS = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2   # default bin count at L = 128
 WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
 # algorithmic work per unit (stated in the design doc)
 PROJ_FLOPS_PER_CELL_ANGLE = 8           # s = <x, e> (FMA), frac, 1-t, two FMA accumulations
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
+# of the four-angle projection kernel, from one ncu capture of its 2048-image
+# launch (266,798,080 bytes); None once that kernel changes.
+PROJ_DRAM_BYTES_PER_IMAGE = 266798080 / 2048
 CORR_FLOPS_PER_PAIR_FREQ = 8 * M_LEVELS  # complex multiply-add per level
 
 
@@ -358,8 +364,13 @@ def main():
     if dom == "project":
         flops = args.steps * nimg * L * L * (N_THETA // 2) * PROJ_FLOPS_PER_CELL_ANGLE
         achieved = flops / (stages[dom][0] / 1e3) / 1e12
-        roof = {"kernel": "k_project", "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+        per_launch = nimg / max(1.0, stages[dom][1] / args.steps)
+        traffic = (PROJ_DRAM_BYTES_PER_IMAGE * per_launch
+                   if PROJ_DRAM_BYTES_PER_IMAGE is not None else None)
+        roof = {"kernel": "k_project4", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch (average launch of the step)",
+                "algorithmic_bytes_per_launch": per_launch * (L * L * 4 + (N_THETA // 2) * B_BINS * 4),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
     elif dom == "corr" and args.precision == "fp32":
         flops = args.steps * nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
