@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp32_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -296,7 +296,7 @@ def main():
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
     variants = {}
     if args.precision == "fp32" and not args.no_variants:
-        for prec in ("bf16", "fp16"):
+        for prec in ("bf16", "fp16", "fp32_simt"):
             pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec)
             al.reserve(pv, nq, nt)
             for _ in range(3):
@@ -317,14 +317,17 @@ def main():
             flops = nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
             peaks_v, _ = measured_peaks()
             tf = flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else None
+            simt = prec == "fp32_simt"
+            peak_v = (SM_COUNT * FP32_LANES * 2 * peaks_v.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL)
+                      * 1e6 / 1e12) if simt else peaks_v.get("bf16_tflops")
             variants[prec] = {
                 "value": sum_over_ranks(nq * nt, world, dev) / (ms_v / 1e3), "unit": "pairs/s",
                 "ms_per_step": ms_v, "status_ok": bool(np.all(rv["status"] == 0)),
                 "stages": {k: v[0] / args.steps for k, v in st_v.items()},
-                "corr_tensor": {"achieved": tf, "unit": "TFLOP/s",
-                                "peak": peaks_v.get("bf16_tflops"),
-                                "frac": tf / peaks_v["bf16_tflops"] if tf else None,
-                                "flops_per_launch": flops},
+                "corr": {"achieved": tf, "unit": "TFLOP/s", "peak": peak_v,
+                         "peak_kind": "FP32 FMA (unit counts)" if simt else "measured BF16 burst",
+                         "frac": tf / peak_v if tf else None,
+                         "algorithmic_flops_per_launch": flops},
             }
         al.reserve(p, nq, nt)
 
@@ -372,7 +375,7 @@ def main():
                 "traffic_unit": "bytes per launch (average launch of the step)",
                 "algorithmic_bytes_per_launch": per_launch * (L * L * 4 + (N_THETA // 2) * B_BINS * 4),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
-    elif dom == "corr" and args.precision == "fp32":
+    elif dom == "corr" and args.precision == "fp32_simt":
         flops = args.steps * nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
         achieved = flops / (stages[dom][0] / 1e3) / 1e12
         roof = {"kernel": "k_corr_simt", "bound": "alu", "achieved": achieved, "peak": alu_peak,
@@ -387,12 +390,15 @@ def main():
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "dtype": "f32" if args.precision.startswith("fp32") else args.precision,
         "data": "synthetic",
         "config": {"workload": WORKLOAD if (nq, nt) == (NQ, NT) else
                    f"many-to-many {nq}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
                    "Nq": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
                    "n_levels": M_LEVELS, "precision": args.precision, "translation": 1,
+                   "correlation": {"fp32": "tcgen05, 3-term FP16 split, FP32 accumulate",
+                                   "bf16": "tcgen05 BF16", "fp16": "tcgen05 FP16",
+                                   "fp32_simt": "CUDA-core FP32"}[args.precision],
                    "parallelism": f"{world} independent replicas (weak)",
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},
         "roofline": roof, "peaks": peak_src, "stages": per_stage, "cpu_baseline": cpu,

@@ -57,9 +57,11 @@ typedef enum {
 } sw_status;
 
 typedef enum {
-    SW_PREC_FP32 = 0, /* correlation in FP32 on the CUDA cores                  */
-    SW_PREC_BF16 = 1, /* correlation GEMM on tcgen05, BF16 in, FP32 accumulate  */
-    SW_PREC_FP16 = 2  /* correlation GEMM on tcgen05, FP16 in, FP32 accumulate  */
+    SW_PREC_FP32 = 0,      /* FP32-accurate correlation: tcgen05 GEMM on a 3-term FP16 */
+                           /* split, x = hi + lo, hi*hi + hi*lo + lo*hi, FP32 accumulate */
+    SW_PREC_BF16 = 1,      /* correlation GEMM on tcgen05, BF16 in, FP32 accumulate    */
+    SW_PREC_FP16 = 2,      /* correlation GEMM on tcgen05, FP16 in, FP32 accumulate    */
+    SW_PREC_FP32_SIMT = 3  /* correlation in FP32 on the CUDA cores                    */
 } sw_precision;
 
 typedef struct {

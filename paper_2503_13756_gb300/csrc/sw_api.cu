@@ -99,7 +99,19 @@ struct Layout {
 
 int bins_of(const sw_params *p) { return p->n_bins > 0 ? p->n_bins : sw_default_bins(p->L); }
 
-Layout batch_layout(const sw_params *p, int Nq, int Nt, bool lp, bool scratch)
+// Low-precision spectra kind of a precision: 3 = FP16 split (FP32-accurate
+// tensor-core path), 1 = BF16, 2 = FP16, 0 = none (CUDA-core FP32).
+int lp_kind_of(int precision)
+{
+    switch (precision) {
+    case SW_PREC_FP32: return 3;
+    case SW_PREC_BF16: return 1;
+    case SW_PREC_FP16: return 2;
+    default: return 0;
+    }
+}
+
+Layout batch_layout(const sw_params *p, int Nq, int Nt, int lp_kind, bool scratch)
 {
     const size_t nimg = (size_t)Nq + Nt;
     const size_t n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
@@ -110,13 +122,13 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, bool lp, bool scratch)
         o = align_up(o + bytes);
         return at;
     };
+    const size_t row = lp_kind ? (size_t)swk::lp_row_len((int)M, lp_kind) : 0;
     l.status = take(4 * nimg);
     l.proj = take(4 * nimg * nh * B);
     l.quant = take(4 * nimg * n * M);
-    l.spec32 = take(4 * nh * nimg * 2 * M);
-    const size_t ldk = swk::tc_ldk((int)M);
-    l.lp_q = take(lp ? 2 * nh * (size_t)Nq * ldk : 0);
-    l.lp_t = take(lp ? 2 * nh * (size_t)2 * Nt * ldk : 0);
+    l.spec32 = take(lp_kind ? 0 : 4 * nh * nimg * 2 * M);
+    l.lp_q = take(2 * nh * (size_t)Nq * row);
+    l.lp_t = take(2 * nh * (size_t)2 * Nt * row);
     l.prof = take(4 * nimg * M);
     l.center = take(16 * nimg);
     l.norm32 = take(8 * nimg);
@@ -133,8 +145,8 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, bool lp, bool scratch)
 Layout bank_layout(const sw_params *p, int Nq, int Nt, bool scratch)
 {
     const size_t n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
-    const bool lp = p->gemm_precision != SW_PREC_FP32;
-    const size_t ldk = swk::tc_ldk((int)M);
+    const int lp_kind = lp_kind_of(p->gemm_precision);
+    const size_t row = lp_kind ? (size_t)swk::lp_row_len((int)M, lp_kind) : 0;
     Layout l{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -145,8 +157,8 @@ Layout bank_layout(const sw_params *p, int Nq, int Nt, bool scratch)
     l.status = take(4 * (size_t)Nq);
     l.proj = take(4 * (size_t)Nq * nh * B);
     l.quant = take(4 * (size_t)Nq * n * M);
-    l.spec32 = take(4 * nh * (size_t)Nq * 2 * M);
-    l.lp_q = take(lp ? 2 * nh * (size_t)Nq * ldk : 0);
+    l.spec32 = take(lp_kind ? 0 : 4 * nh * (size_t)Nq * 2 * M);
+    l.lp_q = take(2 * nh * (size_t)Nq * row);
     l.lp_t = take(0);
     l.prof = take(4 * (size_t)Nq * M);
     l.center = take(16 * (size_t)Nq);
@@ -265,7 +277,7 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
         return fail(c, SW_ERR_INVALID_ARG, "translation must be 0 or 1");
     if (p->level_rule != 0 && p->level_rule != 1)
         return fail(c, SW_ERR_INVALID_ARG, "level_rule must be 0 or 1");
-    if (p->gemm_precision < SW_PREC_FP32 || p->gemm_precision > SW_PREC_FP16)
+    if (p->gemm_precision < SW_PREC_FP32 || p->gemm_precision > SW_PREC_FP32_SIMT)
         return fail(c, SW_ERR_INVALID_ARG, "gemm_precision=%d unknown", p->gemm_precision);
     return SW_OK;
 }
@@ -494,7 +506,7 @@ sw_status sw_set_workspace_limit(sw_ctx *c, size_t bytes)
 size_t sw_batch_workspace_bytes(const sw_params *p, int Nq, int Nt)
 {
     if (!p || Nq < 0 || Nt < 0 || check_params(nullptr, p) != SW_OK) return 0;
-    return batch_layout(p, Nq, Nt, p->gemm_precision != SW_PREC_FP32, true).total;
+    return batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total;
 }
 
 sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
@@ -507,7 +519,7 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if ((s = set_device(c))) return s;
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t))) return s;
-    return ensure_ws(c, batch_layout(p, Nq, Nt, p->gemm_precision != SW_PREC_FP32, true).total);
+    return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);
 }
 
 sw_status sw_project(sw_ctx *c, const sw_params *p, const float *d_img, int nb, float *d_proj,
@@ -577,26 +589,27 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
                            double *shifts, bool force_fp32, cudaStream_t st)
 {
     const int n = p->n_theta, nh = n / 2, M = p->n_levels;
-    const bool lp = !force_fp32 && p->gemm_precision != SW_PREC_FP32;
+    const int kind = force_fp32 ? 0 : lp_kind_of(p->gemm_precision);
+    const bool lp = kind != 0;
     const Tables *t;
     sw_status s = get_tables(c, n, &t);
     if (s) return s;
-    const Layout l = batch_layout(p, Nq, Nt, lp, mode == 1);
+    const Layout l = batch_layout(p, Nq, Nt, kind, mode == 1);
     if ((s = ensure_ws(c, l.total))) return s;
     char *w = c->ws;
     const int nimg = Nq + Nt;
+    const int row = lp ? swk::lp_row_len(M, kind) : 0;
     ImageOut o{};
     o.status = at<int32_t>(w, l.status);
     o.proj = at<float>(w, l.proj);
     o.quant = at<float>(w, l.quant);
-    o.spec32 = at<float>(w, l.spec32);
+    o.spec32 = lp ? nullptr : at<float>(w, l.spec32);
     o.fstride = (size_t)nimg * 2 * M;
-    o.lp_kind = lp ? p->gemm_precision : 0;
+    o.lp_kind = kind;
     o.lp_q = lp ? (void *)(w + l.lp_q) : nullptr;
-    const int ldk = swk::tc_ldk(M);
-    o.lpq_fstride = (size_t)Nq * ldk;
+    o.lpq_fstride = (size_t)Nq * row;
     o.lp_t = lp ? (void *)(w + l.lp_t) : nullptr;
-    o.lpt_fstride = (size_t)2 * Nt * ldk;
+    o.lpt_fstride = (size_t)2 * Nt * row;
     o.Nq = Nq;
     o.prof = at<float>(w, l.prof);
     o.center = at<double>(w, l.center);
@@ -610,8 +623,8 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     SW_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), st));
     if (lp) {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
-                    return swk::launch_corr_tc(o.lp_q, o.lp_t, Nq, Nt, M, nh, p->gemm_precision,
-                                               C, err, c->num_sms, st);
+                    return swk::launch_corr_tc(o.lp_q, o.lp_t, Nq, Nt, M, nh, kind, C, err,
+                                               c->num_sms, st);
                 }));
     } else {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
@@ -630,7 +643,9 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     a.prof_t = o.prof + (size_t)Nq * M;
     a.ctr_q = o.center;
     a.ctr_t = o.center + 2 * (size_t)Nq;
-    const double *nrm = lp ? o.norm16 : o.norm32;
+    // the split path approximates the FP32 product: FP32 norms; BF16/FP16: the
+    // norms of the rounded spectra, so that self-distances cancel
+    const double *nrm = (kind == 1 || kind == 2) ? o.norm16 : o.norm32;
     a.norm_q = nrm;
     a.norm_t = nrm + Nq;
     a.st_q = o.status;
@@ -710,8 +725,9 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     if ((s = get_tables(c, p->n_theta, &t))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
-    const bool lp = p->gemm_precision != SW_PREC_FP32;
-    const int ldk = swk::tc_ldk(M);
+    const int kind = lp_kind_of(p->gemm_precision);
+    const bool lp = kind != 0;
+    const int row = lp ? swk::lp_row_len(M, kind) : 0;
     // bank memory (owned by the bank)
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -719,8 +735,8 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
         o = align_up(o + bytes);
         return at_;
     };
-    const size_t o_spec = take(4 * (size_t)nh * Nt * 2 * M);
-    const size_t o_lp = take(lp ? 2 * (size_t)nh * 2 * Nt * ldk : 0);
+    const size_t o_spec = take(lp ? 0 : 4 * (size_t)nh * Nt * 2 * M);
+    const size_t o_lp = take(2 * (size_t)nh * 2 * Nt * row);
     const size_t o_prof = take(4 * (size_t)Nt * M);
     const size_t o_ctr = take(16 * (size_t)Nt);
     const size_t o_n32 = take(8 * (size_t)Nt);
@@ -736,7 +752,7 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
         delete b;
         return fail(c, SW_ERR_OOM, "bank of %zu bytes does not fit", o);
     }
-    b->spec32 = at<float>(b->mem, o_spec);
+    b->spec32 = lp ? nullptr : at<float>(b->mem, o_spec);
     b->lp_t = lp ? (void *)(b->mem + o_lp) : nullptr;
     b->prof = at<float>(b->mem, o_prof);
     b->center = at<double>(b->mem, o_ctr);
@@ -756,11 +772,11 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     io.quant = at<float>(c->ws, align_up(4 * (size_t)Nt * nh * B));
     io.spec32 = b->spec32;
     io.fstride = (size_t)Nt * 2 * M;
-    io.lp_kind = lp ? p->gemm_precision : 0;
+    io.lp_kind = kind;
     io.lp_q = nullptr;
     io.lpq_fstride = 0;
     io.lp_t = b->lp_t;
-    io.lpt_fstride = (size_t)2 * Nt * ldk;
+    io.lpt_fstride = (size_t)2 * Nt * row;
     io.Nq = 0;  // every image is a template (doubled low-precision rows)
     io.prof = b->prof;
     io.center = b->center;
@@ -806,20 +822,21 @@ sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, in
     if ((s = get_tables(c, p->n_theta, &t))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int n = p->n_theta, nh = n / 2, M = p->n_levels, Nt = bank->Nt;
-    const bool lp = p->gemm_precision != SW_PREC_FP32;
+    const int kind = lp_kind_of(p->gemm_precision);
+    const bool lp = kind != 0;
     const Layout l = bank_layout(p, Nq, Nt, mode == 1);
     if ((s = ensure_ws(c, l.total))) return s;
     char *w = c->ws;
-    const int ldk = swk::tc_ldk(M);
+    const int row = lp ? swk::lp_row_len(M, kind) : 0;
     ImageOut o{};
     o.status = at<int32_t>(w, l.status);
     o.proj = at<float>(w, l.proj);
     o.quant = at<float>(w, l.quant);
-    o.spec32 = at<float>(w, l.spec32);
+    o.spec32 = lp ? nullptr : at<float>(w, l.spec32);
     o.fstride = (size_t)Nq * 2 * M;
-    o.lp_kind = lp ? p->gemm_precision : 0;
+    o.lp_kind = kind;
     o.lp_q = lp ? (void *)(w + l.lp_q) : nullptr;
-    o.lpq_fstride = (size_t)Nq * ldk;
+    o.lpq_fstride = (size_t)Nq * row;
     o.lp_t = nullptr;
     o.lpt_fstride = 0;
     o.Nq = Nq;  // every image is a query
@@ -834,8 +851,8 @@ sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, in
     SW_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), st));
     if (lp) {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
-                    return swk::launch_corr_tc(o.lp_q, bank->lp_t, Nq, Nt, M, nh,
-                                               p->gemm_precision, C, err, c->num_sms, st);
+                    return swk::launch_corr_tc(o.lp_q, bank->lp_t, Nq, Nt, M, nh, kind, C, err,
+                                               c->num_sms, st);
                 }));
     } else {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
@@ -853,8 +870,9 @@ sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, in
     a.prof_t = bank->prof;
     a.ctr_q = o.center;
     a.ctr_t = bank->center;
-    a.norm_q = lp ? o.norm16 : o.norm32;
-    a.norm_t = lp ? bank->norm16 : bank->norm32;
+    const bool n16 = kind == 1 || kind == 2;
+    a.norm_q = n16 ? o.norm16 : o.norm32;
+    a.norm_t = n16 ? bank->norm16 : bank->norm32;
     a.st_q = o.status;
     a.st_t = bank->status;
     a.cs64 = t->cs64;
@@ -940,7 +958,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
         return SW_ERR_INVALID_ARG;
     const int n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
     // scratch: the FP32 batch layout for one query and one template, then the tables
-    const Layout l = batch_layout(p, 1, 1, false, false);
+    const Layout l = batch_layout(p, 1, 1, 0, false);
     const size_t o_cs = align_up(l.total);
     const size_t o_cs64 = align_up(o_cs + sizeof(float2) * nh);
     const size_t o_tw = align_up(o_cs64 + sizeof(double2) * n);

@@ -334,8 +334,8 @@ bool make_map(CUtensorMap *m, const void *base, int kind, uint64_t ldk, uint64_t
     const cuuint64_t strides[2] = {ldk * 2, ldk * 2 * rows};
     const cuuint32_t box[3] = {(cuuint32_t)BK, box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(m, kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+    const CUresult r = enc(m, kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                            3, const_cast<void *>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -345,12 +345,13 @@ bool make_map(CUtensorMap *m, const void *base, int kind, uint64_t ldk, uint64_t
 }  // namespace
 
 int tc_ldk(int M) { return ((2 * M + BK - 1) / BK) * BK; }
+int lp_row_len(int M, int lp_kind) { return lp_kind == 3 ? 3 * tc_ldk(M) : tc_ldk(M); }
 
 cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
                            int kind, float2 *C, int *err, int num_sms, cudaStream_t st)
 {
     if (Nq <= 0 || Nt <= 0 || nf <= 0) return cudaSuccess;
-    const int ldk = tc_ldk(M);
+    const int ldk = lp_row_len(M, kind);
     CUtensorMap ma, mb;
     if (!make_map(&ma, Xq, kind, ldk, (uint64_t)Nq, nf, BM) ||
         !make_map(&mb, Yt, kind, ldk, (uint64_t)2 * Nt, nf, BN))
@@ -364,7 +365,7 @@ cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M
     a.ntiles = (2 * Nt + BN - 1) / BN;
     // kind::f16 instruction descriptor: FP32 accumulator, A/B BF16 (1) or
     // FP16 (0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-    const uint32_t fmt = kind == 2 ? 0u : 1u;
+    const uint32_t fmt = kind == 1 ? 1u : 0u;  // BF16, else FP16 (plain or split)
     a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
               ((uint32_t)(BM >> 4) << 24);
     a.C = reinterpret_cast<float *>(C);

@@ -211,6 +211,10 @@ cudaError_t launch_center_norm(const float *q, int nb, int n, int M, const doubl
 // lp_q[(k'-1)*lpq_fstride + img*ldk] = [re | im | 0], templates to the doubled
 // layout lp_t[(k'-1)*lpt_fstride + (2j)*ldk] = [re | im | 0] and
 // [(2j+1)*ldk] = [-im | re | 0], and norm16 from the rounded values.
+// lp_kind 3 writes the FP16 split x = hi + lo in rows of 3 ldk elements:
+// queries [hi | hi | lo], templates [hi | lo | hi] (of the same [re|im|0] and
+// [-im|re|0] rows), so that one GEMM over K = 3 ldk sums hi*hi + hi*lo + lo*hi.
+// With lp_kind != 0, spec32 is not written (may be NULL).
 cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan &plan,
                             const float2 *tw, float *spec32, size_t fstride, int lp_kind,
                             void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
@@ -228,8 +232,10 @@ cudaError_t launch_corr_simt(const float *X, size_t xf, const float *Y, size_t y
 // launch_spectrum: Xq [nf][Nq][ldk], Yt [nf][2Nt][ldk] (doubled template rows).
 // *err is set to 1 if a bounded wait gave up.
 int tc_ldk(int M);  // K row length: 2M rounded up to 64
+int lp_row_len(int M, int lp_kind);  // low-precision row length: ldk, or 3 ldk for the split
 cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
                            int kind, float2 *C, int *err, int num_sms, cudaStream_t st);
+// kind: 1 bf16, 2 fp16, 3 fp16 split (rows of lp_row_len(M, 3) elements)
 
 // Inverse angle FFT of the correlation spectra, argmin over the rotation
 // grid and the FP64 distance at the optimum.  See sw_decide.cu.

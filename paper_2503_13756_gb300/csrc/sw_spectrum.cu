@@ -48,38 +48,68 @@ struct SpecOut {
     void *lp_t;
     size_t lpt_fstride;
     int Nq;
-    int ldk;  // low-precision row length (>= 2M, zero padded)
-    int lp;   // write low-precision copies (queries to lp_q, templates to lp_t)
+    int ldk;    // low-precision segment length (>= 2M, zero padded)
+    int lp;     // write low-precision copies (queries to lp_q, templates to lp_t)
+    int split;  // FP16 hi/lo split: rows of 3 segments
 };
 
-// Writes Qhat(kf, p) (kf >= 1) for image img; returns |.|^2 weight-summed
-// contributions through acc32 / acc16.
+// Writes Qhat(kf, p) (kf >= 1) for image img and adds its |.|^2 (weight w)
+// to acc32 (FP32 values) and acc16 (the low-precision values the GEMM sees).
 template <typename T>
 __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, int p, float2 X,
                                      double w, double &acc32, double &acc16)
 {
-    float *row = o.spec32 + (size_t)(kf - 1) * o.fstride + (size_t)img * 2 * M;
-    row[p] = X.x;
-    row[M + p] = X.y;
     acc32 += w * ((double)X.x * X.x + (double)X.y * X.y);
-    if (o.lp) {
-        const T re = to_lp<T>(X.x), im = to_lp<T>(X.y);
-        const float rf = from_lp<T>(re), imf = from_lp<T>(im);
+    if (!o.lp) {
+        float *row = o.spec32 + (size_t)(kf - 1) * o.fstride + (size_t)img * 2 * M;
+        row[p] = X.x;
+        row[M + p] = X.y;
+        return;
+    }
+    const T re = to_lp<T>(X.x), im = to_lp<T>(X.y);
+    const float rf = from_lp<T>(re), imf = from_lp<T>(im);
+    const T nim = to_lp<T>(-imf);
+    const bool tmpl = img >= o.Nq;
+    const int seg = o.ldk;                     // one [re|im|0] segment
+    const int row_len = o.split ? 3 * seg : seg;
+    T *r = tmpl ? reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
+                      (size_t)(2 * (img - o.Nq)) * row_len
+                : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
+                      (size_t)img * row_len;
+    if (!o.split) {
         acc16 += w * ((double)rf * rf + (double)imf * imf);
-        if (img < o.Nq) {
-            T *r = reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
-                   (size_t)img * o.ldk;
-            r[p] = re;
-            r[M + p] = im;
-        } else {
-            const int j = img - o.Nq;
-            T *r = reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
-                   (size_t)(2 * j) * o.ldk;
-            r[p] = re;                        // row 2j:   [ re | im | 0 ]
-            r[M + p] = im;
-            r[o.ldk + p] = to_lp<T>(-imf);    // row 2j+1: [ -im | re | 0 ]
-            r[o.ldk + M + p] = re;
+        r[p] = re;
+        r[M + p] = im;
+        if (tmpl) {
+            r[row_len + p] = nim;  // row 2j+1: [ -im | re | 0 ]
+            r[row_len + M + p] = re;
         }
+        return;
+    }
+    // FP16 split: lo = x - hi, exact in FP32, rounded to FP16
+    const T rel = to_lp<T>(X.x - rf), iml = to_lp<T>(X.y - imf);
+    const T nrel = to_lp<T>(-(X.y - imf));
+    if (!tmpl) {  // A' = [hi | hi | lo]
+        r[p] = re;
+        r[M + p] = im;
+        r[seg + p] = re;
+        r[seg + M + p] = im;
+        r[2 * seg + p] = rel;
+        r[2 * seg + M + p] = iml;
+    } else {      // B' = [hi | lo | hi], rows [re|im] and [-im|re]
+        r[p] = re;
+        r[M + p] = im;
+        r[seg + p] = rel;
+        r[seg + M + p] = iml;
+        r[2 * seg + p] = re;
+        r[2 * seg + M + p] = im;
+        T *r2 = r + row_len;
+        r2[p] = nim;
+        r2[M + p] = re;
+        r2[seg + p] = nrel;
+        r2[seg + M + p] = rel;
+        r2[2 * seg + p] = nim;
+        r2[2 * seg + M + p] = re;
     }
 }
 
@@ -178,18 +208,22 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
         const float2 X = make_float2(x1[p].x - c1r, x1[p].y - c1i);
         emit<T>(o, img, M, 1, p, X, 2.0, acc32, acc16);  // n >= 4: k' = 1 < n/2
     }
-    // ---- zero padding of the low-precision rows, [2M, ldk)
+    // ---- zero padding of the low-precision rows: [2M, ldk) of every segment
     if (o.lp && o.ldk > 2 * M) {
         const int pad = o.ldk - 2 * M;
         const bool tmpl = img >= o.Nq;
+        const int nseg = o.split ? 3 : 1;
+        const int row_len = nseg * o.ldk;
         const int rows = tmpl ? 2 : 1;
-        for (int t = threadIdx.x; t < nh * rows * pad; t += blockDim.x) {
-            const int kf = 1 + t / (rows * pad), rr = (t / pad) % rows, e = 2 * M + t % pad;
+        const int per_f = rows * nseg * pad;
+        for (int t = threadIdx.x; t < nh * per_f; t += blockDim.x) {
+            const int kf = 1 + t / per_f, rem = t % per_f;
+            const int rr = rem / (nseg * pad), sg = (rem / pad) % nseg, e = 2 * M + rem % pad;
             T *r = tmpl ? reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
-                              (size_t)(2 * (img - o.Nq) + rr) * o.ldk
+                              (size_t)(2 * (img - o.Nq) + rr) * row_len
                         : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
-                              (size_t)img * o.ldk;
-            r[e] = to_lp<T>(0.f);
+                              (size_t)img * row_len;
+            r[sg * o.ldk + e] = to_lp<T>(0.f);
         }
     }
     // ---- norms: Parseval over k' != 0 of the centred spectra, / n
@@ -228,7 +262,7 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
     const int nsig = n <= 512 ? 16 : 8;
     const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M + n);
     SpecOut o{spec32, fstride, lp_q, lpq_fstride, lp_t, lpt_fstride, Nq, tc_ldk(M),
-              lp_kind != 0};
+              lp_kind != 0, lp_kind == 3};
 #define SW_SPEC_LAUNCH(T, NS)                                                                    \
     do {                                                                                        \
         cudaFuncSetAttribute(k_spectrum<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
@@ -236,7 +270,7 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
         k_spectrum<T, NS><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, o, prof, center,  \
                                                           norm32, norm16);                      \
     } while (0)
-    if (lp_kind == 2) {
+    if (lp_kind == 2 || lp_kind == 3) {
         if (nsig == 16) SW_SPEC_LAUNCH(__half, 16);
         else SW_SPEC_LAUNCH(__half, 8);
     } else {

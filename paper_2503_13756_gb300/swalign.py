@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 SW_OK, SW_ERR_INVALID_ARG, SW_ERR_UNSUPPORTED, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT = range(6)
-PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
+PREC = {"fp32": 0, "bf16": 1, "fp16": 2, "fp32_simt": 3}
 
 RESULT_DTYPE = np.dtype(
     [("best_l", "<i4"), ("status", "<i4"), ("angle_rad", "<f4"), ("reserved", "<f4"),

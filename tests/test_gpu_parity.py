@@ -102,10 +102,11 @@ def test_single_pair_curve_matches_oracle(al, translation):
 
 # ------------------------------------------------------------- many pairs
 
-def compare_batch(al, q, t, n, M, translation=1, level_rule=0, n_bins=0, rel=REL_FP32):
+def compare_batch(al, q, t, n, M, translation=1, level_rule=0, n_bins=0, rel=REL_FP32,
+                  precision="fp32"):
     L = q.shape[-1]
     p = swalign.make_params(L, n, M, n_bins=n_bins, translation=translation,
-                            level_rule=level_rule)
+                            level_rule=level_rule, precision=precision)
     got = swalign.results_to_numpy(al.align_batch(q, t, p)).reshape(len(q), len(t))
     B = n_bins or None
     ref = oracle.align_all_pairs(q.astype(np.float64), t.astype(np.float64), n, M, B=B,
@@ -129,11 +130,13 @@ def compare_batch(al, q, t, n, M, translation=1, level_rule=0, n_bins=0, rel=REL
     return worst
 
 
-def test_batch_ragged_tiles_match_oracle(al):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
+def test_batch_ragged_tiles_match_oracle(al, precision):
+    # FP32-accurate correlation on tcgen05 (FP16 split) and on the CUDA cores
     rng = np.random.default_rng(31)
     q = f32(blobs(rng, 5, 48))
-    t = f32(blobs(rng, 70, 48))  # ragged against the 64-wide pair tile
-    compare_batch(al, q, t, n=60, M=36)
+    t = f32(blobs(rng, 70, 48))  # ragged against the 64-wide and 128-row tiles
+    compare_batch(al, q, t, n=60, M=36, precision=precision)
 
 
 @pytest.mark.parametrize("case", [
@@ -142,12 +145,14 @@ def test_batch_ragged_tiles_match_oracle(al):
     dict(L=24, n=40, M=9, translation=0, level_rule=1, n_bins=0),
     dict(L=32, n=30, M=16, translation=1, level_rule=0, n_bins=60),
 ])
-def test_batch_edge_parameters(al, case):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
+def test_batch_edge_parameters(al, case, precision):
     rng = np.random.default_rng(case["n"] * 7 + case["M"])
+    case = dict(case)
     L = case.pop("L")
     q = f32(blobs(rng, 3, L))
     t = f32(blobs(rng, 4, L))
-    compare_batch(al, q, t, **case)
+    compare_batch(al, q, t, precision=precision, **case)
 
 
 def test_quarter_turn_is_exact(al):

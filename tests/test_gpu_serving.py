@@ -19,7 +19,7 @@ def al():
     a.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_simt"])
 def test_bank_equals_batch(al, precision):
     rng = np.random.default_rng(4)
     L, n, M = 64, 60, 32
