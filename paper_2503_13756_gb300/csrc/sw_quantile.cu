@@ -22,7 +22,7 @@ constexpr int kQThreads = 256;  // 8 warps = 8 projections per block
 
 __global__ void __launch_bounds__(kQThreads)
 k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int level_rule,
-            int half, float *__restrict__ q, int32_t *__restrict__ status)
+            int half, int mirror_out, float *__restrict__ q, int32_t *__restrict__ status)
 {
     extern __shared__ float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -32,10 +32,11 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
     // per warp: U (B+1 floats, padded to even) then F (B+1 float2): every
     // region and every F starts 8-byte aligned
     const int ue = (B + 1) + ((B + 1) & 1);
-    const int stride = ue + 2 * (B + 1);
+    const int stride = ue + 2 * (B + 1) + M + (M & 1);
     float *U = sm + warp * stride;                          // [B]
     float2 *F = reinterpret_cast<float2 *>(U + ue);         // [B+1] (hi, lo)
-    if (k >= n) return;              // whole warp leaves; no block barrier below
+    float *qb = reinterpret_cast<float *>(F + (B + 1));     // [M] this projection's quantiles
+    if (k >= (mirror_out ? n / 2 : n)) return;  // whole warp leaves; no block barrier below
     const int nh = n / 2;
     const float *row;
     bool mirror = false;
@@ -78,12 +79,21 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
     float *qo = q + ((size_t)imgi * n + k) * M;
     if (!(total.hi > 0.f) || !isfinite(total.hi)) {
         for (int p = lane; p < M; p += 32) qo[p] = __int_as_float(0x7fc00000);
+        if (mirror_out) {
+            float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
+            for (int p = lane; p < M; p += 32) qm[p] = __int_as_float(0x7fc00000);
+        }
         if (lane == 0) atomicOr(status + imgi, 1);
         return;
     }
     const float dz = level_rule == 0 ? 2.f * M : (float)M;
     const float inv_dz = 1.f / dz;
-    for (int p = lane; p < M; p += 32) {
+    // lane owns levels [pb, pe): one binary search, then a forward walk (the
+    // levels increase, so j* never decreases)
+    const int P = (M + 31) / 32;
+    const int pb = min(M, lane * P), pe = min(M, pb + P);
+    int j = 1;
+    for (int p = pb; p < pe; ++p) {
         // tau = z_p F_B with z_p = (2p+1)/(2M) or p/M, formed exactly
         const float kz = level_rule == 0 ? 2.f * p + 1.f : (float)p;
         float Q;
@@ -91,14 +101,22 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
             Q = -0.5f * (float)B * h;  // inf{t : F(t) >= 0}: the domain's left end e_0
         } else {
             const DF tau = df_scale_ratio(total, kz, dz, inv_dz);
-            int lo = 1, hi = B;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                const float2 f = F[mid];
-                if (df_ge(DF{f.x, f.y}, tau)) hi = mid;
-                else lo = mid + 1;
+            if (p == pb || (level_rule == 1 && p == 1)) {
+                int lo = 1, hi = B;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const float2 f = F[mid];
+                    if (df_ge(DF{f.x, f.y}, tau)) hi = mid;
+                    else lo = mid + 1;
+                }
+                j = lo;
+            } else {
+                while (j < B) {
+                    const float2 f = F[j];
+                    if (df_ge(DF{f.x, f.y}, tau)) break;
+                    ++j;
+                }
             }
-            const int j = lo;
             const float2 fj = F[j - 1];
             const float num = (tau.hi - fj.x) + (tau.lo - fj.y);
             const float den = U[j - 1];
@@ -108,7 +126,15 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
             const float ej = ((float)(j - 1) - 0.5f * (float)B) * h;
             Q = fmaf(h, frac, ej);
         }
-        qo[p] = Q;
+        qb[p] = Q;
+    }
+    __syncwarp();
+    for (int p = lane; p < M; p += 32) qo[p] = qb[p];
+    if (mirror_out) {
+        // theta + pi: the mirrored histogram has Q'(z) = -Q(1 - z), and with
+        // midpoint levels 1 - z_p = z_{M-1-p}
+        float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
+        for (int p = lane; p < M; p += 32) qm[p] = -qb[M - 1 - p];
     }
 }
 
@@ -182,10 +208,15 @@ cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, flo
     if (nb <= 0) return cudaSuccess;
     const int nw = kQThreads / 32;
     const int ue = (B + 1) + ((B + 1) & 1);
-    const size_t smem = sizeof(float) * (size_t)nw * (ue + 2 * (B + 1));
+    const size_t smem = sizeof(float) * (size_t)nw * (ue + 2 * (B + 1) + M + (M & 1));
+    // with half projections and midpoint levels, angles k and k + n/2 come
+    // from one quantile computation
+    const int mirror = half && level_rule == 0;
+    const int nang = mirror ? n / 2 : n;
     cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    dim3 grid((n + nw - 1) / nw, nb);
-    k_quantiles<<<grid, kQThreads, smem, st>>>(proj, n, B, M, h, level_rule, half, q, status);
+    dim3 grid((nang + nw - 1) / nw, nb);
+    k_quantiles<<<grid, kQThreads, smem, st>>>(proj, n, B, M, h, level_rule, half, mirror, q,
+                                                status);
     return cudaGetLastError();
 }
 

@@ -57,9 +57,9 @@ struct SpecOut {
 // to acc32 (FP32 values) and acc16 (the low-precision values the GEMM sees).
 template <typename T>
 __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, int p, float2 X,
-                                     double w, double &acc32, double &acc16)
+                                     float w, DF &acc32, DF &acc16)
 {
-    acc32 += w * ((double)X.x * X.x + (double)X.y * X.y);
+    acc32 = df_add(acc32, DF{w * fmaf(X.x, X.x, X.y * X.y), 0.f});
     if (!o.lp) {
         float *row = o.spec32 + (size_t)(kf - 1) * o.fstride + (size_t)img * 2 * M;
         row[p] = X.x;
@@ -77,7 +77,7 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
                 : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
                       (size_t)img * row_len;
     if (!o.split) {
-        acc16 += w * ((double)rf * rf + (double)imf * imf);
+        acc16 = df_add(acc16, DF{w * fmaf(rf, rf, imf * imf), 0.f});
         r[p] = re;
         r[M + p] = im;
         if (tmpl) {
@@ -130,7 +130,9 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     const int img = blockIdx.x;
     const float *qi = q + (size_t)img * n * M;
     const int nh = n / 2;
-    double acc32 = 0.0, acc16 = 0.0;
+    // norms in double-float (TwoSum-compensated FP32): FP64 arithmetic is
+    // scarce on this part
+    DF acc32 = {0.f, 0.f}, acc16 = {0.f, 0.f};
     const float invn = 1.f / (float)n;
 
     for (int p0 = 0; p0 < M; p0 += 2 * nsig) {
@@ -165,7 +167,7 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
                     x1[p] = X;
                 } else {
                     if (kf == nh) X.y = 0.f;  // Nyquist term of a real signal
-                    const double w = kf == nh ? 1.0 : 2.0;
+                    const float w = kf == nh ? 1.f : 2.f;
                     emit<T>(o, img, M, kf, p, X, w, acc32, acc16);
                 }
             }
@@ -206,7 +208,7 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     const float c1r = (float)s_c1[0], c1i = (float)s_c1[1];
     for (int p = threadIdx.x; p < M; p += blockDim.x) {
         const float2 X = make_float2(x1[p].x - c1r, x1[p].y - c1i);
-        emit<T>(o, img, M, 1, p, X, 2.0, acc32, acc16);  // n >= 4: k' = 1 < n/2
+        emit<T>(o, img, M, 1, p, X, 2.f, acc32, acc16);  // n >= 4: k' = 1 < n/2
     }
     // ---- zero padding of the low-precision rows: [2M, ldk) of every segment
     if (o.lp && o.ldk > 2 * M) {
@@ -228,15 +230,17 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     }
     // ---- norms: Parseval over k' != 0 of the centred spectra, / n
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a32 = (double)acc32.hi + (double)acc32.lo;
+    double a16 = (double)acc16.hi + (double)acc16.lo;
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
-        acc32 += __shfl_xor_sync(0xffffffffu, acc32, off);
-        acc16 += __shfl_xor_sync(0xffffffffu, acc16, off);
+        a32 += __shfl_xor_sync(0xffffffffu, a32, off);
+        a16 += __shfl_xor_sync(0xffffffffu, a16, off);
     }
     __syncthreads();
     if (lane == 0) {
-        red[0][warp] = acc32;
-        red[1][warp] = acc16;
+        red[0][warp] = a32;
+        red[1][warp] = a16;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
