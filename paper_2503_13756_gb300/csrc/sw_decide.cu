@@ -85,7 +85,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
         }
     }
     __syncthreads();
-    const float2 *R = fft_smem<nsig>(b0, b1, plan, tws, +1);  // R[l][s] = n (corr_a + i corr_b)
+    const float2 *R = fft_smem<nsig, +1>(b0, b1, plan, tws);  // R[l][s] = n (corr_a + i corr_b)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // ---- k' = 0 part: n |m_i - m_j|^2
@@ -183,18 +183,18 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 r.d2 = nan;
             } else {
                 const float2 z = R[bl * nsig + sg];
-                const double corr = (double)(comp ? z.y : z.x) / n;
+                const double corr = (double)(comp ? z.y : z.x) * A.inv_n;
                 const double2 c = A.cs64[bl];
                 double sx = aix - (c.x * ajx - c.y * ajy);
                 double sy = aiy - (c.y * ajx + c.x * ajy);
-                double d = (base - 2.0 * corr) / nM;
+                double d = (base - 2.0 * corr) * A.inv_nM;
                 if (!A.translation) {
                     d += 0.5 * (sx * sx + sy * sy);
                     sx = sy = 0.0;
                 }
                 r.best_l = bl;
                 r.status = 0;
-                r.angle_rad = (float)(6.283185307179586 * bl / n);
+                r.angle_rad = (float)(A.dalpha * bl);
                 r.shift[0] = sx;
                 r.shift[1] = sy;
                 r.d2 = d;
@@ -209,11 +209,11 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
         const double base = (double)delta[0] + A.norm_q[0] + A.norm_t[0];
         const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
         for (int l = threadIdx.x; l < n; l += blockDim.x) {
-            const double corr = (double)R[l * nsig].x / n;
+            const double corr = (double)R[l * nsig].x * A.inv_n;
             const double2 c = A.cs64[l];
             double sx = aix - (c.x * ajx - c.y * ajy);
             double sy = aiy - (c.y * ajx + c.x * ajy);
-            double d = (base - 2.0 * corr) / nM;
+            double d = (base - 2.0 * corr) * A.inv_nM;
             if (!A.translation) {
                 d += 0.5 * (sx * sx + sy * sy);
                 sx = sy = 0.0;
@@ -275,10 +275,14 @@ __global__ void k_best_template(const sw_result *__restrict__ all, int Nq, int N
 
 }  // namespace
 
-cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
+cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const float2 *tw,
                           cudaStream_t st)
 {
-    if (a.Nq <= 0 || a.Nt <= 0) return cudaSuccess;
+    if (args.Nq <= 0 || args.Nt <= 0) return cudaSuccess;
+    DecideArgs a = args;
+    a.inv_n = 1.0 / a.n;
+    a.inv_nM = 1.0 / ((double)a.n * a.M);
+    a.dalpha = 6.283185307179586 / a.n;
     // 8 signals (16 pairs) per CTA keeps the shared footprint small enough
     // for several CTAs per SM; 4 at n = 1024
     const int nsig = a.n <= 512 ? 8 : 4;

@@ -90,85 +90,98 @@ __device__ __forceinline__ float2 cmul_i(float2 a, int dir)
 // ------------------------------------------------------------------------
 // Batched complex FFT of length n over NSIG signals held in shared memory
 // as buf[k * NSIG + s] (signal s, element k), Stockham self-sorting, mixed
-// radix 2/3/4/5.  dir = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};
-// dir = +1: the unnormalised inverse.  tw[m] = e^{-2 pi i m / n} (shared
+// radix 2/3/4/5.  DIR = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};
+// DIR = +1: the unnormalised inverse.  tw[m] = e^{-2 pi i m / n} (shared
 // memory).  Each stage reads one buffer and writes the other; returns the
 // buffer that holds the result.  Must be called by every thread of the block;
 // ends with a __syncthreads().
-template <int NSIG>
+
+// One stage of radix R: item t = (j, s) takes x[j + i n/R] (i < R), twiddled
+// by w^{i k}, k = j mod Ns, and writes its R outputs at stride Ns from
+// (j div Ns) Ns R + k.
+template <int R, int NSIG, int DIR>
+__device__ __forceinline__ void fft_stage(const float2 *__restrict__ a, float2 *__restrict__ b,
+                                          int n, int Ns, unsigned rcp, int tstep,
+                                          const float2 *__restrict__ tw)
+{
+    const int nr = n / R;
+    const int total = nr * NSIG;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int s = t % NSIG;
+        const int j = t / NSIG;
+        const int jq = Ns == 1 ? j : (int)__umulhi((unsigned)j, rcp);  // j / Ns
+        const int k = j - jq * Ns;
+        float2 v[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            float2 x = a[(j + i * nr) * NSIG + s];
+            if (i > 0 && k > 0) {
+                float2 w = tw[i * k * tstep];  // i k < R Ns, so the index is < n
+                if (DIR > 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[i] = x;
+        }
+        float2 V[R];
+        if (R == 2) {
+            V[0] = cadd(v[0], v[1]);
+            V[1] = csub(v[0], v[1]);
+        } else if (R == 4) {
+            float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+            float2 s13 = cadd(v[1], v[3]), d13 = cmul_i(csub(v[1], v[3]), DIR);
+            V[0] = cadd(s02, s13);
+            V[2] = csub(s02, s13);
+            V[1] = cadd(d02, d13);
+            V[3] = csub(d02, d13);
+        } else if (R == 3) {
+            // w3 = e^{DIR 2 pi i / 3} = -1/2 + DIR i sqrt(3)/2
+            const float c3 = -0.5f, s3 = 0.86602540378443864676f;
+            float2 t1 = cadd(v[1], v[2]);
+            float2 t2 = make_float2(v[0].x + c3 * t1.x, v[0].y + c3 * t1.y);
+            float2 t3 = cmul_i(csub(v[1], v[2]), DIR);
+            t3.x *= s3;
+            t3.y *= s3;
+            V[0] = cadd(v[0], t1);
+            V[1] = cadd(t2, t3);
+            V[2] = csub(t2, t3);
+        } else {  // R == 5
+            const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+            const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+            const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+            const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+            float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+            float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+            float2 r1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+            float2 r2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+            // i1 = DIR*i*(s1 b1 + s2 b2), i2 = DIR*i*(s2 b1 - s1 b2)
+            float2 i1 = cmul_i(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y), DIR);
+            float2 i2 = cmul_i(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y), DIR);
+            V[0] = make_float2(v[0].x + a1.x + a2.x, v[0].y + a1.y + a2.y);
+            V[1] = cadd(r1, i1);
+            V[4] = csub(r1, i1);
+            V[2] = cadd(r2, i2);
+            V[3] = csub(r2, i2);
+        }
+        const int base = jq * Ns * R + k;
+#pragma unroll
+        for (int i = 0; i < R; ++i) b[(base + i * Ns) * NSIG + s] = V[i];
+    }
+}
+
+template <int NSIG, int DIR>
 __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan &plan,
-                                            const float2 *tw, int dir)
+                                            const float2 *tw)
 {
     const int n = plan.n;
     for (int st = 0; st < plan.nst; ++st) {
-        const int r = plan.radix[st];
         const int Ns = plan.ns[st];
         const unsigned rcp = plan.ns_rcp[st];
-        const int nr = n / r;
         const int tstep = plan.tstep[st];
-        const int total = nr * NSIG;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int s = t % NSIG;
-            const int j = t / NSIG;
-            const int jq = Ns == 1 ? j : (int)__umulhi((unsigned)j, rcp);  // j / Ns
-            const int k = j - jq * Ns;
-            float2 v[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                if (i < r) {
-                    float2 x = a[(j + i * nr) * NSIG + s];
-                    if (i > 0 && k > 0) {
-                        float2 w = tw[i * k * tstep];  // i k < r Ns, so the index is < n
-                        if (dir > 0) w.y = -w.y;
-                        x = cmul(x, w);
-                    }
-                    v[i] = x;
-                }
-            }
-            float2 V[5];
-            if (r == 2) {
-                V[0] = cadd(v[0], v[1]);
-                V[1] = csub(v[0], v[1]);
-            } else if (r == 4) {
-                float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-                float2 s13 = cadd(v[1], v[3]), d13 = cmul_i(csub(v[1], v[3]), dir);
-                V[0] = cadd(s02, s13);
-                V[2] = csub(s02, s13);
-                V[1] = cadd(d02, d13);
-                V[3] = csub(d02, d13);
-            } else if (r == 3) {
-                // w3 = e^{dir 2 pi i / 3} = -1/2 + dir i sqrt(3)/2
-                const float c3 = -0.5f, s3 = 0.86602540378443864676f;
-                float2 t1 = cadd(v[1], v[2]);
-                float2 t2 = make_float2(v[0].x + c3 * t1.x, v[0].y + c3 * t1.y);
-                float2 t3 = cmul_i(csub(v[1], v[2]), dir);
-                t3.x *= s3;
-                t3.y *= s3;
-                V[0] = cadd(v[0], t1);
-                V[1] = cadd(t2, t3);
-                V[2] = csub(t2, t3);
-            } else {  // r == 5
-                const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
-                const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
-                const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
-                const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
-                float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
-                float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
-                float2 r1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
-                float2 r2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
-                // i1 = dir*i*(s1 b1 + s2 b2), i2 = dir*i*(s2 b1 - s1 b2)
-                float2 i1 = cmul_i(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y), dir);
-                float2 i2 = cmul_i(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y), dir);
-                V[0] = make_float2(v[0].x + a1.x + a2.x, v[0].y + a1.y + a2.y);
-                V[1] = cadd(r1, i1);
-                V[4] = csub(r1, i1);
-                V[2] = cadd(r2, i2);
-                V[3] = csub(r2, i2);
-            }
-            const int base = jq * Ns * r + k;
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-                if (i < r) b[(base + i * Ns) * NSIG + s] = V[i];
+        switch (plan.radix[st]) {
+        case 4: fft_stage<4, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
+        case 2: fft_stage<2, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
+        case 3: fft_stage<3, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
+        default: fft_stage<5, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
         }
         __syncthreads();
         float2 *tmp = a;
@@ -256,6 +269,8 @@ struct DecideArgs {
     void *out;            // sw_result [Nq][Nt]
     double *curve;        // [n] or NULL (pair 0,0 only)
     double *shifts;       // [n][2] or NULL
+    // filled by launch_decide: 1/n, 1/(nM), 2 pi/n (no FP64 divisions on the device)
+    double inv_n, inv_nM, dalpha;
 };
 cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
                           cudaStream_t st);

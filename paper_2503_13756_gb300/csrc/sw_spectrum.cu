@@ -145,7 +145,7 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
             b0[t] = make_float2(xr, xi);
         }
         __syncthreads();
-        const float2 *R = fft_smem<nsig>(b0, b1, plan, tws, -1);
+        const float2 *R = fft_smem<nsig, -1>(b0, b1, plan, tws);
         // ---- unpack two real spectra per signal, k' = 0..n/2
         for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
             const int kf = t / nsig, s = t % nsig;
