@@ -127,6 +127,30 @@ sw_status sw_profile_read(sw_ctx *ctx, double *ms, int64_t *launches);
 /* Kernels launched through ctx since its creation. */
 int64_t sw_launch_count(const sw_ctx *ctx);
 
+/* Autotuning of launch shapes (no counterpart in the paper: it concerns this
+ * implementation's kernels only).  For the parameter set p, times candidate
+ * values of four launch choices on a trial batch of random images (up to
+ * 1,024 x 64 pairs, ~64 MB of images, within the workspace limit) and keeps
+ * the fastest for every later call on ctx with the same L, n_theta, n_levels,
+ * bins and gemm_precision:
+ *   choice[0] target CTA count of the projection's split over angles,
+ *   choice[1] signals per FFT batch of the angle spectra (4, 8 or 16),
+ *   choice[2] signals per CTA of the decision's inverse FFT (4, 8 or 16),
+ *   choice[3] FFT radix order (0: radix-4 stages first, then 2, 3, 5;
+ *             1: 2, 3, 5 first; 2: radix 4 first, then 5, 3, 2; 3: 5, 3, 2
+ *             first); a value of 0 in choice[0..2] means the built-in default.
+ * None of them changes what is computed; the radix order changes the
+ * rounding only.  cache_path (may be NULL): a text file of lines
+ * "swtune1 <device> L= n= M= B= prec= w s d r"; a matching line is used
+ * without timing, and a new result is appended.  Synchronous (waits for its
+ * own work); allocates trial buffers for the duration of the call.  Banks
+ * keep the choice in force when they were created.  Returns SW_ERR_OOM if the
+ * trial buffers do not fit, SW_ERR_INVALID_ARG if the cache cannot be
+ * written. */
+sw_status sw_autotune(sw_ctx *ctx, const sw_params *p, const char *cache_path);
+/* The choice in force for p on ctx (zeros before sw_autotune). */
+sw_status sw_autotune_get(const sw_ctx *ctx, const sw_params *p, int *choice);
+
 /* Radon projections (Eq. radon_transform, Sec. 2.1; Sec. 2.3 "Computation")
  * of nb images, discretised as a pixel-driven linear splat: the mass of each
  * cell goes to the two bins around s = <(x, y), theta_k>, split linearly.

@@ -3,11 +3,15 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <fstream>
+#include <random>
+#include <sstream>
 #include <mutex>
 #include <new>
 #include <string>
@@ -25,6 +29,7 @@ namespace {
 // k = n/4, n/2, 3n/4 are exactly 0 and +-1 and theta + pi is exactly -theta.
 struct Tables {
     int n = 0;
+    int variant = 0;  // radix order of the FFT plan (fft_plan)
     FftPlan plan{};
     float2 *cs = nullptr;     // [n] (cos, sin) fp32
     double2 *cs64 = nullptr;  // [n] (cos, sin) fp64
@@ -64,21 +69,36 @@ void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
     }
 }
 
-bool fft_plan(int n, FftPlan &p)
+// Mixed-radix plan of length n.  The radix order is free (any order is a
+// valid Stockham factorisation; only the rounding and the speed change):
+// variant 0: radix-4 stages first, then 2, 3, 5; 1: 2, 3, 5 first, then the
+// 4s; 2: the 4s first, then 5, 3, 2; 3: 5, 3, 2 first, then the 4s.
+constexpr int kPlanVariants = 4;
+
+bool fft_plan(int n, FftPlan &p, int variant = 0)
 {
     p.n = n;
     p.nst = 0;
-    int m = n;
-    while (m % 4 == 0 && p.nst < swk::kMaxStages) {
-        p.radix[p.nst++] = 4;
+    int m = n, fours = 0;
+    while (m % 4 == 0) {
+        ++fours;
         m /= 4;
     }
-    const int primes[3] = {2, 3, 5};
-    for (int q : primes)
-        while (m % q == 0 && p.nst < swk::kMaxStages) {
-            p.radix[p.nst++] = q;
+    int rest[swk::kMaxStages], nrest = 0;
+    const bool desc = variant == 2 || variant == 3;
+    const int asc[3] = {2, 3, 5}, dsc[3] = {5, 3, 2};
+    for (int q : desc ? dsc : asc)
+        while (m % q == 0 && nrest < swk::kMaxStages) {
+            rest[nrest++] = q;
             m /= q;
         }
+    if (m != 1 || fours + nrest > swk::kMaxStages) return false;
+    const bool fours_first = variant == 0 || variant == 2;
+    if (!fours_first)
+        for (int i = 0; i < nrest; ++i) p.radix[p.nst++] = rest[i];
+    for (int i = 0; i < fours; ++i) p.radix[p.nst++] = 4;
+    if (fours_first)
+        for (int i = 0; i < nrest; ++i) p.radix[p.nst++] = rest[i];
     int Ns = 1;
     for (int st = 0; st < p.nst; ++st) {
         p.ns[st] = Ns;
@@ -86,7 +106,7 @@ bool fft_plan(int n, FftPlan &p)
         p.tstep[st] = n / (Ns * p.radix[st]);
         Ns *= p.radix[st];
     }
-    return m == 1;
+    return true;
 }
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -178,6 +198,24 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
+// Launch shapes chosen by sw_autotune for one parameter set; 0 = the
+// built-in default.  None of them changes what is computed: the FFT radix
+// order only changes the rounding.
+struct Tune {
+    int want = 0;  // target CTA count of the projection's angle split
+    int spec = 0;  // signals per FFT batch of the spectra (4, 8, 16)
+    int dec = 0;   // signals per CTA of the decision (4, 8, 16)
+    int plan = 0;  // FFT radix order (fft_plan variant)
+};
+
+struct TuneKey {
+    int L, n, M, B, prec;
+    bool operator==(const TuneKey &o) const
+    {
+        return L == o.L && n == o.n && M == o.M && B == o.B && prec == o.prec;
+    }
+};
+
 struct sw_ctx {
     int device = 0;
     int num_sms = 0;
@@ -190,10 +228,13 @@ struct sw_ctx {
     bool prof = false;
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<TuneKey, Tune>> tunes;
+    const Tune *trial = nullptr;  // overrides the lookup (autotuning, banks)
 };
 
 struct sw_bank {
     sw_params p{};
+    Tune tune{};  // launch shapes at creation, kept for every alignment
     int Nt = 0;
     int device = 0;
     char *mem = nullptr;
@@ -305,16 +346,32 @@ sw_status set_device(sw_ctx *c)
     return SW_OK;
 }
 
-sw_status get_tables(sw_ctx *c, int n, const Tables **out)
+TuneKey tune_key(const sw_params *p)
+{
+    return TuneKey{p->L, p->n_theta, p->n_levels, bins_of(p), (int)p->gemm_precision};
+}
+
+Tune tune_of(const sw_ctx *c, const sw_params *p)
+{
+    if (c->trial) return *c->trial;
+    const TuneKey k = tune_key(p);
+    for (const auto &e : c->tunes)
+        if (e.first == k) return e.second;
+    return Tune{};
+}
+
+sw_status get_tables(sw_ctx *c, int n, const Tables **out, int variant = 0)
 {
     for (const Tables &t : c->tables)
-        if (t.n == n) {
+        if (t.n == n && t.variant == variant) {
             *out = &t;
             return SW_OK;
         }
     Tables t;
     t.n = n;
-    if (!fft_plan(n, t.plan)) return fail(c, SW_ERR_INVALID_ARG, "no FFT plan for n=%d", n);
+    t.variant = variant;
+    if (!fft_plan(n, t.plan, variant))
+        return fail(c, SW_ERR_INVALID_ARG, "no FFT plan for n=%d", n);
     std::vector<double> co, si;
     angle_table(n, co, si);
     std::vector<float2> cs(n), tw(n);
@@ -380,7 +437,7 @@ sw_status run_images(sw_ctx *c, const sw_params *p, const Tables *t, const float
     SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                 return swk::launch_project(img, nb, p->L, srcL, nh, B, t->cs,
                                            o.proj + (size_t)img_off * nh * B, 0,
-                                           o.status + img_off, st);
+                                           o.status + img_off, st, tune_of(c, p).want);
             }));
     return SW_OK;
 }
@@ -398,7 +455,7 @@ sw_status run_after_projection(sw_ctx *c, const sw_params *p, const Tables *t, i
                 return swk::launch_spectrum(o.quant, nb, n, M, t->plan, t->tw, o.spec32,
                                             o.fstride, o.lp_kind, o.lp_q, o.lpq_fstride, o.lp_t,
                                             o.lpt_fstride, o.Nq, o.prof, o.center, o.norm32,
-                                            o.norm16, st);
+                                            o.norm16, st, tune_of(c, p).spec);
             }));
     return SW_OK;
 }
@@ -591,8 +648,9 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     const int n = p->n_theta, nh = n / 2, M = p->n_levels;
     const int kind = force_fp32 ? 0 : lp_kind_of(p->gemm_precision);
     const bool lp = kind != 0;
+    const Tune tu = tune_of(c, p);
     const Tables *t;
-    sw_status s = get_tables(c, n, &t);
+    sw_status s = get_tables(c, n, &t, tu.plan);
     if (s) return s;
     const Layout l = batch_layout(p, Nq, Nt, kind, mode == 1);
     if ((s = ensure_ws(c, l.total))) return s;
@@ -657,7 +715,7 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     a.curve = curve;
     a.shifts = shifts;
     SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st,
-                      [&] { return swk::launch_decide(a, t->plan, t->tw, st); }));
+                      [&] { return swk::launch_decide(a, t->plan, t->tw, st, tu.dec); }));
     if (mode == 1)
         SW_CUDA(c, launch(c, SW_STAGE_BEST, st, [&] {
                     return swk::launch_best_template(w + l.scratch, Nq, Nt, out, st);
@@ -721,8 +779,9 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     if (Nt <= 0) return fail(c, SW_ERR_INVALID_ARG, "Nt=%d", Nt);
     if ((s = check_ptr(c, d_t_img, "d_t_img", true))) return s;
     if ((s = set_device(c))) return s;
+    const Tune tu = tune_of(c, p);
     const Tables *t;
-    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    if ((s = get_tables(c, p->n_theta, &t, tu.plan))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
     const int kind = lp_kind_of(p->gemm_precision);
@@ -745,6 +804,7 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     sw_bank *b = new (std::nothrow) sw_bank;
     if (!b) return fail(c, SW_ERR_OOM, "bank descriptor");
     b->p = *p;
+    b->tune = tu;
     b->Nt = Nt;
     b->device = c->device;
     if (cudaMalloc(&b->mem, o) != cudaSuccess) {
@@ -782,8 +842,12 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     io.center = b->center;
     io.norm32 = b->norm32;
     io.norm16 = b->norm16;
-    if ((s = run_images(c, p, t, d_t_img, p->L, Nt, 0, io, st)) ||
-        (s = run_after_projection(c, p, t, Nt, io, st))) {
+    const Tune *prev = c->trial;
+    c->trial = &b->tune;
+    s = run_images(c, p, t, d_t_img, p->L, Nt, 0, io, st);
+    if (!s) s = run_after_projection(c, p, t, Nt, io, st);
+    c->trial = prev;
+    if (s) {
         cudaStreamSynchronize(st);
         cudaFree(b->mem);
         delete b;
@@ -799,10 +863,28 @@ size_t sw_bank_workspace_bytes(const sw_bank *bank, int Nq, int mode)
     return bank_layout(&bank->p, Nq, bank->Nt, mode == 1).total;
 }
 
+static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_q_img, int Nq,
+                                 int q_L, int mode, sw_result *d_out, sw_stream_t stream);
+
 sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, int Nq, int q_L,
                         int mode, sw_result *d_out, sw_stream_t stream)
 {
     if (!c) return SW_ERR_INVALID_ARG;
+    if (!bank) {
+        c->err = "bank is NULL";
+        return SW_ERR_INVALID_ARG;
+    }
+    // the bank's launch shapes (its template spectra used the same FFT plan)
+    const Tune *prev = c->trial;
+    c->trial = &bank->tune;
+    const sw_status s = bank_align_impl(c, bank, d_q_img, Nq, q_L, mode, d_out, stream);
+    c->trial = prev;
+    return s;
+}
+
+static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_q_img, int Nq,
+                                 int q_L, int mode, sw_result *d_out, sw_stream_t stream)
+{
     c->err.clear();
     if (!bank) return fail(c, SW_ERR_INVALID_ARG, "bank is NULL");
     const sw_params *p = &bank->p;
@@ -819,7 +901,7 @@ sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, in
                     c->device);
     if ((s = set_device(c))) return s;
     const Tables *t;
-    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    if ((s = get_tables(c, p->n_theta, &t, bank->tune.plan))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int n = p->n_theta, nh = n / 2, M = p->n_levels, Nt = bank->Nt;
     const int kind = lp_kind_of(p->gemm_precision);
@@ -879,8 +961,9 @@ sw_status sw_bank_align(sw_ctx *c, const sw_bank *bank, const float *d_q_img, in
     a.translation = p->translation;
     a.dev_err = err;
     a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)d_out;
-    SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st,
-                      [&] { return swk::launch_decide(a, t->plan, t->tw, st); }));
+    SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st, [&] {
+                return swk::launch_decide(a, t->plan, t->tw, st, bank->tune.dec);
+            }));
     if (mode == 1)
         SW_CUDA(c, launch(c, SW_STAGE_BEST, st, [&] {
                     return swk::launch_best_template(w + l.scratch, Nq, Nt, d_out, st);
@@ -1065,3 +1148,205 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
 #undef SW_NA
     return SW_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Autotuning (sw_autotune): per parameter set, the projection's CTA split,
+// the FFT batch widths of the spectra and of the decision, and the FFT radix
+// order are chosen by timing candidates on a batch of random images with the
+// stage events of the profiler.  The stages are separate kernels, so each
+// stage's choice is taken from its own time; the radix order is judged by the
+// spectra and decision together (both run the FFT).
+namespace {
+
+struct TrialTimes {
+    double proj = 1e30, spec = 1e30, dec = 1e30;
+};
+
+sw_status run_trial(sw_ctx *c, const sw_params *p, const Tune &tu, const float *dq, int Nq,
+                    const float *dt, int Nt, sw_result *out, cudaStream_t st, TrialTimes &tt)
+{
+    c->trial = &tu;
+    sw_status s = SW_OK;
+    for (int r = 0; r < 4 && s == SW_OK; ++r) {
+        s = align_batch_impl(c, p, dq, Nq, dt, Nt, 0, out, nullptr, nullptr, false, st);
+        double ms[SW_STAGE_COUNT];
+        int64_t cnt[SW_STAGE_COUNT];
+        const sw_status sr = sw_profile_read(c, ms, cnt);  // waits for the events
+        if (s == SW_OK) s = sr;
+        if (s != SW_OK || r == 0) continue;  // the first run warms up
+        tt.proj = std::min(tt.proj, ms[SW_STAGE_PROJECT]);
+        tt.spec = std::min(tt.spec, ms[SW_STAGE_SPECTRUM]);
+        tt.dec = std::min(tt.dec, ms[SW_STAGE_DECIDE]);
+    }
+    c->trial = nullptr;
+    return s;
+}
+
+bool same_plan(const FftPlan &a, const FftPlan &b)
+{
+    if (a.nst != b.nst) return false;
+    for (int i = 0; i < a.nst; ++i)
+        if (a.radix[i] != b.radix[i]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if ((s = set_device(c))) return s;
+    cudaDeviceProp prop;
+    SW_CUDA(c, cudaGetDeviceProperties(&prop, c->device));
+    std::string dev = prop.name;
+    for (char &ch : dev)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    char kb[256];
+    snprintf(kb, sizeof kb, "swtune1 %s L=%d n=%d M=%d B=%d prec=%d", dev.c_str(), p->L,
+             p->n_theta, p->n_levels, bins_of(p), (int)p->gemm_precision);
+    const std::string key = kb;
+    const TuneKey tk = tune_key(p);
+    auto store = [&](const Tune &tu) {
+        for (auto &e : c->tunes)
+            if (e.first == tk) {
+                e.second = tu;
+                return;
+            }
+        c->tunes.push_back({tk, tu});
+    };
+    if (cache_path) {
+        std::ifstream f(cache_path);
+        std::string line;
+        while (std::getline(f, line)) {
+            if (line.size() <= key.size() || line.compare(0, key.size(), key) != 0 ||
+                line[key.size()] != ' ')
+                continue;
+            Tune tu;
+            std::istringstream is(line.substr(key.size()));
+            if (is >> tu.want >> tu.spec >> tu.dec >> tu.plan && tu.want >= 0 && tu.spec >= 0 &&
+                tu.dec >= 0 && tu.plan >= 0 && tu.plan < kPlanVariants) {
+                store(tu);
+                return SW_OK;
+            }
+        }
+    }
+
+    // trial batch: up to 1,024 queries x 64 templates of random images,
+    // at most ~64 MB of images, within the workspace limit
+    const int L = p->L, n = p->n_theta;
+    const int Nt = 64;
+    int Nq = (int)std::min<size_t>(1024, std::max<size_t>(64, (64u << 20) / (4u * L * L)));
+    const int kind = lp_kind_of(p->gemm_precision);
+    while (c->limit && Nq > 1 && batch_layout(p, Nq, Nt, kind, false).total > c->limit) Nq /= 2;
+    const size_t nimg = (size_t)Nq + Nt;
+    std::vector<float> h(nimg * L * L);
+    std::mt19937 rng(20250317u);
+    std::uniform_real_distribution<float> U(0.f, 1.f);
+    for (float &x : h) x = U(rng);
+    float *d_img = nullptr;
+    sw_result *d_out = nullptr;
+    cudaStream_t st = nullptr;
+    auto cleanup = [&] {
+        if (st) cudaStreamSynchronize(st);
+        if (d_img) cudaFree(d_img);
+        if (d_out) cudaFree(d_out);
+        if (st) cudaStreamDestroy(st);
+    };
+    if (cudaMalloc(&d_img, sizeof(float) * h.size()) != cudaSuccess ||
+        cudaMalloc(&d_out, sizeof(sw_result) * (size_t)Nq * Nt) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(c, SW_ERR_OOM, "autotune trial buffers");
+    }
+    if (cudaMemcpy(d_img, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+        cleanup();
+        return fail(c, SW_ERR_CUDA, "autotune upload");
+    }
+    const float *dq = d_img, *dt = d_img + (size_t)Nq * L * L;
+
+    // the profiler's state is the caller's: set it aside
+    const bool was_prof = c->prof;
+    std::vector<ProfRec> saved;
+    saved.swap(c->recs);
+    c->prof = true;
+
+    const int wants[3] = {456, 304, 912};
+    const int widths_small[3] = {16, 8, 4}, widths_large[3] = {8, 4, 4};
+    const int *specs = n <= 512 ? widths_small : widths_large;
+    const int dec_small[3] = {8, 16, 4}, dec_large[3] = {4, 8, 4};
+    const int *decs = n <= 512 ? dec_small : dec_large;
+    TrialTimes t1[3];
+    for (int i = 0; i < 3 && s == SW_OK; ++i) {
+        Tune tu;
+        tu.want = wants[i];
+        tu.spec = specs[i];
+        tu.dec = decs[i];
+        s = run_trial(c, p, tu, dq, Nq, dt, Nt, d_out, st, t1[i]);
+    }
+    Tune best;
+    if (s == SW_OK) {
+        int bw = 0, bs = 0, bd = 0;
+        for (int i = 1; i < 3; ++i) {
+            if (t1[i].proj < t1[bw].proj) bw = i;
+            if (t1[i].spec < t1[bs].spec) bs = i;
+            if (t1[i].dec < t1[bd].dec) bd = i;
+        }
+        best.want = wants[bw];
+        best.spec = specs[bs];
+        best.dec = decs[bd];
+        double best_fft = t1[bs].spec + t1[bd].dec;
+        FftPlan tried[kPlanVariants];
+        fft_plan(n, tried[0], 0);
+        for (int v = 1; v < kPlanVariants && s == SW_OK; ++v) {
+            fft_plan(n, tried[v], v);
+            bool dup = false;
+            for (int u = 0; u < v; ++u) dup = dup || same_plan(tried[u], tried[v]);
+            if (dup) continue;
+            Tune tu = best;
+            tu.plan = v;
+            TrialTimes tv;
+            s = run_trial(c, p, tu, dq, Nq, dt, Nt, d_out, st, tv);
+            if (s == SW_OK && tv.spec + tv.dec < best_fft) {
+                best_fft = tv.spec + tv.dec;
+                best.plan = v;
+            }
+        }
+    }
+    c->trial = nullptr;
+    c->prof = was_prof;
+    c->recs.swap(saved);
+    cleanup();
+    if (s != SW_OK) return s;
+    store(best);
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        if (!f) return fail(c, SW_ERR_INVALID_ARG, "cannot append to %s", cache_path);
+        f << key << ' ' << best.want << ' ' << best.spec << ' ' << best.dec << ' ' << best.plan
+          << '\n';
+    }
+    return SW_OK;
+}
+
+sw_status sw_autotune_get(const sw_ctx *c, const sw_params *p, int *choice)
+{
+    if (!c || !choice) return SW_ERR_INVALID_ARG;
+    if (check_params(nullptr, p) != SW_OK) return SW_ERR_INVALID_ARG;
+    const TuneKey k = tune_key(p);
+    Tune tu;
+    for (const auto &e : c->tunes)
+        if (e.first == k) tu = e.second;
+    choice[0] = tu.want;
+    choice[1] = tu.spec;
+    choice[2] = tu.dec;
+    choice[3] = tu.plan;
+    return SW_OK;
+}
+
+}  // extern "C"

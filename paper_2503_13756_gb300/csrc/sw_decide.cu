@@ -276,7 +276,7 @@ __global__ void k_best_template(const sw_result *__restrict__ all, int Nq, int N
 }  // namespace
 
 cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const float2 *tw,
-                          cudaStream_t st)
+                          cudaStream_t st, int nsig_req)
 {
     if (args.Nq <= 0 || args.Nt <= 0) return cudaSuccess;
     DecideArgs a = args;
@@ -284,17 +284,23 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
     a.inv_nM = 1.0 / ((double)a.n * a.M);
     a.dalpha = 6.283185307179586 / a.n;
     // 8 signals (16 pairs) per CTA keeps the shared footprint small enough
-    // for several CTAs per SM; 4 at n = 1024
-    const int nsig = a.n <= 512 ? 8 : 4;
+    // for several CTAs per SM; 4 at n = 1024.  A requested width is taken
+    // when its buffers fit (2 n nsig complex values).
+    int nsig = a.n <= 512 ? 8 : 4;
+    if ((nsig_req == 4 || nsig_req == 8 || nsig_req == 16) && (size_t)a.n * nsig_req <= 8192)
+        nsig = nsig_req;
     const size_t smem = sizeof(float2) * ((size_t)2 * a.n * nsig + a.n) + sizeof(float) * a.M;
     dim3 grid(a.Nq, (a.Nt + 2 * nsig - 1) / (2 * nsig));  // queries on x (no 65535 cap)
-    if (nsig == 8) {
-        cudaFuncSetAttribute(k_decide<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_decide<8><<<grid, kDecThreads, smem, st>>>(a, plan, tw);
-    } else {
-        cudaFuncSetAttribute(k_decide<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_decide<4><<<grid, kDecThreads, smem, st>>>(a, plan, tw);
-    }
+#define SW_DEC_LAUNCH(NS)                                                                    \
+    do {                                                                                    \
+        cudaFuncSetAttribute(k_decide<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                             200 * 1024);                                                   \
+        k_decide<NS><<<grid, kDecThreads, smem, st>>>(a, plan, tw);                         \
+    } while (0)
+    if (nsig == 16) SW_DEC_LAUNCH(16);
+    else if (nsig == 8) SW_DEC_LAUNCH(8);
+    else SW_DEC_LAUNCH(4);
+#undef SW_DEC_LAUNCH
     return cudaGetLastError();
 }
 

@@ -201,7 +201,7 @@ __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan 
 // cs: [nh] (cos, sin) of theta_k.  status: [nb], 1 for an unusable image.
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
                            const float2 *cs, float *out, int full_n, int32_t *status,
-                           cudaStream_t st);
+                           cudaStream_t st, int want_ctas = 0);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
 //                        : [nb][2nh][B].
@@ -232,7 +232,7 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
                             const float2 *tw, float *spec32, size_t fstride, int lp_kind,
                             void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
                             int Nq, float *prof, double *center, double *norm32,
-                            double *norm16, cudaStream_t st);
+                            double *norm16, cudaStream_t st, int nsig = 0);
 
 // FP32 SIMT correlation: for f < nf, i < Nq, j < Nt
 // C[(f*Nq + i)*Nt + j] = sum_p Qhat_i(f,p) conj(Qhat_j(f,p)) as (re, im).
@@ -273,7 +273,7 @@ struct DecideArgs {
     double inv_n, inv_nM, dalpha;
 };
 cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
-                          cudaStream_t st);
+                          cudaStream_t st, int nsig = 0);
 
 // Best template per query from the [Nq][Nt] results.
 cudaError_t launch_best_template(const void *all, int Nq, int Nt, void *out, cudaStream_t st);

@@ -306,14 +306,15 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
 
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
                            const float2 *cs, float *out, int full_n, int32_t *status,
-                           cudaStream_t st)
+                           cudaStream_t st, int want_ctas)
 {
     if (nb <= 0) return cudaSuccess;
     const int n = 2 * nh;
     if (n % 4 == 0 && L <= kMaxL4) {
-        // canonical angles k = 0..n/8; split over CTAs when the batch is small
+        // canonical angles k = 0..n/8; split over CTAs when the batch is
+        // small.  Default target: ~3 resident CTAs per SM on 152 SMs.
         const int kc = n / 8 + 1;
-        const int want = 456;  // ~3 resident CTAs per SM on 152 SMs
+        const int want = want_ctas > 0 ? want_ctas : 456;
         int groups = nb >= want ? 1 : (want + nb - 1) / nb;
         if (groups > kc) groups = kc;
         const int per = (kc + groups - 1) / groups;

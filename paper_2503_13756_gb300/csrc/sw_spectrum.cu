@@ -260,10 +260,14 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
                             const float2 *tw, float *spec32, size_t fstride, int lp_kind,
                             void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
                             int Nq, float *prof, double *center, double *norm32,
-                            double *norm16, cudaStream_t st)
+                            double *norm16, cudaStream_t st, int nsig_req)
 {
     if (nb <= 0) return cudaSuccess;
-    const int nsig = n <= 512 ? 16 : 8;
+    // signals per FFT batch: 16 by default, 8 at n = 1024; a requested
+    // width is taken when its buffers fit (2 n nsig complex values)
+    int nsig = n <= 512 ? 16 : 8;
+    if ((nsig_req == 4 || nsig_req == 8 || nsig_req == 16) && (size_t)n * nsig_req <= 8192)
+        nsig = nsig_req;
     const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M + n);
     SpecOut o{spec32, fstride, lp_q, lpq_fstride, lp_t, lpt_fstride, Nq, tc_ldk(M),
               lp_kind != 0, lp_kind == 3};
@@ -276,10 +280,12 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
     } while (0)
     if (lp_kind == 2 || lp_kind == 3) {
         if (nsig == 16) SW_SPEC_LAUNCH(__half, 16);
-        else SW_SPEC_LAUNCH(__half, 8);
+        else if (nsig == 8) SW_SPEC_LAUNCH(__half, 8);
+        else SW_SPEC_LAUNCH(__half, 4);
     } else {
         if (nsig == 16) SW_SPEC_LAUNCH(__nv_bfloat16, 16);
-        else SW_SPEC_LAUNCH(__nv_bfloat16, 8);
+        else if (nsig == 8) SW_SPEC_LAUNCH(__nv_bfloat16, 8);
+        else SW_SPEC_LAUNCH(__nv_bfloat16, 4);
     }
 #undef SW_SPEC_LAUNCH
     return cudaGetLastError();

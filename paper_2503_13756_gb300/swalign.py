@@ -53,7 +53,8 @@ EXPORTS = (
     "sw_batch_workspace_bytes", "sw_reserve", "sw_project", "sw_quantiles",
     "sw_align_all_rotations", "sw_align_batch", "sw_bank_create", "sw_bank_align",
     "sw_bank_size", "sw_bank_destroy", "sw_profile", "sw_profile_read", "sw_launch_count",
-    "sw_align_all_rotations_noalloc", "sw_bank_workspace_bytes",
+    "sw_align_all_rotations_noalloc", "sw_bank_workspace_bytes", "sw_autotune",
+    "sw_autotune_get",
 )
 STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best")
 
@@ -87,6 +88,8 @@ def load(path: str | None = None):
                 "sw_launch_count": ([vp], ctypes.c_int64),
                 "sw_align_all_rotations_noalloc": ([P, vp, vp, vp, vp, vp, vp], ci),
                 "sw_bank_workspace_bytes": ([vp, ci, ci], ctypes.c_size_t),
+                "sw_autotune": ([vp, P, ctypes.c_char_p], ci),
+                "sw_autotune_get": ([vp, P, ctypes.POINTER(ci)], ci),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -146,6 +149,19 @@ class Aligner:
         self._check(getattr(self.lib, name)(self.ctx, *args), self.ctx)
 
     # ---------------------------------------------------------------- API
+    def autotune(self, params: Params, cache_path: str | None = None):
+        """Times candidate launch shapes for params and keeps the fastest
+        (sw_autotune); returns the choice (projection CTA target, spectrum
+        width, decision width, FFT radix order)."""
+        path = None if cache_path is None else str(cache_path).encode()
+        self.call("sw_autotune", ctypes.byref(params), path)
+        return self.tune_choice(params)
+
+    def tune_choice(self, params: Params):
+        out = (ctypes.c_int * 4)()
+        self.call("sw_autotune_get", ctypes.byref(params), out)
+        return tuple(int(v) for v in out)
+
     def profile(self, enable: bool):
         self.call("sw_profile", int(bool(enable)))
 

@@ -64,20 +64,36 @@ def draw_mixtures(rng, count, L, ncomp=(3, 3), box_px=None, sigma_px=None):
 
 def _smooth_field(rng, count, L, sigma_px, amp_px):
     """Displacement fields [count][2][L][L]: white noise filtered by a
-    Gaussian of std sigma_px (periodic), scaled so max |d| = amp_px."""
+    Gaussian of std sigma_px (periodic), scaled so max |d| = amp_px.  Chunks
+    of 256 fields draw from their own child generators (spawned in order from
+    rng) and run on a thread pool, so the result does not depend on the
+    number of threads."""
     out = np.zeros((count, 2, L, L), dtype=np.float32)
     if amp_px == 0.0:
         return out
     f = np.fft.fftfreq(L)
     g = np.exp(-2.0 * (np.pi * sigma_px) ** 2 * (f[:, None] ** 2 + f[None, :] ** 2))
     g = g[:, : L // 2 + 1].astype(np.float32)
-    for c0 in range(0, count, 256):
+    starts = list(range(0, count, 256))
+    kids = rng.spawn(len(starts))
+
+    def chunk(c0, kid):
         c1 = min(count, c0 + 256)
-        noise = rng.standard_normal((c1 - c0, 2, L, L), dtype=np.float32)
-        d = _fft.irfft2(_fft.rfft2(noise, **_FFT_KW) * g, s=(L, L), **_FFT_KW)
+        noise = kid.standard_normal((c1 - c0, 2, L, L), dtype=np.float32)
+        d = _fft.irfft2(_fft.rfft2(noise) * g, s=(L, L))
         mag = np.sqrt((d ** 2).sum(axis=1)).reshape(c1 - c0, -1).max(axis=1)
         out[c0:c1] = d * (amp_px / np.maximum(mag, 1e-30))[:, None, None, None]
+
+    _parallel(chunk, zip(starts, kids))
     return out
+
+
+def _parallel(fn, items):
+    import concurrent.futures as cf
+    import os
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        for fut in [ex.submit(fn, *it) for it in items]:
+            fut.result()
 
 
 def render(params, L, idx=None, beta=None, shift=None, warp=None, noise_std=0.0,
@@ -101,8 +117,7 @@ def render(params, L, idx=None, beta=None, shift=None, warp=None, noise_std=0.0,
     def col(a):
         return np.asarray(a, dtype=wt)[:, None, None]
 
-    for c0 in range(0, count, 128):
-        sl = slice(c0, min(count, c0 + 128))
+    def chunk(sl, noise):
         n = sl.stop - sl.start
         px = X[None] - col(shift[sl, 0])
         py = Y[None] - col(shift[sl, 1])
@@ -128,12 +143,26 @@ def render(params, L, idx=None, beta=None, shift=None, warp=None, noise_std=0.0,
             dy = qy - col(params["mu"][ii, j, 1])
             e = pxx * dx * dx + pyy * dy * dy + pxy * dx * dy
             img += col(w) * np.exp(e)
-        if noise_std > 0.0:
-            img += rng.normal(0.0, noise_std, size=img.shape).astype(wt)
+        if noise is not None:
+            img += noise
         np.maximum(img, 0.0, out=img)
         mass = img.reshape(n, -1).sum(axis=1, dtype=np.float64)
         img /= col(np.where(mass > 0, mass, 1.0))
         out[sl] = img
+
+    # chunks of 128 images run on a thread pool (numpy releases the GIL); each
+    # draws its noise from its own child generator, spawned in order from rng
+    starts = list(range(0, count, 128))
+    kids = rng.spawn(len(starts)) if noise_std > 0.0 else [None] * len(starts)
+
+    def run(c0, kid):
+        sl = slice(c0, min(count, c0 + 128))
+        noise = None
+        if kid is not None:
+            noise = kid.normal(0.0, noise_std, size=(sl.stop - sl.start, L, L)).astype(wt)
+        chunk(sl, noise)
+
+    _parallel(run, zip(starts, kids))
     return out
 
 

@@ -296,3 +296,28 @@ def test_many_to_many_full_size_sampled(al):
     l_true = np.round(d["beta"] * n / (2 * np.pi)) % n
     dl = np.abs(((own["best_l"] - l_true) + n / 2) % n - n / 2)
     assert np.mean(dl <= 3) > 0.95
+
+
+def test_one_reference_full_size_sampled(al):
+    """10,000 queries x 1 reference, 128 x 128, n = 512, M = 256, FP32:
+    20 sampled queries against the oracle, and the generated rotation found
+    for nearly all queries."""
+    d = synth.one_reference_batch()
+    q, ref = d["queries"], d["reference"]
+    n, M = 512, 256
+    p = swalign.make_params(128, n, M)
+    res = swalign.results_to_numpy(al.align_batch(q, ref, p)).reshape(len(q))
+    assert np.all(res["status"] == 0)
+    fr = ref[0].astype(np.float64)
+    for i in np.random.default_rng(11).integers(0, len(q), 20):
+        fq = q[i].astype(np.float64)
+        rr, Dref, Sref = oracle.align_pair(fq, fr, n, M)
+        Sc = norm_scale(fq, fr, n, M)
+        gr = res[i]
+        l = int(gr["best_l"])
+        assert check_argmin(l, rr["best_l"], Dref, d2_tol(rr["d2"], Sc)), (i, l, rr["best_l"])
+        assert abs(gr["d2"] - Dref[l]) <= d2_tol(Dref[l], Sc)
+        np.testing.assert_allclose(gr["shift"], Sref[l], rtol=0, atol=1e-6)
+    l_true = np.round(d["beta"] * n / (2 * np.pi)) % n
+    dl = np.abs(((res["best_l"] - l_true) + n / 2) % n - n / 2)
+    assert np.mean(dl <= 3) > 0.95

@@ -1,0 +1,90 @@
+"""Autotuned launch shapes (sw_autotune).
+
+The choice is kept per parameter set and read back from the cache file
+without timing; every candidate launch shape and every FFT radix order gives
+results within the FP32 parity bar of the oracle (the radix order changes the
+rounding only); a bank keeps the shapes it was created with.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_13756_gb300 import swalign
+from tests.test_gpu_parity import blobs, compare_batch, f32
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def al():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    a = swalign.Aligner(0)
+    yield a
+    a.close()
+
+
+def cache_key(al, p):
+    dev = torch.cuda.get_device_name(0).replace(" ", "_").replace("\t", "_")
+    B = p.n_bins or al.default_bins(p.L)
+    return f"swtune1 {dev} L={p.L} n={p.n_theta} M={p.n_levels} B={B} prec={p.gemm_precision}"
+
+
+def test_autotune_keeps_and_caches_its_choice(al, tmp_path):
+    p = swalign.make_params(48, 60, 32)  # n = 60 = 4 * 3 * 5: the radix orders differ
+    cache = tmp_path / "tune.txt"
+    assert al.tune_choice(p) == (0, 0, 0, 0)
+    want, spec, dec, plan = al.autotune(p, cache)
+    assert want in (304, 456, 912) and spec in (4, 8, 16) and dec in (4, 8, 16)
+    assert plan in (0, 1, 2, 3)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith(cache_key(al, p) + " ")
+    # a second context reads the cache and launches nothing
+    b = swalign.Aligner(0)
+    try:
+        n0 = b.launch_count()
+        assert b.autotune(p, cache) == (want, spec, dec, plan)
+        assert b.launch_count() == n0
+        # other parameters are untouched
+        assert b.tune_choice(swalign.make_params(48, 60, 16)) == (0, 0, 0, 0)
+    finally:
+        b.close()
+    assert len(cache.read_text().splitlines()) == 1
+
+
+@pytest.mark.parametrize("n,plan,spec,dec", [
+    (60, 0, 16, 8), (60, 1, 8, 16), (60, 2, 4, 4), (60, 3, 16, 16),
+    (36, 1, 4, 16), (36, 3, 8, 4), (256, 0, 4, 16), (40, 2, 8, 8),
+])
+def test_every_launch_shape_matches_oracle(al, tmp_path, n, plan, spec, dec):
+    rng = np.random.default_rng(n * 10 + plan)
+    L, M = 40, 24
+    q = f32(blobs(rng, 3, L))
+    t = f32(blobs(rng, 5, L))
+    p = swalign.make_params(L, n, M)
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{cache_key(al, p)} 304 {spec} {dec} {plan}\n")
+    assert al.autotune(p, cache) == (304, spec, dec, plan)
+    compare_batch(al, q, t, n=n, M=M)
+
+
+def test_bank_keeps_its_launch_shapes(al, tmp_path):
+    rng = np.random.default_rng(8)
+    L, n, M = 48, 60, 32
+    t = f32(blobs(rng, 9, L))
+    q = f32(blobs(rng, 4, L))
+    p = swalign.make_params(L, n, M)
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{cache_key(al, p)} 456 8 16 3\n")
+    al.autotune(p, cache)
+    bank = swalign.Bank(al, t, p)
+    try:
+        batch = swalign.results_to_numpy(al.align_batch(q, t, p))
+        # retune the context: the bank keeps the shapes it was built with
+        cache.write_text(f"{cache_key(al, p)} 456 16 8 0\n")
+        al.autotune(p, cache)
+        viab = swalign.results_to_numpy(bank.align(q, q_L=L, mode=0))
+        np.testing.assert_array_equal(viab["best_l"], batch["best_l"])
+        np.testing.assert_array_equal(viab["d2"], batch["d2"])
+    finally:
+        bank.close()
