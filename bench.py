@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
@@ -190,7 +192,7 @@ def serving_block(args, device):
     for prec in ("bf16", "fp32"):
         p = swalign.make_params(256, 360, 256, precision=prec)
         eng = serving.ServingEngine(bank["templates"], p, n_slots=3, max_batch_images=512,
-                                    device=device)
+                                    device=device, autotune=not args.no_autotune)
         try:
             warm = serving.make_requests(pool, synth.serving_schedule(8, 1000.0, 64, Lb=256))
             eng.run(warm, realtime=False)
@@ -204,6 +206,54 @@ def serving_block(args, device):
         finally:
             eng.close()
     return out
+
+
+def uneven_block(args, device):
+    """Uneven batch: 20,000 queries with L in {64, 96, 128, 192, 256}
+    (0.3/0.25/0.2/0.15/0.1), 64 templates per size, n = 256, M = L, BF16 GEMM,
+    all sizes in one CUDA graph with autotuned launch shapes.  Device time per
+    graph launch (CUDA events on the graph's stream), and the same calls made
+    eagerly for comparison."""
+    import torch
+
+    from paper_2503_13756_gb300 import synth, uneven
+    batch = synth.uneven_batch()
+    g = uneven.UnevenGraph(uneven.buckets_from(batch, 256, "bf16", device), mode=0,
+                           device=device, autotune=not args.no_autotune)
+    try:
+        st = g.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            g.replay()
+        st.synchronize()
+        reps = 5
+        e0.record(st)
+        for _ in range(reps):
+            g.replay()
+        e1.record(st)
+        e1.synchronize()
+        ms_graph = e0.elapsed_time(e1) / reps
+        e0.record(st)
+        for _ in range(reps):
+            g.run_eager()
+        e1.record(st)
+        e1.synchronize()
+        ms_eager = e0.elapsed_time(e1) / reps
+        res = g.results()
+        ok = all(bool(np.all(r["status"] == 0)) for r in res.values())
+        stages = {int(k): {s_: round(v, 4) for s_, v in d.items()}
+                  for k, d in g.stage_times().items()}
+        return {"workload": "uneven 20,000 queries, L in {64,96,128,192,256}, 64 templates per L, "
+                            "n=256, M=L, BF16 GEMM, one CUDA graph",
+                "pairs": g.pairs, "ms_per_graph": ms_graph, "pairs_per_s": g.pairs / (ms_graph / 1e3),
+                "eager_ms": ms_eager, "kernels_per_graph": g.launches_per_replay,
+                "queries_per_L": {int(b.L): int(b.queries.shape[0]) for b in g.buckets},
+                "stages_ms_per_L": stages,
+                "status_ok": ok}
+    finally:
+        g.close()
+        del g, batch
+        torch.cuda.empty_cache()
 
 
 def run_reference(args, world, rank):
@@ -263,6 +313,7 @@ def main():
     t_h = torch.from_numpy(data["templates"]).pin_memory()
     q_d, t_d = q_h.to(dev), t_h.to(dev)
     out = torch.empty((nq * nt, 40), dtype=torch.uint8, device=dev)
+    tune = None if args.no_autotune else list(al.autotune(p))
     al.reserve(p, nq, nt)
     stream = torch.cuda.current_stream()
 
@@ -298,6 +349,8 @@ def main():
     if args.precision == "fp32" and not args.no_variants:
         for prec in ("bf16", "fp16", "fp32_simt"):
             pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec)
+            if not args.no_autotune:
+                al.autotune(pv)
             al.reserve(pv, nq, nt)
             for _ in range(3):
                 al.align_batch(q_d, t_d, pv, out=out)
@@ -386,6 +439,7 @@ def main():
                 "unit": None, "frac": None, "traffic": None}
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(data)
     serve = None if (args.no_serving or world > 1) else serving_block(args, local)
+    unev = None if (args.no_uneven or world > 1) else uneven_block(args, local)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -400,10 +454,11 @@ def main():
                                    "bf16": "tcgen05 BF16", "fp16": "tcgen05 FP16",
                                    "fp32_simt": "CUDA-core FP32"}[args.precision],
                    "parallelism": f"{world} independent replicas (weak)",
+                   "launch_shapes": tune,
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},
         "roofline": roof, "peaks": peak_src, "stages": per_stage, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-        "variants": variants, "serving": serve,
+        "variants": variants, "serving": serve, "uneven": unev,
     }
     print(json.dumps(line), flush=True)
 

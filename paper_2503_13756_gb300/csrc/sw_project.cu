@@ -182,21 +182,32 @@ k_project(const float *__restrict__ img, int L, int srcL, int nh, int B, int G,
 //   view 3: F[q][L-1-m]    -> angle n/4 + k
 //   view 4: F[m][L-1-q]    -> angle n/2 - k
 // for canonical k with 8k <= n (needs n % 4 == 0).  Duplicates (k = 0, 8k = n)
-// are written once.  The whole image sits in shared memory with a zero
-// border of two cells, so every view reads it in place.
+// are written once.  The image sits in shared memory with a zero border of
+// two cells, so every view reads it in place.
+//
+// BANDED (images too large for shared memory): the CTA holds the rows
+// [r0, r1) of the image only (blockIdx.z = band, two bands).  Its rows give
+// views 1 and 4 of the canonical rows m in the band, and, as rows q of
+// views 2 and 3, their cells' share of every canonical row m; cells outside
+// the band read as zero.  The two bands' partial sums are added into the
+// output (zeroed by the launcher): two addends onto an exact zero give the
+// same sum in either order, so the result stays deterministic.
 constexpr int kMaxL4 = 200;
 
+template <bool BANDED>
 __global__ void __launch_bounds__(kProjThreads)
 k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per, int kc,
            const float2 *__restrict__ cs, float *__restrict__ out, int full_n,
-           int32_t *__restrict__ status)
+           int32_t *__restrict__ status, int band_rows)
 {
     // this CTA's canonical angles: [kc0, kc0 + kcn)
     const int kc0 = blockIdx.x * per;
     const int kcn = min(per, kc - kc0);
     extern __shared__ float tile[];
     const int S = ((L + 2 * kPad) & 1) ? L + 2 * kPad : L + 2 * kPad + 1;
-    const int rowsT = L + 2 * kPad;
+    const int r0 = BANDED ? blockIdx.z * band_rows : 0;
+    const int r1 = BANDED ? min(L, r0 + band_rows) : L;
+    const int rowsT = (r1 - r0) + 2 * kPad;
     __shared__ int s_bad, s_mass;
     const int imgi = blockIdx.y;
     const float *src = img + (size_t)imgi * srcL * srcL;
@@ -204,11 +215,12 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
         s_bad = 0;
         s_mass = 0;
     }
+    __syncthreads();
     int bad = 0, mass = 0;
     for (int idx = threadIdx.x; idx < rowsT * S; idx += blockDim.x) {
-        const int r = idx / S - kPad, c = idx % S - kPad;
+        const int r = idx / S - kPad + r0, c = idx % S - kPad;
         float v = 0.f;
-        if (r >= 0 && r < L && c >= 0 && c < L) {
+        if (r >= r0 && r < r1 && c >= 0 && c < L) {
             if (srcL == L) v = __ldg(src + (size_t)r * L + c);
             else v = 0.25f * __ldg(src + (size_t)(r >> 1) * srcL + (c >> 1));
             if (!isfinite(v)) {
@@ -223,7 +235,10 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
     if (bad) atomicOr(&s_bad, 1);
     if (mass) atomicOr(&s_mass, 1);
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) status[imgi] = (s_bad || !s_mass) ? 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!BANDED) status[imgi] = (s_bad || !s_mass) ? 1 : 0;
+        else if (s_bad) atomicOr(status + imgi, 1);  // no mass: flagged by the quantiles
+    }
 
     const int nh = n / 2, n4 = n / 4;
     const int nrow = full_n ? n : nh;
@@ -235,6 +250,8 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
     const float c0 = 0.5f * (float)(L - 1);
     const float half_B1 = 0.5f * (float)(B - 1);
     float *outi = out + (size_t)imgi * nrow * B;
+    // tile row of image row r (views 1, 4 read rows m; views 2, 3 rows q)
+    const float *trow = tile + (kPad - r0) * S + kPad;
 
     for (int it = warp; it < nitems; it += nwarps) {
         const int k = kc0 + it / ngroups, g = it % ngroups;
@@ -244,9 +261,10 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
         // u(q, m) = q kq + m km + U0 on the canonical frame, q, m in [0, L)
         const float U0 = fmaf(-c0, kq, fmaf(-c0, km, half_B1));
         const float ext = (float)(L - 1) * kq;
-        // rows that can reach bins [b0-1, b0+32]; an empty range still writes
-        // its (zero) bins below
-        int mlo = 0, mhi = L - 1;
+        // rows m that can reach bins [b0-1, b0+32] (views 1, 4: any q; views
+        // 2, 3 in a band: q in [r0, r1)); an empty range still writes its
+        // (zero) bins below
+        int mlo = 0, mhi = L - 1, nlo = 0, nhi = L - 1;
         if (km > 1e-6f) {
             float hi = ((float)b0 + 32.f - U0) / km;
             float lo = ((float)b0 - 1.f - U0 - ext) / km;
@@ -254,39 +272,77 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
             hi = fminf(ceilf(hi) + 1.f, (float)(L - 1));
             mlo = (int)lo;
             mhi = lo > hi ? mlo - 1 : (int)hi;
+            if (BANDED) {
+                float h2 = ((float)b0 + 32.f - U0 - (float)r0 * kq) / km;
+                float l2 = ((float)b0 - 1.f - U0 - (float)(r1 - 1) * kq) / km;
+                l2 = fmaxf(floorf(l2) - 1.f, 0.f);
+                h2 = fminf(ceilf(h2) + 1.f, (float)(L - 1));
+                nlo = (int)l2;
+                nhi = l2 > h2 ? nlo - 1 : (int)h2;
+            }
         } else if (U0 + ext < (float)b0 - 1.f || U0 > (float)b0 + 32.f) {
             mhi = -1;
+            nhi = -1;
         }
+        int m14lo = mlo, m14hi = mhi, m23lo = mlo, m23hi = mhi;
+        if (BANDED) {
+            m14lo = max(mlo, r0);
+            m14hi = min(mhi, r1 - 1);
+            m23lo = max(mlo, nlo);
+            m23hi = min(mhi, nhi);
+        }
+        const int mfrom = min(m14lo, m23lo), mto = max(m14hi, m23hi);
         const int b = b0 + lane;
         const float Ab = fmaf(-c0, kq, half_B1 - (float)b);
         const float invk = 1.f / kq;
         float s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
-        for (int m = mlo; m <= mhi; ++m) {
+        for (int m = mfrom; m <= mto; ++m) {
             const float beta = fmaf((float)m - c0, km, Ab);  // d(q) = q kq + beta
             const float qlo = fmaf(-beta, invk, -invk);       // window (qlo, qlo + 2/kq)
-            float qs = floorf(qlo) + 1.f;
-            qs = fminf(fmaxf(qs, -2.f), (float)(L - 1));
-            const int qi = __float_as_int(qs + 12582912.f) - 0x4B400000;  // exact small int
-            const float d0 = fmaf(qs, kq, beta), d1 = d0 + kq, d2 = d1 + kq;
-            const float w0 = fmaxf(0.f, 1.f - fabsf(d0));
-            const float w1 = fmaxf(0.f, 1.f - fabsf(d1));
-            const float w2 = fmaxf(0.f, 1.f - fabsf(d2));
-            const float *r1 = tile + (m + kPad) * S + (qi + kPad);
-            const float *r2 = tile + (qi + kPad) * S + (m + kPad);
-            const float *r3 = tile + (qi + kPad) * S + (L - 1 - m + kPad);
-            const float *r4 = tile + (m + kPad) * S + (L - 1 - qi + kPad);
-            s1 = fmaf(w0, r1[0], s1);
-            s2 = fmaf(w0, r2[0], s2);
-            s3 = fmaf(w0, r3[0], s3);
-            s4 = fmaf(w0, r4[0], s4);
-            s1 = fmaf(w1, r1[1], s1);
-            s2 = fmaf(w1, r2[S], s2);
-            s3 = fmaf(w1, r3[S], s3);
-            s4 = fmaf(w1, r4[-1], s4);
-            s1 = fmaf(w2, r1[2], s1);
-            s2 = fmaf(w2, r2[2 * S], s2);
-            s3 = fmaf(w2, r3[2 * S], s3);
-            s4 = fmaf(w2, r4[-2], s4);
+            const float qf = floorf(qlo) + 1.f;
+            if (!BANDED || (m >= m14lo && m <= m14hi)) {
+                const float qs = fminf(fmaxf(qf, -2.f), (float)(L - 1));
+                const int qi = __float_as_int(qs + 12582912.f) - 0x4B400000;  // exact small int
+                const float d0 = fmaf(qs, kq, beta), d1 = d0 + kq, d2 = d1 + kq;
+                const float w0 = fmaxf(0.f, 1.f - fabsf(d0));
+                const float w1 = fmaxf(0.f, 1.f - fabsf(d1));
+                const float w2 = fmaxf(0.f, 1.f - fabsf(d2));
+                const float *r1p = trow + m * S + qi;
+                const float *r4p = trow + m * S + (L - 1 - qi);
+                s1 = fmaf(w0, r1p[0], s1);
+                s4 = fmaf(w0, r4p[0], s4);
+                s1 = fmaf(w1, r1p[1], s1);
+                s4 = fmaf(w1, r4p[-1], s4);
+                s1 = fmaf(w2, r1p[2], s1);
+                s4 = fmaf(w2, r4p[-2], s4);
+                if (!BANDED) {  // same cells as rows q: views 2, 3 share the weights
+                    const float *r2p = trow + qi * S + m;
+                    const float *r3p = trow + qi * S + (L - 1 - m);
+                    s2 = fmaf(w0, r2p[0], s2);
+                    s3 = fmaf(w0, r3p[0], s3);
+                    s2 = fmaf(w1, r2p[S], s2);
+                    s3 = fmaf(w1, r3p[S], s3);
+                    s2 = fmaf(w2, r2p[2 * S], s2);
+                    s3 = fmaf(w2, r3p[2 * S], s3);
+                }
+            }
+            if (BANDED && m >= m23lo && m <= m23hi) {
+                // rows q of views 2, 3 clamped to the band's tile rows
+                const float qs = fminf(fmaxf(qf, (float)(r0 - 2)), (float)(r1 - 1));
+                const int qi = __float_as_int(qs + 12582912.f) - 0x4B400000;
+                const float d0 = fmaf(qs, kq, beta), d1 = d0 + kq, d2 = d1 + kq;
+                const float w0 = fmaxf(0.f, 1.f - fabsf(d0));
+                const float w1 = fmaxf(0.f, 1.f - fabsf(d1));
+                const float w2 = fmaxf(0.f, 1.f - fabsf(d2));
+                const float *r2p = trow + qi * S + m;
+                const float *r3p = trow + qi * S + (L - 1 - m);
+                s2 = fmaf(w0, r2p[0], s2);
+                s3 = fmaf(w0, r3p[0], s3);
+                s2 = fmaf(w1, r2p[S], s2);
+                s3 = fmaf(w1, r3p[S], s3);
+                s2 = fmaf(w2, r2p[2 * S], s2);
+                s3 = fmaf(w2, r3p[2 * S], s3);
+            }
         }
         if (b >= B) continue;
         const int angle[4] = {k, n4 - k, n4 + k, nh - k};
@@ -296,8 +352,13 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
         for (int v = 0; v < 4; ++v) {
             if (!keep[v]) continue;
             float *o = outi + (size_t)angle[v] * B;
-            o[b] = val[v];
-            if (full_n) o[(size_t)nh * B + (B - 1 - b)] = val[v];
+            if (BANDED) {
+                atomicAdd(o + b, val[v]);
+                if (full_n) atomicAdd(o + (size_t)nh * B + (B - 1 - b), val[v]);
+            } else {
+                o[b] = val[v];
+                if (full_n) o[(size_t)nh * B + (B - 1 - b)] = val[v];
+            }
         }
     }
 }
@@ -310,21 +371,39 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
 {
     if (nb <= 0) return cudaSuccess;
     const int n = 2 * nh;
-    if (n % 4 == 0 && L <= kMaxL4) {
+    // four-view kernel: the whole image in shared memory up to L = 200;
+    // beyond, two row bands per image while a band fits in 200 KB (L <= 312)
+    const int S4 = ((L + 2 * kPad) & 1) ? L + 2 * kPad : L + 2 * kPad + 1;
+    const int band = (L + 1) / 2;
+    const size_t band_smem = sizeof(float) * (size_t)(band + 2 * kPad) * S4;
+    const bool banded = L > kMaxL4 && band_smem <= 200 * 1024;
+    if (n % 4 == 0 && (L <= kMaxL4 || banded)) {
         // canonical angles k = 0..n/8; split over CTAs when the batch is
         // small.  Default target: ~3 resident CTAs per SM on 152 SMs.
         const int kc = n / 8 + 1;
         const int want = want_ctas > 0 ? want_ctas : 456;
-        int groups = nb >= want ? 1 : (want + nb - 1) / nb;
+        const int nbands = banded ? 2 : 1;
+        int groups = nb * nbands >= want ? 1 : (want + nb * nbands - 1) / (nb * nbands);
         if (groups > kc) groups = kc;
         const int per = (kc + groups - 1) / groups;
         groups = (kc + per - 1) / per;
-        const int S = ((L + 2 * kPad) & 1) ? L + 2 * kPad : L + 2 * kPad + 1;
-        const size_t smem = sizeof(float) * (size_t)(L + 2 * kPad) * S;
-        cudaFuncSetAttribute(k_project4, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        dim3 grid(groups, nb);
-        k_project4<<<grid, kProjThreads, smem, st>>>(img, L, srcL, n, B, per, kc, cs, out, full_n,
-                                                      status);
+        dim3 grid(groups, nb, nbands);
+        if (!banded) {
+            const size_t smem = sizeof(float) * (size_t)(L + 2 * kPad) * S4;
+            cudaFuncSetAttribute(k_project4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            k_project4<false><<<grid, kProjThreads, smem, st>>>(img, L, srcL, n, B, per, kc, cs,
+                                                                out, full_n, status, L);
+        } else {
+            const size_t rows = (size_t)nb * (full_n ? n : nh) * B;
+            cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * rows, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t) * nb, st);
+            if (e != cudaSuccess) return e;
+            cudaFuncSetAttribute(k_project4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            k_project4<true><<<grid, kProjThreads, band_smem, st>>>(img, L, srcL, n, B, per, kc,
+                                                                    cs, out, full_n, status, band);
+        }
         return cudaGetLastError();
     }
     const TileGeom tg = tile_geom(L);

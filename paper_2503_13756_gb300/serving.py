@@ -84,13 +84,16 @@ class ServingEngine:
     """Continuous-batching front end of sw_bank_align."""
 
     def __init__(self, templates, params: swalign.Params, n_slots: int = 3,
-                 max_batch_images: int = 512, device: int = 0, mem_fraction: float = 0.5):
+                 max_batch_images: int = 512, device: int = 0, mem_fraction: float = 0.5,
+                 autotune: bool = False):
         import torch
         torch.cuda.set_device(device)
         self.device = device
         self.params = params
         self.L = params.L
         self.main = swalign.Aligner(device)
+        if autotune:  # the bank keeps the launch shapes in force at its creation
+            self.main.autotune(params)
         self.bank = swalign.Bank(self.main, templates, params)
         self.Nt = self.bank.Nt
         free, _ = torch.cuda.mem_get_info(device)

@@ -68,11 +68,33 @@ class UnevenGraph:
                                 stream=self.torch.cuda.current_stream())
 
     def replay(self):
-        """Runs every bucket once (asynchronously, on the graph's stream)."""
-        self.graph.replay()
+        """Runs every bucket once (asynchronously, on the graph's stream,
+        after the work already queued on the caller's current stream, such as
+        a refill of the inputs)."""
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        with self.torch.cuda.stream(self.stream):
+            self.graph.replay()
+
+    def stage_times(self):
+        """Milliseconds per stage for every size, from one eager pass with
+        the kernel events of the profiler (waits for the device)."""
+        out = {}
+        self.stream.synchronize()
+        self.al.profile(True)
+        self.al.profile_read()
+        try:
+            with self.torch.cuda.stream(self.stream):
+                for b in self.buckets:
+                    self.al.align_batch(b.queries, b.templates, b.params, mode=self.mode,
+                                        out=b.out, stream=self.stream)
+                    out[b.L] = {k: v[0] for k, v in self.al.profile_read().items()}
+        finally:
+            self.al.profile(False)
+        return out
 
     def run_eager(self):
         """The same calls without the graph (for comparison)."""
+        self.stream.wait_stream(self.torch.cuda.current_stream())
         with self.torch.cuda.stream(self.stream):
             self._run_all()
 

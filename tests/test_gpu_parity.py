@@ -38,7 +38,8 @@ def blobs(rng, count, L, ncomp=(2, 4)):
 # ------------------------------------------------------------- projection
 
 @pytest.mark.parametrize("L,n", [(16, 8), (33, 36), (64, 60), (128, 256), (200, 24),  # 4 angles/weight
-                                 (48, 30), (130, 18), (256, 16)])                   # generic, tiled
+                                 (231, 40), (256, 16), (300, 12),                   # two row bands
+                                 (48, 30), (130, 18), (400, 8)])                    # generic, tiled
 def test_project_matches_oracle(al, L, n):
     rng = np.random.default_rng(L * 1000 + n)
     imgs = blobs(rng, 3, L)
@@ -172,13 +173,14 @@ def test_quarter_turn_is_exact(al):
     np.testing.assert_allclose(r["shift"], 0.0, atol=1e-6)
 
 
-def test_status_flags(al):
-    L, n, M = 16, 8, 4
+@pytest.mark.parametrize("L", [16, 256])  # whole image in shared memory; two row bands
+def test_status_flags(al, L):
+    n, M = 8, 4
     rng = np.random.default_rng(1)
     good = f32(blobs(rng, 2, L))
     zero = np.zeros((L, L), np.float32)
     nan = good[0].copy()
-    nan[3, 4] = np.nan
+    nan[L - 3, 4] = np.nan  # in the second band at L = 256
     neg = -good[1]
     q = f32(np.stack([good[0], zero, nan]))
     t = f32(np.stack([good[1], neg]))
