@@ -88,6 +88,16 @@ def _load():
             lib.orc_align_all_pairs.argtypes = [dp, ci, dp, ci, ci, ci, ci, ci, ci,
                                                 ci, ci, ctypes.c_void_p]
             lib.orc_align_all_pairs.restype = ci
+            lib.orc_ramp_filter.argtypes = [dp, ci, ci, dp]
+            lib.orc_ramp_filter.restype = None
+            lib.orc_rfsw_parts.argtypes = [dp, ci, ci, dp, dp]
+            lib.orc_rfsw_parts.restype = None
+            lib.orc_rfsw_curve.argtypes = [dp, dp, ci, ci, ci, dp, dp]
+            lib.orc_rfsw_curve.restype = None
+            lib.orc_align_pair_rfsw.argtypes = lib.orc_align_pair.argtypes
+            lib.orc_align_pair_rfsw.restype = None
+            lib.orc_align_all_pairs_rfsw.argtypes = lib.orc_align_all_pairs.argtypes
+            lib.orc_align_all_pairs_rfsw.restype = ci
             _lib = lib
     return _lib
 
@@ -186,6 +196,86 @@ def align_all_pairs(queries, templates, n: int, M: int, B: int | None = None,
     ok = _load().orc_align_all_pairs(_dp(q), Nq, _dp(t), Nt, L, int(n), int(M), B,
                                      int(level_rule), int(translation), nthreads,
                                      out.ctypes.data)
+    if not ok:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Ramp-filtered sliced W2 (Sec. 2.1 "High-pass filter", Eq.
+# signed_sliced_wasserstein, Eq. discrete_rot_signed_sw2).
+
+def rfsw_bins(L: int) -> int:
+    """Bins of the ramp-filtered path: the smallest even 2/3/5-smooth count at
+    least the default B (the filter is circular on the bin grid, so B is part
+    of the definition; a smooth B lets the CUDA path use its FFT)."""
+    B = default_bins(L)
+    while True:
+        m = B
+        for q in (2, 3, 5):
+            while m % q == 0:
+                m //= q
+        if m == 1 and B % 2 == 0:
+            return B
+        B += 1
+
+
+def ramp_filter(U) -> np.ndarray:
+    """Rows of U filtered by |xi| circularly on the bin grid (plain DFT sums)."""
+    U = _f64(U)
+    rows = U.reshape(-1, U.shape[-1])
+    out = np.empty_like(rows)
+    _load().orc_ramp_filter(_dp(rows), rows.shape[0], rows.shape[1], _dp(out))
+    return out.reshape(U.shape)
+
+
+def rfsw_parts(U) -> tuple[np.ndarray, np.ndarray]:
+    """Positive part and absolute negative part of the filtered rows."""
+    U = _f64(U)
+    rows = U.reshape(-1, U.shape[-1])
+    up, um = np.empty_like(rows), np.empty_like(rows)
+    _load().orc_rfsw_parts(_dp(rows), rows.shape[0], rows.shape[1], _dp(up), _dp(um))
+    return up.reshape(U.shape), um.reshape(U.shape)
+
+
+def rfsw_curve(Qf, Qg, translation: int = 1):
+    """Qf, Qg: [2][n][M] quantiles of the two parts (uncentred).  Returns
+    (D[n], shifts[n][2]) from the definition (s* per rotation)."""
+    Qf, Qg = _f64(Qf), _f64(Qg)
+    _, n, M = Qf.shape
+    D = np.empty(n, dtype=np.float64)
+    S = np.empty((n, 2), dtype=np.float64)
+    _load().orc_rfsw_curve(_dp(Qf), _dp(Qg), n, M, int(translation), _dp(D), _dp(S))
+    return D, S
+
+
+def align_pair_rfsw(f, g, n: int, M: int, B: int | None = None, level_rule: int = 0,
+                    translation: int = 1):
+    """RFSW curve for one pair.  Returns (result dict, D[n], shifts[n][2])."""
+    f, g = _f64(f), _f64(g)
+    L = f.shape[-1]
+    B = rfsw_bins(L) if B is None else int(B)
+    D = np.empty(n, dtype=np.float64)
+    S = np.empty((n, 2), dtype=np.float64)
+    res = OrcResult()
+    _load().orc_align_pair_rfsw(_dp(f), _dp(g), L, int(n), int(M), B, int(level_rule),
+                                int(translation), _dp(D), _dp(S), ctypes.byref(res))
+    out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
+           "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
+    return out, D, S
+
+
+def align_all_pairs_rfsw(queries, templates, n: int, M: int, B: int | None = None,
+                         level_rule: int = 0, translation: int = 1,
+                         nthreads: int | None = None) -> np.ndarray:
+    q, t = _f64(queries), _f64(templates)
+    Nq, Nt, L = q.shape[0], t.shape[0], q.shape[-1]
+    B = rfsw_bins(L) if B is None else int(B)
+    nthreads = os.cpu_count() or 1 if nthreads is None else int(nthreads)
+    out = np.zeros((Nq, Nt), dtype=RESULT_DTYPE)
+    ok = _load().orc_align_all_pairs_rfsw(_dp(q), Nq, _dp(t), Nt, L, int(n), int(M), B,
+                                          int(level_rule), int(translation), nthreads,
+                                          out.ctypes.data)
     if not ok:
         raise MemoryError("oracle allocation failed")
     return out

@@ -479,3 +479,260 @@ int orc_align_all_pairs(const double *queries, int Nq, const double *templates,
     free(imgs); free(Q); free(A); free(ok);
     return 1;
 }
+
+/* ======================================================================
+ * Ramp-filtered sliced W2 (RFSW).  Sec. 2.1 "High-pass filter (optional)"
+ * (Eq. 1d_ift_ramp, Eq. line_decomp) and Eq. signed_sliced_wasserstein;
+ * the appendix on ramp-filtered distances fixes the negative part as the
+ * absolute value max(-mu~, 0) and normalises each part to unit mass.
+ * Discrete form (Eq. discrete_ssw2, Eq. discrete_rot_signed_sw2):
+ *   D(l) = 1/(n M) (|U+ - T_l V+|^2 + |U- - T_l V-|^2)
+ * over the quantiles of the two parts.
+ *
+ * Reading of the discrete filter (the paper filters NUFFT central slices,
+ * which we do not form): each projection row U[0..B) is filtered circularly
+ * on its own bin grid,
+ *   Ut[b] = (1/B) sum_j |xi_j| Uh[j] e^{+2 pi i j b / B},
+ *   Uh[j] = sum_b U[b] e^{-2 pi i j b / B},  |xi_j| = min(j, B - j),
+ * the frequency in cycles per B bins (a constant factor would cancel in the
+ * normalisation of each part).  Plain DFT sums, O(B^2) per row.
+ * ====================================================================== */
+
+/* Ut = ramp-filtered rows of U ([nrows][B] each). */
+void orc_ramp_filter(const double *U, int nrows, int B, double *Ut)
+{
+    double *cs = (double *)malloc(sizeof(double) * B);
+    double *sn = (double *)malloc(sizeof(double) * B);
+    double *re = (double *)malloc(sizeof(double) * B);
+    double *im = (double *)malloc(sizeof(double) * B);
+    for (int m = 0; m < B; ++m) {
+        cs[m] = cos(2.0 * ORC_PI * m / B);
+        sn[m] = sin(2.0 * ORC_PI * m / B);
+    }
+    for (int r = 0; r < nrows; ++r) {
+        const double *u = U + (size_t)r * B;
+        for (int j = 0; j < B; ++j) {
+            double a = 0.0, c = 0.0;
+            for (int b = 0; b < B; ++b) {
+                const int m = (int)(((long long)j * b) % B);
+                a += u[b] * cs[m];
+                c -= u[b] * sn[m];
+            }
+            re[j] = a;
+            im[j] = c;
+        }
+        double *o = Ut + (size_t)r * B;
+        for (int b = 0; b < B; ++b) {
+            double acc = 0.0;
+            for (int j = 0; j < B; ++j) {
+                const int m = (int)(((long long)j * b) % B);
+                const double xi = j < B - j ? j : B - j;
+                acc += xi * (re[j] * cs[m] - im[j] * sn[m]);  /* Re(Uh e^{+i..}) */
+            }
+            o[b] = acc / B;
+        }
+    }
+    free(cs);
+    free(sn);
+    free(re);
+    free(im);
+}
+
+/* Positive part and absolute negative part of the filtered rows. */
+void orc_rfsw_parts(const double *U, int nrows, int B, double *Up, double *Um)
+{
+    double *Ut = (double *)malloc(sizeof(double) * (size_t)nrows * B);
+    orc_ramp_filter(U, nrows, B, Ut);
+    for (size_t i = 0; i < (size_t)nrows * B; ++i) {
+        Up[i] = Ut[i] > 0.0 ? Ut[i] : 0.0;
+        Um[i] = Ut[i] < 0.0 ? -Ut[i] : 0.0;
+    }
+    free(Ut);
+}
+
+/* Per image: prepare, project, filter, split, and the quantiles of both
+ * parts (uncentred): Q = [2][n][M] (part 0 positive, part 1 negative).  A
+ * part with no mass at some angle (only for an image without mass) makes
+ * the image unusable.  Returns 0 then. */
+static int orc_rfsw_transform(const orc_cfg *cfg, const double *img, double *Q)
+{
+    const int L = cfg->L, n = cfg->n, M = cfg->M, B = cfg->B;
+    double *F = (double *)malloc(sizeof(double) * (size_t)L * L);
+    double *U = (double *)malloc(sizeof(double) * (size_t)n * B);
+    double *Up = (double *)malloc(sizeof(double) * (size_t)n * B);
+    double *Um = (double *)malloc(sizeof(double) * (size_t)n * B);
+    int ok = orc_prepare(img, L, F) > 0.0;
+    if (ok) {
+        orc_project(F, L, n, B, U);
+        orc_rfsw_parts(U, n, B, Up, Um);
+        ok = orc_quantiles(Up, n, B, 2.0 / L, M, cfg->level_rule, Q);
+        ok &= orc_quantiles(Um, n, B, 2.0 / L, M, cfg->level_rule, Q + (size_t)n * M);
+    }
+    free(F);
+    free(U);
+    free(Up);
+    free(Um);
+    return ok;
+}
+
+/* RFSW squared distance over the rotation grid from its definition.  With
+ * w+-_pk = Qf+-[k][p] - Qg+-[(k-l) mod n][p] (parts + and -):
+ *   translation 0:  D(l) = 1/(nM) sum_parts sum_k sum_p w^2;
+ *   translation 1:  one translation s of the whole image adds <s, e_k> to
+ *     every quantile of column k of both parts, so
+ *       D(l) = min_s 1/(nM) sum_parts sum_k sum_p (w_pk - <s, e_k>)^2.
+ *     Setting the gradient to zero with sum_k e_k e_k^T = (n/2) I gives
+ *     s*(l) = (c+ + c-)/2, c = (2/n) sum_k (mean_p w_pk) e_k per part; D(l)
+ *     is then evaluated at s*(l) by the same triple sum.
+ * shifts[l] (may be NULL) = s*(l), or 0 without translation. */
+void orc_rfsw_curve(const double *Qf, const double *Qg, int n, int M, int translation,
+                    double *D, double *shifts)
+{
+    const double inv = 1.0 / ((double)n * M);
+    for (int l = 0; l < n; ++l) {
+        double s[2] = {0.0, 0.0};
+        if (translation) {
+            for (int part = 0; part < 2; ++part) {
+                const double *qf = Qf + (size_t)part * n * M, *qg = Qg + (size_t)part * n * M;
+                for (int k = 0; k < n; ++k) {
+                    const int kg = ((k - l) % n + n) % n;
+                    double wbar = 0.0;
+                    for (int p = 0; p < M; ++p) wbar += qf[(size_t)k * M + p] - qg[(size_t)kg * M + p];
+                    wbar /= M;
+                    double ct, st;
+                    orc_direction(k, n, &ct, &st);
+                    s[0] += wbar * ct;
+                    s[1] += wbar * st;
+                }
+            }
+            /* (c+ + c-)/2 with c = (2/n) sum_k wbar_k e_k */
+            s[0] *= 1.0 / n;
+            s[1] *= 1.0 / n;
+        }
+        double acc = 0.0;
+        for (int part = 0; part < 2; ++part) {
+            const double *qf = Qf + (size_t)part * n * M, *qg = Qg + (size_t)part * n * M;
+            for (int k = 0; k < n; ++k) {
+                const int kg = ((k - l) % n + n) % n;
+                double ct, st;
+                orc_direction(k, n, &ct, &st);
+                const double off = s[0] * ct + s[1] * st;
+                for (int p = 0; p < M; ++p) {
+                    const double d = qf[(size_t)k * M + p] - qg[(size_t)kg * M + p] - off;
+                    acc += d * d;
+                }
+            }
+        }
+        D[l] = acc * inv;
+        if (shifts) {
+            shifts[2 * l] = s[0];
+            shifts[2 * l + 1] = s[1];
+        }
+    }
+}
+
+static void orc_rfsw_decide(const double *D, const double *S, int n, orc_result *res)
+{
+    int best = 0;
+    for (int l = 1; l < n; ++l)
+        if (D[l] < D[best]) best = l;
+    res->best_l = best;
+    res->status = 0;
+    res->angle = 2.0 * ORC_PI * best / n;
+    res->shift[0] = S[2 * best];
+    res->shift[1] = S[2 * best + 1];
+    res->d2 = D[best];
+}
+
+/* One pair under RFSW; arguments as orc_align_pair (B must be the bin count
+ * the filter runs on). */
+void orc_align_pair_rfsw(const double *f, const double *g, int L, int n, int M, int B,
+                         int level_rule, int translation, double *D, double *shifts,
+                         orc_result *res)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    double *Qf = (double *)malloc(sizeof(double) * 2 * (size_t)n * M);
+    double *Qg = (double *)malloc(sizeof(double) * 2 * (size_t)n * M);
+    double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Sl = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    const int okf = orc_rfsw_transform(&cfg, f, Qf);
+    const int okg = orc_rfsw_transform(&cfg, g, Qg);
+    if (!okf || !okg) {
+        orc_bad(res, okf ? 2 : 1);
+        if (D) for (int l = 0; l < n; ++l) D[l] = NAN;
+        if (shifts) for (int l = 0; l < 2 * n; ++l) shifts[l] = NAN;
+    } else {
+        orc_rfsw_curve(Qf, Qg, n, M, translation, Dl, Sl);
+        orc_rfsw_decide(Dl, Sl, n, res);
+        if (D) memcpy(D, Dl, sizeof(double) * (size_t)n);
+        if (shifts) memcpy(shifts, Sl, sizeof(double) * 2 * (size_t)n);
+    }
+    free(Qf);
+    free(Qg);
+    free(Dl);
+    free(Sl);
+}
+
+static void *orc_rfsw_image_worker(void *arg)
+{
+    orc_job *job = (orc_job *)arg;
+    const orc_cfg *c = job->cfg;
+    for (int i; (i = orc_take(job, job->nimg)) >= 0;)
+        job->ok[i] = orc_rfsw_transform(c, job->imgs + (size_t)i * c->L * c->L,
+                                        job->Q + 2 * (size_t)i * c->n * c->M);
+    return NULL;
+}
+
+static void *orc_rfsw_pair_worker(void *arg)
+{
+    orc_job *job = (orc_job *)arg;
+    const orc_cfg *c = job->cfg;
+    double *D = (double *)malloc(sizeof(double) * c->n);
+    double *S = (double *)malloc(sizeof(double) * 2 * c->n);
+    for (int w; (w = orc_take(job, job->Nq * job->Nt)) >= 0;) {
+        const int i = w / job->Nt, j = job->Nq + w % job->Nt;
+        orc_result *res = job->out + w;
+        if (!job->ok[i]) { orc_bad(res, 1); continue; }
+        if (!job->ok[j]) { orc_bad(res, 2); continue; }
+        orc_rfsw_curve(job->Q + 2 * (size_t)i * c->n * c->M, job->Q + 2 * (size_t)j * c->n * c->M,
+                       c->n, c->M, c->translation, D, S);
+        orc_rfsw_decide(D, S, c->n, res);
+    }
+    free(D);
+    free(S);
+    return NULL;
+}
+
+/* All pairs under RFSW; arguments as orc_align_all_pairs. */
+int orc_align_all_pairs_rfsw(const double *queries, int Nq, const double *templates,
+                             int Nt, int L, int n, int M, int B, int level_rule,
+                             int translation, int nthreads, orc_result *out)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    const int nimg = Nq + Nt;
+    double *imgs = (double *)malloc(sizeof(double) * (size_t)nimg * L * L);
+    double *Q = (double *)malloc(sizeof(double) * 2 * (size_t)nimg * n * M);
+    int *ok = (int *)malloc(sizeof(int) * (size_t)nimg);
+    if (!imgs || !Q || !ok) {
+        free(imgs); free(Q); free(ok);
+        return 0;
+    }
+    memcpy(imgs, queries, sizeof(double) * (size_t)Nq * L * L);
+    memcpy(imgs + (size_t)Nq * L * L, templates, sizeof(double) * (size_t)Nt * L * L);
+    orc_job job;
+    memset(&job, 0, sizeof(job));
+    job.cfg = &cfg;
+    job.imgs = imgs;
+    job.Q = Q;
+    job.ok = ok;
+    job.nimg = nimg;
+    job.Nq = Nq;
+    job.Nt = Nt;
+    job.out = out;
+    pthread_mutex_init(&job.mu, NULL);
+    orc_run(&job, orc_rfsw_image_worker, nthreads);
+    orc_run(&job, orc_rfsw_pair_worker, nthreads);
+    pthread_mutex_destroy(&job.mu);
+    free(imgs); free(Q); free(ok);
+    return 1;
+}
