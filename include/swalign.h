@@ -64,6 +64,20 @@ typedef enum {
     SW_PREC_FP32_SIMT = 3  /* correlation in FP32 on the CUDA cores                    */
 } sw_precision;
 
+/* Distance between two images. */
+typedef enum {
+    SW_METRIC_SW2 = 0,   /* sliced 2-Wasserstein of the projections (Eq.          */
+                         /* sliced_wasserstein_2, discrete Eq. discrete_sw2)       */
+    SW_METRIC_RFSW2 = 1  /* ramp-filtered sliced 2-Wasserstein (Sec. 2.1 "High-    */
+                         /* pass filter", Eq. signed_sliced_wasserstein, discrete  */
+                         /* Eq. discrete_ssw2): each projection row is filtered by */
+                         /* |xi| circularly on its bin grid, split into its        */
+                         /* positive part and absolute negative part, each         */
+                         /* normalised; the squared distance is the sum of the two */
+                         /* parts' sliced W2^2 (1/(n M) with M levels per part).   */
+                         /* One translation moves both parts: s* = (c+ + c-)/2.    */
+} sw_metric;
+
 typedef struct {
     int32_t L;              /* image side, 2..512                                   */
     int32_t n_theta;        /* n: even, 4..1024, factors 2, 3, 5 only               */
@@ -74,6 +88,10 @@ typedef struct {
                             /* only (the paper's Eq. discrete_rot_sw2)              */
     int32_t level_rule;     /* 0 = midpoints (p+1/2)/M, 1 = p/M (App. A, Thm. E3)   */
     int32_t gemm_precision; /* sw_precision, used by sw_align_batch / sw_bank_align */
+    int32_t metric;         /* sw_metric (0 = sliced W2).  RFSW2: the default bin   */
+                            /* count is the smallest even 2/3/5-smooth count >= the */
+                            /* default B (the filter's FFT length), an explicit     */
+                            /* n_bins must be 2/3/5-smooth, n_levels <= 512         */
 } sw_params;
 
 typedef struct {
@@ -114,6 +132,7 @@ typedef enum {
     SW_STAGE_CORR = 3,      /* per-frequency correlation GEMM           */
     SW_STAGE_DECIDE = 4,    /* inverse FFT + argmin + FP64 distance     */
     SW_STAGE_BEST = 5,      /* best template per query                  */
+    SW_STAGE_RAMP = 6,      /* ramp filter + split (RFSW2)              */
     SW_STAGE_COUNT = 8
 } sw_stage;
 
@@ -166,7 +185,10 @@ sw_status sw_project(sw_ctx *ctx, const sw_params *p, const float *d_img, int nb
  *   d_q      [nb][n][M] float32 (output): d_q[i][k][p] = Q_k(z_p), uncentred
  *   d_center [nb][2] double (output, may be NULL): a = (2/n) sum_k ubar_k theta_k,
  *            the centring vector (= the translation-optimal offset)
- *   d_norm   [nb] double (output, may be NULL): sum_k sum_p (Q_k(z_p) - <a, theta_k>)^2 */
+ *   d_norm   [nb] double (output, may be NULL): sum_k sum_p (Q_k(z_p) - <a, theta_k>)^2
+ * With metric RFSW2 every row is first ramp-filtered and split (see sw_metric):
+ * d_q is [nb][2][n][M] (positive part, then absolute negative part), d_center
+ * [nb][2][2] and d_norm [nb][2], per part. */
 sw_status sw_quantiles(sw_ctx *ctx, const sw_params *p, const float *d_proj, int nb,
                        float *d_q, double *d_center, double *d_norm, sw_stream_t stream);
 

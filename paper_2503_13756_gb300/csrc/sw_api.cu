@@ -113,11 +113,32 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Offsets of the batch workspace.
 struct Layout {
-    size_t status, proj, quant, spec32, lp_q, lp_t, prof, center, norm32, norm16, C, scratch,
-        err, total;
+    size_t status, proj, ramp, quant, spec32, lp_q, lp_t, prof, center, norm32, norm16, C,
+        scratch, err, total;
 };
 
-int bins_of(const sw_params *p) { return p->n_bins > 0 ? p->n_bins : sw_default_bins(p->L); }
+bool smooth235(int n);
+
+// Ramp-filtered sliced W2: the filter is circular on the bin grid, so the
+// default bin count is the smallest even 2/3/5-smooth count >= the default
+// B (the FFT's lengths).
+int rfsw_default_bins(int L)
+{
+    int B = sw_default_bins(L);
+    while (B % 2 || !smooth235(B)) ++B;
+    return B;
+}
+
+int bins_of(const sw_params *p)
+{
+    if (p->n_bins > 0) return p->n_bins;
+    return p->metric == SW_METRIC_RFSW2 ? rfsw_default_bins(p->L) : sw_default_bins(p->L);
+}
+
+// Quantile sets per image: 2 for the ramp-filtered distance (positive and
+// negative parts), stored one after the other as levels [0, M) and [M, 2M).
+int parts_of(const sw_params *p) { return p->metric == SW_METRIC_RFSW2 ? 2 : 1; }
+int levels_of(const sw_params *p) { return p->n_levels * parts_of(p); }
 
 // Low-precision spectra kind of a precision: 3 = FP16 split (FP32-accurate
 // tensor-core path), 1 = BF16, 2 = FP16, 0 = none (CUDA-core FP32).
@@ -134,7 +155,8 @@ int lp_kind_of(int precision)
 Layout batch_layout(const sw_params *p, int Nq, int Nt, int lp_kind, bool scratch)
 {
     const size_t nimg = (size_t)Nq + Nt;
-    const size_t n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    const size_t n = p->n_theta, nh = n / 2, M = levels_of(p), B = bins_of(p);
+    const size_t parts = parts_of(p);
     Layout l{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -145,12 +167,13 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, int lp_kind, bool scratc
     const size_t row = lp_kind ? (size_t)swk::lp_row_len((int)M, lp_kind) : 0;
     l.status = take(4 * nimg);
     l.proj = take(4 * nimg * nh * B);
+    l.ramp = take(parts == 2 ? 4 * nimg * 2 * nh * B : 0);
     l.quant = take(4 * nimg * n * M);
     l.spec32 = take(lp_kind ? 0 : 4 * nh * nimg * 2 * M);
     l.lp_q = take(2 * nh * (size_t)Nq * row);
     l.lp_t = take(2 * nh * (size_t)2 * Nt * row);
     l.prof = take(4 * nimg * M);
-    l.center = take(16 * nimg);
+    l.center = take(16 * parts * nimg);
     l.norm32 = take(8 * nimg);
     l.norm16 = take(8 * nimg);
     l.C = take(8 * nh * (size_t)Nq * Nt);
@@ -164,7 +187,8 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, int lp_kind, bool scratc
 // Nq queries against Nt bank templates.
 Layout bank_layout(const sw_params *p, int Nq, int Nt, bool scratch)
 {
-    const size_t n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    const size_t n = p->n_theta, nh = n / 2, M = levels_of(p), B = bins_of(p);
+    const size_t parts = parts_of(p);
     const int lp_kind = lp_kind_of(p->gemm_precision);
     const size_t row = lp_kind ? (size_t)swk::lp_row_len((int)M, lp_kind) : 0;
     Layout l{};
@@ -176,12 +200,13 @@ Layout bank_layout(const sw_params *p, int Nq, int Nt, bool scratch)
     };
     l.status = take(4 * (size_t)Nq);
     l.proj = take(4 * (size_t)Nq * nh * B);
+    l.ramp = take(parts == 2 ? 4 * (size_t)Nq * 2 * nh * B : 0);
     l.quant = take(4 * (size_t)Nq * n * M);
     l.spec32 = take(lp_kind ? 0 : 4 * nh * (size_t)Nq * 2 * M);
     l.lp_q = take(2 * nh * (size_t)Nq * row);
     l.lp_t = take(0);
     l.prof = take(4 * (size_t)Nq * M);
-    l.center = take(16 * (size_t)Nq);
+    l.center = take(16 * parts * (size_t)Nq);
     l.norm32 = take(8 * (size_t)Nq);
     l.norm16 = take(8 * (size_t)Nq);
     l.C = take(8 * nh * (size_t)Nq * Nt);
@@ -320,6 +345,15 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
         return fail(c, SW_ERR_INVALID_ARG, "level_rule must be 0 or 1");
     if (p->gemm_precision < SW_PREC_FP32 || p->gemm_precision > SW_PREC_FP32_SIMT)
         return fail(c, SW_ERR_INVALID_ARG, "gemm_precision=%d unknown", p->gemm_precision);
+    if (p->metric != SW_METRIC_SW2 && p->metric != SW_METRIC_RFSW2)
+        return fail(c, SW_ERR_INVALID_ARG, "metric=%d unknown", p->metric);
+    if (p->metric == SW_METRIC_RFSW2) {
+        if (p->n_bins != 0 && !smooth235(p->n_bins))
+            return fail(c, SW_ERR_INVALID_ARG,
+                        "n_bins=%d: the ramp filter needs a 2/3/5-smooth bin count", p->n_bins);
+        if (p->n_levels > 512)
+            return fail(c, SW_ERR_INVALID_ARG, "n_levels=%d: at most 512 per part", p->n_levels);
+    }
     return SW_OK;
 }
 
@@ -417,6 +451,7 @@ sw_status ensure_ws(sw_ctx *c, size_t bytes)
 struct ImageOut {
     int32_t *status;
     float *proj;  // scratch [nb][nh][B]
+    float *ramp;  // scratch [nb][2][nh][B] (ramp-filtered parts), or NULL
     float *quant; // scratch [nb][n][M]
     float *spec32;
     size_t fstride;
@@ -447,15 +482,31 @@ sw_status run_after_projection(sw_ctx *c, const sw_params *p, const Tables *t, i
 {
     const int L = p->L, n = p->n_theta, M = p->n_levels, B = bins_of(p);
     const float h = 2.0f / (float)L;
-    SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
-                return swk::launch_quantiles(o.proj, nb, n, B, M, h, p->level_rule, 1, o.quant,
-                                             o.status, st);
-            }));
+    const int parts = parts_of(p);
+    if (parts == 2) {
+        // ramp filter and split, then the quantiles of both parts (rows
+        // 2 img + part, their status folded onto the image)
+        const Tables *tb;
+        sw_status s = get_tables(c, B, &tb);
+        if (s) return s;
+        SW_CUDA(c, launch(c, SW_STAGE_RAMP, st, [&] {
+                    return swk::launch_ramp(o.proj, nb, n / 2, B, tb->plan, tb->tw, o.ramp, st);
+                }));
+        SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                    return swk::launch_quantiles(o.ramp, 2 * nb, n, B, M, h, p->level_rule, 1,
+                                                 o.quant, o.status, st, 1);
+                }));
+    } else {
+        SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                    return swk::launch_quantiles(o.proj, nb, n, B, M, h, p->level_rule, 1,
+                                                 o.quant, o.status, st);
+                }));
+    }
     SW_CUDA(c, launch(c, SW_STAGE_SPECTRUM, st, [&] {
-                return swk::launch_spectrum(o.quant, nb, n, M, t->plan, t->tw, o.spec32,
+                return swk::launch_spectrum(o.quant, nb, n, M * parts, t->plan, t->tw, o.spec32,
                                             o.fstride, o.lp_kind, o.lp_q, o.lpq_fstride, o.lp_t,
                                             o.lpt_fstride, o.Nq, o.prof, o.center, o.norm32,
-                                            o.norm16, st, tune_of(c, p).spec);
+                                            o.norm16, st, tune_of(c, p).spec, parts);
             }));
     return SW_OK;
 }
@@ -576,6 +627,7 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if ((s = set_device(c))) return s;
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t))) return s;
+    if (parts_of(p) == 2 && (s = get_tables(c, bins_of(p), &t))) return s;
     return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);
 }
 
@@ -619,18 +671,30 @@ sw_status sw_quantiles(sw_ctx *c, const sw_params *p, const float *d_proj, int n
     if ((s = set_device(c))) return s;
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t))) return s;
-    if ((s = ensure_ws(c, align_up(4 * (size_t)nb)))) return s;
+    const int n = p->n_theta, B = bins_of(p), parts = parts_of(p);
+    const size_t ramp_bytes = parts == 2 ? 4 * (size_t)nb * 2 * n * B : 0;
+    if ((s = ensure_ws(c, align_up(4 * (size_t)nb) + ramp_bytes))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     int32_t *status = at<int32_t>(c->ws, 0);
     SW_CUDA(c, cudaMemsetAsync(status, 0, 4 * (size_t)nb, st));
+    const float *rows = d_proj;
+    if (parts == 2) {  // ramp-filtered parts: rows 2 img + part
+        const Tables *tb;
+        if ((s = get_tables(c, B, &tb))) return s;
+        float *ramp = at<float>(c->ws, align_up(4 * (size_t)nb));
+        SW_CUDA(c, launch(c, SW_STAGE_RAMP, st, [&] {
+                    return swk::launch_ramp(d_proj, nb, n, B, tb->plan, tb->tw, ramp, st);
+                }));
+        rows = ramp;
+    }
     SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
-                return swk::launch_quantiles(d_proj, nb, p->n_theta, bins_of(p), p->n_levels,
+                return swk::launch_quantiles(rows, parts * nb, n, B, p->n_levels,
                                              2.0f / (float)p->L, p->level_rule, 0, d_q, status,
-                                             st);
+                                             st, parts == 2 ? 1 : 0);
             }));
     if (d_center || d_norm)
         SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
-                    return swk::launch_center_norm(d_q, nb, p->n_theta, p->n_levels, t->cs64,
+                    return swk::launch_center_norm(d_q, parts * nb, n, p->n_levels, t->cs64,
                                                    d_center, d_norm, st);
                 }));
     return SW_OK;
@@ -645,7 +709,7 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
                            const float *dt, int Nt, int mode, sw_result *out, double *curve,
                            double *shifts, bool force_fp32, cudaStream_t st)
 {
-    const int n = p->n_theta, nh = n / 2, M = p->n_levels;
+    const int n = p->n_theta, nh = n / 2, M = levels_of(p);
     const int kind = force_fp32 ? 0 : lp_kind_of(p->gemm_precision);
     const bool lp = kind != 0;
     const Tune tu = tune_of(c, p);
@@ -660,6 +724,7 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     ImageOut o{};
     o.status = at<int32_t>(w, l.status);
     o.proj = at<float>(w, l.proj);
+    o.ramp = at<float>(w, l.ramp);
     o.quant = at<float>(w, l.quant);
     o.spec32 = lp ? nullptr : at<float>(w, l.spec32);
     o.fstride = (size_t)nimg * 2 * M;
@@ -697,10 +762,11 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     a.Nt = Nt;
     a.n = n;
     a.M = M;
+    a.parts = parts_of(p);
     a.prof_q = o.prof;
     a.prof_t = o.prof + (size_t)Nq * M;
     a.ctr_q = o.center;
-    a.ctr_t = o.center + 2 * (size_t)Nq;
+    a.ctr_t = o.center + 2 * (size_t)a.parts * Nq;
     // the split path approximates the FP32 product: FP32 norms; BF16/FP16: the
     // norms of the rounded spectra, so that self-distances cancel
     const double *nrm = (kind == 1 || kind == 2) ? o.norm16 : o.norm32;
@@ -783,7 +849,8 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t, tu.plan))) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const int n = p->n_theta, nh = n / 2, M = p->n_levels, B = bins_of(p);
+    const int n = p->n_theta, nh = n / 2, M = levels_of(p), B = bins_of(p);
+    const int parts = parts_of(p);
     const int kind = lp_kind_of(p->gemm_precision);
     const bool lp = kind != 0;
     const int row = lp ? swk::lp_row_len(M, kind) : 0;
@@ -797,7 +864,7 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     const size_t o_spec = take(lp ? 0 : 4 * (size_t)nh * Nt * 2 * M);
     const size_t o_lp = take(2 * (size_t)nh * 2 * Nt * row);
     const size_t o_prof = take(4 * (size_t)Nt * M);
-    const size_t o_ctr = take(16 * (size_t)Nt);
+    const size_t o_ctr = take(16 * (size_t)parts * Nt);
     const size_t o_n32 = take(8 * (size_t)Nt);
     const size_t o_n16 = take(8 * (size_t)Nt);
     const size_t o_st = take(4 * (size_t)Nt);
@@ -819,8 +886,10 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     b->norm32 = at<double>(b->mem, o_n32);
     b->norm16 = at<double>(b->mem, o_n16);
     b->status = at<int32_t>(b->mem, o_st);
-    // projections and quantiles pass through the context workspace
-    const size_t need = align_up(4 * (size_t)Nt * nh * B) + align_up(4 * (size_t)Nt * n * M);
+    // projections, ramp-filtered parts and quantiles pass through the
+    // context workspace
+    const size_t need = align_up(4 * (size_t)Nt * nh * B) + align_up(4 * (size_t)Nt * n * M) +
+                        (parts == 2 ? align_up(4 * (size_t)Nt * 2 * nh * B) : 0);
     if ((s = ensure_ws(c, need))) {
         cudaFree(b->mem);
         delete b;
@@ -830,6 +899,9 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     io.status = b->status;
     io.proj = at<float>(c->ws, 0);
     io.quant = at<float>(c->ws, align_up(4 * (size_t)Nt * nh * B));
+    io.ramp = parts == 2 ? at<float>(c->ws, align_up(4 * (size_t)Nt * nh * B) +
+                                                align_up(4 * (size_t)Nt * n * M))
+                         : nullptr;
     io.spec32 = b->spec32;
     io.fstride = (size_t)Nt * 2 * M;
     io.lp_kind = kind;
@@ -903,7 +975,7 @@ static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t, bank->tune.plan))) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const int n = p->n_theta, nh = n / 2, M = p->n_levels, Nt = bank->Nt;
+    const int n = p->n_theta, nh = n / 2, M = levels_of(p), Nt = bank->Nt;
     const int kind = lp_kind_of(p->gemm_precision);
     const bool lp = kind != 0;
     const Layout l = bank_layout(p, Nq, Nt, mode == 1);
@@ -913,6 +985,7 @@ static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_
     ImageOut o{};
     o.status = at<int32_t>(w, l.status);
     o.proj = at<float>(w, l.proj);
+    o.ramp = at<float>(w, l.ramp);
     o.quant = at<float>(w, l.quant);
     o.spec32 = lp ? nullptr : at<float>(w, l.spec32);
     o.fstride = (size_t)Nq * 2 * M;
@@ -948,6 +1021,7 @@ static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_
     a.Nt = Nt;
     a.n = n;
     a.M = M;
+    a.parts = parts_of(p);
     a.prof_q = o.prof;
     a.prof_t = bank->prof;
     a.ctr_q = o.center;
@@ -1036,6 +1110,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
                                                     sw_stream_t stream)
 {
     if (check_params(nullptr, p) != SW_OK) return SW_ERR_INVALID_ARG;
+    if (p->metric != SW_METRIC_SW2) return SW_ERR_UNSUPPORTED;  // sliced W2 only
     if (!d_f || !d_g || !d_best || !aligned16(d_f) || !aligned16(d_g) || !aligned16(d_best) ||
         ((uintptr_t)d_D & 7) || ((uintptr_t)d_shift & 7))
         return SW_ERR_INVALID_ARG;

@@ -23,6 +23,25 @@ namespace {
 
 constexpr int kDecThreads = 256;
 
+// Centre of image idx for the decision: parts = 1: (a, 0); parts = 2 (two
+// parts with vectors a+ and a-, centre array [..][2][2]): abar = (a+ + a-)/2
+// (the joint translation is s* = abar_i - R abar_j) and d = a+ - a-.
+__device__ __forceinline__ void centre_of(const double *ctr, int idx, int parts, double &ax,
+                                          double &ay, double &dx, double &dy)
+{
+    if (parts == 1) {
+        ax = ctr[2 * idx];
+        ay = ctr[2 * idx + 1];
+        dx = dy = 0.0;
+    } else {
+        const double *c = ctr + 4 * (size_t)idx;
+        ax = 0.5 * (c[0] + c[2]);
+        ay = 0.5 * (c[1] + c[3]);
+        dx = c[0] - c[2];
+        dy = c[1] - c[3];
+    }
+}
+
 template <int nsig>
 __global__ void __launch_bounds__(kDecThreads)
 k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
@@ -107,33 +126,49 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     // ---- argmin over l (FP32 keys, lowest l on ties).  Thread (s, lq) scans
     // l = lq, lq + LQ, ... for both pairs of signal s: a warp then reads 32
     // consecutive complex values (conflict-free).
-    const double nM = (double)n * M;
-    const double aix = A.ctr_q[2 * i], aiy = A.ctr_q[2 * i + 1];
+    // the distance's M is the levels per part (parts = 2: ramp-filtered)
+    const double nM = (double)n * (M / A.parts);
+    double aix, aiy, dix, diy;
+    centre_of(A.ctr_q, i, A.parts, aix, aiy, dix, diy);
     const float invn = 1.f / (float)n;
     constexpr int LQ = kDecThreads / nsig;
     const int s = threadIdx.x % nsig, lq = threadIdx.x / nsig;
     float best0 = __int_as_float(0x7f800000), best1 = best0;
     int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
-    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;  // a_j of the two pairs (rotation only)
-    if (!A.translation) {
+    // rotation-dependent terms of the two pairs: rc |abar_i - R abar_j|^2
+    // (rotation only) and xc |d_i - R d_j|^2 (two parts)
+    const bool rot_t = !A.translation, x_t = A.parts == 2;
+    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ex0 = 0.f, ey0 = 0.f, ex1 = 0.f, ey1 = 0.f;
+    if (rot_t || x_t) {
         const int ja = min(j0 + 2 * s, Nt - 1), jb = min(j0 + 2 * s + 1, Nt - 1);
-        ax0 = (float)A.ctr_t[2 * ja];
-        ay0 = (float)A.ctr_t[2 * ja + 1];
-        ax1 = (float)A.ctr_t[2 * jb];
-        ay1 = (float)A.ctr_t[2 * jb + 1];
+        double x, y, u, v;
+        centre_of(A.ctr_t, ja, A.parts, x, y, u, v);
+        ax0 = (float)x, ay0 = (float)y, ex0 = (float)u, ey0 = (float)v;
+        centre_of(A.ctr_t, jb, A.parts, x, y, u, v);
+        ax1 = (float)x, ay1 = (float)y, ex1 = (float)u, ey1 = (float)v;
     }
-    const float hnm = 0.5f * (float)nM;
+    const float hnm = (A.parts == 2 ? 1.f : 0.5f) * (float)nM;
+    const float qnm = 0.25f * (float)nM;
     for (int l = lq; l < n; l += LQ) {
         const float2 z = R[l * nsig + s];
         float k0 = -2.f * z.x * invn, k1 = -2.f * z.y * invn;
-        if (!A.translation) {
+        if (rot_t || x_t) {
             const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
             const float c = w.x, sn = -w.y;
-            float sx = (float)aix - (c * ax0 - sn * ay0), sy = (float)aiy - (sn * ax0 + c * ay0);
-            k0 = fmaf(hnm, sx * sx + sy * sy, k0);
-            sx = (float)aix - (c * ax1 - sn * ay1);
-            sy = (float)aiy - (sn * ax1 + c * ay1);
-            k1 = fmaf(hnm, sx * sx + sy * sy, k1);
+            if (rot_t) {
+                float sx = (float)aix - (c * ax0 - sn * ay0), sy = (float)aiy - (sn * ax0 + c * ay0);
+                k0 = fmaf(hnm, sx * sx + sy * sy, k0);
+                sx = (float)aix - (c * ax1 - sn * ay1);
+                sy = (float)aiy - (sn * ax1 + c * ay1);
+                k1 = fmaf(hnm, sx * sx + sy * sy, k1);
+            }
+            if (x_t) {
+                float sx = (float)dix - (c * ex0 - sn * ey0), sy = (float)diy - (sn * ex0 + c * ey0);
+                k0 = fmaf(qnm, sx * sx + sy * sy, k0);
+                sx = (float)dix - (c * ex1 - sn * ey1);
+                sy = (float)diy - (sn * ex1 + c * ey1);
+                k1 = fmaf(qnm, sx * sx + sy * sy, k1);
+            }
         }
         if (k0 < best0) { best0 = k0; bl0 = l; }   // l increases: ties keep the lowest
         if (k1 < best1) { best1 = k1; bl1 = l; }
@@ -170,7 +205,8 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
             }
             if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
             const int sg = pr >> 1, comp = pr & 1;
-            const double ajx = A.ctr_t[2 * j], ajy = A.ctr_t[2 * j + 1];
+            double ajx, ajy, djx, djy;
+            centre_of(A.ctr_t, j, A.parts, ajx, ajy, djx, djy);
             const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
             const int st = A.st_q[i] ? 1 : (stt[pr] ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
             sw_result r;
@@ -188,8 +224,13 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 double sx = aix - (c.x * ajx - c.y * ajy);
                 double sy = aiy - (c.y * ajx + c.x * ajy);
                 double d = (base - 2.0 * corr) * A.inv_nM;
+                if (x_t) {
+                    const double ex = dix - (c.x * djx - c.y * djy);
+                    const double ey = diy - (c.y * djx + c.x * djy);
+                    d += 0.25 * (ex * ex + ey * ey);
+                }
                 if (!A.translation) {
-                    d += 0.5 * (sx * sx + sy * sy);
+                    d += (A.parts == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
                     sx = sy = 0.0;
                 }
                 r.best_l = bl;
@@ -205,7 +246,8 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     }
     // ---- full curve of pair (0, 0) (single-pair call)
     if (A.curve && i == 0 && j0 == 0) {
-        const double ajx = A.ctr_t[0], ajy = A.ctr_t[1];
+        double ajx, ajy, djx, djy;
+        centre_of(A.ctr_t, 0, A.parts, ajx, ajy, djx, djy);
         const double base = (double)delta[0] + A.norm_q[0] + A.norm_t[0];
         const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
         for (int l = threadIdx.x; l < n; l += blockDim.x) {
@@ -214,8 +256,13 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
             double sx = aix - (c.x * ajx - c.y * ajy);
             double sy = aiy - (c.y * ajx + c.x * ajy);
             double d = (base - 2.0 * corr) * A.inv_nM;
+            if (x_t) {
+                const double ex = dix - (c.x * djx - c.y * djy);
+                const double ey = diy - (c.y * djx + c.x * djy);
+                d += 0.25 * (ex * ex + ey * ey);
+            }
             if (!A.translation) {
-                d += 0.5 * (sx * sx + sy * sy);
+                d += (A.parts == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
                 sx = sy = 0.0;
             }
             A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
@@ -280,8 +327,9 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
 {
     if (args.Nq <= 0 || args.Nt <= 0) return cudaSuccess;
     DecideArgs a = args;
+    if (a.parts != 1 && (a.parts != 2 || a.M % 2)) return cudaErrorInvalidValue;
     a.inv_n = 1.0 / a.n;
-    a.inv_nM = 1.0 / ((double)a.n * a.M);
+    a.inv_nM = 1.0 / ((double)a.n * (a.M / a.parts));
     a.dalpha = 6.283185307179586 / a.n;
     // 8 signals (16 pairs) per CTA keeps the shared footprint small enough
     // for several CTAs per SM; 4 at n = 1024.  A requested width is taken

@@ -205,10 +205,18 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
 //                        : [nb][2nh][B].
-// q: [nb][n][M].  status: [nb], OR-ed with 1 when a projection has no mass.
+// q: [nb][n][M].  status[r >> status_shift] is OR-ed with 1 when a
+// projection of row r has no mass (status_shift 1: two rows per image).
 cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, float h,
                              int level_rule, int half, float *q, int32_t *status,
-                             cudaStream_t st);
+                             cudaStream_t st, int status_shift = 0);
+
+// Ramp filter and split of the projections (ramp-filtered sliced W2):
+// proj [nb][nh][B] -> parts [nb][2][nh][B] (positive part, absolute negative
+// part) of the rows filtered circularly by |xi| on the bin grid.  plan and
+// tw are the FFT plan and twiddles of length B (2/3/5-smooth).
+cudaError_t launch_ramp(const float *proj, int nb, int nh, int B, const FftPlan &plan,
+                        const float2 *tw, float *parts, cudaStream_t st);
 
 // Centring vector and centred norm of quantiles (public sw_quantiles):
 // a = (2/n) sum_k ubar_k theta_k, norm = sum (q - <a, theta_k>)^2.
@@ -228,11 +236,14 @@ cudaError_t launch_center_norm(const float *q, int nb, int n, int M, const doubl
 // queries [hi | hi | lo], templates [hi | lo | hi] (of the same [re|im|0] and
 // [-im|re|0] rows), so that one GEMM over K = 3 ldk sums hi*hi + hi*lo + lo*hi.
 // With lp_kind != 0, spec32 is not written (may be NULL).
+// parts = 2 (ramp-filtered distance): M counts the levels of both parts,
+// q is [nb][2][n][M/2], each part is centred by its own vector and center
+// is [nb][2][2]; the norms are the sums over both parts.
 cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan &plan,
                             const float2 *tw, float *spec32, size_t fstride, int lp_kind,
                             void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
                             int Nq, float *prof, double *center, double *norm32,
-                            double *norm16, cudaStream_t st, int nsig = 0);
+                            double *norm16, cudaStream_t st, int nsig = 0, int parts = 1);
 
 // FP32 SIMT correlation: for f < nf, i < Nq, j < Nt
 // C[(f*Nq + i)*Nt + j] = sum_p Qhat_i(f,p) conj(Qhat_j(f,p)) as (re, im).
@@ -269,6 +280,11 @@ struct DecideArgs {
     void *out;            // sw_result [Nq][Nt]
     double *curve;        // [n] or NULL (pair 0,0 only)
     double *shifts;       // [n][2] or NULL
+    // 1: sliced W2 (ctr [N][2]); 2: ramp-filtered sliced W2, M counts the
+    // levels of both parts and ctr is [N][2][2] (a+, a-); the distance adds
+    // |d_i - R d_j|^2 / 4, d = a+ - a-, and the rotation-only term is
+    // |abar_i - R abar_j|^2 with abar = (a+ + a-)/2 (derivation in the oracle)
+    int parts = 1;
     // filled by launch_decide: 1/n, 1/(nM), 2 pi/n (no FP64 divisions on the device)
     double inv_n, inv_nM, dalpha;
 };

@@ -22,7 +22,8 @@ constexpr int kQThreads = 256;  // 8 warps = 8 projections per block
 
 __global__ void __launch_bounds__(kQThreads)
 k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int level_rule,
-            int half, int mirror_out, float *__restrict__ q, int32_t *__restrict__ status)
+            int half, int mirror_out, float *__restrict__ q, int32_t *__restrict__ status,
+            int status_shift)
 {
     extern __shared__ float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -83,7 +84,7 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
             float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
             for (int p = lane; p < M; p += 32) qm[p] = __int_as_float(0x7fc00000);
         }
-        if (lane == 0) atomicOr(status + imgi, 1);
+        if (lane == 0) atomicOr(status + (imgi >> status_shift), 1);
         return;
     }
     const float dz = level_rule == 0 ? 2.f * M : (float)M;
@@ -203,7 +204,7 @@ __global__ void k_center_norm(const float *__restrict__ q, int n, int M,
 
 cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, float h,
                              int level_rule, int half, float *q, int32_t *status,
-                             cudaStream_t st)
+                             cudaStream_t st, int status_shift)
 {
     if (nb <= 0) return cudaSuccess;
     const int nw = kQThreads / 32;
@@ -216,7 +217,7 @@ cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, flo
     cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid((nang + nw - 1) / nw, nb);
     k_quantiles<<<grid, kQThreads, smem, st>>>(proj, n, B, M, h, level_rule, half, mirror, q,
-                                                status);
+                                                status, status_shift);
     return cudaGetLastError();
 }
 

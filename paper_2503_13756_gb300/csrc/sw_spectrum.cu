@@ -117,8 +117,12 @@ template <typename T, int nsig>
 __global__ void __launch_bounds__(kSpecThreads)
 k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2 *__restrict__ tw,
            SpecOut o, float *__restrict__ prof, double *__restrict__ center,
-           double *__restrict__ norm32, double *__restrict__ norm16)
+           double *__restrict__ norm32, double *__restrict__ norm16, int parts)
 {
+    // M levels in all; with parts = 2 (ramp-filtered distance) the levels
+    // [0, M/2) and [M/2, M) are the quantiles of the positive and negative
+    // parts, stored as [parts][n][M/2], and each part is centred by its own
+    // vector.
     extern __shared__ float2 smc[];
     float2 *b0 = smc;
     float2 *b1 = b0 + n * nsig;
@@ -126,7 +130,8 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     float2 *tws = x1 + M;        // [n] twiddles
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __shared__ double red[2][kSpecThreads / 32];
-    __shared__ double s_c1[2];
+    __shared__ double s_c1[2][2];
+    const int Mp = M / parts;  // levels per part
     const int img = blockIdx.x;
     const float *qi = q + (size_t)img * n * M;
     const int nh = n / 2;
@@ -140,8 +145,15 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
         for (int t = threadIdx.x; t < n * nsig; t += blockDim.x) {
             const int k = t / nsig, s = t % nsig;
             const int p = p0 + 2 * s;
-            const float xr = p < M ? qi[(size_t)k * M + p] : 0.f;
-            const float xi = p + 1 < M ? qi[(size_t)k * M + p + 1] : 0.f;
+            float xr = 0.f, xi = 0.f;
+            if (parts == 1) {
+                if (p < M) xr = qi[(size_t)k * M + p];
+                if (p + 1 < M) xi = qi[(size_t)k * M + p + 1];
+            } else {
+                if (p < M) xr = qi[(size_t)(p / Mp) * n * Mp + (size_t)k * Mp + p % Mp];
+                if (p + 1 < M)
+                    xi = qi[(size_t)((p + 1) / Mp) * n * Mp + (size_t)k * Mp + (p + 1) % Mp];
+            }
             b0[t] = make_float2(xr, xi);
         }
         __syncthreads();
@@ -174,10 +186,10 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
         }
         __syncthreads();
     }
-    // ---- centring: c1 = mean_p Qhat_u(1, p);  a = (2/n)(Re c1, -Im c1)
-    {
+    // ---- centring, per part: c1 = mean_p Qhat_u(1, p);  a = (2/n)(Re c1, -Im c1)
+    for (int part = 0; part < parts; ++part) {
         double cr = 0.0, ci = 0.0;
-        for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        for (int p = part * Mp + threadIdx.x; p < (part + 1) * Mp; p += blockDim.x) {
             cr += x1[p].x;
             ci += x1[p].y;
         }
@@ -198,15 +210,17 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
                 sr += red[0][w];
                 si += red[1][w];
             }
-            s_c1[0] = sr / M;
-            s_c1[1] = si / M;
-            center[2 * img] = 2.0 * s_c1[0] / n;
-            center[2 * img + 1] = -2.0 * s_c1[1] / n;
+            s_c1[part][0] = sr / Mp;
+            s_c1[part][1] = si / Mp;
+            double *cimg = center + 2 * ((size_t)img * parts + part);
+            cimg[0] = 2.0 * s_c1[part][0] / n;
+            cimg[1] = -2.0 * s_c1[part][1] / n;
         }
         __syncthreads();
     }
-    const float c1r = (float)s_c1[0], c1i = (float)s_c1[1];
     for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        const int part = p / Mp;
+        const float c1r = (float)s_c1[part][0], c1i = (float)s_c1[part][1];
         const float2 X = make_float2(x1[p].x - c1r, x1[p].y - c1i);
         emit<T>(o, img, M, 1, p, X, 2.f, acc32, acc16);  // n >= 4: k' = 1 < n/2
     }
@@ -260,8 +274,9 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
                             const float2 *tw, float *spec32, size_t fstride, int lp_kind,
                             void *lp_q, size_t lpq_fstride, void *lp_t, size_t lpt_fstride,
                             int Nq, float *prof, double *center, double *norm32,
-                            double *norm16, cudaStream_t st, int nsig_req)
+                            double *norm16, cudaStream_t st, int nsig_req, int parts)
 {
+    if (parts != 1 && (parts != 2 || M % 2)) return cudaErrorInvalidValue;
     if (nb <= 0) return cudaSuccess;
     // signals per FFT batch: 16 by default, 8 at n = 1024; a requested
     // width is taken when its buffers fit (2 n nsig complex values)
@@ -276,7 +291,7 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
         cudaFuncSetAttribute(k_spectrum<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                              200 * 1024);                                                       \
         k_spectrum<T, NS><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, o, prof, center,  \
-                                                          norm32, norm16);                      \
+                                                          norm32, norm16, parts);               \
     } while (0)
     if (lp_kind == 2 || lp_kind == 3) {
         if (nsig == 16) SW_SPEC_LAUNCH(__half, 16);

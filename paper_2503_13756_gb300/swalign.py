@@ -8,6 +8,7 @@ or no GPU is present, the calls raise.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -29,14 +30,37 @@ assert RESULT_DTYPE.itemsize == 40
 class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
                 ("L", "n_theta", "n_levels", "n_bins", "translation", "level_rule",
-                 "gemm_precision")]
+                 "gemm_precision", "metric")]
+
+
+METRIC = {"sw2": 0, "rfsw2": 1}
 
 
 def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
-                precision="fp32") -> Params:
+                precision="fp32", metric="sw2") -> Params:
     prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    met = METRIC[metric] if isinstance(metric, str) else int(metric)
     return Params(int(L), int(n_theta), int(n_levels), int(n_bins), int(translation),
-                  int(level_rule), prec)
+                  int(level_rule), prec, met)
+
+
+def bins_of(params: Params) -> int:
+    """Bin count B the library uses for params (sw_params.n_bins, else the
+    default; the ramp-filtered metric rounds the default up to an even
+    2/3/5-smooth count)."""
+    if params.n_bins:
+        return int(params.n_bins)
+    L = int(params.L)
+    B = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2 if L >= 1 else 0
+    if params.metric == METRIC["rfsw2"]:
+        def smooth(m):
+            for q in (2, 3, 5):
+                while m % q == 0:
+                    m //= q
+            return m == 1
+        while B % 2 or not smooth(B):
+            B += 1
+    return B
 
 
 class SwError(RuntimeError):
@@ -56,7 +80,7 @@ EXPORTS = (
     "sw_align_all_rotations_noalloc", "sw_bank_workspace_bytes", "sw_autotune",
     "sw_autotune_get",
 )
-STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best")
+STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best", "ramp")
 
 
 def load(path: str | None = None):
@@ -188,7 +212,7 @@ class Aligner:
         import torch
         x = _f32(imgs, self.torch_device)
         nb = x.shape[0]
-        B = params.n_bins or self.default_bins(params.L)
+        B = bins_of(params)
         if out is None:
             out = torch.empty((nb, params.n_theta, B), dtype=torch.float32, device=x.device)
         self.call("sw_project", ctypes.byref(params), _ptr(x), nb, _ptr(out), _stream(stream))
@@ -198,10 +222,11 @@ class Aligner:
         import torch
         x = _f32(proj, self.torch_device)
         nb = x.shape[0]
-        q = torch.empty((nb, params.n_theta, params.n_levels), dtype=torch.float32,
+        parts = (2,) if params.metric == METRIC["rfsw2"] else ()
+        q = torch.empty((nb, *parts, params.n_theta, params.n_levels), dtype=torch.float32,
                         device=x.device)
-        center = torch.empty((nb, 2), dtype=torch.float64, device=x.device)
-        norm = torch.empty((nb,), dtype=torch.float64, device=x.device)
+        center = torch.empty((nb, *parts, 2), dtype=torch.float64, device=x.device)
+        norm = torch.empty((nb, *parts), dtype=torch.float64, device=x.device)
         self.call("sw_quantiles", ctypes.byref(params), _ptr(x), nb, _ptr(q), _ptr(center),
                   _ptr(norm), _stream(stream))
         return q, center, norm

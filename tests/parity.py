@@ -40,6 +40,43 @@ def norm_scale(f, g, n, M, level_rule=0):
     return tot / (n * M)
 
 
+def norm_scale_rfsw(f, g, n, M, B, level_rule=0):
+    """S for the ramp-filtered distance: both parts' centred norms."""
+    tot = 0.0
+    for img in (f, g):
+        F, mass = oracle.prepare(img)
+        if mass <= 0:
+            return np.nan
+        for part in oracle.rfsw_parts(oracle.project(F, n, B)):
+            Q = oracle.quantiles(part, 2.0 / F.shape[0], M, level_rule)
+            _, Qc = oracle.center(Q)
+            tot += float((Qc ** 2).sum())
+    return tot / (n * M)
+
+
+# Quantiles of the ramp-filtered parts are checked in CDF space: the FP32
+# FFT filter leaves an absolute error of at most (2 ceil(log2 B) + 2) u
+# max|Ut| in every filtered bin (u = 2^-24, forward and inverse transform),
+# so the part's normalised CDF is off by at most B times that over its mass
+# T; a GPU quantile q must then sit at a level F_ref(q) within that of its
+# own level z_p.  (A bar on q itself would be unbounded where a part is thin:
+# the negative part's tails hold ~1e-3 of the peak per bin.)  The distances,
+# which average over levels and angles, stay within the FP32 bar above.
+def rfsw_level_tol(Ut_row, part_row):
+    B = Ut_row.size
+    gamma = (2 * np.ceil(np.log2(B)) + 2) * 2.0 ** -24
+    return B * gamma * np.abs(Ut_row).max() / part_row.sum()
+
+
+def level_of(q, part_row, h):
+    """The oracle's normalised CDF of a part row at positions q (nodes
+    e_j = (j - B/2) h, linear in between)."""
+    B = part_row.size
+    F = np.concatenate([[0.0], np.cumsum(part_row)]) / part_row.sum()
+    e = (np.arange(B + 1) - 0.5 * B) * h
+    return np.interp(q, e, F)
+
+
 ABS_FLOOR = 1e-12
 
 
@@ -56,3 +93,4 @@ def check_argmin(l_gpu, l_ref, D_ref, tol):
     if l_gpu == l_ref:
         return True
     return D_ref[l_gpu] - D_ref[l_ref] <= tol
+

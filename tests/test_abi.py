@@ -36,13 +36,23 @@ def test_result_struct_layout():
     # double shift[2], double d2 -> 40 bytes, d2 at offset 32
     assert swalign.RESULT_DTYPE.itemsize == 40
     assert swalign.RESULT_DTYPE.fields["d2"][1] == 32
-    assert ctypes.sizeof(swalign.Params) == 28
+    assert ctypes.sizeof(swalign.Params) == 32
+
+
+def test_params_fields_follow_the_header():
+    with open(os.path.join(ROOT, "include", "swalign.h")) as fh:
+        text = fh.read()
+    body = text[text.index("typedef struct {\n    int32_t L;"):text.index("} sw_params;")]
+    fields = re.findall(r"int32_t\s+(\w+);", body)
+    assert fields == [f[0] for f in swalign.Params._fields_]
 
 
 def test_default_bins_agree_with_oracle():
     lib = swalign.load()
     for L in [2, 3, 16, 39, 64, 85, 96, 128, 192, 256, 512]:
         assert lib.sw_default_bins(L) == oracle.default_bins(L)
+        p = swalign.make_params(L, 8, 4, metric="rfsw2")
+        assert swalign.bins_of(p) == oracle.rfsw_bins(L)
 
 
 def test_workspace_size_is_host_computable():
