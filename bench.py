@@ -36,8 +36,9 @@ WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
 PROJ_FLOPS_PER_CELL_ANGLE = 8           # s = <x, e> (FMA), frac, 1-t, two FMA accumulations
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the four-angle projection kernel, from one ncu capture of its 2048-image
-# launch (266,798,080 bytes); None once that kernel changes.
-PROJ_DRAM_BYTES_PER_IMAGE = 266798080 / 2048
+# launch (266,622,208 bytes; profiles/k_project4_many_to_many_2048x64.md);
+# None once that kernel changes.
+PROJ_DRAM_BYTES_PER_IMAGE = 266622208 / 2048
 CORR_FLOPS_PER_PAIR_FREQ = 8 * M_LEVELS  # complex multiply-add per level
 
 
@@ -53,6 +54,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--metric", default="sw2", choices=["sw2", "rfsw2"],
+                    help="distance of the main workload (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
@@ -308,7 +311,7 @@ def main():
     data = synth.many_to_many(n_queries=nq, n_templates=nt, seed=synth.SEED_BASE + 2 + 1000 * rank)
     pairs_per_rank = nq * nt
     al = swalign.Aligner(local)
-    p = swalign.make_params(L, N_THETA, M_LEVELS, precision=args.precision)
+    p = swalign.make_params(L, N_THETA, M_LEVELS, precision=args.precision, metric=args.metric)
     q_h = torch.from_numpy(data["queries"]).pin_memory()
     t_h = torch.from_numpy(data["templates"]).pin_memory()
     q_d, t_d = q_h.to(dev), t_h.to(dev)
@@ -346,9 +349,11 @@ def main():
 
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
     variants = {}
-    if args.precision == "fp32" and not args.no_variants:
-        for prec in ("bf16", "fp16", "fp32_simt"):
-            pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec)
+    if args.precision == "fp32" and args.metric == "sw2" and not args.no_variants:
+        for name in ("bf16", "fp16", "fp32_simt", "rfsw2_fp32", "rfsw2_bf16"):
+            metric = "rfsw2" if name.startswith("rfsw2") else "sw2"
+            prec = name.split("_", 1)[1] if metric == "rfsw2" else name
+            pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec, metric=metric)
             if not args.no_autotune:
                 al.autotune(pv)
             al.reserve(pv, nq, nt)
@@ -367,13 +372,16 @@ def main():
             ms_v = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
             rv = swalign.results_to_numpy(out[:nt])
             corr_ms = st_v.get("corr", (0.0, 1))[0] / args.steps
-            flops = nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
+            # the ramp-filtered metric correlates both parts: K = 4M instead of 2M
+            flops = (nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
+                     * (2 if metric == "rfsw2" else 1))
             peaks_v, _ = measured_peaks()
             tf = flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else None
             simt = prec == "fp32_simt"
             peak_v = (SM_COUNT * FP32_LANES * 2 * peaks_v.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL)
                       * 1e6 / 1e12) if simt else peaks_v.get("bf16_tflops")
-            variants[prec] = {
+            variants[name] = {
+                "metric": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2"}[metric],
                 "value": sum_over_ranks(nq * nt, world, dev) / (ms_v / 1e3), "unit": "pairs/s",
                 "ms_per_step": ms_v, "status_ok": bool(np.all(rv["status"] == 0)),
                 "stages": {k: v[0] / args.steps for k, v in st_v.items()},
@@ -450,6 +458,7 @@ def main():
                    f"many-to-many {nq}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
                    "Nq": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
                    "n_levels": M_LEVELS, "precision": args.precision, "translation": 1,
+                   "distance": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2"}[args.metric],
                    "correlation": {"fp32": "tcgen05, 3-term FP16 split, FP32 accumulate",
                                    "bf16": "tcgen05 BF16", "fp16": "tcgen05 FP16",
                                    "fp32_simt": "CUDA-core FP32"}[args.precision],

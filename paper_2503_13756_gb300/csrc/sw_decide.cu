@@ -42,7 +42,7 @@ __device__ __forceinline__ void centre_of(const double *ctr, int idx, int parts,
     }
 }
 
-template <int nsig>
+template <int nsig, int PARTS>
 __global__ void __launch_bounds__(kDecThreads)
 k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
 {
@@ -127,9 +127,9 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     // l = lq, lq + LQ, ... for both pairs of signal s: a warp then reads 32
     // consecutive complex values (conflict-free).
     // the distance's M is the levels per part (parts = 2: ramp-filtered)
-    const double nM = (double)n * (M / A.parts);
+    const double nM = (double)n * (M / PARTS);
     double aix, aiy, dix, diy;
-    centre_of(A.ctr_q, i, A.parts, aix, aiy, dix, diy);
+    centre_of(A.ctr_q, i, PARTS, aix, aiy, dix, diy);
     const float invn = 1.f / (float)n;
     constexpr int LQ = kDecThreads / nsig;
     const int s = threadIdx.x % nsig, lq = threadIdx.x / nsig;
@@ -137,17 +137,17 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
     // rotation-dependent terms of the two pairs: rc |abar_i - R abar_j|^2
     // (rotation only) and xc |d_i - R d_j|^2 (two parts)
-    const bool rot_t = !A.translation, x_t = A.parts == 2;
+    const bool rot_t = !A.translation, x_t = PARTS == 2;
     float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ex0 = 0.f, ey0 = 0.f, ex1 = 0.f, ey1 = 0.f;
     if (rot_t || x_t) {
         const int ja = min(j0 + 2 * s, Nt - 1), jb = min(j0 + 2 * s + 1, Nt - 1);
         double x, y, u, v;
-        centre_of(A.ctr_t, ja, A.parts, x, y, u, v);
+        centre_of(A.ctr_t, ja, PARTS, x, y, u, v);
         ax0 = (float)x, ay0 = (float)y, ex0 = (float)u, ey0 = (float)v;
-        centre_of(A.ctr_t, jb, A.parts, x, y, u, v);
+        centre_of(A.ctr_t, jb, PARTS, x, y, u, v);
         ax1 = (float)x, ay1 = (float)y, ex1 = (float)u, ey1 = (float)v;
     }
-    const float hnm = (A.parts == 2 ? 1.f : 0.5f) * (float)nM;
+    const float hnm = (PARTS == 2 ? 1.f : 0.5f) * (float)nM;
     const float qnm = 0.25f * (float)nM;
     for (int l = lq; l < n; l += LQ) {
         const float2 z = R[l * nsig + s];
@@ -206,7 +206,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
             if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
             const int sg = pr >> 1, comp = pr & 1;
             double ajx, ajy, djx, djy;
-            centre_of(A.ctr_t, j, A.parts, ajx, ajy, djx, djy);
+            centre_of(A.ctr_t, j, PARTS, ajx, ajy, djx, djy);
             const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
             const int st = A.st_q[i] ? 1 : (stt[pr] ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
             sw_result r;
@@ -230,7 +230,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                     d += 0.25 * (ex * ex + ey * ey);
                 }
                 if (!A.translation) {
-                    d += (A.parts == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
+                    d += (PARTS == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
                     sx = sy = 0.0;
                 }
                 r.best_l = bl;
@@ -247,7 +247,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     // ---- full curve of pair (0, 0) (single-pair call)
     if (A.curve && i == 0 && j0 == 0) {
         double ajx, ajy, djx, djy;
-        centre_of(A.ctr_t, 0, A.parts, ajx, ajy, djx, djy);
+        centre_of(A.ctr_t, 0, PARTS, ajx, ajy, djx, djy);
         const double base = (double)delta[0] + A.norm_q[0] + A.norm_t[0];
         const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
         for (int l = threadIdx.x; l < n; l += blockDim.x) {
@@ -262,7 +262,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 d += 0.25 * (ex * ex + ey * ey);
             }
             if (!A.translation) {
-                d += (A.parts == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
+                d += (PARTS == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
                 sx = sy = 0.0;
             }
             A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
@@ -339,15 +339,21 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
         nsig = nsig_req;
     const size_t smem = sizeof(float2) * ((size_t)2 * a.n * nsig + a.n) + sizeof(float) * a.M;
     dim3 grid(a.Nq, (a.Nt + 2 * nsig - 1) / (2 * nsig));  // queries on x (no 65535 cap)
-#define SW_DEC_LAUNCH(NS)                                                                    \
+#define SW_DEC_LAUNCH(NS, P)                                                                 \
     do {                                                                                    \
-        cudaFuncSetAttribute(k_decide<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+        cudaFuncSetAttribute(k_decide<NS, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                              200 * 1024);                                                   \
-        k_decide<NS><<<grid, kDecThreads, smem, st>>>(a, plan, tw);                         \
+        k_decide<NS, P><<<grid, kDecThreads, smem, st>>>(a, plan, tw);                      \
     } while (0)
-    if (nsig == 16) SW_DEC_LAUNCH(16);
-    else if (nsig == 8) SW_DEC_LAUNCH(8);
-    else SW_DEC_LAUNCH(4);
+    if (a.parts == 1) {
+        if (nsig == 16) SW_DEC_LAUNCH(16, 1);
+        else if (nsig == 8) SW_DEC_LAUNCH(8, 1);
+        else SW_DEC_LAUNCH(4, 1);
+    } else {
+        if (nsig == 16) SW_DEC_LAUNCH(16, 2);
+        else if (nsig == 8) SW_DEC_LAUNCH(8, 2);
+        else SW_DEC_LAUNCH(4, 2);
+    }
 #undef SW_DEC_LAUNCH
     return cudaGetLastError();
 }
