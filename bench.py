@@ -36,7 +36,7 @@ WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
 PROJ_FLOPS_PER_CELL_ANGLE = 8           # s = <x, e> (FMA), frac, 1-t, two FMA accumulations
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the four-angle projection kernel, from one ncu capture of its 2048-image
-# launch (266,622,208 bytes; profiles/k_project4_many_to_many_2048x64.md);
+# launch (266,622,208 bytes);
 # None once that kernel changes.
 PROJ_DRAM_BYTES_PER_IMAGE = 266622208 / 2048
 CORR_FLOPS_PER_PAIR_FREQ = 8 * M_LEVELS  # complex multiply-add per level
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--metric", default="sw2", choices=["sw2", "rfsw2"],
                     help="distance of the main workload (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time the single-pair, one-reference and random-dense "
+                         "configurations (GPU and oracle) and print them as a second line")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
@@ -257,6 +260,98 @@ def uneven_block(args, device):
         g.close()
         del g, batch
         torch.cuda.empty_cache()
+
+
+def configs_block(device):
+    """The other configurations of the method, each on the GPU (device time
+    from CUDA events; single-pair latency also as host wall time) and the
+    FP64 oracle on a bounded sample (1 thread and all host threads):
+      single pair 64 x 64, n = 360, M = 128, all rotations + translation;
+      one reference x 10,000 queries, 128 x 128, n = 512, M = 256;
+      random dense U[0,1) images, L = n = M in {32, 64, 96, 128}, rotation only
+      (the paper's Table 3 timing setting), one pair per call and batched."""
+    import torch
+
+    import oracle
+    from paper_2503_13756_gb300 import swalign, synth
+    al = swalign.Aligner(device)
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cores = os.cpu_count() or 1
+
+    def dev_ms(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def wall_ms(fn, reps):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return float(np.median(ts))
+
+    def oracle_rate(q, t, n, M, translation, threads):
+        t0 = time.perf_counter()
+        oracle.align_all_pairs(q, t, n, M, translation=translation, nthreads=threads)
+        return len(q) * len(t) / (time.perf_counter() - t0)
+
+    # ---- single pair
+    d = synth.single_pair()
+    f, g = d["f"].astype(np.float32), d["g"].astype(np.float32)
+    p = swalign.make_params(64, 360, 128)
+    fd, gd = torch.from_numpy(f).cuda(device), torch.from_numpy(g).cuda(device)
+    al.reserve(p, 1, 1)
+    fn = lambda: al.align_all_rotations(fd, gd, p)
+    out["single_pair_64_n360_M128"] = {
+        "device_ms": dev_ms(fn, 50), "host_wall_ms": wall_ms(fn, 50),
+        "oracle_pairs_per_s_1thread": oracle_rate(f[None].astype(np.float64),
+                                                  g[None].astype(np.float64), 360, 128, 1, 1)}
+    # ---- one reference x 10,000 queries
+    d = synth.one_reference_batch()
+    q, ref = d["queries"], d["reference"]
+    p = swalign.make_params(128, 512, 256)
+    qd, rd = torch.from_numpy(q).cuda(device), torch.from_numpy(ref).cuda(device)
+    res = torch.empty((len(q), 40), dtype=torch.uint8, device=qd.device)
+    al.autotune(p)
+    al.reserve(p, len(q), 1)
+    ms = dev_ms(lambda: al.align_batch(qd, rd, p, out=res), 5)
+    sub = q[:256].astype(np.float64)
+    out["one_reference_10000_n512_M256"] = {
+        "pairs_per_s": len(q) / (ms / 1e3), "ms_per_batch": ms,
+        "oracle_pairs_per_s": oracle_rate(sub, ref.astype(np.float64), 512, 256, 1, cores),
+        "oracle_threads": cores, "oracle_sample": "first 256 queries"}
+    del qd, res
+    # ---- random dense, rotation only, L = n = M
+    wa = {}
+    for Lw in (32, 64, 96, 128):
+        x = synth.random_dense(Lw, count=1024 + 64, seed=synth.SEED_BASE + 9 + Lw)
+        p = swalign.make_params(Lw, Lw, Lw, translation=0)
+        xd = torch.from_numpy(x).cuda(device)
+        one = lambda: al.align_all_rotations(xd[0], xd[1], p)
+        res = torch.empty((1024 * 64, 40), dtype=torch.uint8, device=xd.device)
+        al.reserve(p, 1024, 64)
+        ms_b = dev_ms(lambda: al.align_batch(xd[:1024], xd[1024:], p, out=res), 5)
+        xs = x[:32].astype(np.float64)
+        wa[str(Lw)] = {"single_pair_host_wall_ms": wall_ms(one, 30),
+                       "single_pair_device_ms": dev_ms(one, 30),
+                       "batched_pairs_per_s": 1024 * 64 / (ms_b / 1e3),
+                       "oracle_pairs_per_s_1thread": oracle_rate(xs[:4], xs[4:8], Lw, Lw, 0, 1),
+                       "paper_pairs_per_s_skylake": {32: 769, 64: 370, 96: 159, 128: 103}[Lw]}
+        del xd, res
+    out["random_dense_rotation_only"] = wa
+    al.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, world, rank):
@@ -470,6 +565,8 @@ def main():
         "variants": variants, "serving": serve, "uneven": unev,
     }
     print(json.dumps(line), flush=True)
+    if args.configs and world == 1:
+        print(json.dumps({"configs": configs_block(local)}), flush=True)
 
 
 if __name__ == "__main__":
