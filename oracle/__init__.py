@@ -98,6 +98,11 @@ def _load():
             lib.orc_align_pair_rfsw.restype = None
             lib.orc_align_all_pairs_rfsw.argtypes = lib.orc_align_all_pairs.argtypes
             lib.orc_align_all_pairs_rfsw.restype = ci
+            lib.orc_grid_curve.argtypes = [dp, dp, ci, ci, ci, ci, ctypes.c_double, dp, dp]
+            lib.orc_grid_curve.restype = None
+            lib.orc_align_pair_grid.argtypes = [dp, dp, ci, ci, ci, ci, ci, ci, ci,
+                                                ctypes.c_double, dp, dp, ctypes.POINTER(OrcResult)]
+            lib.orc_align_pair_grid.restype = None
             _lib = lib
     return _lib
 
@@ -279,3 +284,36 @@ def align_all_pairs_rfsw(queries, templates, n: int, M: int, B: int | None = Non
     if not ok:
         raise MemoryError("oracle allocation failed")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Explicit translation sampling: the translation restricted to the grid
+# (i, j) * step, |i|, |j| <= K, by brute force over the grid.
+
+def grid_curve(Qf, Qg, K: int, step: float):
+    """Qf, Qg: [parts][n][M] uncentred quantiles.  Returns (D[n], shifts[n][2])."""
+    Qf, Qg = _f64(Qf), _f64(Qg)
+    parts, n, M = Qf.shape
+    D = np.empty(n, dtype=np.float64)
+    S = np.empty((n, 2), dtype=np.float64)
+    _load().orc_grid_curve(_dp(Qf), _dp(Qg), parts, n, M, int(K), float(step), _dp(D), _dp(S))
+    return D, S
+
+
+def align_pair_grid(f, g, n: int, M: int, K: int, step: float, B: int | None = None,
+                    level_rule: int = 0, metric: int = 0):
+    """One pair with the translation on the grid.  step in domain units
+    (the image spans [-1, 1]); metric 0 sliced W2, 1 ramp-filtered."""
+    f, g = _f64(f), _f64(g)
+    L = f.shape[-1]
+    if B is None:
+        B = rfsw_bins(L) if metric else default_bins(L)
+    D = np.empty(n, dtype=np.float64)
+    S = np.empty((n, 2), dtype=np.float64)
+    res = OrcResult()
+    _load().orc_align_pair_grid(_dp(f), _dp(g), L, int(n), int(M), int(B), int(level_rule),
+                                int(metric), int(K), float(step), _dp(D), _dp(S),
+                                ctypes.byref(res))
+    out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
+           "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
+    return out, D, S

@@ -736,3 +736,89 @@ int orc_align_all_pairs_rfsw(const double *queries, int Nq, const double *templa
     free(imgs); free(Q); free(ok);
     return 1;
 }
+
+/* ======================================================================
+ * Explicit translation sampling (Sec. 1 lists exhaustive search over a
+ * grid of translations; Sec. 7 names explicit translation sampling as an
+ * extension).  The translation of g is restricted to the grid
+ *   s = (i, j) * step,  -K <= i, j <= K,
+ * and for every rotation l the distance is the minimum over the grid of
+ *   J(l, s) = 1/(n M) sum_parts sum_k sum_p (Qf[k][p] - Qg[(k-l) mod n][p] - <s, e_k>)^2
+ * evaluated directly for every grid point (brute force, no closed form).
+ * Qf, Qg: [parts][n][M] uncentred quantiles.  shifts[l] = the minimising
+ * grid point (lowest (i, j) in row-major order on exact ties). */
+void orc_grid_curve(const double *Qf, const double *Qg, int parts, int n, int M, int K,
+                    double step, double *D, double *shifts)
+{
+    const double inv = 1.0 / ((double)n * M);
+    for (int l = 0; l < n; ++l) {
+        double best = INFINITY, bx = 0.0, by = 0.0;
+        for (int i = -K; i <= K; ++i) {
+            for (int j = -K; j <= K; ++j) {
+                const double sx = i * step, sy = j * step;
+                double acc = 0.0;
+                for (int part = 0; part < parts; ++part) {
+                    const double *qf = Qf + (size_t)part * n * M, *qg = Qg + (size_t)part * n * M;
+                    for (int k = 0; k < n; ++k) {
+                        const int kg = ((k - l) % n + n) % n;
+                        double ct, st;
+                        orc_direction(k, n, &ct, &st);
+                        const double off = sx * ct + sy * st;
+                        for (int p = 0; p < M; ++p) {
+                            const double d = qf[(size_t)k * M + p] - qg[(size_t)kg * M + p] - off;
+                            acc += d * d;
+                        }
+                    }
+                }
+                acc *= inv;
+                if (acc < best) {
+                    best = acc;
+                    bx = sx;
+                    by = sy;
+                }
+            }
+        }
+        D[l] = best;
+        if (shifts) {
+            shifts[2 * l] = bx;
+            shifts[2 * l + 1] = by;
+        }
+    }
+}
+
+/* One pair with the translation restricted to the grid; metric 0 = sliced
+ * W2, 1 = ramp-filtered (B must be the filter's bin count). */
+void orc_align_pair_grid(const double *f, const double *g, int L, int n, int M, int B,
+                         int level_rule, int metric, int K, double step, double *D,
+                         double *shifts, orc_result *res)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, 0};
+    const int parts = metric ? 2 : 1;
+    double *Qf = (double *)malloc(sizeof(double) * parts * (size_t)n * M);
+    double *Qg = (double *)malloc(sizeof(double) * parts * (size_t)n * M);
+    double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Sl = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    double af[2], ag[2];
+    int okf, okg;
+    if (metric) {
+        okf = orc_rfsw_transform(&cfg, f, Qf);
+        okg = orc_rfsw_transform(&cfg, g, Qg);
+    } else {
+        okf = orc_transform(&cfg, f, Qf, af);  /* translation 0: uncentred */
+        okg = orc_transform(&cfg, g, Qg, ag);
+    }
+    if (!okf || !okg) {
+        orc_bad(res, okf ? 2 : 1);
+        if (D) for (int l = 0; l < n; ++l) D[l] = NAN;
+        if (shifts) for (int l = 0; l < 2 * n; ++l) shifts[l] = NAN;
+    } else {
+        orc_grid_curve(Qf, Qg, parts, n, M, K, step, Dl, Sl);
+        orc_rfsw_decide(Dl, Sl, n, res);
+        if (D) memcpy(D, Dl, sizeof(double) * (size_t)n);
+        if (shifts) memcpy(shifts, Sl, sizeof(double) * 2 * (size_t)n);
+    }
+    free(Qf);
+    free(Qg);
+    free(Dl);
+    free(Sl);
+}
