@@ -92,6 +92,16 @@ typedef struct {
                             /* count is the smallest even 2/3/5-smooth count >= the */
                             /* default B (the filter's FFT length), an explicit     */
                             /* n_bins must be 2/3/5-smooth, n_levels <= 512         */
+    int32_t shift_grid;     /* explicit translation sampling (Sec. 1, exhaustive    */
+                            /* search over a translation grid; Sec. 7): with        */
+                            /* translation = 1 and shift_grid = K > 0 the shift is  */
+                            /* restricted to the grid (i, j) * step, |i|, |j| <= K; */
+                            /* 0 = unbounded closed form.  The grid minimum is      */
+                            /* exact: D(l, s) = D_T(l) + rho |s - c(l)|^2 (rho 0.5  */
+                            /* sliced W2, 1 RFSW2), so it is the grid point nearest */
+                            /* the closed-form optimum c(l), per rotation           */
+    int32_t shift_step_q;   /* grid step in sixteenths of a pixel (step = q h / 16, */
+                            /* h = 2/L); must be > 0 when shift_grid > 0            */
 } sw_params;
 
 typedef struct {

@@ -347,6 +347,10 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
         return fail(c, SW_ERR_INVALID_ARG, "gemm_precision=%d unknown", p->gemm_precision);
     if (p->metric != SW_METRIC_SW2 && p->metric != SW_METRIC_RFSW2)
         return fail(c, SW_ERR_INVALID_ARG, "metric=%d unknown", p->metric);
+    if (p->shift_grid < 0 || p->shift_grid > 4096 ||
+        (p->shift_grid > 0 && (p->shift_step_q <= 0 || p->shift_step_q > 65536)))
+        return fail(c, SW_ERR_INVALID_ARG, "shift_grid=%d, shift_step_q=%d", p->shift_grid,
+                    p->shift_step_q);
     if (p->metric == SW_METRIC_RFSW2) {
         if (p->n_bins != 0 && !smooth235(p->n_bins))
             return fail(c, SW_ERR_INVALID_ARG,
@@ -776,6 +780,8 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     a.st_t = o.status + Nq;
     a.cs64 = t->cs64;
     a.translation = p->translation;
+    a.grid_k = p->translation ? p->shift_grid : 0;
+    a.grid_step = (double)p->shift_step_q * (2.0 / p->L) / 16.0;
     a.dev_err = err;
     a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)out;
     a.curve = curve;
@@ -1033,6 +1039,8 @@ static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_
     a.st_t = bank->status;
     a.cs64 = t->cs64;
     a.translation = p->translation;
+    a.grid_k = p->translation ? p->shift_grid : 0;
+    a.grid_step = (double)p->shift_step_q * (2.0 / p->L) / 16.0;
     a.dev_err = err;
     a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)d_out;
     SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st, [&] {
@@ -1215,6 +1223,8 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
     a.st_t = status + 1;
     a.cs64 = cs64;
     a.translation = p->translation;
+    a.grid_k = p->translation ? p->shift_grid : 0;
+    a.grid_step = (double)p->shift_step_q * (2.0 / p->L) / 16.0;
     a.dev_err = err;
     a.out = d_best;
     a.curve = d_D;

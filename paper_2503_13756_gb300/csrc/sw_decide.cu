@@ -23,6 +23,25 @@ namespace {
 
 constexpr int kDecThreads = 256;
 
+// Shift restriction (FP64): (sx, sy) holds the closed-form optimum c.
+// tmode 0 (rotation only): the shift is 0 and d grows by rho |c|^2;
+// tmode 2 (grid): the shift is the grid point g nearest c (clamped to
+// |i|, |j| <= K) and d grows by rho |g - c|^2; tmode 1: unchanged.
+__device__ __forceinline__ void restrict_shift(int tmode, int K, double step, double rho,
+                                               double &sx, double &sy, double &d)
+{
+    if (tmode == 0) {
+        d += rho * (sx * sx + sy * sy);
+        sx = sy = 0.0;
+    } else if (tmode == 2) {
+        const double gx = fmin(fmax(rint(sx / step), -(double)K), (double)K) * step;
+        const double gy = fmin(fmax(rint(sy / step), -(double)K), (double)K) * step;
+        d += rho * ((sx - gx) * (sx - gx) + (sy - gy) * (sy - gy));
+        sx = gx;
+        sy = gy;
+    }
+}
+
 // Centre of image idx for the decision: parts = 1: (a, 0); parts = 2 (two
 // parts with vectors a+ and a-, centre array [..][2][2]): abar = (a+ + a-)/2
 // (the joint translation is s* = abar_i - R abar_j) and d = a+ - a-.
@@ -42,8 +61,11 @@ __device__ __forceinline__ void centre_of(const double *ctr, int idx, int parts,
     }
 }
 
-template <int nsig, int PARTS>
-__global__ void __launch_bounds__(kDecThreads)
+// XTRA: a rotation-dependent term is present (rotation only, a translation
+// grid, or two parts); without it (sliced W2 with the closed-form
+// translation) the argmin reads the correlation alone.
+template <int nsig, int PARTS, bool XTRA>
+__global__ void __launch_bounds__(kDecThreads, 6)
 k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
 {
     constexpr int NP = 2 * nsig;                               // pairs per CTA
@@ -135,9 +157,13 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     const int s = threadIdx.x % nsig, lq = threadIdx.x / nsig;
     float best0 = __int_as_float(0x7f800000), best1 = best0;
     int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
-    // rotation-dependent terms of the two pairs: rc |abar_i - R abar_j|^2
-    // (rotation only) and xc |d_i - R d_j|^2 (two parts)
-    const bool rot_t = !A.translation, x_t = PARTS == 2;
+    // rotation-dependent terms of the two pairs: rc |s - c|^2 with
+    // c = abar_i - R abar_j and s = 0 (rotation only) or the grid point
+    // nearest c (translation on a grid), and xc |d_i - R d_j|^2 (two parts)
+    const int tmode = !XTRA ? 1 : (!A.translation ? 0 : (A.grid_k > 0 ? 2 : 1));
+    const bool rot_t = XTRA && tmode != 1, x_t = PARTS == 2;
+    const float gstep = (float)A.grid_step, ginv = tmode == 2 ? (float)(1.0 / A.grid_step) : 0.f;
+    const float gk = (float)A.grid_k;
     float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ex0 = 0.f, ey0 = 0.f, ex1 = 0.f, ey1 = 0.f;
     if (rot_t || x_t) {
         const int ja = min(j0 + 2 * s, Nt - 1), jb = min(j0 + 2 * s + 1, Nt - 1);
@@ -157,9 +183,17 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
             const float c = w.x, sn = -w.y;
             if (rot_t) {
                 float sx = (float)aix - (c * ax0 - sn * ay0), sy = (float)aiy - (sn * ax0 + c * ay0);
+                if (tmode == 2) {
+                    sx -= fminf(fmaxf(rintf(sx * ginv), -gk), gk) * gstep;
+                    sy -= fminf(fmaxf(rintf(sy * ginv), -gk), gk) * gstep;
+                }
                 k0 = fmaf(hnm, sx * sx + sy * sy, k0);
                 sx = (float)aix - (c * ax1 - sn * ay1);
                 sy = (float)aiy - (sn * ax1 + c * ay1);
+                if (tmode == 2) {
+                    sx -= fminf(fmaxf(rintf(sx * ginv), -gk), gk) * gstep;
+                    sy -= fminf(fmaxf(rintf(sy * ginv), -gk), gk) * gstep;
+                }
                 k1 = fmaf(hnm, sx * sx + sy * sy, k1);
             }
             if (x_t) {
@@ -229,10 +263,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                     const double ey = diy - (c.y * djx + c.x * djy);
                     d += 0.25 * (ex * ex + ey * ey);
                 }
-                if (!A.translation) {
-                    d += (PARTS == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
-                    sx = sy = 0.0;
-                }
+                restrict_shift(tmode, A.grid_k, A.grid_step, PARTS == 2 ? 1.0 : 0.5, sx, sy, d);
                 r.best_l = bl;
                 r.status = 0;
                 r.angle_rad = (float)(A.dalpha * bl);
@@ -261,10 +292,7 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 const double ey = diy - (c.y * djx + c.x * djy);
                 d += 0.25 * (ex * ex + ey * ey);
             }
-            if (!A.translation) {
-                d += (PARTS == 2 ? 1.0 : 0.5) * (sx * sx + sy * sy);
-                sx = sy = 0.0;
-            }
+            restrict_shift(tmode, A.grid_k, A.grid_step, PARTS == 2 ? 1.0 : 0.5, sx, sy, d);
             A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
             if (A.shifts) {
                 A.shifts[2 * l] = sx;
@@ -328,6 +356,7 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
     if (args.Nq <= 0 || args.Nt <= 0) return cudaSuccess;
     DecideArgs a = args;
     if (a.parts != 1 && (a.parts != 2 || a.M % 2)) return cudaErrorInvalidValue;
+    if (a.grid_k > 0 && !(a.grid_step > 0.0)) return cudaErrorInvalidValue;
     a.inv_n = 1.0 / a.n;
     a.inv_nM = 1.0 / ((double)a.n * (a.M / a.parts));
     a.dalpha = 6.283185307179586 / a.n;
@@ -339,20 +368,25 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
         nsig = nsig_req;
     const size_t smem = sizeof(float2) * ((size_t)2 * a.n * nsig + a.n) + sizeof(float) * a.M;
     dim3 grid(a.Nq, (a.Nt + 2 * nsig - 1) / (2 * nsig));  // queries on x (no 65535 cap)
-#define SW_DEC_LAUNCH(NS, P)                                                                 \
+#define SW_DEC_LAUNCH(NS, P, X)                                                              \
     do {                                                                                    \
-        cudaFuncSetAttribute(k_decide<NS, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+        cudaFuncSetAttribute(k_decide<NS, P, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              200 * 1024);                                                   \
-        k_decide<NS, P><<<grid, kDecThreads, smem, st>>>(a, plan, tw);                      \
+        k_decide<NS, P, X><<<grid, kDecThreads, smem, st>>>(a, plan, tw);                   \
     } while (0)
-    if (a.parts == 1) {
-        if (nsig == 16) SW_DEC_LAUNCH(16, 1);
-        else if (nsig == 8) SW_DEC_LAUNCH(8, 1);
-        else SW_DEC_LAUNCH(4, 1);
+    const bool plain = a.parts == 1 && a.translation && a.grid_k == 0;
+    if (plain) {
+        if (nsig == 16) SW_DEC_LAUNCH(16, 1, false);
+        else if (nsig == 8) SW_DEC_LAUNCH(8, 1, false);
+        else SW_DEC_LAUNCH(4, 1, false);
+    } else if (a.parts == 1) {
+        if (nsig == 16) SW_DEC_LAUNCH(16, 1, true);
+        else if (nsig == 8) SW_DEC_LAUNCH(8, 1, true);
+        else SW_DEC_LAUNCH(4, 1, true);
     } else {
-        if (nsig == 16) SW_DEC_LAUNCH(16, 2);
-        else if (nsig == 8) SW_DEC_LAUNCH(8, 2);
-        else SW_DEC_LAUNCH(4, 2);
+        if (nsig == 16) SW_DEC_LAUNCH(16, 2, true);
+        else if (nsig == 8) SW_DEC_LAUNCH(8, 2, true);
+        else SW_DEC_LAUNCH(4, 2, true);
     }
 #undef SW_DEC_LAUNCH
     return cudaGetLastError();

@@ -285,6 +285,11 @@ struct DecideArgs {
     // |d_i - R d_j|^2 / 4, d = a+ - a-, and the rotation-only term is
     // |abar_i - R abar_j|^2 with abar = (a+ + a-)/2 (derivation in the oracle)
     int parts = 1;
+    // translation restricted to the grid (i, j) * grid_step, |i|, |j| <= grid_k
+    // (grid_k > 0 with translation): the shift is the grid point nearest the
+    // closed-form optimum and the distance adds rho |s - c|^2
+    int grid_k = 0;
+    double grid_step = 0.0;
     // filled by launch_decide: 1/n, 1/(nM), 2 pi/n (no FP64 divisions on the device)
     double inv_n, inv_nM, dalpha;
 };

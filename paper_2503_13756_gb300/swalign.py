@@ -30,18 +30,20 @@ assert RESULT_DTYPE.itemsize == 40
 class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
                 ("L", "n_theta", "n_levels", "n_bins", "translation", "level_rule",
-                 "gemm_precision", "metric")]
+                 "gemm_precision", "metric", "shift_grid", "shift_step_q")]
 
 
 METRIC = {"sw2": 0, "rfsw2": 1}
 
 
 def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
-                precision="fp32", metric="sw2") -> Params:
+                precision="fp32", metric="sw2", shift_grid=0, shift_step_q=0) -> Params:
+    """shift_grid = K > 0 restricts the translation to the grid (i, j) * step,
+    |i|, |j| <= K, step = shift_step_q / 16 pixel."""
     prec = PREC[precision] if isinstance(precision, str) else int(precision)
     met = METRIC[metric] if isinstance(metric, str) else int(metric)
     return Params(int(L), int(n_theta), int(n_levels), int(n_bins), int(translation),
-                  int(level_rule), prec, met)
+                  int(level_rule), prec, met, int(shift_grid), int(shift_step_q))
 
 
 def bins_of(params: Params) -> int:

@@ -36,7 +36,7 @@ def test_result_struct_layout():
     # double shift[2], double d2 -> 40 bytes, d2 at offset 32
     assert swalign.RESULT_DTYPE.itemsize == 40
     assert swalign.RESULT_DTYPE.fields["d2"][1] == 32
-    assert ctypes.sizeof(swalign.Params) == 32
+    assert ctypes.sizeof(swalign.Params) == 40
 
 
 def test_params_fields_follow_the_header():
