@@ -103,6 +103,10 @@ def _load():
             lib.orc_align_pair_grid.argtypes = [dp, dp, ci, ci, ci, ci, ci, ci, ci,
                                                 ctypes.c_double, dp, dp, ctypes.POINTER(OrcResult)]
             lib.orc_align_pair_grid.restype = None
+            lib.orc_msw_curve.argtypes = [dp, dp, ci, ci, dp]
+            lib.orc_msw_curve.restype = None
+            lib.orc_align_pair_msw.argtypes = lib.orc_align_pair.argtypes
+            lib.orc_align_pair_msw.restype = None
             _lib = lib
     return _lib
 
@@ -314,6 +318,34 @@ def align_pair_grid(f, g, n: int, M: int, K: int, step: float, B: int | None = N
     _load().orc_align_pair_grid(_dp(f), _dp(g), L, int(n), int(M), int(B), int(level_rule),
                                 int(metric), int(K), float(step), _dp(D), _dp(S),
                                 ctypes.byref(res))
+    out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
+           "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
+    return out, D, S
+
+
+# ---------------------------------------------------------------------------
+# Max-sliced W2 over rotations (Eq. max_sliced_wasserstein).
+
+def msw_curve(Qf, Qg) -> np.ndarray:
+    """D[l] = max_k (1/M) sum_p (Qf[k,p] - Qg[(k-l) mod n, p])^2 (direct)."""
+    Qf, Qg = _f64(Qf), _f64(Qg)
+    n, M = Qf.shape
+    D = np.empty(n, dtype=np.float64)
+    _load().orc_msw_curve(_dp(Qf), _dp(Qg), n, M, _dp(D))
+    return D
+
+
+def align_pair_msw(f, g, n: int, M: int, B: int | None = None, level_rule: int = 0,
+                   translation: int = 1):
+    """Max-sliced curve for one pair.  Returns (result dict, D[n], shifts[n][2])."""
+    f, g = _f64(f), _f64(g)
+    L = f.shape[-1]
+    B = default_bins(L) if B is None else int(B)
+    D = np.empty(n, dtype=np.float64)
+    S = np.empty((n, 2), dtype=np.float64)
+    res = OrcResult()
+    _load().orc_align_pair_msw(_dp(f), _dp(g), L, int(n), int(M), B, int(level_rule),
+                               int(translation), _dp(D), _dp(S), ctypes.byref(res))
     out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
            "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
     return out, D, S

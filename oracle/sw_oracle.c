@@ -822,3 +822,56 @@ void orc_align_pair_grid(const double *f, const double *g, int L, int n, int M, 
     free(Dl);
     free(Sl);
 }
+
+/* ======================================================================
+ * Max-sliced W2 over rotations (App. "alignment extended", Eq.
+ * max_sliced_wasserstein): the squared distance at rotation l is the
+ * largest, over the angles, of the squared 1-D W2 between the columns,
+ *   D(l) = max_k (1/M) sum_p (Qf[k][p] - Qg[(k-l) mod n][p])^2 ,
+ * read with the level average 1/M (the per-angle W2^2 of the sampled
+ * quantiles, the normalisation of Eq. discrete_sw2 without the angle
+ * average).  No FFT applies; direct O(n^2 M).  With translation the
+ * quantiles are centred (the sliced-W2 optimal translation, s*(l) =
+ * a_f - R a_g, applied before the maximum). */
+void orc_msw_curve(const double *Qf, const double *Qg, int n, int M, double *D)
+{
+    for (int l = 0; l < n; ++l) {
+        double mx = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const int kg = ((k - l) % n + n) % n;
+            double acc = 0.0;
+            for (int p = 0; p < M; ++p) {
+                const double d = Qf[(size_t)k * M + p] - Qg[(size_t)kg * M + p];
+                acc += d * d;
+            }
+            acc /= M;
+            if (acc > mx) mx = acc;
+        }
+        D[l] = mx;
+    }
+}
+
+void orc_align_pair_msw(const double *f, const double *g, int L, int n, int M, int B,
+                        int level_rule, int translation, double *D, double *shifts,
+                        orc_result *res)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    double *Qf = (double *)malloc(sizeof(double) * (size_t)n * M);
+    double *Qg = (double *)malloc(sizeof(double) * (size_t)n * M);
+    double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
+    double af[2] = {0, 0}, ag[2] = {0, 0};
+    const int okf = orc_transform(&cfg, f, Qf, af);
+    const int okg = orc_transform(&cfg, g, Qg, ag);
+    if (!okf || !okg) {
+        orc_bad(res, okf ? 2 : 1);
+        if (D) for (int l = 0; l < n; ++l) D[l] = NAN;
+        if (shifts) for (int l = 0; l < 2 * n; ++l) shifts[l] = NAN;
+    } else {
+        orc_msw_curve(Qf, Qg, n, M, Dl);
+        orc_decide(Dl, n, af, ag, translation, shifts, res);
+        if (D) memcpy(D, Dl, sizeof(double) * (size_t)n);
+    }
+    free(Qf);
+    free(Qg);
+    free(Dl);
+}
