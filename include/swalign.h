@@ -68,7 +68,7 @@ typedef enum {
 typedef enum {
     SW_METRIC_SW2 = 0,   /* sliced 2-Wasserstein of the projections (Eq.          */
                          /* sliced_wasserstein_2, discrete Eq. discrete_sw2)       */
-    SW_METRIC_RFSW2 = 1  /* ramp-filtered sliced 2-Wasserstein (Sec. 2.1 "High-    */
+    SW_METRIC_RFSW2 = 1, /* ramp-filtered sliced 2-Wasserstein (Sec. 2.1 "High-    */
                          /* pass filter", Eq. signed_sliced_wasserstein, discrete  */
                          /* Eq. discrete_ssw2): each projection row is filtered by */
                          /* |xi| circularly on its bin grid, split into its        */
@@ -76,6 +76,14 @@ typedef enum {
                          /* normalised; the squared distance is the sum of the two */
                          /* parts' sliced W2^2 (1/(n M) with M levels per part).   */
                          /* One translation moves both parts: s* = (c+ + c-)/2.    */
+    SW_METRIC_MSW2 = 2   /* max-sliced 2-Wasserstein (Eq. max_sliced_wasserstein): */
+                         /* D(l) = max_k (1/M) sum_p (u_pk - v_p,(k-l))^2, direct  */
+                         /* O(n^2 M) per pair in FP32 on the CUDA cores (the FFT   */
+                         /* correlation does not apply to a maximum); with         */
+                         /* translation = 1 the quantiles are centred first (the   */
+                         /* sliced-W2 optimal shift, reported as the shift).  Not  */
+                         /* for banks, translation grids or the allocation-free    */
+                         /* call (SW_ERR_UNSUPPORTED / SW_ERR_INVALID_ARG).        */
 } sw_metric;
 
 typedef struct {

@@ -157,6 +157,8 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, int lp_kind, bool scratc
     const size_t nimg = (size_t)Nq + Nt;
     const size_t n = p->n_theta, nh = n / 2, M = levels_of(p), B = bins_of(p);
     const size_t parts = parts_of(p);
+    const bool msw = p->metric == SW_METRIC_MSW2;  // quantiles only, no spectra
+    if (msw) lp_kind = 0;
     Layout l{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -169,7 +171,7 @@ Layout batch_layout(const sw_params *p, int Nq, int Nt, int lp_kind, bool scratc
     l.proj = take(4 * nimg * nh * B);
     l.ramp = take(parts == 2 ? 4 * nimg * 2 * nh * B : 0);
     l.quant = take(4 * nimg * n * M);
-    l.spec32 = take(lp_kind ? 0 : 4 * nh * nimg * 2 * M);
+    l.spec32 = take(lp_kind || msw ? 0 : 4 * nh * nimg * 2 * M);
     l.lp_q = take(2 * nh * (size_t)Nq * row);
     l.lp_t = take(2 * nh * (size_t)2 * Nt * row);
     l.prof = take(4 * nimg * M);
@@ -345,8 +347,11 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
         return fail(c, SW_ERR_INVALID_ARG, "level_rule must be 0 or 1");
     if (p->gemm_precision < SW_PREC_FP32 || p->gemm_precision > SW_PREC_FP32_SIMT)
         return fail(c, SW_ERR_INVALID_ARG, "gemm_precision=%d unknown", p->gemm_precision);
-    if (p->metric != SW_METRIC_SW2 && p->metric != SW_METRIC_RFSW2)
+    if (p->metric != SW_METRIC_SW2 && p->metric != SW_METRIC_RFSW2 &&
+        p->metric != SW_METRIC_MSW2)
         return fail(c, SW_ERR_INVALID_ARG, "metric=%d unknown", p->metric);
+    if (p->metric == SW_METRIC_MSW2 && p->shift_grid > 0)
+        return fail(c, SW_ERR_INVALID_ARG, "max-sliced W2 takes no translation grid");
     if (p->shift_grid < 0 || p->shift_grid > 4096 ||
         (p->shift_grid > 0 && (p->shift_step_q <= 0 || p->shift_step_q > 65536)))
         return fail(c, SW_ERR_INVALID_ARG, "shift_grid=%d, shift_step_q=%d", p->shift_grid,
@@ -744,6 +749,42 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     o.norm16 = at<double>(w, l.norm16);
     if ((s = run_images(c, p, t, dq, p->L, Nq, 0, o, st))) return s;
     if ((s = run_images(c, p, t, dt, p->L, Nt, Nq, o, st))) return s;
+    if (p->metric == SW_METRIC_MSW2) {
+        // max-sliced: quantiles (and centring vectors), then every column pair
+        SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                    return swk::launch_quantiles(o.proj, nimg, n, bins_of(p), M,
+                                                 2.0f / (float)p->L, p->level_rule, 1, o.quant,
+                                                 o.status, st);
+                }));
+        if (p->translation)
+            SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
+                        return swk::launch_center_norm(o.quant, nimg, n, M, t->cs64, o.center,
+                                                       nullptr, st);
+                    }));
+        swk::MswArgs a{};
+        a.q = o.quant;
+        a.t = o.quant + (size_t)Nq * n * M;
+        a.Nq = Nq;
+        a.Nt = Nt;
+        a.n = n;
+        a.M = M;
+        a.ctr_q = o.center;
+        a.ctr_t = o.center + 2 * (size_t)Nq;
+        a.st_q = o.status;
+        a.st_t = o.status + Nq;
+        a.cs64 = t->cs64;
+        a.translation = p->translation;
+        a.curve = at<float>(w, l.C);
+        a.out = mode == 1 ? (void *)(w + l.scratch) : (void *)out;
+        a.full = curve;
+        a.shifts = shifts;
+        SW_CUDA(c, launch(c, SW_STAGE_DECIDE, st, [&] { return swk::launch_msw(a, st); }));
+        if (mode == 1)
+            SW_CUDA(c, launch(c, SW_STAGE_BEST, st, [&] {
+                        return swk::launch_best_template(w + l.scratch, Nq, Nt, out, st);
+                    }));
+        return SW_OK;
+    }
     if ((s = run_after_projection(c, p, t, nimg, o, st))) return s;
     float2 *C = at<float2>(w, l.C);
     int *err = at<int>(w, l.err);
@@ -849,6 +890,8 @@ sw_status sw_bank_create(sw_ctx *c, const sw_params *p, const float *d_t_img, in
     sw_status s = check_params(c, p);
     if (s) return s;
     if (Nt <= 0) return fail(c, SW_ERR_INVALID_ARG, "Nt=%d", Nt);
+    if (p->metric == SW_METRIC_MSW2)
+        return fail(c, SW_ERR_UNSUPPORTED, "banks hold spectra; max-sliced W2 needs quantiles");
     if ((s = check_ptr(c, d_t_img, "d_t_img", true))) return s;
     if ((s = set_device(c))) return s;
     const Tune tu = tune_of(c, p);
@@ -1296,6 +1339,7 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
              p->n_theta, p->n_levels, bins_of(p), (int)p->gemm_precision);
     const std::string key = kb;
     const TuneKey tk = tune_key(p);
+    if (p->metric == SW_METRIC_MSW2) return SW_OK;  // no spectra or FFT: defaults stand
     auto store = [&](const Tune &tu) {
         for (auto &e : c->tunes)
             if (e.first == tk) {

@@ -296,6 +296,24 @@ struct DecideArgs {
 cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
                           cudaStream_t st, int nsig = 0);
 
+// Max-sliced W2 over rotations: q [Nq][n][M], t [Nt][n][M] uncentred
+// quantiles; with translation the columns are centred by ctr ([N][2]).
+// curve: scratch [Nq][Nt][n] floats (M times the curve); out: sw_result
+// [Nq][Nt]; full / shifts: the curve and shifts of pair (0, 0) or NULL.
+struct MswArgs {
+    const float *q, *t;
+    int Nq, Nt, n, M;
+    const double *ctr_q, *ctr_t;
+    const int32_t *st_q, *st_t;
+    const double2 *cs64;
+    int translation;
+    float *curve;
+    void *out;
+    double *full, *shifts;
+    double dalpha;  // filled by the launcher
+};
+cudaError_t launch_msw(const MswArgs &a, cudaStream_t st);
+
 // Best template per query from the [Nq][Nt] results.
 cudaError_t launch_best_template(const void *all, int Nq, int Nt, void *out, cudaStream_t st);
 

@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                  "gemm_precision", "metric", "shift_grid", "shift_step_q")]
 
 
-METRIC = {"sw2": 0, "rfsw2": 1}
+METRIC = {"sw2": 0, "rfsw2": 1, "msw2": 2}
 
 
 def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
