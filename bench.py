@@ -349,6 +349,26 @@ def configs_block(device):
                        "paper_pairs_per_s_skylake": {32: 769, 64: 370, 96: 159, 128: 103}[Lw]}
         del xd, res
     out["random_dense_rotation_only"] = wa
+    # ---- max-sliced W2 over rotations: 512 x 64 pairs of the many-to-many images
+    d = synth.many_to_many(n_queries=512, n_templates=64)
+    qd = torch.from_numpy(d["queries"]).cuda(device)
+    td = torch.from_numpy(d["templates"]).cuda(device)
+    p = swalign.make_params(128, 256, 128, metric="msw2")
+    res = torch.empty((512 * 64, 40), dtype=torch.uint8, device=qd.device)
+    al.reserve(p, 512, 64)
+    al.profile(True)
+    al.profile_read()
+    ms = dev_ms(lambda: al.align_batch(qd, td, p, out=res), 3)
+    st_m = al.profile_read()
+    al.profile(False)
+    k_ms = st_m.get("decide", (0.0, 1))[0] / st_m.get("decide", (0.0, 1))[1]
+    flops = 512 * 64 * 256 * 256 * 128 * 3  # subtract + fused multiply-add per term
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    out["max_sliced_512x64_n256_M128"] = {
+        "pairs_per_s": 512 * 64 / (ms / 1e3), "ms_per_batch": ms,
+        "k_msw": {"ms": k_ms, "achieved_tflops": flops / (k_ms / 1e3) / 1e12, "peak": peak,
+                  "frac": flops / (k_ms / 1e3) / 1e12 / peak,
+                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}}
     al.close()
     torch.cuda.empty_cache()
     return out
