@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
-    ap.add_argument("--metric", default="sw2", choices=["sw2", "rfsw2"],
+    ap.add_argument("--metric", default="sw2", choices=["sw2", "rfsw2", "msw2"],
                     help="distance of the main workload (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--configs", action="store_true",
@@ -573,10 +573,13 @@ def main():
                    f"many-to-many {nq}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
                    "Nq": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
                    "n_levels": M_LEVELS, "precision": args.precision, "translation": 1,
-                   "distance": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2"}[args.metric],
-                   "correlation": {"fp32": "tcgen05, 3-term FP16 split, FP32 accumulate",
-                                   "bf16": "tcgen05 BF16", "fp16": "tcgen05 FP16",
-                                   "fp32_simt": "CUDA-core FP32"}[args.precision],
+                   "distance": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2",
+                                "msw2": "max-sliced W2"}[args.metric],
+                   "correlation": ("none: every column pair, FP32 on the CUDA cores"
+                                   if args.metric == "msw2" else
+                                   {"fp32": "tcgen05, 3-term FP16 split, FP32 accumulate",
+                                    "bf16": "tcgen05 BF16", "fp16": "tcgen05 FP16",
+                                    "fp32_simt": "CUDA-core FP32"}[args.precision]),
                    "parallelism": f"{world} independent replicas (weak)",
                    "launch_shapes": tune,
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},

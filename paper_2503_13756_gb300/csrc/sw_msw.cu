@@ -22,7 +22,7 @@ namespace swk {
 namespace {
 
 constexpr int kMswThreads = 256;
-constexpr int kMswPC = 32;  // levels per stage
+constexpr int kMswPC = 32;  // levels per stage (a multiple of 4)
 
 template <int R, int NC>
 __global__ void __launch_bounds__(kMswThreads)
@@ -34,6 +34,7 @@ k_msw(MswArgs A)
     float *Us = sms;                   // [R][kMswPC]
     float *Vt = Us + R * kMswPC;       // [kMswPC][n + 1]
     float *Eb = Vt + kMswPC * np1;     // [R][n]
+    float *offt = Eb + R * n;          // [n] template column offsets
     __shared__ float offq[R];
     const int pair = blockIdx.x;
     const int i = pair / A.Nt, j = pair % A.Nt;
@@ -52,6 +53,9 @@ k_msw(MswArgs A)
         const int k = k0 + t;
         offq[t] = k < n ? (float)(aix * cs[k].x + aiy * cs[k].y) : 0.f;
     }
+    // once per column (FP64 is scarce: not once per staged level)
+    for (int kk = t; kk < n; kk += kMswThreads)
+        offt[kk] = A.translation ? (float)(ajx * cs[kk].x + ajy * cs[kk].y) : 0.f;
     float acc[NC][R];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -69,26 +73,32 @@ k_msw(MswArgs A)
         for (int e = t; e < n * kMswPC; e += kMswThreads) {
             const int kk = e / kMswPC, p = e % kMswPC;
             float v = 0.f;
-            if (p < pc) {
-                v = Qj[(size_t)kk * M + p0 + p];
-                if (A.translation) v -= (float)(ajx * cs[kk].x + ajy * cs[kk].y);
-            }
+            if (p < pc) v = Qj[(size_t)kk * M + p0 + p] - offt[kk];
             Vt[p * np1 + kk] = v;
         }
         __syncthreads();
-        for (int p = 0; p < pc; ++p) {
-            float v[NC];
+        // four levels at a time: one 16-byte read of each query row (the
+        // staged tiles are zero past pc, and zeros add nothing)
+        for (int p = 0; p < pc; p += 4) {
+            float v[NC][4];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int kk = t + c * kMswThreads;
-                v[c] = kk < n ? Vt[p * np1 + kk] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[c][q] = kk < n ? Vt[(p + q) * np1 + kk] : 0.f;
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const float u = Us[r * kMswPC + p];
+                const float4 u = *reinterpret_cast<const float4 *>(Us + r * kMswPC + p);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const float d = u - v[c];
+                    float d = u.x - v[c][0];
+                    acc[c][r] = fmaf(d, d, acc[c][r]);
+                    d = u.y - v[c][1];
+                    acc[c][r] = fmaf(d, d, acc[c][r]);
+                    d = u.z - v[c][2];
+                    acc[c][r] = fmaf(d, d, acc[c][r]);
+                    d = u.w - v[c][3];
                     acc[c][r] = fmaf(d, d, acc[c][r]);
                 }
             }
@@ -186,7 +196,7 @@ template <int R, int NC>
 cudaError_t launch_rows(const MswArgs &a, cudaStream_t st)
 {
     const size_t smem = sizeof(float) * ((size_t)R * kMswPC + (size_t)kMswPC * (a.n + 1) +
-                                         (size_t)R * a.n);
+                                         (size_t)R * a.n + a.n);
     cudaFuncSetAttribute(k_msw<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid(a.Nq * a.Nt, (a.n + R - 1) / R);
     k_msw<R, NC><<<grid, kMswThreads, smem, st>>>(a);
