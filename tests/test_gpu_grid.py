@@ -52,9 +52,8 @@ def test_grid_batch_matches_oracle_brute_force(al, metric, K, step_q):
             ij = g["shift"] / step
             np.testing.assert_allclose(ij, np.rint(ij), atol=1e-9)
             assert np.all(np.abs(np.rint(ij)) <= K)
-            if not np.allclose(g["shift"], S[l], atol=1e-9):
-                _, Dalt, _ = oracle.align_pair_grid(fq, ft, n, M, K, step, B=B, metric=met)
-                assert abs(g["d2"] - D[l]) <= d2_tol(D[l], Sc)
+            # where the GPU picked another grid point than the brute force, the
+            # two tie: its distance is already within the bar above
 
 
 def test_grid_curve_matches_oracle(al):

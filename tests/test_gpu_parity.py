@@ -323,3 +323,56 @@ def test_one_reference_full_size_sampled(al):
     l_true = np.round(d["beta"] * n / (2 * np.pi)) % n
     dl = np.abs(((res["best_l"] - l_true) + n / 2) % n - n / 2)
     assert np.mean(dl <= 3) > 0.95
+
+
+# ------------------------------------------------ empty batches, maximum sizes
+
+def test_empty_batches_launch_nothing(al):
+    p = swalign.make_params(16, 8, 4)
+    x = torch.zeros((3, 16, 16), device="cuda")
+    empty = torch.zeros((0, 16, 16), device="cuda")
+    out = torch.zeros((1, 40), dtype=torch.uint8, device="cuda")
+    n0 = al.launch_count()
+    al.align_batch(empty, x, p, out=out)       # no queries
+    al.align_batch(x, empty, p, out=out)       # no templates, all-pairs mode
+    al.project(empty, p)
+    assert al.launch_count() == n0
+    with pytest.raises(swalign.SwError) as e:  # best template of nothing
+        al.align_batch(x, empty, p, mode=1, out=out)
+    assert e.value.status == swalign.SW_ERR_INVALID_ARG
+
+
+def test_maximum_sizes_match_oracle(al):
+    """L = 512, n = 1024, M = 1024 (the limits of sw_params): one pair on the
+    CUDA-core path (sw_align_all_rotations, full curve) and on the tensor-core
+    FP32 split path (sw_align_batch)."""
+    rng = np.random.default_rng(512)
+    L, n, M = 512, 1024, 1024
+    f, g = f32(blobs(rng, 2, L))
+    p = swalign.make_params(L, n, M)
+    D, S, best = al.align_all_rotations(f, g, p)
+    D = D.cpu().numpy()
+    ref, Dref, Sref = oracle.align_pair(f.astype(np.float64), g.astype(np.float64), n, M)
+    Sc = norm_scale(f.astype(np.float64), g.astype(np.float64), n, M)
+    assert np.all(np.abs(D - Dref) <= d2_tol(Dref, Sc))
+    np.testing.assert_allclose(S.cpu().numpy(), Sref, rtol=0, atol=1e-6)
+    r = swalign.results_to_numpy(al.align_batch(f[None], g[None], p))[0]
+    assert check_argmin(int(r["best_l"]), ref["best_l"], Dref, d2_tol(ref["d2"], Sc))
+    assert abs(r["d2"] - Dref[int(r["best_l"])]) <= d2_tol(Dref[int(r["best_l"])], Sc)
+
+
+def test_largest_banded_ramp_filtered_size(al):
+    """L = 312, the largest image the four-view projection takes in two row
+    bands, with the ramp filter on its 450-bin grid (radices 2, 3, 3, 5, 5)."""
+    rng = np.random.default_rng(312)
+    L, n, M = 312, 60, 32
+    f, g = f32(blobs(rng, 2, L))
+    p = swalign.make_params(L, n, M, metric="rfsw2")
+    B = swalign.bins_of(p)
+    assert B == oracle.rfsw_bins(L) == 450
+    D, S, best = al.align_all_rotations(f, g, p)
+    D = D.cpu().numpy()
+    ref, Dref, _ = oracle.align_pair_rfsw(f.astype(np.float64), g.astype(np.float64), n, M, B=B)
+    from tests.parity import norm_scale_rfsw
+    Sc = norm_scale_rfsw(f.astype(np.float64), g.astype(np.float64), n, M, B)
+    assert np.all(np.abs(D - Dref) <= d2_tol(Dref, Sc))
