@@ -19,6 +19,9 @@ namespace swk {
 namespace {
 
 constexpr int kRampThreads = 256;
+#ifndef RAMP_NSIG_MAX
+#define RAMP_NSIG_MAX 8
+#endif
 
 template <int nsig>
 __global__ void __launch_bounds__(kRampThreads)
@@ -28,7 +31,9 @@ k_ramp(const float *__restrict__ proj, int nh, int B, FftPlan plan,
     extern __shared__ float2 smr[];
     float2 *b0 = smr;
     float2 *b1 = b0 + B * nsig;
-    float2 *tws = b1 + B * nsig;  // [B]
+    float2 *tws = b1 + B * nsig;                            // [B]
+    float *tile = reinterpret_cast<float *>(tws + B);       // [2 nsig][B + 1] rows of the chunk
+    const int TS = B + 1;  // odd row stride (B is even): column reads hit distinct banks
     for (int i = threadIdx.x; i < B; i += blockDim.x) tws[i] = tw[i];
     const int img = blockIdx.x;
     const float *U = proj + (size_t)img * nh * B;
@@ -36,13 +41,17 @@ k_ramp(const float *__restrict__ proj, int nh, int B, FftPlan plan,
     float *Pm = Pp + (size_t)nh * B;                // part 1 (negative)
     const float invB = 1.f / (float)B;
     for (int r0 = 0; r0 < nh; r0 += 2 * nsig) {
-        // ---- load: signal s = rows (r0 + 2s, r0 + 2s + 1) as (re, im)
+        const int rows = min(2 * nsig, nh - r0);
+        // ---- load the chunk's rows (coalesced), then pack: signal s =
+        // rows (2s, 2s + 1) as (re, im), element-major for the FFT
+        for (int e = threadIdx.x; e < 2 * nsig * B; e += blockDim.x) {
+            const int r = e / B, b = e - r * B;
+            tile[r * TS + b] = r < rows ? U[(size_t)(r0 + r) * B + b] : 0.f;
+        }
+        __syncthreads();
         for (int t = threadIdx.x; t < B * nsig; t += blockDim.x) {
-            const int b = t / nsig, s = t % nsig;
-            const int ra = r0 + 2 * s, rb = ra + 1;
-            const float xr = ra < nh ? U[(size_t)ra * B + b] : 0.f;
-            const float xi = rb < nh ? U[(size_t)rb * B + b] : 0.f;
-            b0[t] = make_float2(xr, xi);
+            const int b = t / nsig, sg = t % nsig;
+            b0[t] = make_float2(tile[(2 * sg) * TS + b], tile[(2 * sg + 1) * TS + b]);
         }
         __syncthreads();
         float2 *X = fft_smem<nsig, -1>(b0, b1, plan, tws);
@@ -54,19 +63,19 @@ k_ramp(const float *__restrict__ proj, int nh, int B, FftPlan plan,
         }
         __syncthreads();
         const float2 *R = fft_smem<nsig, +1>(X, Y, plan, tws);
-        // ---- split and write
+        // ---- unpack to rows, then split and write (coalesced)
         for (int t = threadIdx.x; t < B * nsig; t += blockDim.x) {
-            const int b = t / nsig, s = t % nsig;
-            const int ra = r0 + 2 * s, rb = ra + 1;
+            const int b = t / nsig, sg = t % nsig;
             const float2 v = R[t];
-            if (ra < nh) {
-                Pp[(size_t)ra * B + b] = fmaxf(v.x, 0.f);
-                Pm[(size_t)ra * B + b] = fmaxf(-v.x, 0.f);
-            }
-            if (rb < nh) {
-                Pp[(size_t)rb * B + b] = fmaxf(v.y, 0.f);
-                Pm[(size_t)rb * B + b] = fmaxf(-v.y, 0.f);
-            }
+            tile[(2 * sg) * TS + b] = v.x;
+            tile[(2 * sg + 1) * TS + b] = v.y;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * B; e += blockDim.x) {
+            const int r = e / B, b = e - r * B;
+            const float v = tile[r * TS + b];
+            Pp[(size_t)(r0 + r) * B + b] = fmaxf(v, 0.f);
+            Pm[(size_t)(r0 + r) * B + b] = fmaxf(-v, 0.f);
         }
         __syncthreads();
     }
@@ -79,15 +88,25 @@ cudaError_t launch_ramp(const float *proj, int nb, int nh, int B, const FftPlan 
 {
     if (nb <= 0) return cudaSuccess;
     if (plan.n != B) return cudaErrorInvalidValue;
-    const int nsig = B <= 512 ? 16 : 4;
-    const size_t smem = sizeof(float2) * ((size_t)2 * B * nsig + B);
-    if (nsig == 16) {
-        cudaFuncSetAttribute(k_ramp<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_ramp<16><<<nb, kRampThreads, smem, st>>>(proj, nh, B, plan, tw, parts);
-    } else {
-        cudaFuncSetAttribute(k_ramp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_ramp<4><<<nb, kRampThreads, smem, st>>>(proj, nh, B, plan, tw, parts);
-    }
+    // the widest signal batch (up to RAMP_NSIG_MAX) whose buffers fit 200 KB
+    auto smem_of = [&](int ns) {
+        return sizeof(float2) * ((size_t)2 * B * ns + B) + sizeof(float) * (size_t)2 * ns * (B + 1);
+    };
+    int nsig = RAMP_NSIG_MAX;
+    while (nsig > 2 && smem_of(nsig) > 200 * 1024) nsig /= 2;
+    if (smem_of(nsig) > 200 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = smem_of(nsig);
+#define SW_RAMP_LAUNCH(NS)                                                                     \
+    do {                                                                                      \
+        cudaFuncSetAttribute(k_ramp<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                             200 * 1024);                                                     \
+        k_ramp<NS><<<nb, kRampThreads, smem, st>>>(proj, nh, B, plan, tw, parts);             \
+    } while (0)
+    if (nsig == 16) SW_RAMP_LAUNCH(16);
+    else if (nsig == 8) SW_RAMP_LAUNCH(8);
+    else if (nsig == 4) SW_RAMP_LAUNCH(4);
+    else SW_RAMP_LAUNCH(2);
+#undef SW_RAMP_LAUNCH
     return cudaGetLastError();
 }
 
