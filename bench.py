@@ -35,10 +35,10 @@ WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
 # algorithmic work per unit (stated in the design doc)
 PROJ_FLOPS_PER_CELL_ANGLE = 8           # s = <x, e> (FMA), frac, 1-t, two FMA accumulations
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
-# of the four-angle projection kernel, from one ncu capture of its 2048-image
-# launch (266,622,208 bytes);
+# of the four-angle projection kernel, from one ncu capture of its 2112-image
+# launch (2048 queries and 64 templates in one launch: 277,210,112 bytes);
 # None once that kernel changes.
-PROJ_DRAM_BYTES_PER_IMAGE = 266622208 / 2048
+PROJ_DRAM_BYTES_PER_IMAGE = 277210112 / 2112
 CORR_FLOPS_PER_PAIR_FREQ = 8 * M_LEVELS  # complex multiply-add per level
 
 

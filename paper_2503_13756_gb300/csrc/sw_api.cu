@@ -747,8 +747,14 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     o.center = at<double>(w, l.center);
     o.norm32 = at<double>(w, l.norm32);
     o.norm16 = at<double>(w, l.norm16);
-    if ((s = run_images(c, p, t, dq, p->L, Nq, 0, o, st))) return s;
-    if ((s = run_images(c, p, t, dt, p->L, Nt, Nq, o, st))) return s;
+    // queries and templates projected in one launch
+    {
+        const int nh = n / 2, B = bins_of(p);
+        SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                    return swk::launch_project(dq, nimg, p->L, p->L, nh, B, t->cs, o.proj, 0,
+                                               o.status, st, tune_of(c, p).want, dt, Nq);
+                }));
+    }
     if (p->metric == SW_METRIC_MSW2) {
         // max-sliced: quantiles (and centring vectors), then every column pair
         SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {

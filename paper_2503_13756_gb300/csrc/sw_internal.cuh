@@ -199,9 +199,12 @@ __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan 
 // out: full_n ? [nb][2*nh][B] (angles k and k+nh, the latter mirrored)
 //             : [nb][nh][B] (angles k < nh only).
 // cs: [nh] (cos, sin) of theta_k.  status: [nb], 1 for an unusable image.
+// With img2: images [0, nb_first) come from img and [nb_first, nb) from img2
+// (two batches in one launch).
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
                            const float2 *cs, float *out, int full_n, int32_t *status,
-                           cudaStream_t st, int want_ctas = 0);
+                           cudaStream_t st, int want_ctas = 0, const float *img2 = nullptr,
+                           int nb_first = -1);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
 //                        : [nb][2nh][B].

@@ -42,7 +42,7 @@ __host__ __device__ inline TileGeom tile_geom(int L)
 __global__ void __launch_bounds__(kProjThreads)
 k_project(const float *__restrict__ img, int L, int srcL, int nh, int B, int G,
           const float2 *__restrict__ cs, float *__restrict__ out, int full_n,
-          int32_t *__restrict__ status)
+          int32_t *__restrict__ status, const float *__restrict__ img2, int nb1)
 {
     extern __shared__ float smem[];
     const TileGeom tg = tile_geom(L);
@@ -57,7 +57,9 @@ k_project(const float *__restrict__ img, int L, int srcL, int nh, int B, int G,
     const int k0 = blockIdx.x * G;
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float *src = img + (size_t)imgi * srcL * srcL;
+    // images [0, nb1) from img, the rest from img2 (two batches in one launch)
+    const float *src = imgi < nb1 ? img + (size_t)imgi * srcL * srcL
+                                  : img2 + (size_t)(imgi - nb1) * srcL * srcL;
 
     if (threadIdx.x == 0) {
         s_bad = 0;
@@ -198,7 +200,7 @@ template <bool BANDED>
 __global__ void __launch_bounds__(kProjThreads)
 k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per, int kc,
            const float2 *__restrict__ cs, float *__restrict__ out, int full_n,
-           int32_t *__restrict__ status, int band_rows)
+           int32_t *__restrict__ status, int band_rows, const float *__restrict__ img2, int nb1)
 {
     // this CTA's canonical angles: [kc0, kc0 + kcn)
     const int kc0 = blockIdx.x * per;
@@ -210,7 +212,9 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
     const int rowsT = (r1 - r0) + 2 * kPad;
     __shared__ int s_bad, s_mass;
     const int imgi = blockIdx.y;
-    const float *src = img + (size_t)imgi * srcL * srcL;
+    // images [0, nb1) from img, the rest from img2 (two batches in one launch)
+    const float *src = imgi < nb1 ? img + (size_t)imgi * srcL * srcL
+                                  : img2 + (size_t)(imgi - nb1) * srcL * srcL;
     if (threadIdx.x == 0) {
         s_bad = 0;
         s_mass = 0;
@@ -367,9 +371,10 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
 
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
                            const float2 *cs, float *out, int full_n, int32_t *status,
-                           cudaStream_t st, int want_ctas)
+                           cudaStream_t st, int want_ctas, const float *img2, int nb_first)
 {
     if (nb <= 0) return cudaSuccess;
+    const int nb1 = (img2 && nb_first >= 0) ? nb_first : nb;
     const int n = 2 * nh;
     // four-view kernel: the whole image in shared memory up to L = 200;
     // beyond, two row bands per image while a band fits in 200 KB (L <= 312)
@@ -393,7 +398,8 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
             cudaFuncSetAttribute(k_project4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024);
             k_project4<false><<<grid, kProjThreads, smem, st>>>(img, L, srcL, n, B, per, kc, cs,
-                                                                out, full_n, status, L);
+                                                                out, full_n, status, L, img2,
+                                                                nb1);
         } else {
             const size_t rows = (size_t)nb * (full_n ? n : nh) * B;
             cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * rows, st);
@@ -402,7 +408,8 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
             cudaFuncSetAttribute(k_project4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024);
             k_project4<true><<<grid, kProjThreads, band_smem, st>>>(img, L, srcL, n, B, per, kc,
-                                                                    cs, out, full_n, status, band);
+                                                                    cs, out, full_n, status, band,
+                                                                    img2, nb1);
         }
         return cudaGetLastError();
     }
@@ -413,7 +420,8 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
     const size_t smem = sizeof(float) * ((size_t)(tg.T + 2 * kPad) * tg.S + (size_t)G * Bp);
     cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid((nh + G - 1) / G, nb);
-    k_project<<<grid, kProjThreads, smem, st>>>(img, L, srcL, nh, B, G, cs, out, full_n, status);
+    k_project<<<grid, kProjThreads, smem, st>>>(img, L, srcL, nh, B, G, cs, out, full_n, status,
+                                                img2, nb1);
     return cudaGetLastError();
 }
 

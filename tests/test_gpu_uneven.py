@@ -55,7 +55,7 @@ def test_graph_replay_equals_eager_calls_and_oracle():
     batch = synth.uneven_batch(n_queries=150, n_templates_per_L=6)
     g = uneven.UnevenGraph(uneven.buckets_from(batch, N_THETA, "bf16"), mode=0)
     try:
-        assert g.launches_per_replay >= 5 * 6  # every size's kernels are in the graph
+        assert g.launches_per_replay == 5 * 5  # five kernels per size, all in the graph
         for b in g.buckets:
             b.out.zero_()
         g.replay()
