@@ -173,10 +173,13 @@ int64_t sw_launch_count(const sw_ctx *ctx);
  *   choice[0] target CTA count of the projection's split over angles,
  *   choice[1] signals per FFT batch of the angle spectra (4, 8 or 16),
  *   choice[2] signals per CTA of the decision's inverse FFT (4, 8 or 16),
- *   choice[3] FFT radix order (0: radix-4 stages first, then 2, 3, 5;
- *             1: 2, 3, 5 first; 2: radix 4 first, then 5, 3, 2; 3: 5, 3, 2
- *             first); a value of 0 in choice[0..2] means the built-in default.
- * None of them changes what is computed; the radix order changes the
+ *   choice[3] FFT plan, 0..7: bit 2 clear takes the power-of-two part of
+ *             the length in radix-4 stages, set in radix-8 stages (with at
+ *             most one radix-4 stage); bits 0-1 give the order (0: the
+ *             power-of-two stages first, then 2, 3, 5; 1: 2, 3, 5 first;
+ *             2: power-of-two first, then 5, 3, 2; 3: 5, 3, 2 first);
+ *             a value of 0 in choice[0..2] means the built-in default.
+ * None of them changes what is computed; the FFT plan changes the
  * rounding only.  cache_path (may be NULL): a text file of lines
  * "swtune1 <device> L= n= M= B= prec= w s d r"; a matching line is used
  * without timing, and a new result is appended.  Synchronous (waits for its

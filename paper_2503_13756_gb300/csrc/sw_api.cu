@@ -70,34 +70,45 @@ void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
 }
 
 // Mixed-radix plan of length n.  The radix order is free (any order is a
-// valid Stockham factorisation; only the rounding and the speed change):
-// variant 0: radix-4 stages first, then 2, 3, 5; 1: 2, 3, 5 first, then the
-// 4s; 2: the 4s first, then 5, 3, 2; 3: 5, 3, 2 first, then the 4s.
-constexpr int kPlanVariants = 4;
+// valid Stockham factorisation; only the rounding and the speed change).
+// The power-of-two part is taken in radix-4 stages (variants 0-3), or in
+// radix-8 stages with at most one radix-4 stage (variants 4-7; fewer passes
+// over shared memory, more registers per item); the rest in 2, 3, 5.  Order
+// (variant & 3): 0: the power-of-two stages first, then 2, 3, 5; 1: 2, 3, 5
+// first, then the power-of-two stages; 2: power-of-two first, then 5, 3, 2;
+// 3: 5, 3, 2 first, then the power-of-two stages.
+constexpr int kPlanVariants = 8;
 
 bool fft_plan(int n, FftPlan &p, int variant = 0)
 {
     p.n = n;
     p.nst = 0;
-    int m = n, fours = 0;
-    while (m % 4 == 0) {
-        ++fours;
+    int m = n, npow = 0;
+    int pow2[swk::kMaxStages];
+    if (variant & 4)
+        while (m % 8 == 0 && npow < swk::kMaxStages) {
+            pow2[npow++] = 8;
+            m /= 8;
+        }
+    while (m % 4 == 0 && npow < swk::kMaxStages) {
+        pow2[npow++] = 4;
         m /= 4;
     }
     int rest[swk::kMaxStages], nrest = 0;
-    const bool desc = variant == 2 || variant == 3;
+    const int order = variant & 3;
+    const bool desc = order == 2 || order == 3;
     const int asc[3] = {2, 3, 5}, dsc[3] = {5, 3, 2};
     for (int q : desc ? dsc : asc)
         while (m % q == 0 && nrest < swk::kMaxStages) {
             rest[nrest++] = q;
             m /= q;
         }
-    if (m != 1 || fours + nrest > swk::kMaxStages) return false;
-    const bool fours_first = variant == 0 || variant == 2;
-    if (!fours_first)
+    if (m != 1 || npow + nrest > swk::kMaxStages) return false;
+    const bool pow2_first = order == 0 || order == 2;
+    if (!pow2_first)
         for (int i = 0; i < nrest; ++i) p.radix[p.nst++] = rest[i];
-    for (int i = 0; i < fours; ++i) p.radix[p.nst++] = 4;
-    if (fours_first)
+    for (int i = 0; i < npow; ++i) p.radix[p.nst++] = pow2[i];
+    if (pow2_first)
         for (int i = 0; i < nrest; ++i) p.radix[p.nst++] = rest[i];
     int Ns = 1;
     for (int st = 0; st < p.nst; ++st) {

@@ -65,7 +65,7 @@ __device__ __forceinline__ void centre_of(const double *ctr, int idx, int parts,
 // grid, or two parts); without it (sliced W2 with the closed-form
 // translation) the argmin reads the correlation alone.
 template <int nsig, int PARTS, bool XTRA>
-__global__ void __launch_bounds__(kDecThreads, 6)
+__global__ void __launch_bounds__(kDecThreads, XTRA ? 5 : 6)
 k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
 {
     constexpr int NP = 2 * nsig;                               // pairs per CTA

@@ -90,7 +90,7 @@ __device__ __forceinline__ float2 cmul_i(float2 a, int dir)
 // ------------------------------------------------------------------------
 // Batched complex FFT of length n over NSIG signals held in shared memory
 // as buf[k * NSIG + s] (signal s, element k), Stockham self-sorting, mixed
-// radix 2/3/4/5.  DIR = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};
+// radix 2/3/4/5/8.  DIR = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};
 // DIR = +1: the unnormalised inverse.  tw[m] = e^{-2 pi i m / n} (shared
 // memory).  Each stage reads one buffer and writes the other; returns the
 // buffer that holds the result.  Must be called by every thread of the block;
@@ -144,6 +144,31 @@ __device__ __forceinline__ void fft_stage(const float2 *__restrict__ a, float2 *
             V[0] = cadd(v[0], t1);
             V[1] = cadd(t2, t3);
             V[2] = csub(t2, t3);
+        } else if (R == 8) {
+            // two radix-4 butterflies over the even and the odd inputs, then
+            // V[m] = E[m] + w8^m O[m], V[m+4] = E[m] - w8^m O[m], with
+            // w8 = e^{DIR 2 pi i / 8} = (1 + DIR i) / sqrt(2)
+            const float r2 = 0.70710678118654752440f;
+            float2 E[4], O[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float2 e0 = cadd(v[h], v[h + 4]), e1 = csub(v[h], v[h + 4]);
+                float2 e2 = cadd(v[h + 2], v[h + 6]);
+                float2 e3 = cmul_i(csub(v[h + 2], v[h + 6]), DIR);
+                float2 *X = h == 0 ? E : O;
+                X[0] = cadd(e0, e2);
+                X[2] = csub(e0, e2);
+                X[1] = cadd(e1, e3);
+                X[3] = csub(e1, e3);
+            }
+            O[1] = make_float2(r2 * (O[1].x - DIR * O[1].y), r2 * (O[1].y + DIR * O[1].x));
+            O[2] = cmul_i(O[2], DIR);
+            O[3] = make_float2(r2 * (-O[3].x - DIR * O[3].y), r2 * (-O[3].y + DIR * O[3].x));
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                V[m] = cadd(E[m], O[m]);
+                V[m + 4] = csub(E[m], O[m]);
+            }
         } else {  // R == 5
             const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
             const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
@@ -179,6 +204,7 @@ __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan 
         const int tstep = plan.tstep[st];
         switch (plan.radix[st]) {
         case 4: fft_stage<4, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
+        case 8: fft_stage<8, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
         case 2: fft_stage<2, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
         case 3: fft_stage<3, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;
         default: fft_stage<5, NSIG, DIR>(a, b, n, Ns, rcp, tstep, tw); break;

@@ -178,7 +178,7 @@ class Aligner:
     def autotune(self, params: Params, cache_path: str | None = None):
         """Times candidate launch shapes for params and keeps the fastest
         (sw_autotune); returns the choice (projection CTA target, spectrum
-        width, decision width, FFT radix order)."""
+        width, decision width, FFT plan: radix order, radix-4 or radix-8 stages)."""
         path = None if cache_path is None else str(cache_path).encode()
         self.call("sw_autotune", ctypes.byref(params), path)
         return self.tune_choice(params)

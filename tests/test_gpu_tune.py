@@ -1,9 +1,10 @@
 """Autotuned launch shapes (sw_autotune).
 
 The choice is kept per parameter set and read back from the cache file
-without timing; every candidate launch shape and every FFT radix order gives
-results within the FP32 parity bar of the oracle (the radix order changes the
-rounding only); a bank keeps the shapes it was created with.
+without timing; every candidate launch shape and every FFT plan (radix order,
+radix-4 or radix-8 stages) gives results within the FP32 parity bar of the
+oracle (the plan changes the rounding only); a bank keeps the shapes it was
+created with.
 """
 import numpy as np
 import pytest
@@ -36,7 +37,7 @@ def test_autotune_keeps_and_caches_its_choice(al, tmp_path):
     assert al.tune_choice(p) == (0, 0, 0, 0)
     want, spec, dec, plan = al.autotune(p, cache)
     assert want in (304, 456, 912) and spec in (4, 8, 16) and dec in (4, 8, 16)
-    assert plan in (0, 1, 2, 3)
+    assert plan in range(8)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith(cache_key(al, p) + " ")
     # a second context reads the cache and launches nothing
@@ -55,6 +56,8 @@ def test_autotune_keeps_and_caches_its_choice(al, tmp_path):
 @pytest.mark.parametrize("n,plan,spec,dec", [
     (60, 0, 16, 8), (60, 1, 8, 16), (60, 2, 4, 4), (60, 3, 16, 16),
     (36, 1, 4, 16), (36, 3, 8, 4), (256, 0, 4, 16), (40, 2, 8, 8),
+    # radix-8 plans: 256 = 8 8 4, 512 = 8 8 8, 120 = 8 3 5 / 5 3 8, 1024 = 8 8 8 2
+    (256, 4, 8, 8), (512, 6, 16, 4), (120, 5, 4, 8), (120, 7, 16, 16), (1024, 4, 8, 16),
 ])
 def test_every_launch_shape_matches_oracle(al, tmp_path, n, plan, spec, dec):
     rng = np.random.default_rng(n * 10 + plan)
