@@ -6,7 +6,8 @@ leg of ``bench.py`` may.  The oracle shares no code with the CUDA library;
 ``sw_oracle.c`` is plain C compiled with gcc into ``oracle/_build``.
 
 Every routine follows a passage of the paper (cited in the C source):
-projection (Eq. radon_transform, Sec. 2.1), CDF / ICDF by cumulative sum and
+projection (Eq. radon_transform, Sec. 2.1; the linear splat, or the
+band-limited Fourier-slice projection of Sec. 2.3 and Theorem proj_nufft), CDF / ICDF by cumulative sum and
 linear interpolation (Sec. 2.3), the discrete SW2 and its rotation search
 (Eq. discrete_sw2, Eq. discrete_rot_sw2), and the translation centring derived
 from the shift lemma of App. B.  All routines are pinned by ``tests/
@@ -82,11 +83,13 @@ def _load():
             lib.orc_center.restype = None
             lib.orc_rotation_curve.argtypes = [dp, dp, ci, ci, dp]
             lib.orc_rotation_curve.restype = None
-            lib.orc_align_pair.argtypes = [dp, dp, ci, ci, ci, ci, ci, ci, dp, dp,
+            lib.orc_project_slice.argtypes = [dp, ci, ci, ci, dp]
+            lib.orc_project_slice.restype = None
+            lib.orc_align_pair.argtypes = [dp, dp, ci, ci, ci, ci, ci, ci, ci, dp, dp,
                                            ctypes.POINTER(OrcResult)]
             lib.orc_align_pair.restype = None
             lib.orc_align_all_pairs.argtypes = [dp, ci, dp, ci, ci, ci, ci, ci, ci,
-                                                ci, ci, ctypes.c_void_p]
+                                                ci, ci, ci, ctypes.c_void_p]
             lib.orc_align_all_pairs.restype = ci
             lib.orc_ramp_filter.argtypes = [dp, ci, ci, dp]
             lib.orc_ramp_filter.restype = None
@@ -101,7 +104,8 @@ def _load():
             lib.orc_grid_curve.argtypes = [dp, dp, ci, ci, ci, ci, ctypes.c_double, dp, dp]
             lib.orc_grid_curve.restype = None
             lib.orc_align_pair_grid.argtypes = [dp, dp, ci, ci, ci, ci, ci, ci, ci,
-                                                ctypes.c_double, dp, dp, ctypes.POINTER(OrcResult)]
+                                                ctypes.c_double, ci, dp, dp,
+                                                ctypes.POINTER(OrcResult)]
             lib.orc_align_pair_grid.restype = None
             lib.orc_msw_curve.argtypes = [dp, dp, ci, ci, dp]
             lib.orc_msw_curve.restype = None
@@ -142,6 +146,26 @@ def project(F, n: int, B: int | None = None) -> np.ndarray:
     return U
 
 
+def project_slice(F, n: int, B: int | None = None) -> np.ndarray:
+    """Band-limited Fourier-slice projection (signed rows), [n][B] float64:
+    U[k][b] = h g~(s_b), g~ the trigonometric polynomial on the period B h
+    whose coefficients are the exact slice samples of the cell image."""
+    F = _f64(F)
+    L = F.shape[-1]
+    B = bins_for(L, projector=1) if B is None else int(B)
+    U = np.empty((n, B), dtype=np.float64)
+    _load().orc_project_slice(_dp(F), L, int(n), B, _dp(U))
+    return U
+
+
+def bins_for(L: int, metric: int = 0, projector: int = 0) -> int:
+    """Default bin count: the smallest even 2/3/5-smooth count >= the
+    default B when the rows are filtered (metric 1) or come from the
+    Fourier-slice projector (both are transforms on the bin grid), else the
+    default B."""
+    return rfsw_bins(L) if (metric == 1 or projector) else default_bins(L)
+
+
 def quantiles(U, h: float, M: int, level_rule: int = 0) -> np.ndarray:
     """Quantile functions of the rows of ``U`` ([n][B]) at M levels -> [n][M]."""
     U = _f64(U)
@@ -178,16 +202,18 @@ def rotation_curve(Qf, Qg) -> np.ndarray:
 
 
 def align_pair(f, g, n: int, M: int, B: int | None = None, level_rule: int = 0,
-               translation: int = 1):
-    """Full curve for one pair.  Returns (result dict, D[n], shifts[n][2])."""
+               translation: int = 1, projector: int = 0):
+    """Full curve for one pair.  Returns (result dict, D[n], shifts[n][2]).
+    projector 0: linear splat; 1: Fourier slice, clipped at zero."""
     f, g = _f64(f), _f64(g)
     L = f.shape[-1]
-    B = default_bins(L) if B is None else int(B)
+    B = bins_for(L, 0, projector) if B is None else int(B)
     D = np.empty(n, dtype=np.float64)
     S = np.empty((n, 2), dtype=np.float64)
     res = OrcResult()
     _load().orc_align_pair(_dp(f), _dp(g), L, int(n), int(M), B, int(level_rule),
-                           int(translation), _dp(D), _dp(S), ctypes.byref(res))
+                           int(translation), int(projector), _dp(D), _dp(S),
+                           ctypes.byref(res))
     out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
            "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
     return out, D, S
@@ -195,16 +221,16 @@ def align_pair(f, g, n: int, M: int, B: int | None = None, level_rule: int = 0,
 
 def align_all_pairs(queries, templates, n: int, M: int, B: int | None = None,
                     level_rule: int = 0, translation: int = 1,
-                    nthreads: int | None = None) -> np.ndarray:
+                    nthreads: int | None = None, projector: int = 0) -> np.ndarray:
     """All pairs: result[i, j] aligns template j onto query i (structured array)."""
     q, t = _f64(queries), _f64(templates)
     Nq, Nt, L = q.shape[0], t.shape[0], q.shape[-1]
-    B = default_bins(L) if B is None else int(B)
+    B = bins_for(L, 0, projector) if B is None else int(B)
     nthreads = os.cpu_count() or 1 if nthreads is None else int(nthreads)
     out = np.zeros((Nq, Nt), dtype=RESULT_DTYPE)
     ok = _load().orc_align_all_pairs(_dp(q), Nq, _dp(t), Nt, L, int(n), int(M), B,
-                                     int(level_rule), int(translation), nthreads,
-                                     out.ctypes.data)
+                                     int(level_rule), int(translation), int(projector),
+                                     nthreads, out.ctypes.data)
     if not ok:
         raise MemoryError("oracle allocation failed")
     return out
@@ -259,7 +285,7 @@ def rfsw_curve(Qf, Qg, translation: int = 1):
 
 
 def align_pair_rfsw(f, g, n: int, M: int, B: int | None = None, level_rule: int = 0,
-                    translation: int = 1):
+                    translation: int = 1, projector: int = 0):
     """RFSW curve for one pair.  Returns (result dict, D[n], shifts[n][2])."""
     f, g = _f64(f), _f64(g)
     L = f.shape[-1]
@@ -268,7 +294,8 @@ def align_pair_rfsw(f, g, n: int, M: int, B: int | None = None, level_rule: int 
     S = np.empty((n, 2), dtype=np.float64)
     res = OrcResult()
     _load().orc_align_pair_rfsw(_dp(f), _dp(g), L, int(n), int(M), B, int(level_rule),
-                                int(translation), _dp(D), _dp(S), ctypes.byref(res))
+                                int(translation), int(projector), _dp(D), _dp(S),
+                                ctypes.byref(res))
     out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
            "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
     return out, D, S
@@ -276,15 +303,15 @@ def align_pair_rfsw(f, g, n: int, M: int, B: int | None = None, level_rule: int 
 
 def align_all_pairs_rfsw(queries, templates, n: int, M: int, B: int | None = None,
                          level_rule: int = 0, translation: int = 1,
-                         nthreads: int | None = None) -> np.ndarray:
+                         nthreads: int | None = None, projector: int = 0) -> np.ndarray:
     q, t = _f64(queries), _f64(templates)
     Nq, Nt, L = q.shape[0], t.shape[0], q.shape[-1]
     B = rfsw_bins(L) if B is None else int(B)
     nthreads = os.cpu_count() or 1 if nthreads is None else int(nthreads)
     out = np.zeros((Nq, Nt), dtype=RESULT_DTYPE)
     ok = _load().orc_align_all_pairs_rfsw(_dp(q), Nq, _dp(t), Nt, L, int(n), int(M), B,
-                                          int(level_rule), int(translation), nthreads,
-                                          out.ctypes.data)
+                                          int(level_rule), int(translation), int(projector),
+                                          nthreads, out.ctypes.data)
     if not ok:
         raise MemoryError("oracle allocation failed")
     return out
@@ -305,19 +332,19 @@ def grid_curve(Qf, Qg, K: int, step: float):
 
 
 def align_pair_grid(f, g, n: int, M: int, K: int, step: float, B: int | None = None,
-                    level_rule: int = 0, metric: int = 0):
+                    level_rule: int = 0, metric: int = 0, projector: int = 0):
     """One pair with the translation on the grid.  step in domain units
     (the image spans [-1, 1]); metric 0 sliced W2, 1 ramp-filtered."""
     f, g = _f64(f), _f64(g)
     L = f.shape[-1]
     if B is None:
-        B = rfsw_bins(L) if metric else default_bins(L)
+        B = bins_for(L, metric, projector)
     D = np.empty(n, dtype=np.float64)
     S = np.empty((n, 2), dtype=np.float64)
     res = OrcResult()
     _load().orc_align_pair_grid(_dp(f), _dp(g), L, int(n), int(M), int(B), int(level_rule),
-                                int(metric), int(K), float(step), _dp(D), _dp(S),
-                                ctypes.byref(res))
+                                int(metric), int(K), float(step), int(projector), _dp(D),
+                                _dp(S), ctypes.byref(res))
     out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
            "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
     return out, D, S
@@ -336,16 +363,17 @@ def msw_curve(Qf, Qg) -> np.ndarray:
 
 
 def align_pair_msw(f, g, n: int, M: int, B: int | None = None, level_rule: int = 0,
-                   translation: int = 1):
+                   translation: int = 1, projector: int = 0):
     """Max-sliced curve for one pair.  Returns (result dict, D[n], shifts[n][2])."""
     f, g = _f64(f), _f64(g)
     L = f.shape[-1]
-    B = default_bins(L) if B is None else int(B)
+    B = bins_for(L, 0, projector) if B is None else int(B)
     D = np.empty(n, dtype=np.float64)
     S = np.empty((n, 2), dtype=np.float64)
     res = OrcResult()
     _load().orc_align_pair_msw(_dp(f), _dp(g), L, int(n), int(M), B, int(level_rule),
-                               int(translation), _dp(D), _dp(S), ctypes.byref(res))
+                               int(translation), int(projector), _dp(D), _dp(S),
+                               ctypes.byref(res))
     out = {"best_l": res.best_l, "status": res.status, "angle": res.angle,
            "shift": np.array([res.shift[0], res.shift[1]]), "d2": res.d2}
     return out, D, S

@@ -18,6 +18,9 @@
  *            nodes e_j = (j - B/2) h, j = 0..B.
  *   levels   z_p = (p + 1/2)/M (level_rule 0) or z_p = p/M (level_rule 1,
  *            the left Riemann points of Theorem E3 in App. A).
+ *   projector 0 = pixel-driven linear splat (orc_project), 1 = band-limited
+ *            Fourier-slice projection (orc_project_slice, Sec. 2.3 and
+ *            Theorem proj_nufft).
  */
 #include <math.h>
 #include <stdint.h>
@@ -117,6 +120,83 @@ void orc_project(const double *F, int L, int n, int B, double *U)
             }
         }
     }
+}
+
+/* sinc(x) = sin(x)/x, sinc(0) = 1. */
+static double orc_sinc(double x)
+{
+    return x == 0.0 ? 1.0 : sin(x) / x;
+}
+
+/* Band-limited Radon projection through the Fourier slice theorem (Sec. 2.1,
+ * Eq. 1d_ift; Sec. 2.3 "Computation"; Theorem proj_nufft in App. A).  The
+ * image is the piecewise-constant density f_L that puts the mass F[r][c]
+ * uniformly on its cell, so its 2-D transform (convention
+ * H^(xi) = integral H(x) e^{-i xi.x} dx) is
+ *   f_L^(xi) = sinc(xi_1 h/2) sinc(xi_2 h/2) sum_{r,c} F[r][c] e^{-i (xi_1 x_c + xi_2 y_r)}.
+ * The projection P_theta f_L is supported on the diagonal of the square, so
+ * it is expanded on the period P = B h (the bin grid, B >= sqrt(2) L), with
+ * the slice samples at omega_j = 2 pi j / P, j = -B/2 .. B/2-1: the
+ * coefficients c_j = f_L^(omega_j e_k) / P (the slice theorem), and
+ *   g~(s) = Re sum_j c_j e^{i omega_j s},
+ * the trigonometric polynomial of the theorem (whose frequencies k pi,
+ * |k| <= L/2 on the period 2, reach the same Nyquist limit pi/h; the real
+ * part drops the imaginary contribution of the unpaired j = -B/2 term).
+ * Reading: the discrete projection is the bin mass U[k][b] = h g~(s_b) at
+ * the bin centres s_b (the piecewise-constant identification of Sec. 2.3).
+ * The rows are signed (g~ rings where f_L has edges); sum_b U[k][b] = sum F
+ * exactly, since sum_b e^{i omega_j s_b} = 0 for j != 0.
+ * Every sum is taken from its definition: f_L^ directly over all cells for
+ * every j (negative j included), g~ directly over all j; every angle k of
+ * the n is computed (no mirror or symmetry shortcut).  O(n B L^2). */
+void orc_project_slice(const double *F, int L, int n, int B, double *U)
+{
+    const double h = 2.0 / L, P = B * h;
+    double *er = (double *)malloc(sizeof(double) * L), *ei = (double *)malloc(sizeof(double) * L);
+    double *cr = (double *)malloc(sizeof(double) * B), *ci = (double *)malloc(sizeof(double) * B);
+    for (int k = 0; k < n; ++k) {
+        double ct, st;
+        orc_direction(k, n, &ct, &st);
+        for (int jj = 0; jj < B; ++jj) {
+            const int j = jj - B / 2;
+            const double om = 2.0 * ORC_PI * j / P;
+            const double x1 = om * ct, x2 = om * st;  /* xi = omega_j e_k */
+            for (int c = 0; c < L; ++c) {             /* e^{-i xi_1 x_c} */
+                const double x = -1.0 + (c + 0.5) * h;
+                er[c] = cos(x1 * x);
+                ei[c] = -sin(x1 * x);
+            }
+            double sr = 0.0, si = 0.0;
+            for (int r = 0; r < L; ++r) {
+                const double y = -1.0 + (r + 0.5) * h;
+                double rr = 0.0, ri = 0.0;            /* sum_c F[r][c] e^{-i xi_1 x_c} */
+                for (int c = 0; c < L; ++c) {
+                    rr += F[r * L + c] * er[c];
+                    ri += F[r * L + c] * ei[c];
+                }
+                const double yr = cos(x2 * y), yi = -sin(x2 * y);  /* e^{-i xi_2 y_r} */
+                sr += rr * yr - ri * yi;
+                si += rr * yi + ri * yr;
+            }
+            const double w = orc_sinc(0.5 * x1 * h) * orc_sinc(0.5 * x2 * h) / P;
+            cr[jj] = w * sr;
+            ci[jj] = w * si;
+        }
+        double *Uk = U + (size_t)k * B;
+        for (int b = 0; b < B; ++b) {
+            const double s = (b - 0.5 * (B - 1)) * h;
+            double g = 0.0;
+            for (int jj = 0; jj < B; ++jj) {
+                const double ph = 2.0 * ORC_PI * (jj - B / 2) / P * s;
+                g += cr[jj] * cos(ph) - ci[jj] * sin(ph);  /* Re(c_j e^{i omega_j s}) */
+            }
+            Uk[b] = h * g;
+        }
+    }
+    free(er);
+    free(ei);
+    free(cr);
+    free(ci);
 }
 
 /* Quantile function of one histogram (Sec. 2.3 "Computation": CDF by
@@ -278,13 +358,31 @@ void orc_rotation_curve(const double *Qf, const double *Qg, int n, int M,
     }
 }
 
-/* Per-image transform: prepare, project, quantiles and (if translation)
+/* Per-image transform: prepare, project (splat, or Fourier slice clipped at
+ * zero), quantiles and (if translation)
  * centring.  Q receives the quantiles used in the distance (centred when
  * translation != 0), a the centring vector.  Returns 0 for an unusable
  * image. */
 typedef struct {
-    int L, n, M, B, level_rule, translation;
+    int L, n, M, B, level_rule, translation, projector;
 } orc_cfg;
+
+/* Projection rows of a prepared image for the configured projector.  With
+ * the Fourier-slice projector, clip != 0 keeps max(U, 0): reading, the paper
+ * normalises the projections to probability measures (Sec. 2.3), which
+ * needs nonnegative bins, and the band-limited rows ring slightly below
+ * zero; the ramp-filtered path splits signed rows itself (clip = 0). */
+static void orc_project_cfg(const orc_cfg *cfg, const double *F, double *U, int clip)
+{
+    if (!cfg->projector) {
+        orc_project(F, cfg->L, cfg->n, cfg->B, U);
+        return;
+    }
+    orc_project_slice(F, cfg->L, cfg->n, cfg->B, U);
+    if (clip)
+        for (size_t i = 0; i < (size_t)cfg->n * cfg->B; ++i)
+            if (U[i] < 0.0) U[i] = 0.0;
+}
 
 static int orc_transform(const orc_cfg *cfg, const double *img, double *Q,
                          double *a)
@@ -295,7 +393,7 @@ static int orc_transform(const orc_cfg *cfg, const double *img, double *Q,
     double *Qraw = (double *)malloc(sizeof(double) * (size_t)n * M);
     int ok = orc_prepare(img, L, F) > 0.0;
     if (ok) {
-        orc_project(F, L, n, B, U);
+        orc_project_cfg(cfg, F, U, 1);
         ok = orc_quantiles(U, n, B, 2.0 / L, M, cfg->level_rule, Qraw);
     }
     if (ok) {
@@ -354,10 +452,10 @@ static void orc_bad(orc_result *res, int status)
  * when translation != 0) onto f.  D (may be NULL) receives the n distances,
  * shifts (may be NULL) the n optimal translations. */
 void orc_align_pair(const double *f, const double *g, int L, int n, int M,
-                    int B, int level_rule, int translation, double *D,
+                    int B, int level_rule, int translation, int projector, double *D,
                     double *shifts, orc_result *res)
 {
-    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    orc_cfg cfg = {L, n, M, B, level_rule, translation, projector};
     double *Qf = (double *)malloc(sizeof(double) * (size_t)n * M);
     double *Qg = (double *)malloc(sizeof(double) * (size_t)n * M);
     double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
@@ -447,9 +545,9 @@ static void orc_run(orc_job *job, void *(*fn)(void *), int nthreads)
  * templates [Nt][L][L], both double.  Returns 0 on allocation failure. */
 int orc_align_all_pairs(const double *queries, int Nq, const double *templates,
                         int Nt, int L, int n, int M, int B, int level_rule,
-                        int translation, int nthreads, orc_result *out)
+                        int translation, int projector, int nthreads, orc_result *out)
 {
-    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    orc_cfg cfg = {L, n, M, B, level_rule, translation, projector};
     const int nimg = Nq + Nt;
     double *imgs = (double *)malloc(sizeof(double) * (size_t)nimg * L * L);
     double *Q = (double *)malloc(sizeof(double) * (size_t)nimg * n * M);
@@ -563,7 +661,7 @@ static int orc_rfsw_transform(const orc_cfg *cfg, const double *img, double *Q)
     double *Um = (double *)malloc(sizeof(double) * (size_t)n * B);
     int ok = orc_prepare(img, L, F) > 0.0;
     if (ok) {
-        orc_project(F, L, n, B, U);
+        orc_project_cfg(cfg, F, U, 0);
         orc_rfsw_parts(U, n, B, Up, Um);
         ok = orc_quantiles(Up, n, B, 2.0 / L, M, cfg->level_rule, Q);
         ok &= orc_quantiles(Um, n, B, 2.0 / L, M, cfg->level_rule, Q + (size_t)n * M);
@@ -647,10 +745,10 @@ static void orc_rfsw_decide(const double *D, const double *S, int n, orc_result 
 /* One pair under RFSW; arguments as orc_align_pair (B must be the bin count
  * the filter runs on). */
 void orc_align_pair_rfsw(const double *f, const double *g, int L, int n, int M, int B,
-                         int level_rule, int translation, double *D, double *shifts,
-                         orc_result *res)
+                         int level_rule, int translation, int projector, double *D,
+                         double *shifts, orc_result *res)
 {
-    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    orc_cfg cfg = {L, n, M, B, level_rule, translation, projector};
     double *Qf = (double *)malloc(sizeof(double) * 2 * (size_t)n * M);
     double *Qg = (double *)malloc(sizeof(double) * 2 * (size_t)n * M);
     double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
@@ -706,9 +804,9 @@ static void *orc_rfsw_pair_worker(void *arg)
 /* All pairs under RFSW; arguments as orc_align_all_pairs. */
 int orc_align_all_pairs_rfsw(const double *queries, int Nq, const double *templates,
                              int Nt, int L, int n, int M, int B, int level_rule,
-                             int translation, int nthreads, orc_result *out)
+                             int translation, int projector, int nthreads, orc_result *out)
 {
-    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    orc_cfg cfg = {L, n, M, B, level_rule, translation, projector};
     const int nimg = Nq + Nt;
     double *imgs = (double *)malloc(sizeof(double) * (size_t)nimg * L * L);
     double *Q = (double *)malloc(sizeof(double) * 2 * (size_t)nimg * n * M);
@@ -789,10 +887,10 @@ void orc_grid_curve(const double *Qf, const double *Qg, int parts, int n, int M,
 /* One pair with the translation restricted to the grid; metric 0 = sliced
  * W2, 1 = ramp-filtered (B must be the filter's bin count). */
 void orc_align_pair_grid(const double *f, const double *g, int L, int n, int M, int B,
-                         int level_rule, int metric, int K, double step, double *D,
-                         double *shifts, orc_result *res)
+                         int level_rule, int metric, int K, double step, int projector,
+                         double *D, double *shifts, orc_result *res)
 {
-    orc_cfg cfg = {L, n, M, B, level_rule, 0};
+    orc_cfg cfg = {L, n, M, B, level_rule, 0, projector};
     const int parts = metric ? 2 : 1;
     double *Qf = (double *)malloc(sizeof(double) * parts * (size_t)n * M);
     double *Qg = (double *)malloc(sizeof(double) * parts * (size_t)n * M);
@@ -852,10 +950,10 @@ void orc_msw_curve(const double *Qf, const double *Qg, int n, int M, double *D)
 }
 
 void orc_align_pair_msw(const double *f, const double *g, int L, int n, int M, int B,
-                        int level_rule, int translation, double *D, double *shifts,
-                        orc_result *res)
+                        int level_rule, int translation, int projector, double *D,
+                        double *shifts, orc_result *res)
 {
-    orc_cfg cfg = {L, n, M, B, level_rule, translation};
+    orc_cfg cfg = {L, n, M, B, level_rule, translation, projector};
     double *Qf = (double *)malloc(sizeof(double) * (size_t)n * M);
     double *Qg = (double *)malloc(sizeof(double) * (size_t)n * M);
     double *Dl = (double *)malloc(sizeof(double) * (size_t)n);
