@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--metric", default="sw2", choices=["sw2", "rfsw2", "msw2"],
                     help="distance of the main workload (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--projector", default="splat", choices=["splat", "slice"],
+                    help="projection of the headline step: linear splat or Fourier slice")
     ap.add_argument("--configs", action="store_true",
                     help="also time the single-pair, one-reference and random-dense "
                          "configurations (GPU and oracle) and print them as a second line")
@@ -426,7 +428,8 @@ def main():
     data = synth.many_to_many(n_queries=nq, n_templates=nt, seed=synth.SEED_BASE + 2 + 1000 * rank)
     pairs_per_rank = nq * nt
     al = swalign.Aligner(local)
-    p = swalign.make_params(L, N_THETA, M_LEVELS, precision=args.precision, metric=args.metric)
+    p = swalign.make_params(L, N_THETA, M_LEVELS, precision=args.precision, metric=args.metric,
+                            projector=args.projector)
     q_h = torch.from_numpy(data["queries"]).pin_memory()
     t_h = torch.from_numpy(data["templates"]).pin_memory()
     q_d, t_d = q_h.to(dev), t_h.to(dev)

@@ -86,6 +86,25 @@ typedef enum {
                          /* call (SW_ERR_UNSUPPORTED / SW_ERR_INVALID_ARG).        */
 } sw_metric;
 
+/* Projection of the images (Sec. 2.1 Eq. radon_transform, Sec. 2.3). */
+typedef enum {
+    SW_PROJ_SPLAT = 0, /* pixel-driven linear splat: each cell's mass goes to    */
+                       /* the two bins around s = <(x, y), theta_k>, split       */
+                       /* linearly (exact mass and first moment)                 */
+    SW_PROJ_SLICE = 1  /* the paper's Fourier-slice projection (Sec. 2.3,        */
+                       /* Theorem proj_nufft): the slice samples of the cell     */
+                       /* image at omega_j = 2 pi j / (B h), |j| <= B/2, by a     */
+                       /* type-2 NUFFT, and the band-limited projection h g~(s_b) */
+                       /* at the bin centres by an inverse FFT over the bin      */
+                       /* period B h.  Rows are clipped at zero except for       */
+                       /* RFSW2, which splits the signed rows.  The default bin  */
+                       /* count is the smallest even 2/3/5-smooth count >= the   */
+                       /* default B; an explicit n_bins must be 2/3/5-smooth.    */
+                       /* One CTA holds the image's half grid in shared memory:  */
+                       /* L <= 128 (else SW_ERR_UNSUPPORTED).  Not for the       */
+                       /* allocation-free call.                                  */
+} sw_projector;
+
 typedef struct {
     int32_t L;              /* image side, 2..512                                   */
     int32_t n_theta;        /* n: even, 4..1024, factors 2, 3, 5 only               */
@@ -110,6 +129,7 @@ typedef struct {
                             /* the closed-form optimum c(l), per rotation           */
     int32_t shift_step_q;   /* grid step in sixteenths of a pixel (step = q h / 16, */
                             /* h = 2/L); must be > 0 when shift_grid > 0            */
+    int32_t projector;      /* sw_projector: how the Radon projections are formed   */
 } sw_params;
 
 typedef struct {

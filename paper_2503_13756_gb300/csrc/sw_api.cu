@@ -36,6 +36,17 @@ struct Tables {
     float2 *tw = nullptr;     // [n] e^{-2 pi i m / n}
 };
 
+// Spreading-kernel tables of the Fourier-slice projector for one L: the
+// oversampled grid N, the kernel shape beta and psi_inv [L] =
+// 1 / Psi(c - floor(L/2)), where Psi(k) = integral over |u| <= W/2 of
+// psi(u) e^{-2 pi i k u / N} du is the Fourier transform of
+// psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)).
+struct SliceTables {
+    int L = 0, N = 0;
+    float beta = 0.f;
+    float *psi_inv = nullptr;
+};
+
 void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
 {
     c.assign(n, 0.0);
@@ -143,7 +154,9 @@ int rfsw_default_bins(int L)
 int bins_of(const sw_params *p)
 {
     if (p->n_bins > 0) return p->n_bins;
-    return p->metric == SW_METRIC_RFSW2 ? rfsw_default_bins(p->L) : sw_default_bins(p->L);
+    return (p->metric == SW_METRIC_RFSW2 || p->projector == SW_PROJ_SLICE)
+               ? rfsw_default_bins(p->L)
+               : sw_default_bins(p->L);
 }
 
 // Quantile sets per image: 2 for the ramp-filtered distance (positive and
@@ -262,6 +275,7 @@ struct sw_ctx {
     size_t ws_size = 0;
     size_t limit = 0;
     std::deque<Tables> tables;  // stable addresses
+    std::deque<SliceTables> slice_tables;
     int64_t launches = 0;
     bool prof = false;
     std::vector<ProfRec> recs;
@@ -338,6 +352,10 @@ bool smooth235(int n)
     return n == 1;
 }
 
+// Dynamic shared memory one CTA may opt into on this GPU (227 KB), less the
+// projector kernel's static flags.
+constexpr size_t kSliceSmemLimit = 227 * 1024 - 64;
+
 sw_status check_params(sw_ctx *c, const sw_params *p)
 {
     if (!p) return fail(c, SW_ERR_INVALID_ARG, "params is NULL");
@@ -373,6 +391,20 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
                         "n_bins=%d: the ramp filter needs a 2/3/5-smooth bin count", p->n_bins);
         if (p->n_levels > 512)
             return fail(c, SW_ERR_INVALID_ARG, "n_levels=%d: at most 512 per part", p->n_levels);
+    }
+    if (p->projector != SW_PROJ_SPLAT && p->projector != SW_PROJ_SLICE)
+        return fail(c, SW_ERR_INVALID_ARG, "projector=%d unknown", p->projector);
+    if (p->projector == SW_PROJ_SLICE) {
+        if (p->n_bins != 0 && !smooth235(p->n_bins))
+            return fail(c, SW_ERR_INVALID_ARG,
+                        "n_bins=%d: the Fourier-slice projector needs a 2/3/5-smooth bin count",
+                        p->n_bins);
+        const int N = swk::slice_grid_n(p->L);
+        if (swk::slice_smem_bytes(N, bins_of(p)) > kSliceSmemLimit)
+            return fail(c, SW_ERR_UNSUPPORTED,
+                        "L=%d, B=%d: the Fourier-slice projector holds the image's %d-point "
+                        "half grid in one CTA's shared memory (L <= 128)",
+                        p->L, bins_of(p), N);
     }
     return SW_OK;
 }
@@ -446,6 +478,49 @@ sw_status get_tables(sw_ctx *c, int n, const Tables **out, int variant = 0)
     return SW_OK;
 }
 
+// Psi(k) = integral over |u| <= W/2 of psi(u) cos(2 pi k u / N) du.  With
+// u = (W/2) sin(phi) the square root becomes cos(phi) and the integrand
+// W/2 exp(beta (cos phi - 1)) cos(pi k W sin(phi) / N) cos(phi) is smooth on
+// [-pi/2, pi/2]; composite Simpson with 2048 panels in FP64.
+double slice_kernel_ft(int k, int N, int W, double beta)
+{
+    const int m = 2048;
+    const double a = 0.5 * M_PI, hstep = a / m;  // integrate 2 x [0, pi/2]
+    double acc = 0.0;
+    for (int i = 0; i <= m; ++i) {
+        const double ph = i * hstep;
+        const double f = std::exp(beta * (std::cos(ph) - 1.0)) *
+                         std::cos(M_PI * k * W * std::sin(ph) / N) * std::cos(ph);
+        acc += f * (i == 0 || i == m ? 1.0 : (i & 1) ? 4.0 : 2.0);
+    }
+    return 2.0 * (0.5 * W) * acc * hstep / 3.0;
+}
+
+sw_status get_slice_tables(sw_ctx *c, int L, const SliceTables **out)
+{
+    for (const SliceTables &t : c->slice_tables)
+        if (t.L == L) {
+            *out = &t;
+            return SW_OK;
+        }
+    SliceTables t;
+    t.L = L;
+    t.N = swk::slice_grid_n(L);
+    const int W = swk::slice_kernel_width();
+    // shape for the oversampling sigma = N / L: beta = 0.97 pi (1 - 1/(2 sigma)) W
+    const double sigma = (double)t.N / L;
+    const double beta = 0.97 * M_PI * (1.0 - 0.5 / sigma) * W;
+    t.beta = (float)beta;
+    std::vector<float> pinv(L);
+    for (int cidx = 0; cidx < L; ++cidx)
+        pinv[cidx] = (float)(1.0 / slice_kernel_ft(cidx - L / 2, t.N, W, (double)t.beta));
+    SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
+    SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));
+    c->slice_tables.push_back(t);
+    *out = &c->slice_tables.back();
+    return SW_OK;
+}
+
 sw_status ensure_ws(sw_ctx *c, size_t bytes)
 {
     if (bytes <= c->ws_size) return SW_OK;
@@ -485,16 +560,43 @@ struct ImageOut {
     double *center, *norm32, *norm16;
 };
 
+// Projections of nb images with the projector of p (one launch; see
+// launch_project / launch_project_slice for the layouts).  t: angle tables
+// of n_theta.
+sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const float *img,
+                       int srcL, int nb, float *out, int full_n, int32_t *status,
+                       cudaStream_t st, const float *img2 = nullptr, int nb_first = -1)
+{
+    const int nh = p->n_theta / 2, B = bins_of(p);
+    if (p->projector == SW_PROJ_SLICE) {
+        const SliceTables *sl;
+        const Tables *tn, *tb;
+        sw_status s;
+        if ((s = get_slice_tables(c, p->L, &sl)) || (s = get_tables(c, sl->N, &tn)) ||
+            (s = get_tables(c, B, &tb)))
+            return s;
+        const int clip = p->metric != SW_METRIC_RFSW2;
+        SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                    return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
+                                                     sl->psi_inv, sl->beta, sl->N, tn->plan,
+                                                     tn->tw, tb->plan, tb->tw, clip, out, full_n,
+                                                     status, st, img2, nb_first);
+                }));
+        return SW_OK;
+    }
+    SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                return swk::launch_project(img, nb, p->L, srcL, nh, B, t->cs, out, full_n,
+                                           status, st, tune_of(c, p).want, img2, nb_first);
+            }));
+    return SW_OK;
+}
+
 sw_status run_images(sw_ctx *c, const sw_params *p, const Tables *t, const float *img,
                      int srcL, int nb, int img_off, const ImageOut &o, cudaStream_t st)
 {
     const int nh = p->n_theta / 2, B = bins_of(p);
-    SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
-                return swk::launch_project(img, nb, p->L, srcL, nh, B, t->cs,
-                                           o.proj + (size_t)img_off * nh * B, 0,
-                                           o.status + img_off, st, tune_of(c, p).want);
-            }));
-    return SW_OK;
+    return project_rows(c, p, t, img, srcL, nb, o.proj + (size_t)img_off * nh * B, 0,
+                        o.status + img_off, st);
 }
 
 sw_status run_after_projection(sw_ctx *c, const sw_params *p, const Tables *t, int nb,
@@ -586,6 +688,7 @@ void sw_destroy(sw_ctx *c)
         cudaFree(t.cs64);
         cudaFree(t.tw);
     }
+    for (SliceTables &t : c->slice_tables) cudaFree(t.psi_inv);
     delete c;
 }
 
@@ -648,6 +751,12 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t))) return s;
     if (parts_of(p) == 2 && (s = get_tables(c, bins_of(p), &t))) return s;
+    if (p->projector == SW_PROJ_SLICE) {  // tables of the projector, built outside any capture
+        const SliceTables *sl;
+        if ((s = get_slice_tables(c, p->L, &sl)) || (s = get_tables(c, sl->N, &t)) ||
+            (s = get_tables(c, bins_of(p), &t)))
+            return s;
+    }
     return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);
 }
 
@@ -668,11 +777,7 @@ sw_status sw_project(sw_ctx *c, const sw_params *p, const float *d_img, int nb, 
     const size_t need = align_up(4 * (size_t)nb);
     if ((s = ensure_ws(c, need))) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
-                return swk::launch_project(d_img, nb, p->L, p->L, p->n_theta / 2, bins_of(p),
-                                           t->cs, d_proj, 1, at<int32_t>(c->ws, 0), st);
-            }));
-    return SW_OK;
+    return project_rows(c, p, t, d_img, p->L, nb, d_proj, 1, at<int32_t>(c->ws, 0), st);
 }
 
 sw_status sw_quantiles(sw_ctx *c, const sw_params *p, const float *d_proj, int nb, float *d_q,
@@ -759,13 +864,7 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     o.norm32 = at<double>(w, l.norm32);
     o.norm16 = at<double>(w, l.norm16);
     // queries and templates projected in one launch
-    {
-        const int nh = n / 2, B = bins_of(p);
-        SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
-                    return swk::launch_project(dq, nimg, p->L, p->L, nh, B, t->cs, o.proj, 0,
-                                               o.status, st, tune_of(c, p).want, dt, Nq);
-                }));
-    }
+    if ((s = project_rows(c, p, t, dq, p->L, nimg, o.proj, 0, o.status, st, dt, Nq))) return s;
     if (p->metric == SW_METRIC_MSW2) {
         // max-sliced: quantiles (and centring vectors), then every column pair
         SW_CUDA(c, launch(c, SW_STAGE_QUANTILE, st, [&] {
@@ -1178,7 +1277,8 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
                                                     sw_stream_t stream)
 {
     if (check_params(nullptr, p) != SW_OK) return SW_ERR_INVALID_ARG;
-    if (p->metric != SW_METRIC_SW2) return SW_ERR_UNSUPPORTED;  // sliced W2 only
+    if (p->metric != SW_METRIC_SW2 || p->projector != SW_PROJ_SPLAT)
+        return SW_ERR_UNSUPPORTED;  // sliced W2 on the linear splat only
     if (!d_f || !d_g || !d_best || !aligned16(d_f) || !aligned16(d_g) || !aligned16(d_best) ||
         ((uintptr_t)d_D & 7) || ((uintptr_t)d_shift & 7))
         return SW_ERR_INVALID_ARG;

@@ -9,8 +9,8 @@ namespace swk {
 
 constexpr int kMaxStages = 12;
 
-// Radix plan of an angle-length FFT: n = prod(radix[0..nst)), radices in
-// {2, 3, 4, 5}, fours first.  Built on the host with, per stage, the span
+// Radix plan of an FFT of length n: n = prod(radix[0..nst)), radices in
+// {2, 3, 4, 5, 8}.  Built on the host with, per stage, the span
 // Ns of the sub-transforms already done (product of earlier radices), a
 // multiply-high reciprocal of Ns (exact for dividends < 2^16) and the
 // twiddle index step n / (Ns r).
@@ -231,6 +231,24 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
                            const float2 *cs, float *out, int full_n, int32_t *status,
                            cudaStream_t st, int want_ctas = 0, const float *img2 = nullptr,
                            int nb_first = -1);
+
+// Band-limited projection through the Fourier slice theorem (see
+// sw_slice.cu): same input, output and status conventions as
+// launch_project.  B must be 2/3/5-smooth and even; N = slice_grid_n(L) is
+// the oversampled grid, psi_inv [L] = 1 / Psi(c - floor(L/2)) the inverse
+// Fourier transform of the spreading kernel of width slice_kernel_width()
+// and shape beta; planN/twN and planB/twB the FFT plans and twiddles of
+// lengths N and B.  clip = 1 writes max(row, 0).  One CTA per image with
+// slice_smem_bytes(N, B) of dynamic shared memory.
+int slice_grid_n(int L);
+size_t slice_smem_bytes(int N, int B);
+int slice_kernel_width();
+cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
+                                 const float2 *cs, const float *psi_inv, float beta, int N,
+                                 const FftPlan &planN, const float2 *twN, const FftPlan &planB,
+                                 const float2 *twB, int clip, float *out, int full_n,
+                                 int32_t *status, cudaStream_t st, const float *img2 = nullptr,
+                                 int nb_first = -1);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
 //                        : [nb][2nh][B].

@@ -1,0 +1,310 @@
+// sw_slice.cu -- band-limited Radon projection through the Fourier slice
+// theorem (Sec. 2.1 Eq. 1d_ift; Sec. 2.3 "Computation", which obtains the
+// central slices with a NUFFT; Theorem proj_nufft in App. A).
+//
+// The image is the cell density f_L (mass a[r][c] spread over its cell).
+// For every angle theta_k (k < n/2) and slice frequency
+// omega_j = 2 pi j / (B h), j = 0..B/2, the slice sample is
+//   f_L^(omega_j e_k) = sinc(pi t_1) sinc(pi t_2) e^{-2 pi i delta (t_1 + t_2)} T(t),
+//   T(t) = sum_{r', c'} a[r][c] e^{-2 pi i (t_1 c' + t_2 r')},   t = (j / B) e_k,
+// with c' = c - floor(L/2), r' likewise, and delta = 1/2 for even L, 0 for
+// odd (cell centre x_c = (c' + delta) h).  T is evaluated by a type-2 NUFFT,
+// and the row U[k][b] = h g~(s_b) of the band-limited projection is the
+// length-B inverse DFT of X_j = f_L^(omega_j e_k) (-1)^j e^{i pi j / B}
+// extended Hermitian (X_{-j} = conj X_j), scaled by 1/B.  Angles theta + pi
+// are the mirror rows.
+//
+// Design (GB300): one CTA per image runs the whole transform in shared
+// memory, in four phases separated by barriers.
+//  A. a[r][c] / (Psi(r') Psi(c')) (Psi: Fourier transform of the spreading
+//     kernel, host table), two image columns packed per complex signal,
+//     N-point FFTs along r' (N >= 1.5 L, zero padded), unpacked into the
+//     grid rows l2 in [-N/2 - W/2, W/2) that the interpolation reads: the
+//     targets t_2 = (j/B) sin theta >= 0 lie in one half plane, so half the
+//     oversampled grid (plus the kernel's reach) is all that is stored.
+//  B. N-point FFTs along c' of every kept row, written with W columns of
+//     periodic margin so that no tap wraps.
+//  C. per target, W x W taps of the "exponential of semicircle" kernel
+//     psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)) (separable weights);
+//  D. two angles per complex signal (X_a + i X_b, both Hermitian), B-point
+//     inverse FFT; the real and imaginary parts are the two rows.
+// With W = 9 and N / L = 1.5 the rows are within ~3e-7 (relative l2) of the
+// exact band-limited projection, at the level of FP32 rounding.
+#include "sw_internal.cuh"
+
+namespace swk {
+namespace {
+
+constexpr int kSliceThreads = 512;
+constexpr int kSig = 16;  // signals per batched FFT
+constexpr int kW = 9;     // spreading kernel width (taps per dimension)
+
+// Lowest grid index of the taps along either axis: ceil(-N/2 - W/2).
+__host__ __device__ inline int slice_lo(int N) { return -N / 2 - kW / 2; }
+__host__ __device__ inline int slice_rows(int N) { return N / 2 + kW; }
+__host__ __device__ inline int slice_cols(int N) { return N + kW; }
+// Row stride of the grid (complex elements): >= the columns and 1 mod 16, so
+// that 16 lanes reading one column of 16 rows hit 16 distinct bank pairs.
+__host__ __device__ inline int slice_stride(int N)
+{
+    const int S = slice_cols(N);
+    return S + (17 - S % 16) % 16;
+}
+
+__device__ __forceinline__ float sinc_pi(float t)
+{
+    return t == 0.f ? 1.f : sinpif(t) / (3.14159265358979323846f * t);
+}
+
+__device__ __forceinline__ float es_weight(float u, float beta)
+{
+    const float z = u * (2.f / (float)kW);
+    return __expf(beta * (sqrtf(fmaxf(1.f - z * z, 0.f)) - 1.f));
+}
+
+struct SliceArgs {
+    const float *img;   // images [0, nb1)
+    const float *img2;  // images [nb1, nb) (may equal img)
+    int nb1;
+    int L, srcL, nh, B, N;
+    float beta;
+    int clip, full_n;
+    const float2 *cs;       // [nh] (cos, sin) of theta_k
+    const float *psi_inv;   // [L] 1 / Psi(c - floor(L/2))
+    const float2 *twN, *twB;
+    float *out;
+    int32_t *status;
+};
+
+__global__ void __launch_bounds__(kSliceThreads, 1)
+k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
+{
+    extern __shared__ float2 sms[];
+    const int L = A.L, N = A.N, B = A.B, nh = A.nh;
+    const int rows = slice_rows(N), S = slice_stride(N), lo = slice_lo(N);
+    const int Fmax = N > B ? N : B;
+    float2 *G = sms;                 // [rows][S] grid
+    float2 *b0 = G + rows * S;       // FFT buffers [Fmax][kSig]
+    float2 *b1 = b0 + Fmax * kSig;
+    float2 *twn = b1 + Fmax * kSig;  // [N]
+    float2 *twb = twn + N;           // [B]
+    __shared__ int s_bad, s_mass;
+
+    const int imgi = blockIdx.x;
+    const float *src = imgi < A.nb1 ? A.img + (size_t)imgi * A.srcL * A.srcL
+                                    : A.img2 + (size_t)(imgi - A.nb1) * A.srcL * A.srcL;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_mass = 0;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) twn[i] = A.twN[i];
+    for (int i = threadIdx.x; i < B; i += blockDim.x) twb[i] = A.twB[i];
+    __syncthreads();
+    const int half = L / 2;
+    int bad = 0, mass = 0;
+
+    // ---- A: FFTs along r' of column pairs, kept rows l2 = lo + i
+    for (int c0 = 0; c0 < L; c0 += 2 * kSig) {
+        for (int t = threadIdx.x; t < N * kSig; t += blockDim.x) {
+            const int kpos = t / kSig, s = t % kSig;
+            const int r = (kpos < N / 2 ? kpos : kpos - N) + half;
+            const int c = c0 + 2 * s;
+            float2 v = make_float2(0.f, 0.f);
+            if (r >= 0 && r < L && c < L) {
+                float p[2] = {0.f, 0.f};
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int cc = c + h2;
+                    if (cc >= L) continue;
+                    float x = A.srcL == L ? __ldg(src + (size_t)r * L + cc)
+                                          : 0.25f * __ldg(src + (size_t)(r >> 1) * A.srcL + (cc >> 1));
+                    if (!isfinite(x)) {
+                        bad = 1;
+                        x = 0.f;
+                    }
+                    x = fmaxf(x, 0.f);
+                    mass |= x > 0.f;
+                    p[h2] = x * __ldg(A.psi_inv + cc);
+                }
+                const float pr = __ldg(A.psi_inv + r);
+                v = make_float2(p[0] * pr, p[1] * pr);
+            }
+            b0[t] = v;
+        }
+        __syncthreads();
+        const float2 *R = fft_smem<kSig, 1>(b0, b1, planN, twn);
+        for (int t = threadIdx.x; t < rows * kSig; t += blockDim.x) {
+            const int i = t / kSig, s = t % kSig;
+            int m = (lo + i) % N;  // l2 mod N (small grids wrap more than once)
+            if (m < 0) m += N;
+            const int mm = m == 0 ? 0 : N - m;
+            const float2 Z = R[m * kSig + s];
+            const float2 Zc = cconj(R[mm * kSig + s]);
+            // column c: (Z + conj Z(-l2)) / 2; column c + 1: (Z - conj Z(-l2)) / (2i)
+            const float2 d = make_float2(0.5f * (Z.x - Zc.x), 0.5f * (Z.y - Zc.y));
+            const int c = c0 + 2 * s;
+            if (c < L) G[i * S + c] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+            if (c + 1 < L) G[i * S + c + 1] = make_float2(d.y, -d.x);
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(&s_bad, 1);
+    if (mass) atomicOr(&s_mass, 1);
+
+    // ---- B: FFTs along c' of every kept row, columns l1 = lo + q
+    for (int i0 = 0; i0 < rows; i0 += kSig) {
+        for (int t = threadIdx.x; t < N * kSig; t += blockDim.x) {
+            const int kpos = t / kSig, s = t % kSig;
+            const int i = i0 + s;
+            const int c = (kpos < N / 2 ? kpos : kpos - N) + half;
+            b0[t] = (i < rows && c >= 0 && c < L) ? G[i * S + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2 *R = fft_smem<kSig, 1>(b0, b1, planN, twn);
+        for (int t = threadIdx.x; t < slice_cols(N) * kSig; t += blockDim.x) {
+            const int q = t / kSig, s = t % kSig;
+            const int i = i0 + s;
+            if (i >= rows) continue;
+            int m = (lo + q) % N;
+            if (m < 0) m += N;
+            G[i * S + q] = R[m * kSig + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A.status[imgi] = (s_bad || !s_mass) ? 1 : 0;
+
+    // ---- C + D: slice samples of 2 kSig angles, inverse FFTs, rows out
+    const int nj = B / 2 + 1;
+    const float rNB = (float)N / (float)B, invB = 1.f / (float)B, hN = 0.5f * (float)N;
+    const float twodelta = (L & 1) ? 0.f : 1.f;
+    const int nrow = A.full_n ? 2 * nh : nh;
+    float *outi = A.out + (size_t)imgi * nrow * B;
+    for (int k0 = 0; k0 < nh; k0 += 2 * kSig) {
+        for (int t = threadIdx.x; t < nj * kSig; t += blockDim.x) {
+            const int s = t / nj, j = t % nj;
+            const float jf = (float)j;
+            float2 X[2];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int k = k0 + 2 * s + h2;
+                X[h2] = make_float2(0.f, 0.f);
+                if (k >= nh) continue;
+                const float2 e = __ldg(A.cs + k);
+                // target y = -t N on the grid (t = (j/B) e), kept inside the
+                // stored half plane whatever the rounding
+                const float y1 = fminf(fmaxf(-(jf * e.x) * rNB, -hN), hN);
+                const float y2 = fminf(fmaxf(-(jf * e.y) * rNB, -hN), 0.f);
+                const float f1 = ceilf(y1 - 0.5f * (float)kW);
+                const float f2 = ceilf(y2 - 0.5f * (float)kW);
+                float wx[kW], wy[kW];
+#pragma unroll
+                for (int a = 0; a < kW; ++a) {
+                    wx[a] = es_weight(y1 - (f1 + (float)a), A.beta);
+                    wy[a] = es_weight(y2 - (f2 + (float)a), A.beta);
+                }
+                const float2 *g = G + ((int)f2 - lo) * S + ((int)f1 - lo);
+                float tr = 0.f, ti = 0.f;
+#pragma unroll
+                for (int b = 0; b < kW; ++b) {
+                    float rr = 0.f, ri = 0.f;
+#pragma unroll
+                    for (int a = 0; a < kW; ++a) {
+                        const float2 v = g[b * S + a];
+                        rr = fmaf(wx[a], v.x, rr);
+                        ri = fmaf(wx[a], v.y, ri);
+                    }
+                    tr = fmaf(wy[b], rr, tr);
+                    ti = fmaf(wy[b], ri, ti);
+                }
+                // sinc factors of the cell, and the phase
+                // (-1)^j e^{i pi j (1 - 2 delta (e_1 + e_2)) / B}
+                const float sc = sinc_pi(jf * e.x * invB) * sinc_pi(jf * e.y * invB);
+                float sp, cp;
+                sincospif(jf * (1.f - twodelta * (e.x + e.y)) * invB, &sp, &cp);
+                if (j & 1) {
+                    sp = -sp;
+                    cp = -cp;
+                }
+                X[h2] = make_float2(sc * (tr * cp - ti * sp), sc * (tr * sp + ti * cp));
+            }
+            if (j == 0 || 2 * j == B) {
+                b0[j * kSig + s] = make_float2(X[0].x, X[1].x);
+            } else {
+                // Y_j = X_a + i X_b,  Y_{B-j} = conj X_a + i conj X_b
+                b0[j * kSig + s] = make_float2(X[0].x - X[1].y, X[0].y + X[1].x);
+                b0[(B - j) * kSig + s] = make_float2(X[0].x + X[1].y, X[1].x - X[0].y);
+            }
+        }
+        __syncthreads();
+        const float2 *R = fft_smem<kSig, 1>(b0, b1, planB, twb);
+        for (int t = threadIdx.x; t < 2 * kSig * B; t += blockDim.x) {
+            const int row = t / B, b = t % B;
+            const int k = k0 + row;
+            if (k >= nh) continue;
+            const float2 y = R[b * kSig + (row >> 1)];
+            float v = ((row & 1) ? y.y : y.x) * invB;
+            if (A.clip) v = fmaxf(v, 0.f);
+            outi[(size_t)k * B + b] = v;
+            if (A.full_n) outi[(size_t)(nh + k) * B + (B - 1 - b)] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int slice_grid_n(int L)
+{
+    int N = (3 * L + 1) / 2;  // ceil(1.5 L)
+    for (;; ++N) {
+        int m = N;
+        for (int q : {2, 3, 5})
+            while (m % q == 0) m /= q;
+        if (m == 1 && (N & 1) == 0) return N;
+    }
+}
+
+size_t slice_smem_bytes(int N, int B)
+{
+    const int Fmax = N > B ? N : B;
+    return sizeof(float2) * ((size_t)slice_rows(N) * slice_stride(N) + 2 * (size_t)Fmax * kSig +
+                             (size_t)N + (size_t)B);
+}
+
+int slice_kernel_width() { return kW; }
+
+cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
+                                 const float2 *cs, const float *psi_inv, float beta, int N,
+                                 const FftPlan &planN, const float2 *twN, const FftPlan &planB,
+                                 const float2 *twB, int clip, float *out, int full_n,
+                                 int32_t *status, cudaStream_t st, const float *img2,
+                                 int nb_first)
+{
+    if (nb <= 0) return cudaSuccess;
+    SliceArgs a;
+    a.img = img;
+    a.img2 = img2 ? img2 : img;
+    a.nb1 = (img2 && nb_first >= 0) ? nb_first : nb;
+    a.L = L;
+    a.srcL = srcL;
+    a.nh = nh;
+    a.B = B;
+    a.N = N;
+    a.beta = beta;
+    a.clip = clip;
+    a.full_n = full_n;
+    a.cs = cs;
+    a.psi_inv = psi_inv;
+    a.twN = twN;
+    a.twB = twB;
+    a.out = out;
+    a.status = status;
+    const size_t smem = slice_smem_bytes(N, B);
+    cudaError_t e = cudaFuncSetAttribute(k_project_slice,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_project_slice<<<nb, kSliceThreads, smem, st>>>(a, planN, planB);
+    return cudaGetLastError();
+}
+
+}  // namespace swk

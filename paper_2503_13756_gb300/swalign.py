@@ -30,31 +30,35 @@ assert RESULT_DTYPE.itemsize == 40
 class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
                 ("L", "n_theta", "n_levels", "n_bins", "translation", "level_rule",
-                 "gemm_precision", "metric", "shift_grid", "shift_step_q")]
+                 "gemm_precision", "metric", "shift_grid", "shift_step_q", "projector")]
 
 
 METRIC = {"sw2": 0, "rfsw2": 1, "msw2": 2}
+PROJECTOR = {"splat": 0, "slice": 1}
 
 
 def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
-                precision="fp32", metric="sw2", shift_grid=0, shift_step_q=0) -> Params:
+                precision="fp32", metric="sw2", shift_grid=0, shift_step_q=0,
+                projector="splat") -> Params:
     """shift_grid = K > 0 restricts the translation to the grid (i, j) * step,
-    |i|, |j| <= K, step = shift_step_q / 16 pixel."""
+    |i|, |j| <= K, step = shift_step_q / 16 pixel.  projector "splat" (linear
+    splat) or "slice" (band-limited Fourier-slice projection, L <= 128)."""
     prec = PREC[precision] if isinstance(precision, str) else int(precision)
     met = METRIC[metric] if isinstance(metric, str) else int(metric)
+    proj = PROJECTOR[projector] if isinstance(projector, str) else int(projector)
     return Params(int(L), int(n_theta), int(n_levels), int(n_bins), int(translation),
-                  int(level_rule), prec, met, int(shift_grid), int(shift_step_q))
+                  int(level_rule), prec, met, int(shift_grid), int(shift_step_q), proj)
 
 
 def bins_of(params: Params) -> int:
     """Bin count B the library uses for params (sw_params.n_bins, else the
-    default; the ramp-filtered metric rounds the default up to an even
-    2/3/5-smooth count)."""
+    default; the ramp-filtered metric and the Fourier-slice projector round
+    the default up to an even 2/3/5-smooth count)."""
     if params.n_bins:
         return int(params.n_bins)
     L = int(params.L)
     B = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2 if L >= 1 else 0
-    if params.metric == METRIC["rfsw2"]:
+    if params.metric == METRIC["rfsw2"] or params.projector == PROJECTOR["slice"]:
         def smooth(m):
             for q in (2, 3, 5):
                 while m % q == 0:

@@ -36,7 +36,7 @@ def test_result_struct_layout():
     # double shift[2], double d2 -> 40 bytes, d2 at offset 32
     assert swalign.RESULT_DTYPE.itemsize == 40
     assert swalign.RESULT_DTYPE.fields["d2"][1] == 32
-    assert ctypes.sizeof(swalign.Params) == 40
+    assert ctypes.sizeof(swalign.Params) == 44
 
 
 def test_params_fields_follow_the_header():
@@ -53,6 +53,8 @@ def test_default_bins_agree_with_oracle():
         assert lib.sw_default_bins(L) == oracle.default_bins(L)
         p = swalign.make_params(L, 8, 4, metric="rfsw2")
         assert swalign.bins_of(p) == oracle.rfsw_bins(L)
+        p = swalign.make_params(L, 8, 4, projector="slice")
+        assert swalign.bins_of(p) == oracle.bins_for(L, projector=1)
 
 
 def test_workspace_size_is_host_computable():
