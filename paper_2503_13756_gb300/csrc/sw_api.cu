@@ -36,15 +36,17 @@ struct Tables {
     float2 *tw = nullptr;     // [n] e^{-2 pi i m / n}
 };
 
-// Spreading-kernel tables of the Fourier-slice projector for one L: the
-// oversampled grid N, the kernel shape beta and psi_inv [L] =
-// 1 / Psi(c - floor(L/2)), where Psi(k) = integral over |u| <= W/2 of
-// psi(u) e^{-2 pi i k u / N} du is the Fourier transform of
-// psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)).
+// Tables of the Fourier-slice projector for one (L, n, B): the oversampled
+// grid N, the kernel shape beta, psi_inv [L] = 1 / Psi(c - floor(L/2)),
+// where Psi(k) = integral over |u| <= W/2 of psi(u) e^{-2 pi i k u / N} du is
+// the Fourier transform of psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)), the
+// tap-weight polynomials, and the per-target factor table fac [n/2][B/2 + 1].
 struct SliceTables {
-    int L = 0, N = 0;
-    float beta = 0.f;
+    int L = 0, n = 0, B = 0, N = 0;
+    double beta = 0.0;
+    swk::SliceCoef coef{};
     float *psi_inv = nullptr;
+    float2 *fac = nullptr;
 };
 
 void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
@@ -496,26 +498,86 @@ double slice_kernel_ft(int k, int N, int W, double beta)
     return 2.0 * (0.5 * W) * acc * hstep / 3.0;
 }
 
-sw_status get_slice_tables(sw_ctx *c, int L, const SliceTables **out)
+// Tap weights as polynomials in the target's offset x in (-1/2, 1/2]: for
+// tap a, psi(x + W/2 - a) interpolated at the W Chebyshev points of
+// [-1/2, 1/2] (degree W - 1 = kSliceDeg), monomial coefficients by Gaussian
+// elimination in FP64.  Error below 1e-8 for the kernel shapes used here.
+void slice_fit_weights(double beta, swk::SliceCoef &out)
 {
+    constexpr int W = swk::kSliceW, D = swk::kSliceDeg + 1;
+    static_assert(D == W, "one interpolation node per coefficient");
+    for (int a = 0; a < W; ++a) {
+        double A[D][D + 1];
+        for (int k = 0; k < D; ++k) {
+            const double x = 0.5 * std::cos(M_PI * (k + 0.5) / D);
+            const double u = x + W / 2 - a, z = 2.0 * u / W;
+            const double arg = 1.0 - z * z;
+            double xp = 1.0;
+            for (int d = 0; d < D; ++d, xp *= x) A[k][d] = xp;
+            A[k][D] = arg >= 0.0 ? std::exp(beta * (std::sqrt(arg) - 1.0)) : 0.0;
+        }
+        for (int col = 0; col < D; ++col) {  // elimination with partial pivoting
+            int piv = col;
+            for (int r = col + 1; r < D; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            for (int q = 0; q <= D; ++q) std::swap(A[col][q], A[piv][q]);
+            for (int r = 0; r < D; ++r) {
+                if (r == col) continue;
+                const double f = A[r][col] / A[col][col];
+                for (int q = col; q <= D; ++q) A[r][q] -= f * A[col][q];
+            }
+        }
+        for (int d = 0; d < D; ++d) out.c[a][d] = (float)(A[d][D] / A[d][d]);
+    }
+}
+
+sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **out)
+{
+    const int L = p->L, n = p->n_theta, B = bins_of(p);
     for (const SliceTables &t : c->slice_tables)
-        if (t.L == L) {
+        if (t.L == L && t.n == n && t.B == B) {
             *out = &t;
             return SW_OK;
         }
     SliceTables t;
     t.L = L;
+    t.n = n;
+    t.B = B;
     t.N = swk::slice_grid_n(L);
-    const int W = swk::slice_kernel_width();
+    const int W = swk::kSliceW;
     // shape for the oversampling sigma = N / L: beta = 0.97 pi (1 - 1/(2 sigma)) W
     const double sigma = (double)t.N / L;
-    const double beta = 0.97 * M_PI * (1.0 - 0.5 / sigma) * W;
-    t.beta = (float)beta;
+    t.beta = 0.97 * M_PI * (1.0 - 0.5 / sigma) * W;
+    slice_fit_weights(t.beta, t.coef);
     std::vector<float> pinv(L);
     for (int cidx = 0; cidx < L; ++cidx)
-        pinv[cidx] = (float)(1.0 / slice_kernel_ft(cidx - L / 2, t.N, W, (double)t.beta));
+        pinv[cidx] = (float)(1.0 / slice_kernel_ft(cidx - L / 2, t.N, W, t.beta));
+    // per (angle, frequency): sinc(pi t1) sinc(pi t2) (-1)^j e^{i pi j (1 - 2 delta (c + s)) / B}
+    const int nh = n / 2, nj = B / 2 + 1;
+    const double delta = (L & 1) ? 0.0 : 0.5;
+    std::vector<double> co, si;
+    angle_table(n, co, si);
+    std::vector<float2> fac((size_t)nh * nj);
+    auto sinc_pi = [](double x) { return x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x); };
+    for (int k = 0; k < nh; ++k)
+        for (int j = 0; j < nj; ++j) {
+            const double t1 = (double)j / B * co[k], t2 = (double)j / B * si[k];
+            const double amp = sinc_pi(t1) * sinc_pi(t2) * ((j & 1) ? -1.0 : 1.0);
+            const double ph = M_PI * j * (1.0 - 2.0 * delta * (co[k] + si[k])) / B;
+            fac[(size_t)k * nj + j] =
+                make_float2((float)(amp * std::cos(ph)), (float)(amp * std::sin(ph)));
+        }
     SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
     SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));
+    cudaError_t e = cudaMalloc(&t.fac, sizeof(float2) * fac.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.fac, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(t.psi_inv);
+        cudaFree(t.fac);
+        return fail(c, SW_ERR_CUDA, "slice tables: %s", cudaGetErrorString(e));
+    }
     c->slice_tables.push_back(t);
     *out = &c->slice_tables.back();
     return SW_OK;
@@ -572,15 +634,15 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
         const SliceTables *sl;
         const Tables *tn, *tb;
         sw_status s;
-        if ((s = get_slice_tables(c, p->L, &sl)) || (s = get_tables(c, sl->N, &tn)) ||
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &tn)) ||
             (s = get_tables(c, B, &tb)))
             return s;
         const int clip = p->metric != SW_METRIC_RFSW2;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                     return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
-                                                     sl->psi_inv, sl->beta, sl->N, tn->plan,
-                                                     tn->tw, tb->plan, tb->tw, clip, out, full_n,
-                                                     status, st, img2, nb_first);
+                                                     sl->psi_inv, sl->fac, sl->coef, sl->N,
+                                                     tn->plan, tn->tw, tb->plan, tb->tw, clip,
+                                                     out, full_n, status, st, img2, nb_first);
                 }));
         return SW_OK;
     }
@@ -688,7 +750,10 @@ void sw_destroy(sw_ctx *c)
         cudaFree(t.cs64);
         cudaFree(t.tw);
     }
-    for (SliceTables &t : c->slice_tables) cudaFree(t.psi_inv);
+    for (SliceTables &t : c->slice_tables) {
+        cudaFree(t.psi_inv);
+        cudaFree(t.fac);
+    }
     delete c;
 }
 
@@ -753,7 +818,7 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if (parts_of(p) == 2 && (s = get_tables(c, bins_of(p), &t))) return s;
     if (p->projector == SW_PROJ_SLICE) {  // tables of the projector, built outside any capture
         const SliceTables *sl;
-        if ((s = get_slice_tables(c, p->L, &sl)) || (s = get_tables(c, sl->N, &t)) ||
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &t)) ||
             (s = get_tables(c, bins_of(p), &t)))
             return s;
     }

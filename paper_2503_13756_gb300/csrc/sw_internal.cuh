@@ -235,19 +235,29 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
 // Band-limited projection through the Fourier slice theorem (see
 // sw_slice.cu): same input, output and status conventions as
 // launch_project.  B must be 2/3/5-smooth and even; N = slice_grid_n(L) is
-// the oversampled grid, psi_inv [L] = 1 / Psi(c - floor(L/2)) the inverse
-// Fourier transform of the spreading kernel of width slice_kernel_width()
-// and shape beta; planN/twN and planB/twB the FFT plans and twiddles of
-// lengths N and B.  clip = 1 writes max(row, 0).  One CTA per image with
-// slice_smem_bytes(N, B) of dynamic shared memory.
+// the oversampled grid, psi_inv [L] = 1 / Psi(c - floor(L/2)) with Psi the
+// Fourier transform of the spreading kernel; planN/twN and planB/twB the FFT
+// plans and twiddles of lengths N and B.  clip = 1 writes max(row, 0).  One
+// CTA per image with slice_smem_bytes(N, B) of dynamic shared memory.
+// The spreading kernel's width (taps per axis) and the degree of the
+// polynomial that gives each tap's weight from the target's offset x in
+// (-1/2, 1/2] from its grid cell: c[a] holds psi(x + W/2 - a) as
+// sum_d c[a][d] x^d.
+constexpr int kSliceW = 9;
+constexpr int kSliceDeg = 8;
+struct SliceCoef {
+    float c[kSliceW][kSliceDeg + 1];
+};
 int slice_grid_n(int L);
 size_t slice_smem_bytes(int N, int B);
-int slice_kernel_width();
+// fac: [nh][B/2 + 1] sinc(pi t_1) sinc(pi t_2) (-1)^j e^{i pi j (1 - 2 delta (cos + sin)) / B}
+// with t = (j / B)(cos theta_k, sin theta_k), delta = 1/2 for even L, else 0.
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
-                                 const float2 *cs, const float *psi_inv, float beta, int N,
-                                 const FftPlan &planN, const float2 *twN, const FftPlan &planB,
-                                 const float2 *twB, int clip, float *out, int full_n,
-                                 int32_t *status, cudaStream_t st, const float *img2 = nullptr,
+                                 const float2 *cs, const float *psi_inv, const float2 *fac,
+                                 const SliceCoef &coef, int N, const FftPlan &planN,
+                                 const float2 *twN, const FftPlan &planB, const float2 *twB,
+                                 int clip, float *out, int full_n, int32_t *status,
+                                 cudaStream_t st, const float *img2 = nullptr,
                                  int nb_first = -1);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)

@@ -22,12 +22,24 @@
 //     grid rows l2 in [-N/2 - W/2, W/2) that the interpolation reads: the
 //     targets t_2 = (j/B) sin theta >= 0 lie in one half plane, so half the
 //     oversampled grid (plus the kernel's reach) is all that is stored.
-//  B. N-point FFTs along c' of every kept row, written with W columns of
-//     periodic margin so that no tap wraps.
+//  B. N-point FFTs along c' of every kept row, written so that no tap wraps:
+//     the columns l1 <= W - 1 in increasing order ("left", read by targets
+//     whose first tap is at l1 <= 0, i.e. theta <= pi/2), then the columns
+//     l1 >= 1 in decreasing order ("right", theta > pi/2).  With a row stride
+//     of 1 mod 16 (complex elements) the bank of a tap moves by
+//     -(|cos theta| + sin theta) in [-sqrt 2, -1] from one target of a ray to
+//     the next in both halves, so the 16 lanes of a 64-bit access stay within
+//     two passes; one increasing layout for both halves puts every lane of a
+//     ray near theta = 3 pi / 4 on one bank.
 //  C. per target, W x W taps of the "exponential of semicircle" kernel
-//     psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)) (separable weights);
+//     psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)); the W weights along each
+//     axis are degree-8 polynomials in the target's offset from its grid
+//     cell (fitted on the host in FP64 within 1e-8 of psi; coefficients in
+//     the kernel parameters), and the cell's sinc factors and the phase come
+//     from a host table per (angle, frequency).
 //  D. two angles per complex signal (X_a + i X_b, both Hermitian), B-point
-//     inverse FFT; the real and imaginary parts are the two rows.
+//     inverse FFT; the real and imaginary parts are the two rows, staged
+//     through shared memory so that the row stores coalesce.
 // With W = 9 and N / L = 1.5 the rows are within ~3e-7 (relative l2) of the
 // exact band-limited projection, at the level of FP32 rounding.
 #include "sw_internal.cuh"
@@ -37,29 +49,21 @@ namespace {
 
 constexpr int kSliceThreads = 512;
 constexpr int kSig = 16;  // signals per batched FFT
-constexpr int kW = 9;     // spreading kernel width (taps per dimension)
+constexpr int kPad = kSig; // extra complex elements per FFT buffer (output staging)
 
 // Lowest grid index of the taps along either axis: ceil(-N/2 - W/2).
-__host__ __device__ inline int slice_lo(int N) { return -N / 2 - kW / 2; }
-__host__ __device__ inline int slice_rows(int N) { return N / 2 + kW; }
-__host__ __device__ inline int slice_cols(int N) { return N + kW; }
+__host__ __device__ inline int slice_lo(int N) { return -N / 2 - kSliceW / 2; }
+__host__ __device__ inline int slice_rows(int N) { return N / 2 + kSliceW; }
+// Left columns l1 in [lo, W - 1], then right columns l1 in [1, N/2 + W/2]
+// reversed.
+__host__ __device__ inline int slice_left(int N) { return kSliceW - slice_lo(N); }
+__host__ __device__ inline int slice_right(int N) { return N / 2 + kSliceW / 2; }
 // Row stride of the grid (complex elements): >= the columns and 1 mod 16, so
 // that 16 lanes reading one column of 16 rows hit 16 distinct bank pairs.
 __host__ __device__ inline int slice_stride(int N)
 {
-    const int S = slice_cols(N);
+    const int S = slice_left(N) + slice_right(N);
     return S + (17 - S % 16) % 16;
-}
-
-__device__ __forceinline__ float sinc_pi(float t)
-{
-    return t == 0.f ? 1.f : sinpif(t) / (3.14159265358979323846f * t);
-}
-
-__device__ __forceinline__ float es_weight(float u, float beta)
-{
-    const float z = u * (2.f / (float)kW);
-    return __expf(beta * (sqrtf(fmaxf(1.f - z * z, 0.f)) - 1.f));
 }
 
 struct SliceArgs {
@@ -67,13 +71,14 @@ struct SliceArgs {
     const float *img2;  // images [nb1, nb) (may equal img)
     int nb1;
     int L, srcL, nh, B, N;
-    float beta;
     int clip, full_n;
     const float2 *cs;       // [nh] (cos, sin) of theta_k
     const float *psi_inv;   // [L] 1 / Psi(c - floor(L/2))
+    const float2 *fac;      // [nh][B/2 + 1] sinc factors times phase
     const float2 *twN, *twB;
     float *out;
     int32_t *status;
+    SliceCoef coef;         // tap weight polynomials (kernel parameter bank)
 };
 
 __global__ void __launch_bounds__(kSliceThreads, 1)
@@ -82,12 +87,14 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
     extern __shared__ float2 sms[];
     const int L = A.L, N = A.N, B = A.B, nh = A.nh;
     const int rows = slice_rows(N), S = slice_stride(N), lo = slice_lo(N);
+    const int nleft = slice_left(N), nright = slice_right(N);
     const int Fmax = N > B ? N : B;
-    float2 *G = sms;                 // [rows][S] grid
-    float2 *b0 = G + rows * S;       // FFT buffers [Fmax][kSig]
-    float2 *b1 = b0 + Fmax * kSig;
-    float2 *twn = b1 + Fmax * kSig;  // [N]
-    float2 *twb = twn + N;           // [B]
+    const int fbuf = Fmax * kSig + kPad;
+    float2 *G = sms;           // [rows][S] grid
+    float2 *b0 = G + rows * S; // FFT buffers [Fmax][kSig] (+ kPad)
+    float2 *b1 = b0 + fbuf;
+    float2 *twn = b1 + fbuf;   // [N]
+    float2 *twb = twn + N;     // [B]
     __shared__ int s_bad, s_mass;
 
     const int imgi = blockIdx.x;
@@ -161,11 +168,12 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
         }
         __syncthreads();
         const float2 *R = fft_smem<kSig, 1>(b0, b1, planN, twn);
-        for (int t = threadIdx.x; t < slice_cols(N) * kSig; t += blockDim.x) {
+        for (int t = threadIdx.x; t < (nleft + nright) * kSig; t += blockDim.x) {
             const int q = t / kSig, s = t % kSig;
             const int i = i0 + s;
             if (i >= rows) continue;
-            int m = (lo + q) % N;
+            // left: l1 = lo + q;  right (reversed): l1 = N/2 + W/2 - (q - nleft)
+            int m = (q < nleft ? lo + q : nright - (q - nleft)) % N;
             if (m < 0) m += N;
             G[i * S + q] = R[m * kSig + s];
         }
@@ -175,8 +183,7 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
 
     // ---- C + D: slice samples of 2 kSig angles, inverse FFTs, rows out
     const int nj = B / 2 + 1;
-    const float rNB = (float)N / (float)B, invB = 1.f / (float)B, hN = 0.5f * (float)N;
-    const float twodelta = (L & 1) ? 0.f : 1.f;
+    const float rNB = (float)N / (float)B, hN = 0.5f * (float)N, invB = 1.f / (float)B;
     const int nrow = A.full_n ? 2 * nh : nh;
     float *outi = A.out + (size_t)imgi * nrow * B;
     for (int k0 = 0; k0 < nh; k0 += 2 * kSig) {
@@ -194,38 +201,44 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
                 // stored half plane whatever the rounding
                 const float y1 = fminf(fmaxf(-(jf * e.x) * rNB, -hN), hN);
                 const float y2 = fminf(fmaxf(-(jf * e.y) * rNB, -hN), 0.f);
-                const float f1 = ceilf(y1 - 0.5f * (float)kW);
-                const float f2 = ceilf(y2 - 0.5f * (float)kW);
-                float wx[kW], wy[kW];
+                const float f1 = ceilf(y1 - 0.5f * (float)kSliceW);
+                const float f2 = ceilf(y2 - 0.5f * (float)kSliceW);
+                // offsets from the cell, exact: y - f is in (W/2 - 1, W/2]
+                const float x1 = (y1 - f1) - (float)(kSliceW / 2);
+                const float x2 = (y2 - f2) - (float)(kSliceW / 2);
+                float wx[kSliceW], wy[kSliceW];
 #pragma unroll
-                for (int a = 0; a < kW; ++a) {
-                    wx[a] = es_weight(y1 - (f1 + (float)a), A.beta);
-                    wy[a] = es_weight(y2 - (f2 + (float)a), A.beta);
+                for (int a = 0; a < kSliceW; ++a) {
+                    float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
+#pragma unroll
+                    for (int d = kSliceDeg - 1; d >= 0; --d) {
+                        px = fmaf(px, x1, A.coef.c[a][d]);
+                        py = fmaf(py, x2, A.coef.c[a][d]);
+                    }
+                    wx[a] = px;
+                    wy[a] = py;
                 }
-                const float2 *g = G + ((int)f2 - lo) * S + ((int)f1 - lo);
+                const int i1 = (int)f1, i2 = (int)f2 - lo;
+                // left half: taps at increasing addresses; right half reversed
+                const bool left = i1 <= 0;
+                const float2 *g = G + i2 * S + (left ? i1 - lo : nleft + nright - i1);
+                const int da = left ? 1 : -1;
                 float tr = 0.f, ti = 0.f;
 #pragma unroll
-                for (int b = 0; b < kW; ++b) {
+                for (int b = 0; b < kSliceW; ++b) {
                     float rr = 0.f, ri = 0.f;
 #pragma unroll
-                    for (int a = 0; a < kW; ++a) {
-                        const float2 v = g[b * S + a];
+                    for (int a = 0; a < kSliceW; ++a) {
+                        const float2 v = g[b * S + a * da];
                         rr = fmaf(wx[a], v.x, rr);
                         ri = fmaf(wx[a], v.y, ri);
                     }
                     tr = fmaf(wy[b], rr, tr);
                     ti = fmaf(wy[b], ri, ti);
                 }
-                // sinc factors of the cell, and the phase
-                // (-1)^j e^{i pi j (1 - 2 delta (e_1 + e_2)) / B}
-                const float sc = sinc_pi(jf * e.x * invB) * sinc_pi(jf * e.y * invB);
-                float sp, cp;
-                sincospif(jf * (1.f - twodelta * (e.x + e.y)) * invB, &sp, &cp);
-                if (j & 1) {
-                    sp = -sp;
-                    cp = -cp;
-                }
-                X[h2] = make_float2(sc * (tr * cp - ti * sp), sc * (tr * sp + ti * cp));
+                // cell sinc factors and phase (host table, FP64)
+                const float2 fc = __ldg(A.fac + (size_t)k * nj + j);
+                X[h2] = make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
             }
             if (j == 0 || 2 * j == B) {
                 b0[j * kSig + s] = make_float2(X[0].x, X[1].x);
@@ -237,12 +250,22 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
         }
         __syncthreads();
         const float2 *R = fft_smem<kSig, 1>(b0, b1, planB, twb);
+        // stage rows [2 kSig][B + 1] in the free buffer: reads of R run along
+        // the signals (conflict-free), the padded rows spread the writes over
+        // distinct banks, and the stores below run along b
+        float *stg = reinterpret_cast<float *>(R == b0 ? b1 : b0);
+        for (int t = threadIdx.x; t < kSig * B; t += blockDim.x) {
+            const int s = t % kSig, b = t / kSig;
+            const float2 y = R[b * kSig + s];
+            stg[(2 * s) * (B + 1) + b] = y.x * invB;
+            stg[(2 * s + 1) * (B + 1) + b] = y.y * invB;
+        }
+        __syncthreads();
         for (int t = threadIdx.x; t < 2 * kSig * B; t += blockDim.x) {
             const int row = t / B, b = t % B;
             const int k = k0 + row;
             if (k >= nh) continue;
-            const float2 y = R[b * kSig + (row >> 1)];
-            float v = ((row & 1) ? y.y : y.x) * invB;
+            float v = stg[row * (B + 1) + b];
             if (A.clip) v = fmaxf(v, 0.f);
             outi[(size_t)k * B + b] = v;
             if (A.full_n) outi[(size_t)(nh + k) * B + (B - 1 - b)] = v;
@@ -267,18 +290,16 @@ int slice_grid_n(int L)
 size_t slice_smem_bytes(int N, int B)
 {
     const int Fmax = N > B ? N : B;
-    return sizeof(float2) * ((size_t)slice_rows(N) * slice_stride(N) + 2 * (size_t)Fmax * kSig +
-                             (size_t)N + (size_t)B);
+    return sizeof(float2) * ((size_t)slice_rows(N) * slice_stride(N) +
+                             2 * ((size_t)Fmax * kSig + kPad) + (size_t)N + (size_t)B);
 }
 
-int slice_kernel_width() { return kW; }
-
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
-                                 const float2 *cs, const float *psi_inv, float beta, int N,
-                                 const FftPlan &planN, const float2 *twN, const FftPlan &planB,
-                                 const float2 *twB, int clip, float *out, int full_n,
-                                 int32_t *status, cudaStream_t st, const float *img2,
-                                 int nb_first)
+                                 const float2 *cs, const float *psi_inv, const float2 *fac,
+                                 const SliceCoef &coef, int N, const FftPlan &planN,
+                                 const float2 *twN, const FftPlan &planB, const float2 *twB,
+                                 int clip, float *out, int full_n, int32_t *status,
+                                 cudaStream_t st, const float *img2, int nb_first)
 {
     if (nb <= 0) return cudaSuccess;
     SliceArgs a;
@@ -290,7 +311,8 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.nh = nh;
     a.B = B;
     a.N = N;
-    a.beta = beta;
+    a.coef = coef;
+    a.fac = fac;
     a.clip = clip;
     a.full_n = full_n;
     a.cs = cs;
