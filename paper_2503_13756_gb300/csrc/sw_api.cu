@@ -634,8 +634,9 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
         const SliceTables *sl;
         const Tables *tn, *tb;
         sw_status s;
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &tn)) ||
-            (s = get_tables(c, B, &tb)))
+        // radix-8 plans (variant 4): fewer shared-memory passes and barriers
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &tn, 4)) ||
+            (s = get_tables(c, B, &tb, 4)))
             return s;
         const int clip = p->metric != SW_METRIC_RFSW2;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
@@ -818,8 +819,8 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if (parts_of(p) == 2 && (s = get_tables(c, bins_of(p), &t))) return s;
     if (p->projector == SW_PROJ_SLICE) {  // tables of the projector, built outside any capture
         const SliceTables *sl;
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &t)) ||
-            (s = get_tables(c, bins_of(p), &t)))
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &t, 4)) ||
+            (s = get_tables(c, bins_of(p), &t, 4)))
             return s;
     }
     return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);

@@ -37,8 +37,8 @@
 //     cell (fitted on the host in FP64 within 1e-8 of psi; coefficients in
 //     the kernel parameters), and the cell's sinc factors and the phase come
 //     from a host table per (angle, frequency).
-//  D. two angles per complex signal (X_a + i X_b, both Hermitian), B-point
-//     inverse FFT; the real and imaginary parts are the two rows, staged
+//  D. two angles per complex signal (X_a + i X_b, both Hermitian; paired
+//     through shared memory, one target per thread in C), B-point inverse FFT; the real and imaginary parts are the two rows, staged
 //     through shared memory so that the row stores coalesce.
 // With W = 9 and N / L = 1.5 the rows are within ~3e-7 (relative l2) of the
 // exact band-limited projection, at the level of FP32 rounding.
@@ -47,9 +47,20 @@
 namespace swk {
 namespace {
 
-constexpr int kSliceThreads = 512;
-constexpr int kSig = 16;  // signals per batched FFT
-constexpr int kPad = kSig; // extra complex elements per FFT buffer (output staging)
+constexpr int kSliceThreads = 1024;
+constexpr int kSig = 16;       // signals per batched FFT
+constexpr int kPad = 2 * kSig; // extra complex elements per FFT buffer (staging)
+
+// Items of one column-pair batch per thread in phase A (N kSig <= 4 x 1024).
+constexpr int kAItems = 4;
+
+// x mod N for the small excursions of the grid indices (|x| < 2N in practice).
+__device__ __forceinline__ int wrap_n(int x, int N)
+{
+    while (x < 0) x += N;
+    while (x >= N) x -= N;
+    return x;
+}
 
 // Lowest grid index of the taps along either axis: ceil(-N/2 - W/2).
 __host__ __device__ inline int slice_lo(int N) { return -N / 2 - kSliceW / 2; }
@@ -110,14 +121,19 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
     const int half = L / 2;
     int bad = 0, mass = 0;
 
-    // ---- A: FFTs along r' of column pairs, kept rows l2 = lo + i
-    for (int c0 = 0; c0 < L; c0 += 2 * kSig) {
-        for (int t = threadIdx.x; t < N * kSig; t += blockDim.x) {
+    // ---- A: FFTs along r' of column pairs, kept rows l2 = lo + i.  The
+    // pixels of the next batch are loaded into registers before the FFT of
+    // the current one, so that their global-memory latency overlaps it.
+    float2 pre[kAItems];
+    auto load_batch = [&](int c0) {
+#pragma unroll
+        for (int m = 0; m < kAItems; ++m) {
+            const int t = threadIdx.x + m * blockDim.x;
+            float2 v = make_float2(0.f, 0.f);
             const int kpos = t / kSig, s = t % kSig;
             const int r = (kpos < N / 2 ? kpos : kpos - N) + half;
             const int c = c0 + 2 * s;
-            float2 v = make_float2(0.f, 0.f);
-            if (r >= 0 && r < L && c < L) {
+            if (t < N * kSig && r >= 0 && r < L && c < L) {
                 float p[2] = {0.f, 0.f};
 #pragma unroll
                 for (int h2 = 0; h2 < 2; ++h2) {
@@ -136,14 +152,22 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
                 const float pr = __ldg(A.psi_inv + r);
                 v = make_float2(p[0] * pr, p[1] * pr);
             }
-            b0[t] = v;
+            pre[m] = v;
         }
+    };
+    load_batch(0);
+    for (int c0 = 0; c0 < L; c0 += 2 * kSig) {
+#pragma unroll
+        for (int m = 0; m < kAItems; ++m) {
+            const int t = threadIdx.x + m * blockDim.x;
+            if (t < N * kSig) b0[t] = pre[m];
+        }
+        if (c0 + 2 * kSig < L) load_batch(c0 + 2 * kSig);
         __syncthreads();
         const float2 *R = fft_smem<kSig, 1>(b0, b1, planN, twn);
         for (int t = threadIdx.x; t < rows * kSig; t += blockDim.x) {
             const int i = t / kSig, s = t % kSig;
-            int m = (lo + i) % N;  // l2 mod N (small grids wrap more than once)
-            if (m < 0) m += N;
+            const int m = wrap_n(lo + i, N);  // l2 mod N (small grids wrap more than once)
             const int mm = m == 0 ? 0 : N - m;
             const float2 Z = R[m * kSig + s];
             const float2 Zc = cconj(R[mm * kSig + s]);
@@ -173,8 +197,7 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
             const int i = i0 + s;
             if (i >= rows) continue;
             // left: l1 = lo + q;  right (reversed): l1 = N/2 + W/2 - (q - nleft)
-            int m = (q < nleft ? lo + q : nright - (q - nleft)) % N;
-            if (m < 0) m += N;
+            const int m = wrap_n(q < nleft ? lo + q : nright - (q - nleft), N);
             G[i * S + q] = R[m * kSig + s];
         }
         __syncthreads();
@@ -186,16 +209,17 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
     const float rNB = (float)N / (float)B, hN = 0.5f * (float)N, invB = 1.f / (float)B;
     const int nrow = A.full_n ? 2 * nh : nh;
     float *outi = A.out + (size_t)imgi * nrow * B;
+    const unsigned rcp_nj = (unsigned)((((unsigned long long)1 << 32) + nj - 1) / nj);
     for (int k0 = 0; k0 < nh; k0 += 2 * kSig) {
-        for (int t = threadIdx.x; t < nj * kSig; t += blockDim.x) {
-            const int s = t / nj, j = t % nj;
-            const float jf = (float)j;
-            float2 X[2];
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int k = k0 + 2 * s + h2;
-                X[h2] = make_float2(0.f, 0.f);
-                if (k >= nh) continue;
+        // slice samples X[kk][j] of the angles k0 + kk, one target per thread,
+        // consecutive lanes along a ray; staged in b1 (free until the FFT)
+        float2 *Xs = b1;
+        for (int it = threadIdx.x; it < 2 * kSig * nj; it += blockDim.x) {
+            const int kk = (int)__umulhi((unsigned)it, rcp_nj), j = it - kk * nj;
+            const int k = k0 + kk;
+            float2 X = make_float2(0.f, 0.f);
+            if (k < nh) {
+                const float jf = (float)j;
                 const float2 e = __ldg(A.cs + k);
                 // target y = -t N on the grid (t = (j/B) e), kept inside the
                 // stored half plane whatever the rounding
@@ -238,14 +262,21 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
                 }
                 // cell sinc factors and phase (host table, FP64)
                 const float2 fc = __ldg(A.fac + (size_t)k * nj + j);
-                X[h2] = make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
+                X = make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
             }
+            Xs[kk * nj + j] = X;
+        }
+        __syncthreads();
+        // two angles per complex signal: Y_j = X_a + i X_b and
+        // Y_{B-j} = conj X_a + i conj X_b (Y_0, Y_{B/2}: real parts)
+        for (int t = threadIdx.x; t < kSig * nj; t += blockDim.x) {
+            const int s = t % kSig, j = t / kSig;
+            const float2 Xa = Xs[(2 * s) * nj + j], Xb = Xs[(2 * s + 1) * nj + j];
             if (j == 0 || 2 * j == B) {
-                b0[j * kSig + s] = make_float2(X[0].x, X[1].x);
+                b0[j * kSig + s] = make_float2(Xa.x, Xb.x);
             } else {
-                // Y_j = X_a + i X_b,  Y_{B-j} = conj X_a + i conj X_b
-                b0[j * kSig + s] = make_float2(X[0].x - X[1].y, X[0].y + X[1].x);
-                b0[(B - j) * kSig + s] = make_float2(X[0].x + X[1].y, X[1].x - X[0].y);
+                b0[j * kSig + s] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
+                b0[(B - j) * kSig + s] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);
             }
         }
         __syncthreads();
@@ -261,14 +292,18 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
             stg[(2 * s + 1) * (B + 1) + b] = y.y * invB;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < 2 * kSig * B; t += blockDim.x) {
-            const int row = t / B, b = t % B;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int row = warp; row < 2 * kSig; row += blockDim.x >> 5) {
             const int k = k0 + row;
             if (k >= nh) continue;
-            float v = stg[row * (B + 1) + b];
-            if (A.clip) v = fmaxf(v, 0.f);
-            outi[(size_t)k * B + b] = v;
-            if (A.full_n) outi[(size_t)(nh + k) * B + (B - 1 - b)] = v;
+            float *o = outi + (size_t)k * B;
+            float *om = outi + (size_t)(nh + k) * B + (B - 1);
+            for (int b = lane; b < B; b += 32) {
+                float v = stg[row * (B + 1) + b];
+                if (A.clip) v = fmaxf(v, 0.f);
+                o[b] = v;
+                if (A.full_n) om[-b] = v;
+            }
         }
         __syncthreads();
     }
