@@ -47,6 +47,8 @@ struct SliceTables {
     swk::SliceCoef coef{};
     float *psi_inv = nullptr;
     float2 *fac = nullptr;
+    uint16_t *gtab = nullptr;  // target groups per angle batch (launch_project_slice)
+    int *goff = nullptr;
 };
 
 void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
@@ -567,15 +569,55 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
             fac[(size_t)k * nj + j] =
                 make_float2((float)(amp * std::cos(ph)), (float)(amp * std::sin(ph)));
         }
+    // Half-warp groups of the targets of every batch of kSliceBatch angles:
+    // within each half of the grid (taps at increasing or decreasing
+    // addresses), the targets are bucketed by first tap address mod 16 and
+    // group g takes the g-th target of every bucket, so the 16 lanes of a
+    // group read distinct banks at every tap.  Pooling the batch's angles
+    // keeps the buckets even.  Addresses follow the kernel's FP32 arithmetic.
+    std::vector<uint16_t> gtab;
+    std::vector<int> goff(1, 0);
+    {
+        const float rNB = (float)t.N / (float)B;
+        std::vector<int> bucket[2][16];
+        for (int k0 = 0; k0 < nh; k0 += swk::kSliceBatch) {
+            for (auto &half : bucket)
+                for (auto &b : half) b.clear();
+            for (int k = k0; k < std::min(nh, k0 + swk::kSliceBatch); ++k)
+                for (int j = 0; j < nj; ++j) {
+                    bool left;
+                    const int base = swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N,
+                                                         rNB, &left);
+                    bucket[left ? 0 : 1][base & 15].push_back((k - k0) * 2048 + j);
+                }
+            for (auto &half : bucket) {
+                size_t ng = 0;
+                for (auto &b : half) ng = std::max(ng, b.size());
+                for (size_t g = 0; g < ng; ++g)
+                    for (auto &b : half)
+                        gtab.push_back(g < b.size() ? (uint16_t)b[g] : (uint16_t)0xFFFF);
+            }
+            goff.push_back((int)(gtab.size() / 16));
+        }
+    }
     SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
     SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));
     cudaError_t e = cudaMalloc(&t.fac, sizeof(float2) * fac.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(t.fac, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&t.gtab, sizeof(uint16_t) * gtab.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.gtab, gtab.data(), sizeof(uint16_t) * gtab.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&t.goff, sizeof(int) * goff.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.goff, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(t.psi_inv);
         cudaFree(t.fac);
+        cudaFree(t.gtab);
+        cudaFree(t.goff);
         return fail(c, SW_ERR_CUDA, "slice tables: %s", cudaGetErrorString(e));
     }
     c->slice_tables.push_back(t);
@@ -641,7 +683,8 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
         const int clip = p->metric != SW_METRIC_RFSW2;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                     return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
-                                                     sl->psi_inv, sl->fac, sl->coef, sl->N,
+                                                     sl->psi_inv, sl->fac, sl->gtab, sl->goff,
+                                                     sl->coef, sl->N,
                                                      tn->plan, tn->tw, tb->plan, tb->tw, clip,
                                                      out, full_n, status, st, img2, nb_first);
                 }));
@@ -754,6 +797,8 @@ void sw_destroy(sw_ctx *c)
     for (SliceTables &t : c->slice_tables) {
         cudaFree(t.psi_inv);
         cudaFree(t.fac);
+        cudaFree(t.gtab);
+        cudaFree(t.goff);
     }
     delete c;
 }

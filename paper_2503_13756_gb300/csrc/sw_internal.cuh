@@ -245,6 +245,36 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
 // sum_d c[a][d] x^d.
 constexpr int kSliceW = 9;
 constexpr int kSliceDeg = 8;
+// Angles per inverse-FFT batch of the slice projector (two per signal).
+constexpr int kSliceBatch = 32;
+// Grid geometry of the slice projector for an N-point oversampled grid (see
+// sw_slice.cu): lowest tap index, kept rows, left and right column counts
+// and the row stride (complex elements).
+__host__ __device__ inline int slice_lo(int N) { return -N / 2 - kSliceW / 2; }
+__host__ __device__ inline int slice_rows(int N) { return N / 2 + kSliceW; }
+__host__ __device__ inline int slice_left(int N) { return kSliceW - slice_lo(N); }
+__host__ __device__ inline int slice_right(int N) { return N / 2 + kSliceW / 2; }
+__host__ __device__ inline int slice_stride(int N)
+{
+    const int S = slice_left(N) + slice_right(N);
+    return S + (17 - S % 16) % 16;
+}
+// First grid address of the taps of target (j, theta) with e = (cos, sin)
+// of theta in FP32 and rNB = N / B, exactly as the kernel forms it; *left
+// tells the half (taps at increasing addresses when set, decreasing
+// otherwise).
+__host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, float rNB,
+                                              bool *left)
+{
+    const float jf = (float)j, hN = 0.5f * (float)N;
+    const float y1 = fminf(fmaxf(-(jf * ex) * rNB, -hN), hN);
+    const float y2 = fminf(fmaxf(-(jf * ey) * rNB, -hN), 0.f);
+    const int i1 = (int)ceilf(y1 - 0.5f * (float)kSliceW);
+    const int i2 = (int)ceilf(y2 - 0.5f * (float)kSliceW) - slice_lo(N);
+    *left = i1 <= 0;
+    return i2 * slice_stride(N) +
+           (*left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1);
+}
 struct SliceCoef {
     float c[kSliceW][kSliceDeg + 1];
 };
@@ -252,8 +282,14 @@ int slice_grid_n(int L);
 size_t slice_smem_bytes(int N, int B);
 // fac: [nh][B/2 + 1] sinc(pi t_1) sinc(pi t_2) (-1)^j e^{i pi j (1 - 2 delta (cos + sin)) / B}
 // with t = (j / B)(cos theta_k, sin theta_k), delta = 1/2 for even L, else 0.
+// gtab/goff: the targets (kk, j) of angle batch b (angles b kSliceBatch + kk)
+// in half-warp groups of 16 lanes, entries kk * 2048 + j or 0xFFFF (idle),
+// groups goff[b] .. goff[b+1]; every target of the batch appears once.  The
+// grouping only orders the work: each group's targets have distinct tap
+// addresses mod 16, so its loads cost one pass.
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
+                                 const uint16_t *gtab, const int *goff,
                                  const SliceCoef &coef, int N, const FftPlan &planN,
                                  const float2 *twN, const FftPlan &planB, const float2 *twB,
                                  int clip, float *out, int full_n, int32_t *status,

@@ -50,6 +50,7 @@ namespace {
 constexpr int kSliceThreads = 1024;
 constexpr int kSig = 16;       // signals per batched FFT
 constexpr int kPad = 2 * kSig; // extra complex elements per FFT buffer (staging)
+static_assert(2 * kSig == kSliceBatch, "two angles per signal of an inverse-FFT batch");
 
 // Items of one column-pair batch per thread in phase A (N kSig <= 4 x 1024).
 constexpr int kAItems = 4;
@@ -62,20 +63,10 @@ __device__ __forceinline__ int wrap_n(int x, int N)
     return x;
 }
 
-// Lowest grid index of the taps along either axis: ceil(-N/2 - W/2).
-__host__ __device__ inline int slice_lo(int N) { return -N / 2 - kSliceW / 2; }
-__host__ __device__ inline int slice_rows(int N) { return N / 2 + kSliceW; }
-// Left columns l1 in [lo, W - 1], then right columns l1 in [1, N/2 + W/2]
-// reversed.
-__host__ __device__ inline int slice_left(int N) { return kSliceW - slice_lo(N); }
-__host__ __device__ inline int slice_right(int N) { return N / 2 + kSliceW / 2; }
-// Row stride of the grid (complex elements): >= the columns and 1 mod 16, so
-// that 16 lanes reading one column of 16 rows hit 16 distinct bank pairs.
-__host__ __device__ inline int slice_stride(int N)
-{
-    const int S = slice_left(N) + slice_right(N);
-    return S + (17 - S % 16) % 16;
-}
+// Grid layout (sw_internal.cuh): rows l2 = lo + i; left columns l1 in
+// [lo, W - 1], then right columns l1 in [1, N/2 + W/2] reversed; row stride
+// 1 mod 16 complex elements, so that 16 lanes reading one column of 16 rows
+// hit 16 distinct bank pairs.
 
 struct SliceArgs {
     const float *img;   // images [0, nb1)
@@ -86,6 +77,8 @@ struct SliceArgs {
     const float2 *cs;       // [nh] (cos, sin) of theta_k
     const float *psi_inv;   // [L] 1 / Psi(c - floor(L/2))
     const float2 *fac;      // [nh][B/2 + 1] sinc factors times phase
+    const uint16_t *gtab;   // target groups per angle batch (see launch_project_slice)
+    const int *goff;
     const float2 *twN, *twB;
     float *out;
     int32_t *status;
@@ -209,16 +202,22 @@ k_project_slice(SliceArgs A, FftPlan planN, FftPlan planB)
     const float rNB = (float)N / (float)B, hN = 0.5f * (float)N, invB = 1.f / (float)B;
     const int nrow = A.full_n ? 2 * nh : nh;
     float *outi = A.out + (size_t)imgi * nrow * B;
-    const unsigned rcp_nj = (unsigned)((((unsigned long long)1 << 32) + nj - 1) / nj);
     for (int k0 = 0; k0 < nh; k0 += 2 * kSig) {
         // slice samples X[kk][j] of the angles k0 + kk, one target per thread,
-        // consecutive lanes along a ray; staged in b1 (free until the FFT)
+        // in the host's half-warp groups; staged in b1 (free until the FFT)
         float2 *Xs = b1;
-        for (int it = threadIdx.x; it < 2 * kSig * nj; it += blockDim.x) {
-            const int kk = (int)__umulhi((unsigned)it, rcp_nj), j = it - kk * nj;
+        // rows of angles beyond nh (last batch) read as zero
+        for (int it = threadIdx.x + (nh - k0) * nj; it < 2 * kSig * nj; it += blockDim.x)
+            Xs[it] = make_float2(0.f, 0.f);
+        const int bi = k0 / (2 * kSig);
+        const int g0 = __ldg(A.goff + bi), ng = __ldg(A.goff + bi + 1) - g0;
+        for (int slot = threadIdx.x; slot < ng * 16; slot += blockDim.x) {
+            const unsigned ent = __ldg(A.gtab + (size_t)(g0 + (slot >> 4)) * 16 + (slot & 15));
+            if (ent == 0xFFFFu) continue;
+            const int kk = (int)(ent >> 11), j = (int)(ent & 2047u);
             const int k = k0 + kk;
-            float2 X = make_float2(0.f, 0.f);
-            if (k < nh) {
+            float2 X;
+            {
                 const float jf = (float)j;
                 const float2 e = __ldg(A.cs + k);
                 // target y = -t N on the grid (t = (j/B) e), kept inside the
@@ -331,6 +330,7 @@ size_t slice_smem_bytes(int N, int B)
 
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
+                                 const uint16_t *gtab, const int *goff,
                                  const SliceCoef &coef, int N, const FftPlan &planN,
                                  const float2 *twN, const FftPlan &planB, const float2 *twB,
                                  int clip, float *out, int full_n, int32_t *status,
@@ -348,6 +348,8 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.N = N;
     a.coef = coef;
     a.fac = fac;
+    a.gtab = gtab;
+    a.goff = goff;
     a.clip = clip;
     a.full_n = full_n;
     a.cs = cs;
