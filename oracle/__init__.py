@@ -159,11 +159,15 @@ def project_slice(F, n: int, B: int | None = None) -> np.ndarray:
 
 
 def bins_for(L: int, metric: int = 0, projector: int = 0) -> int:
-    """Default bin count: the smallest even 2/3/5-smooth count >= the
-    default B when the rows are filtered (metric 1) or come from the
-    Fourier-slice projector (both are transforms on the bin grid), else the
+    """Default bin count.  Fourier-slice projector: the smallest multiple of
+    32 that is at least the default B and 1.5 L (the CUDA path's grid length;
+    the oracle's direct sums take any B).  Ramp-filtered rows (metric 1):
+    the smallest even 2/3/5-smooth count >= the default B.  Otherwise the
     default B."""
-    return rfsw_bins(L) if (metric == 1 or projector) else default_bins(L)
+    if projector:
+        need = max(default_bins(L), (3 * L + 1) // 2)
+        return 32 * ((need + 31) // 32)
+    return rfsw_bins(L) if metric == 1 else default_bins(L)
 
 
 def quantiles(U, h: float, M: int, level_rule: int = 0) -> np.ndarray:

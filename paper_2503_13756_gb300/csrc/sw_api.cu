@@ -10,6 +10,7 @@
 #include <cstring>
 #include <deque>
 #include <fstream>
+#include <map>
 #include <random>
 #include <sstream>
 #include <mutex>
@@ -158,9 +159,9 @@ int rfsw_default_bins(int L)
 int bins_of(const sw_params *p)
 {
     if (p->n_bins > 0) return p->n_bins;
-    return (p->metric == SW_METRIC_RFSW2 || p->projector == SW_PROJ_SLICE)
-               ? rfsw_default_bins(p->L)
-               : sw_default_bins(p->L);
+    if (p->projector == SW_PROJ_SLICE)
+        return swk::slice_default_bins(p->L, sw_default_bins(p->L));
+    return p->metric == SW_METRIC_RFSW2 ? rfsw_default_bins(p->L) : sw_default_bins(p->L);
 }
 
 // Quantile sets per image: 2 for the ramp-filtered distance (positive and
@@ -399,16 +400,19 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
     if (p->projector != SW_PROJ_SPLAT && p->projector != SW_PROJ_SLICE)
         return fail(c, SW_ERR_INVALID_ARG, "projector=%d unknown", p->projector);
     if (p->projector == SW_PROJ_SLICE) {
-        if (p->n_bins != 0 && !smooth235(p->n_bins))
+        // the bins are also the oversampled grid: a multiple of 32 (one
+        // warp's FFT) and at least 1.5 L (the NUFFT's accuracy)
+        const int B = bins_of(p);
+        if (p->n_bins != 0 && (B % 32 != 0 || 2 * B < 3 * p->L))
             return fail(c, SW_ERR_INVALID_ARG,
-                        "n_bins=%d: the Fourier-slice projector needs a 2/3/5-smooth bin count",
+                        "n_bins=%d: the Fourier-slice projector needs a multiple of 32 that "
+                        "is at least 1.5 L",
                         p->n_bins);
-        const int N = swk::slice_grid_n(p->L);
-        if (swk::slice_smem_bytes(N, bins_of(p)) > kSliceSmemLimit)
+        if (B / 32 > 6 || swk::slice_smem_bytes(B) > kSliceSmemLimit)
             return fail(c, SW_ERR_UNSUPPORTED,
-                        "L=%d, B=%d: the Fourier-slice projector holds the image's %d-point "
-                        "half grid in one CTA's shared memory (L <= 128)",
-                        p->L, bins_of(p), N);
+                        "L=%d, B=%d: the Fourier-slice projector holds the image's half grid "
+                        "in one CTA's shared memory (B <= 192, L <= 128)",
+                        p->L, B);
     }
     return SW_OK;
 }
@@ -545,7 +549,7 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     t.L = L;
     t.n = n;
     t.B = B;
-    t.N = swk::slice_grid_n(L);
+    t.N = B;  // the oversampled grid is the bin count
     const int W = swk::kSliceW;
     // shape for the oversampling sigma = N / L: beta = 0.97 pi (1 - 1/(2 sigma)) W
     const double sigma = (double)t.N / L;
@@ -575,27 +579,53 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     // group g takes the g-th target of every bucket, so the 16 lanes of a
     // group read distinct banks at every tap.  Pooling the batch's angles
     // keeps the buckets even.  Addresses follow the kernel's FP32 arithmetic.
+    // Targets with the same first tap address (near the origin the angles of
+    // a batch meet) read the same words, which the hardware broadcasts: such
+    // a class may fill several lanes of one group.
     std::vector<uint16_t> gtab;
     std::vector<int> goff(1, 0);
     {
-        const float rNB = (float)t.N / (float)B;
-        std::vector<int> bucket[2][16];
         for (int k0 = 0; k0 < nh; k0 += swk::kSliceBatch) {
-            for (auto &half : bucket)
-                for (auto &b : half) b.clear();
+            // [half][residue] -> address classes, each a list of targets
+            std::map<int, std::vector<int>> cls[2][16];
             for (int k = k0; k < std::min(nh, k0 + swk::kSliceBatch); ++k)
                 for (int j = 0; j < nj; ++j) {
                     bool left;
-                    const int base = swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N,
-                                                         rNB, &left);
-                    bucket[left ? 0 : 1][base & 15].push_back((k - k0) * 2048 + j);
+                    const int base =
+                        swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N, &left);
+                    cls[left ? 0 : 1][base & 15][base].push_back((k - k0) * 128 + j);
                 }
-            for (auto &half : bucket) {
-                size_t ng = 0;
-                for (auto &b : half) ng = std::max(ng, b.size());
-                for (size_t g = 0; g < ng; ++g)
-                    for (auto &b : half)
-                        gtab.push_back(g < b.size() ? (uint16_t)b[g] : (uint16_t)0xFFFF);
+            for (auto &half : cls) {
+                std::vector<std::vector<int>> q[16];  // per residue, largest class first
+                for (int r = 0; r < 16; ++r) {
+                    for (auto &kv : half[r]) q[r].push_back(kv.second);
+                    std::stable_sort(q[r].begin(), q[r].end(),
+                                     [](const std::vector<int> &a, const std::vector<int> &b) {
+                                         return a.size() > b.size();
+                                     });
+                    for (auto &v : q[r]) std::reverse(v.begin(), v.end());  // pop from the back
+                }
+                size_t head[16] = {};
+                for (;;) {
+                    int busy = 0;
+                    for (int r = 0; r < 16; ++r) busy += head[r] < q[r].size();
+                    if (!busy) break;
+                    uint16_t lanes[16];
+                    int used = 0;
+                    for (int r = 0; r < 16; ++r) {
+                        if (head[r] >= q[r].size()) continue;
+                        --busy;  // residues after r that still wait keep one lane each
+                        std::vector<int> &v = q[r][head[r]];
+                        int take = std::min<int>((int)v.size(), 16 - used - busy);
+                        take = std::max(take, 1);
+                        for (int i = 0; i < take; ++i) {
+                            lanes[used++] = (uint16_t)v.back();
+                            v.pop_back();
+                        }
+                        if (v.empty()) ++head[r];
+                    }
+                    for (int i = 0; i < 16; ++i) gtab.push_back(i < used ? lanes[i] : 0xFFFF);
+                }
             }
             goff.push_back((int)(gtab.size() / 16));
         }
@@ -674,19 +704,15 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
     const int nh = p->n_theta / 2, B = bins_of(p);
     if (p->projector == SW_PROJ_SLICE) {
         const SliceTables *sl;
-        const Tables *tn, *tb;
+        const Tables *tb;
         sw_status s;
-        // radix-8 plans (variant 4): fewer shared-memory passes and barriers
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &tn, 4)) ||
-            (s = get_tables(c, B, &tb, 4)))
-            return s;
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, B, &tb))) return s;
         const int clip = p->metric != SW_METRIC_RFSW2;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                     return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
                                                      sl->psi_inv, sl->fac, sl->gtab, sl->goff,
-                                                     sl->coef, sl->N,
-                                                     tn->plan, tn->tw, tb->plan, tb->tw, clip,
-                                                     out, full_n, status, st, img2, nb_first);
+                                                     sl->coef, tb->tw, clip, out, full_n, status,
+                                                     st, img2, nb_first);
                 }));
         return SW_OK;
     }
@@ -864,9 +890,7 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if (parts_of(p) == 2 && (s = get_tables(c, bins_of(p), &t))) return s;
     if (p->projector == SW_PROJ_SLICE) {  // tables of the projector, built outside any capture
         const SliceTables *sl;
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, sl->N, &t, 4)) ||
-            (s = get_tables(c, bins_of(p), &t, 4)))
-            return s;
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, bins_of(p), &t))) return s;
     }
     return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);
 }

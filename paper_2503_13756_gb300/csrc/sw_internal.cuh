@@ -232,21 +232,18 @@ cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, in
                            cudaStream_t st, int want_ctas = 0, const float *img2 = nullptr,
                            int nb_first = -1);
 
-// Band-limited projection through the Fourier slice theorem (see
-// sw_slice.cu): same input, output and status conventions as
-// launch_project.  B must be 2/3/5-smooth and even; N = slice_grid_n(L) is
-// the oversampled grid, psi_inv [L] = 1 / Psi(c - floor(L/2)) with Psi the
-// Fourier transform of the spreading kernel; planN/twN and planB/twB the FFT
-// plans and twiddles of lengths N and B.  clip = 1 writes max(row, 0).  One
-// CTA per image with slice_smem_bytes(N, B) of dynamic shared memory.
-// The spreading kernel's width (taps per axis) and the degree of the
-// polynomial that gives each tap's weight from the target's offset x in
-// (-1/2, 1/2] from its grid cell: c[a] holds psi(x + W/2 - a) as
-// sum_d c[a][d] x^d.
+// The slice projector's spreading kernel width (taps per axis) and the
+// degree of the polynomial that gives each tap's weight from the target's
+// offset x in (-1/2, 1/2] from its grid cell: c[a] holds psi(x + W/2 - a)
+// as sum_d c[a][d] x^d.
 constexpr int kSliceW = 9;
 constexpr int kSliceDeg = 8;
-// Angles per inverse-FFT batch of the slice projector (two per signal).
-constexpr int kSliceBatch = 32;
+struct SliceCoef {
+    float c[kSliceW][kSliceDeg + 1];
+};
+// Angles per batch of the slice projector's interpolation (two per warp in
+// the inverse FFTs).
+constexpr int kSliceBatch = 64;
 // Grid geometry of the slice projector for an N-point oversampled grid (see
 // sw_slice.cu): lowest tap index, kept rows, left and right column counts
 // and the row stride (complex elements).
@@ -260,40 +257,43 @@ __host__ __device__ inline int slice_stride(int N)
     return S + (17 - S % 16) % 16;
 }
 // First grid address of the taps of target (j, theta) with e = (cos, sin)
-// of theta in FP32 and rNB = N / B, exactly as the kernel forms it; *left
+// of theta in FP32 on the grid N = B, exactly as the kernel forms it; *left
 // tells the half (taps at increasing addresses when set, decreasing
 // otherwise).
-__host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, float rNB,
-                                              bool *left)
+__host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, bool *left)
 {
     const float jf = (float)j, hN = 0.5f * (float)N;
-    const float y1 = fminf(fmaxf(-(jf * ex) * rNB, -hN), hN);
-    const float y2 = fminf(fmaxf(-(jf * ey) * rNB, -hN), 0.f);
+    const float y1 = fminf(fmaxf(-(jf * ex), -hN), hN);
+    const float y2 = fminf(fmaxf(-(jf * ey), -hN), 0.f);
     const int i1 = (int)ceilf(y1 - 0.5f * (float)kSliceW);
     const int i2 = (int)ceilf(y2 - 0.5f * (float)kSliceW) - slice_lo(N);
     *left = i1 <= 0;
     return i2 * slice_stride(N) +
            (*left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1);
 }
-struct SliceCoef {
-    float c[kSliceW][kSliceDeg + 1];
-};
-int slice_grid_n(int L);
-size_t slice_smem_bytes(int N, int B);
+
+// Band-limited projection through the Fourier slice theorem (see
+// sw_slice.cu): same input, output and status conventions as
+// launch_project.  B = 32 M bins with M <= 6 and B >= 1.5 L, also the
+// oversampled grid length; psi_inv [L] = 1 / Psi(c - floor(L/2)) with Psi
+// the Fourier transform of the spreading kernel; tw [B] = e^{-2 pi i q / B}.
+// clip = 1 writes max(row, 0).  One CTA of 1024 threads per image with
+// slice_smem_bytes(B) of dynamic shared memory.
 // fac: [nh][B/2 + 1] sinc(pi t_1) sinc(pi t_2) (-1)^j e^{i pi j (1 - 2 delta (cos + sin)) / B}
 // with t = (j / B)(cos theta_k, sin theta_k), delta = 1/2 for even L, else 0.
 // gtab/goff: the targets (kk, j) of angle batch b (angles b kSliceBatch + kk)
-// in half-warp groups of 16 lanes, entries kk * 2048 + j or 0xFFFF (idle),
+// in half-warp groups of 16 lanes, entries kk * 128 + j (j <= B/2 <= 96) or
+// 0xFFFF (idle),
 // groups goff[b] .. goff[b+1]; every target of the batch appears once.  The
 // grouping only orders the work: each group's targets have distinct tap
-// addresses mod 16, so its loads cost one pass.
+// addresses mod 16 (or equal ones), so its loads cost one pass.
+int slice_default_bins(int L, int min_bins);  // 32 ceil(max(min_bins, 1.5 L) / 32)
+size_t slice_smem_bytes(int B);
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
-                                 const uint16_t *gtab, const int *goff,
-                                 const SliceCoef &coef, int N, const FftPlan &planN,
-                                 const float2 *twN, const FftPlan &planB, const float2 *twB,
-                                 int clip, float *out, int full_n, int32_t *status,
-                                 cudaStream_t st, const float *img2 = nullptr,
+                                 const uint16_t *gtab, const int *goff, const SliceCoef &coef,
+                                 const float2 *tw, int clip, float *out, int full_n,
+                                 int32_t *status, cudaStream_t st, const float *img2 = nullptr,
                                  int nb_first = -1);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)

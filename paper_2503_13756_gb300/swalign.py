@@ -52,13 +52,19 @@ def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
 
 def bins_of(params: Params) -> int:
     """Bin count B the library uses for params (sw_params.n_bins, else the
-    default; the ramp-filtered metric and the Fourier-slice projector round
-    the default up to an even 2/3/5-smooth count)."""
+    default; the ramp-filtered metric rounds the default up to an even
+    2/3/5-smooth count, the Fourier-slice projector to a multiple of 32 that
+    is at least 1.5 L)."""
     if params.n_bins:
         return int(params.n_bins)
     L = int(params.L)
     B = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2 if L >= 1 else 0
-    if params.metric == METRIC["rfsw2"] or params.projector == PROJECTOR["slice"]:
+    if params.projector == PROJECTOR["slice"]:
+        # the slice projector's bins are its oversampled grid: a multiple of
+        # 32 that is at least 1.5 L
+        need = max(B, (3 * L + 1) // 2)
+        return 32 * ((need + 31) // 32)
+    if params.metric == METRIC["rfsw2"]:
         def smooth(m):
             for q in (2, 3, 5):
                 while m % q == 0:
