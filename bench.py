@@ -3,7 +3,8 @@
 Workload (one step): 4096 query images against 256 templates, 128 x 128
 cells, n = 256 angles, M = 128 quantile levels -- every pair aligned over all
 256 rotations with the closed-form translation, through the C ABI call
-sw_align_batch.  Synthetic, seeded inputs (rotated / shifted / warped copies of
+sw_align_batch.  Projections by the paper's Fourier-slice (NUFFT) projector
+(B = 192 bins); the linear-splat projector is reported as a variant.  Synthetic, seeded inputs (rotated / shifted / warped copies of
 Gaussian-blob templates).  The device number times K steps with inputs
 resident in HBM; "e2e" times the same call with the inputs copied from pinned
 host memory and the results copied back inside the timed region.
@@ -28,12 +29,39 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "aligned image pairs/s (128x128, 256 angles) FP32 vs BF16; p99 request latency"
+PROJECTOR_NAMES = {"slice": "Fourier slice: type-2 NUFFT of the cell image, band-limited rows "
+                            "(Sec. 2.3)",
+                   "splat": "pixel-driven linear splat"}
 NQ, NT, L, N_THETA, M_LEVELS = 4096, 256, 128, 256, 128
 SM_COUNT, FP32_LANES, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
 B_BINS = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2   # default bin count at L = 128
 WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
 # algorithmic work per unit (stated in the design doc)
 PROJ_FLOPS_PER_CELL_ANGLE = 8           # s = <x, e> (FMA), frac, 1-t, two FMA accumulations
+SLICE_W = 9                              # spreading kernel taps per axis
+
+
+def slice_bins(Lc):
+    """Bins (= oversampled grid) of the Fourier-slice projector at side Lc."""
+    B0 = 2 * math.ceil((Lc - 1) / math.sqrt(2.0)) + 2
+    need = max(B0, (3 * Lc + 1) // 2)
+    return 32 * ((need + 31) // 32)
+
+
+def slice_flops_per_image(Lc, n, B):
+    """Transform arithmetic of the slice projector per image: complex FFTs of
+    length B counted 5 B log2 B (ceil(L/2) column pairs, B/2 + W kept grid
+    rows, n/4 inverse transforms of two angles) and 4 flops per tap of the
+    W x W interpolation at each of the (n/2)(B/2 + 1) slice samples."""
+    fft = 5.0 * B * math.log2(B)
+    return ((Lc + 1) // 2 + B // 2 + SLICE_W + n // 4) * fft + \
+        (n // 2) * (B // 2 + 1) * SLICE_W * SLICE_W * 4.0
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
+# of the slice projector kernel from one ncu capture (None until taken, and
+# once that kernel changes).
+SLICE_DRAM_BYTES_PER_IMAGE = None
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the four-angle projection kernel, from one ncu capture of its 2112-image
 # launch (2048 queries and 64 templates in one launch: 277,210,112 bytes);
@@ -57,8 +85,8 @@ def parse():
     ap.add_argument("--metric", default="sw2", choices=["sw2", "rfsw2", "msw2"],
                     help="distance of the main workload (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--projector", default="splat", choices=["splat", "slice"],
-                    help="projection of the headline step: linear splat or Fourier slice")
+    ap.add_argument("--projector", default="slice", choices=["splat", "slice"],
+                    help="projection of the headline step: Fourier slice (default) or splat")
     ap.add_argument("--configs", action="store_true",
                     help="also time the single-pair, one-reference and random-dense "
                          "configurations (GPU and oracle) and print them as a second line")
@@ -170,15 +198,19 @@ def sum_over_ranks(x, world, device):
     return float(t.item())
 
 
-def cpu_baseline(data, sample_q=160, sample_t=160):
+def cpu_baseline(data, projector="slice"):
     """The FP64 oracle as it stands, on the host cores, on the first
-    sample_q x sample_t pairs of the workload."""
+    sample_q x sample_t pairs of the workload (the oracle's slice projector
+    sums the slice samples directly, seconds per image, hence the smaller
+    sample)."""
     import oracle
+    sample_q = sample_t = 32 if projector == "slice" else 160
     q = data["queries"][:sample_q].astype(np.float64)
     t = data["templates"][:sample_t].astype(np.float64)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.align_all_pairs(q, t, N_THETA, M_LEVELS, nthreads=cores)
+    oracle.align_all_pairs(q, t, N_THETA, M_LEVELS, nthreads=cores,
+                           projector=int(projector == "slice"))
     dt = time.perf_counter() - t0
     pairs = sample_q * sample_t
     return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
@@ -384,7 +416,8 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     data = synth.many_to_many(n_queries=64, n_templates=64)
-    sq = st = 6
+    slice_proj = args.projector == "slice"
+    sq = st = 4 if slice_proj else 6
     cores = os.cpu_count() or 1
     times = []
     for k in range(args.warmup + args.steps):
@@ -392,7 +425,8 @@ def run_reference(args, world, rank):
         q = data["queries"][i0:i0 + sq].astype(np.float64)
         t = data["templates"][i0:i0 + st].astype(np.float64)
         t0 = time.perf_counter()
-        oracle.align_all_pairs(q, t, N_THETA, M_LEVELS, nthreads=cores)
+        oracle.align_all_pairs(q, t, N_THETA, M_LEVELS, nthreads=cores,
+                               projector=int(slice_proj))
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
@@ -403,7 +437,8 @@ def run_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "Nq": NQ, "Nt": NT, "L": L, "n_theta": N_THETA,
-                   "n_levels": M_LEVELS, "step_sample": f"{sq}x{st} pairs per step"},
+                   "n_levels": M_LEVELS, "projector": PROJECTOR_NAMES[args.projector],
+                   "step_sample": f"{sq}x{st} pairs per step"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sq} queries x {st} templates per step, {args.steps} steps"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
@@ -468,10 +503,13 @@ def main():
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
     variants = {}
     if args.precision == "fp32" and args.metric == "sw2" and not args.no_variants:
-        for name in ("bf16", "fp16", "fp32_simt", "rfsw2_fp32", "rfsw2_bf16"):
+        other = "splat" if args.projector == "slice" else "slice"
+        for name in ("bf16", "fp16", "fp32_simt", "rfsw2_fp32", "rfsw2_bf16", other + "_fp32"):
             metric = "rfsw2" if name.startswith("rfsw2") else "sw2"
-            prec = name.split("_", 1)[1] if metric == "rfsw2" else name
-            pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec, metric=metric)
+            prec = name.split("_", 1)[1] if "_" in name and not name.startswith("fp32") else name
+            proj = other if name.startswith(other) else args.projector
+            pv = swalign.make_params(L, N_THETA, M_LEVELS, precision=prec, metric=metric,
+                                     projector=proj)
             if not args.no_autotune:
                 al.autotune(pv)
             al.reserve(pv, nq, nt)
@@ -500,6 +538,7 @@ def main():
                       * 1e6 / 1e12) if simt else peaks_v.get("bf16_tflops")
             variants[name] = {
                 "metric": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2"}[metric],
+                "projector": PROJECTOR_NAMES[proj],
                 "value": sum_over_ranks(nq * nt, world, dev) / (ms_v / 1e3), "unit": "pairs/s",
                 "ms_per_step": ms_v, "status_ok": bool(np.all(rv["status"] == 0)),
                 "stages": {k: v[0] / args.steps for k, v in st_v.items()},
@@ -572,7 +611,22 @@ def main():
                  for k, v in stages.items()}
     dom = max(stages, key=lambda k: stages[k][0])
     alu_peak = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL) * 1e6 / 1e12
-    if dom == "project":
+    if dom == "project" and args.projector == "slice":
+        Bs = slice_bins(L)
+        flops = args.steps * nimg * slice_flops_per_image(L, N_THETA, Bs)
+        achieved = flops / (stages[dom][0] / 1e3) / 1e12
+        per_launch = nimg / max(1.0, stages[dom][1] / args.steps)
+        traffic = (SLICE_DRAM_BYTES_PER_IMAGE * per_launch
+                   if SLICE_DRAM_BYTES_PER_IMAGE is not None else None)
+        roof = {"kernel": "k_project_slice", "bound": "alu", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": traffic,
+                "traffic_unit": "bytes per launch (average launch of the step)",
+                "algorithmic_flops_per_image": slice_flops_per_image(L, N_THETA, Bs),
+                "algorithmic_bytes_per_launch": per_launch * (L * L * 4 + (N_THETA // 2) * Bs * 4),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)",
+                "binding_unit": "shared-memory pipe (tap loads) and instruction issue"}
+    elif dom == "project":
         flops = args.steps * nimg * L * L * (N_THETA // 2) * PROJ_FLOPS_PER_CELL_ANGLE
         achieved = flops / (stages[dom][0] / 1e3) / 1e12
         per_launch = nimg / max(1.0, stages[dom][1] / args.steps)
@@ -592,7 +646,7 @@ def main():
     else:
         roof = {"kernel": dom, "bound": "unknown", "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
-    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(data)
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(data, args.projector)
     serve = None if (args.no_serving or world > 1) else serving_block(args, local)
     unev = None if (args.no_uneven or world > 1) else uneven_block(args, local)
     line = {
@@ -605,6 +659,8 @@ def main():
                    f"many-to-many {nq}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
                    "Nq": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
                    "n_levels": M_LEVELS, "precision": args.precision, "translation": 1,
+                   "projector": PROJECTOR_NAMES[args.projector],
+                   "n_bins": swalign.bins_of(p),
                    "distance": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2",
                                 "msw2": "max-sliced W2"}[args.metric],
                    "correlation": ("none: every column pair, FP32 on the CUDA cores"
