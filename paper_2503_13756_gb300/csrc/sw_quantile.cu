@@ -47,7 +47,8 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
     } else {
         row = proj + ((size_t)imgi * n + k) * B;
     }
-    for (int b = lane; b < B; b += 32) U[b] = mirror ? row[B - 1 - b] : row[b];
+#pragma unroll 4
+    for (int b = lane; b < B; b += 32) U[b] = mirror ? __ldg(row + B - 1 - b) : __ldg(row + b);
     __syncwarp();
 
     // ---- compensated prefix sums: lane owns bins [c0, c1)

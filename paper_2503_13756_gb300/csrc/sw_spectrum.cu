@@ -141,14 +141,24 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     const float invn = 1.f / (float)n;
 
     for (int p0 = 0; p0 < M; p0 += 2 * nsig) {
-        // ---- load: signal s = levels (p0 + 2s, p0 + 2s + 1) as (re, im)
+        // ---- load: signal s = levels (p0 + 2s, p0 + 2s + 1) as (re, im).
+        // Unrolled so that a thread's global loads are in flight together
+        // (the trip count is n nsig / blockDim, 16 at n = 256); an aligned
+        // level pair is one 8-byte load.
+#pragma unroll 8
         for (int t = threadIdx.x; t < n * nsig; t += blockDim.x) {
             const int k = t / nsig, s = t % nsig;
             const int p = p0 + 2 * s;
             float xr = 0.f, xi = 0.f;
             if (parts == 1) {
-                if (p < M) xr = qi[(size_t)k * M + p];
-                if (p + 1 < M) xi = qi[(size_t)k * M + p + 1];
+                if (p + 1 < M && !(M & 1)) {
+                    const float2 v = __ldg(reinterpret_cast<const float2 *>(qi + (size_t)k * M + p));
+                    xr = v.x;
+                    xi = v.y;
+                } else {
+                    if (p < M) xr = __ldg(qi + (size_t)k * M + p);
+                    if (p + 1 < M) xi = __ldg(qi + (size_t)k * M + p + 1);
+                }
             } else {
                 if (p < M) xr = qi[(size_t)(p / Mp) * n * Mp + (size_t)k * Mp + p % Mp];
                 if (p + 1 < M)
