@@ -166,7 +166,10 @@ def bins_for(L: int, metric: int = 0, projector: int = 0) -> int:
     default B."""
     if projector:
         need = max(default_bins(L), (3 * L + 1) // 2)
-        return 32 * ((need + 31) // 32)
+        m = (need + 31) // 32
+        if m > 6:  # the CUDA path's grids above L = 128: 256, 320 or 384
+            m = 8 if m <= 8 else (10 if m <= 10 else 12)
+        return 32 * m
     return rfsw_bins(L) if metric == 1 else default_bins(L)
 
 

@@ -281,6 +281,8 @@ struct sw_ctx {
     size_t limit = 0;
     std::deque<Tables> tables;  // stable addresses
     std::deque<SliceTables> slice_tables;
+    float2 *slice_scratch = nullptr;  // grids of the slice projector above L = 128
+    size_t slice_scratch_size = 0;
     int64_t launches = 0;
     bool prof = false;
     std::vector<ProfRec> recs;
@@ -357,10 +359,6 @@ bool smooth235(int n)
     return n == 1;
 }
 
-// Dynamic shared memory one CTA may opt into on this GPU (227 KB), less the
-// projector kernel's static flags.
-constexpr size_t kSliceSmemLimit = 227 * 1024 - 64;
-
 sw_status check_params(sw_ctx *c, const sw_params *p)
 {
     if (!p) return fail(c, SW_ERR_INVALID_ARG, "params is NULL");
@@ -403,16 +401,14 @@ sw_status check_params(sw_ctx *c, const sw_params *p)
         // the bins are also the oversampled grid: a multiple of 32 (one
         // warp's FFT) and at least 1.5 L (the NUFFT's accuracy)
         const int B = bins_of(p);
-        if (p->n_bins != 0 && (B % 32 != 0 || 2 * B < 3 * p->L))
-            return fail(c, SW_ERR_INVALID_ARG,
-                        "n_bins=%d: the Fourier-slice projector needs a multiple of 32 that "
-                        "is at least 1.5 L",
-                        p->n_bins);
-        if (B / 32 > 6 || swk::slice_smem_bytes(B) > kSliceSmemLimit)
+        if (p->L > 256)
             return fail(c, SW_ERR_UNSUPPORTED,
-                        "L=%d, B=%d: the Fourier-slice projector holds the image's half grid "
-                        "in one CTA's shared memory (B <= 192, L <= 128)",
-                        p->L, B);
+                        "L=%d: the Fourier-slice projector is built for L <= 256", p->L);
+        if (!swk::slice_bins_supported(p->L, B))
+            return fail(c, SW_ERR_INVALID_ARG,
+                        "n_bins=%d: the Fourier-slice projector needs a multiple of 32 that is "
+                        "at least 1.5 L (32..192 for L <= 128; 256, 320 or 384 above)",
+                        p->n_bins);
     }
     return SW_OK;
 }
@@ -579,56 +575,72 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     // group g takes the g-th target of every bucket, so the 16 lanes of a
     // group read distinct banks at every tap.  Pooling the batch's angles
     // keeps the buckets even.  Addresses follow the kernel's FP32 arithmetic.
-    // Targets with the same first tap address (near the origin the angles of
-    // a batch meet) read the same words, which the hardware broadcasts: such
-    // a class may fill several lanes of one group.
+    // Half-warp groups of the targets of every batch of angles.  Grid in
+    // shared memory (L <= 128): within each half of the grid (taps at
+    // increasing or decreasing addresses) the targets are bucketed by first
+    // tap address mod 16 and group g takes the g-th of every bucket, so the 16
+    // lanes of a group read distinct banks at every tap; targets with the
+    // same first address (near the origin the angles of a batch meet) read
+    // the same words, which the hardware broadcasts, so such a class may fill
+    // several lanes.  Pooling the batch's angles keeps the buckets even.
+    // Addresses follow the kernel's FP32 arithmetic.  Grid in global memory:
+    // 16 consecutive targets of one ray per group (neighbouring taps share
+    // cache lines).
     std::vector<uint16_t> gtab;
     std::vector<int> goff(1, 0);
-    {
-        for (int k0 = 0; k0 < nh; k0 += swk::kSliceBatch) {
-            // [half][residue] -> address classes, each a list of targets
-            std::map<int, std::vector<int>> cls[2][16];
-            for (int k = k0; k < std::min(nh, k0 + swk::kSliceBatch); ++k)
-                for (int j = 0; j < nj; ++j) {
-                    bool left;
-                    const int base =
-                        swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N, &left);
-                    cls[left ? 0 : 1][base & 15][base].push_back((k - k0) * 128 + j);
-                }
-            for (auto &half : cls) {
-                std::vector<std::vector<int>> q[16];  // per residue, largest class first
-                for (int r = 0; r < 16; ++r) {
-                    for (auto &kv : half[r]) q[r].push_back(kv.second);
-                    std::stable_sort(q[r].begin(), q[r].end(),
-                                     [](const std::vector<int> &a, const std::vector<int> &b) {
-                                         return a.size() > b.size();
-                                     });
-                    for (auto &v : q[r]) std::reverse(v.begin(), v.end());  // pop from the back
-                }
-                size_t head[16] = {};
-                for (;;) {
-                    int busy = 0;
-                    for (int r = 0; r < 16; ++r) busy += head[r] < q[r].size();
-                    if (!busy) break;
-                    uint16_t lanes[16];
-                    int used = 0;
-                    for (int r = 0; r < 16; ++r) {
-                        if (head[r] >= q[r].size()) continue;
-                        --busy;  // residues after r that still wait keep one lane each
-                        std::vector<int> &v = q[r][head[r]];
-                        int take = std::min<int>((int)v.size(), 16 - used - busy);
-                        take = std::max(take, 1);
-                        for (int i = 0; i < take; ++i) {
-                            lanes[used++] = (uint16_t)v.back();
-                            v.pop_back();
-                        }
-                        if (v.empty()) ++head[r];
-                    }
-                    for (int i = 0; i < 16; ++i) gtab.push_back(i < used ? lanes[i] : 0xFFFF);
-                }
-            }
+    const int batch = swk::slice_batch_of(L);
+    for (int k0 = 0; k0 < nh; k0 += batch) {
+        const int k1 = std::min(nh, k0 + batch);
+        if (L > 128) {
+            for (int k = k0; k < k1; ++k)
+                for (int j0 = 0; j0 < nj; j0 += 16)
+                    for (int i = 0; i < 16; ++i)
+                        gtab.push_back(j0 + i < nj ? (uint16_t)((k - k0) * 256 + j0 + i)
+                                                   : (uint16_t)0xFFFF);
             goff.push_back((int)(gtab.size() / 16));
+            continue;
         }
+        // [half][residue] -> address classes, each a list of targets
+        std::map<int, std::vector<int>> cls[2][16];
+        for (int k = k0; k < k1; ++k)
+            for (int j = 0; j < nj; ++j) {
+                bool left;
+                const int base = swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N, &left);
+                cls[left ? 0 : 1][base & 15][base].push_back((k - k0) * 256 + j);
+            }
+        for (auto &half : cls) {
+            std::vector<std::vector<int>> q[16];  // per residue, largest class first
+            for (int r = 0; r < 16; ++r) {
+                for (auto &kv : half[r]) q[r].push_back(kv.second);
+                std::stable_sort(q[r].begin(), q[r].end(),
+                                 [](const std::vector<int> &a, const std::vector<int> &b) {
+                                     return a.size() > b.size();
+                                 });
+                for (auto &v : q[r]) std::reverse(v.begin(), v.end());  // pop from the back
+            }
+            size_t head[16] = {};
+            for (;;) {
+                int busy = 0;
+                for (int r = 0; r < 16; ++r) busy += head[r] < q[r].size();
+                if (!busy) break;
+                uint16_t lanes[16];
+                int used = 0;
+                for (int r = 0; r < 16; ++r) {
+                    if (head[r] >= q[r].size()) continue;
+                    --busy;  // residues after r that still wait keep one lane each
+                    std::vector<int> &v = q[r][head[r]];
+                    int take = std::min<int>((int)v.size(), 16 - used - busy);
+                    take = std::max(take, 1);
+                    for (int i = 0; i < take; ++i) {
+                        lanes[used++] = (uint16_t)v.back();
+                        v.pop_back();
+                    }
+                    if (v.empty()) ++head[r];
+                }
+                for (int i = 0; i < 16; ++i) gtab.push_back(i < used ? lanes[i] : 0xFFFF);
+            }
+        }
+        goff.push_back((int)(gtab.size() / 16));
     }
     SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
     SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));
@@ -676,6 +688,27 @@ sw_status ensure_ws(sw_ctx *c, size_t bytes)
     return SW_OK;
 }
 
+// Scratch of the slice projector above L = 128 (grids of one chunk of images),
+// grown on demand and kept for the context's life (sw_reserve sizes it before
+// any stream capture).
+sw_status ensure_slice_scratch(sw_ctx *c, size_t bytes)
+{
+    if (bytes <= c->slice_scratch_size) return SW_OK;
+    if (c->slice_scratch) {
+        SW_CUDA(c, cudaFree(c->slice_scratch));
+        c->slice_scratch = nullptr;
+        c->slice_scratch_size = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->slice_scratch, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->slice_scratch = nullptr;
+        return fail(c, SW_ERR_OOM, "slice scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    c->slice_scratch_size = bytes;
+    return SW_OK;
+}
+
 // Per-image stages into a spectrum set.
 struct ImageOut {
     int32_t *status;
@@ -706,13 +739,15 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
         const SliceTables *sl;
         const Tables *tb;
         sw_status s;
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, B, &tb))) return s;
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, B, &tb)) ||
+            (s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, B, nb))))
+            return s;
         const int clip = p->metric != SW_METRIC_RFSW2;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                     return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
                                                      sl->psi_inv, sl->fac, sl->gtab, sl->goff,
-                                                     sl->coef, tb->tw, clip, out, full_n, status,
-                                                     st, img2, nb_first);
+                                                     sl->coef, tb->tw, c->slice_scratch, clip,
+                                                     out, full_n, status, st, img2, nb_first);
                 }));
         return SW_OK;
     }
@@ -826,6 +861,7 @@ void sw_destroy(sw_ctx *c)
         cudaFree(t.gtab);
         cudaFree(t.goff);
     }
+    if (c->slice_scratch) cudaFree(c->slice_scratch);
     delete c;
 }
 
@@ -890,7 +926,9 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if (parts_of(p) == 2 && (s = get_tables(c, bins_of(p), &t))) return s;
     if (p->projector == SW_PROJ_SLICE) {  // tables of the projector, built outside any capture
         const SliceTables *sl;
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, bins_of(p), &t))) return s;
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, bins_of(p), &t)) ||
+            (s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, bins_of(p), Nq + Nt))))
+            return s;
     }
     return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);
 }

@@ -274,27 +274,38 @@ __host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, 
 
 // Band-limited projection through the Fourier slice theorem (see
 // sw_slice.cu): same input, output and status conventions as
-// launch_project.  B = 32 M bins with M <= 6 and B >= 1.5 L, also the
-// oversampled grid length; psi_inv [L] = 1 / Psi(c - floor(L/2)) with Psi
+// launch_project.  B = 32 M bins with B >= 1.5 L (M <= 6 for L <= 128;
+// M = 8, 10 or 12 for 128 < L <= 256), also the oversampled grid length; psi_inv [L] = 1 / Psi(c - floor(L/2)) with Psi
 // the Fourier transform of the spreading kernel; tw [B] = e^{-2 pi i q / B}.
-// clip = 1 writes max(row, 0).  One CTA of 1024 threads per image with
-// slice_smem_bytes(B) of dynamic shared memory.
+// clip = 1 writes max(row, 0).  For L <= 128, one CTA of 1024 threads per
+// image with slice_smem_bytes(B) of dynamic shared memory; above, two
+// launches per chunk of images with the grids in scratch.
 // fac: [nh][B/2 + 1] sinc(pi t_1) sinc(pi t_2) (-1)^j e^{i pi j (1 - 2 delta (cos + sin)) / B}
 // with t = (j / B)(cos theta_k, sin theta_k), delta = 1/2 for even L, else 0.
-// gtab/goff: the targets (kk, j) of angle batch b (angles b kSliceBatch + kk)
-// in half-warp groups of 16 lanes, entries kk * 128 + j (j <= B/2 <= 96) or
+// gtab/goff: the targets (kk, j) of angle batch b (angles b batch + kk)
+// in half-warp groups of 16 lanes, entries kk * 256 + j (j <= B/2 <= 192) or
 // 0xFFFF (idle),
 // groups goff[b] .. goff[b+1]; every target of the batch appears once.  The
 // grouping only orders the work: each group's targets have distinct tap
 // addresses mod 16 (or equal ones), so its loads cost one pass.
-int slice_default_bins(int L, int min_bins);  // 32 ceil(max(min_bins, 1.5 L) / 32)
+// L <= 128: the grid in shared memory (one CTA per image, kSliceBatch-angle
+// batches, targets grouped by bank).  128 < L <= 256: the grids of chunks of
+// kSliceChunk images in the caller's scratch (slice_scratch_bytes), 32-angle
+// batches (slice_batch_of), targets ordered along the rays.
+constexpr int kSliceChunk = 256;
+constexpr size_t kSliceSmemMax = 227 * 1024 - 64;  // opt-in dynamic shared memory of a CTA
+// 32 ceil(max(min_bins, 1.5 L) / 32), rounded up to 256, 320 or 384 above 192
+int slice_default_bins(int L, int min_bins);
+bool slice_bins_supported(int L, int B);
 size_t slice_smem_bytes(int B);
+int slice_batch_of(int L);
+size_t slice_scratch_bytes(int L, int B, int nb);
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
                                  const uint16_t *gtab, const int *goff, const SliceCoef &coef,
-                                 const float2 *tw, int clip, float *out, int full_n,
-                                 int32_t *status, cudaStream_t st, const float *img2 = nullptr,
-                                 int nb_first = -1);
+                                 const float2 *tw, float2 *scratch, int clip, float *out,
+                                 int full_n, int32_t *status, cudaStream_t st,
+                                 const float *img2 = nullptr, int nb_first = -1);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
 //                        : [nb][2nh][B].

@@ -14,11 +14,10 @@
 // DFT of X_j = f_L^(omega_j e_k) (-1)^j e^{i pi j / B} extended Hermitian
 // (X_{-j} = conj X_j), scaled by 1/B.  Angles theta + pi are the mirror rows.
 //
-// Design (GB300): one CTA of 32 warps per image, the whole transform in
-// shared memory.  Every FFT is a warp's own: B = 32 M points held M per
+// Design (GB300): every FFT is a warp's own: B = 32 M points held M per
 // lane, an M-point DFT in registers, the twiddles, then five radix-2 stages
 // across the lanes by shuffles (outputs in bit-reversed lane order), so no
-// transform waits on a block barrier; two barriers per angle batch remain.
+// transform waits on a block barrier.  Four phases:
 //  A. a[r][c] / (Psi(r') Psi(c')) (Psi: Fourier transform of the spreading
 //     kernel, host table), two image columns packed per complex signal,
 //     one warp per column pair: N-point FFT along r' (zero padded), unpacked
@@ -37,13 +36,20 @@
 //     axis are degree-8 polynomials in the target's offset from its grid
 //     cell (fitted on the host in FP64 within 1e-8 of psi; coefficients in
 //     the kernel parameters), and the cell's sinc factors and the phase come
-//     from a host table per (angle, frequency).  The targets of a batch of
-//     kSliceBatch angles run in host-made half-warp groups whose first tap
-//     addresses differ mod 16 (or coincide), so each tap load of a group is
-//     one shared-memory pass.
+//     from a host table per (angle, frequency).  The targets of an angle batch
+//     run in host-ordered half-warp groups.
 //  D. one warp per pair of angles (X_a + i X_b, both Hermitian): B-point
 //     inverse FFT; the real and imaginary parts are the two rows, staged in
 //     the warp's own slice-sample rows so that the row stores coalesce.
+// Two arrangements:
+//  - L <= 128 (k_project_slice): one CTA of 32 warps per image with the whole
+//    grid in shared memory (175 KB at L = 128); 64-angle batches; the
+//    targets grouped so that each tap load of a half-warp hits 16 distinct
+//    banks (one pass).
+//  - 128 < L <= 256 (k_slice_grid, then k_slice_interp): the grid of a chunk
+//    of images is built in a global scratch buffer (one CTA of 16 warps per
+//    image, phases A and B), then one CTA per (image, 32-angle batch) reads
+//    its taps through L1/L2, ordered along the rays for locality.
 // With W = 9 and N / L >= 1.5 the rows are within ~3e-7 (relative l2) of the
 // exact band-limited projection, at the level of FP32 rounding.
 #include <algorithm>
@@ -53,9 +59,11 @@
 namespace swk {
 namespace {
 
-constexpr int kSliceThreads = 1024;
-constexpr int kWarps = kSliceThreads / 32;
-static_assert(2 * kWarps == kSliceBatch, "one warp per pair of angles of a batch");
+constexpr int kSliceThreads = 1024;  // shared-memory grid: 32 warps
+constexpr int kBigThreads = 512;     // global grid: 16 warps (more registers per lane)
+constexpr int kBigBatch = 32;        // angles per CTA of k_slice_interp
+static_assert(2 * (kSliceThreads / 32) == kSliceBatch, "one warp per angle pair of a batch");
+static_assert(2 * (kBigThreads / 32) == kBigBatch, "one warp per angle pair of a batch");
 
 __device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
 
@@ -111,6 +119,7 @@ struct SliceArgs {
     const float *img;   // images [0, nb1)
     const float *img2;  // images [nb1, nb) (may equal img)
     int nb1;
+    int img_off;        // global index of this launch's image 0
     int L, srcL, nh;
     int clip, full_n;
     const float2 *cs;       // [nh] (cos, sin) of theta_k
@@ -119,40 +128,31 @@ struct SliceArgs {
     const uint16_t *gtab;   // target groups per angle batch (see launch_project_slice)
     const int *goff;
     const float2 *tw;       // [B] e^{-2 pi i q / B}
+    float2 *grid;           // global grids [chunk][rows][S] (128 < L only)
     float *out;
     int32_t *status;
     SliceCoef coef;         // tap weight polynomials (kernel parameter bank)
 };
 
-template <int M>
-__global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
+__device__ __forceinline__ const float *image_of(const SliceArgs &A, int gi)
 {
-    constexpr int N = 32 * M;  // grid length = bin count
-    extern __shared__ float2 sms[];
-    const int L = A.L, nh = A.nh;
+    const size_t sz = (size_t)A.srcL * A.srcL;
+    return gi < A.nb1 ? A.img + (size_t)gi * sz : A.img2 + (size_t)(gi - A.nb1) * sz;
+}
+
+// Phases A and B for one image into the grid G (shared or global memory),
+// by nw warps; returns the image's bad/mass flags of this thread.
+template <int M>
+__device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__restrict__ src,
+                                           float2 *G, const float2 *tw, int warp, int nw,
+                                           int lane, int &bad, int &mass)
+{
+    constexpr int N = 32 * M;
+    const int L = A.L, half = L / 2;
     const int rows = slice_rows(N), S = slice_stride(N), lo = slice_lo(N);
     const int nleft = slice_left(N), nright = slice_right(N);
-    const int nj = N / 2 + 1;
-    float2 *G = sms;                     // [rows][S] grid
-    float2 *Xs = G + rows * S;           // [kSliceBatch][nj] slice samples / staging
-    float2 *tw = Xs + kSliceBatch * nj;  // [N]
-    __shared__ int s_bad, s_mass;
-
-    const int imgi = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float *src = imgi < A.nb1 ? A.img + (size_t)imgi * A.srcL * A.srcL
-                                    : A.img2 + (size_t)(imgi - A.nb1) * A.srcL * A.srcL;
-    if (threadIdx.x == 0) {
-        s_bad = 0;
-        s_mass = 0;
-    }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
-    __syncthreads();
-    const int half = L / 2;
-    int bad = 0, mass = 0;
-
     // ---- A: one warp per column pair (c, c+1): FFT along r', kept rows
-    for (int c = 2 * warp; c < L; c += 2 * kWarps) {
+    for (int c = 2 * warp; c < L; c += 2 * nw) {
         float2 v[M];
         const float pc0 = __ldg(A.psi_inv + c), pc1 = c + 1 < L ? __ldg(A.psi_inv + c + 1) : 0.f;
 #pragma unroll
@@ -204,13 +204,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
             }
         }
     }
-    if (bad) atomicOr(&s_bad, 1);
-    if (mass) atomicOr(&s_mass, 1);
     __syncthreads();
-    if (threadIdx.x == 0) A.status[imgi] = (s_bad || !s_mass) ? 1 : 0;
-
     // ---- B: one warp per kept row: FFT along c', left and right columns
-    for (int i = warp; i < rows; i += kWarps) {
+    for (int i = warp; i < rows; i += nw) {
         float2 v[M];
 #pragma unroll
         for (int n1 = 0; n1 < M; ++n1) {
@@ -229,117 +225,196 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
             if (kout >= 1 && kout <= nright) G[i * S + nleft + nright - kout] = v[k1];
         }
     }
-    __syncthreads();
+}
 
-    // ---- C + D: slice samples of kSliceBatch angles, inverse FFTs, rows out
+// Phases C and D for the angles [k0, k0 + BATCH) of image gi from the grid G
+// (shared or global memory); Xs [BATCH][B/2 + 1] and tw in shared memory;
+// BATCH / 2 warps.  Ends with a block barrier.
+template <int M, int BATCH>
+__device__ __forceinline__ void slice_batch(const SliceArgs &A, const float2 *G, float2 *Xs,
+                                            const float2 *tw, int gi, int k0, int bi, int warp,
+                                            int lane)
+{
+    constexpr int N = 32 * M;
+    const int nh = A.nh;
+    const int S = slice_stride(N), lo = slice_lo(N);
+    const int nleft = slice_left(N), nright = slice_right(N);
+    const int nj = N / 2 + 1;
     const float hN = 0.5f * (float)N, invB = 1.f / (float)N;
     const int nrow = A.full_n ? 2 * nh : nh;
-    float *outi = A.out + (size_t)imgi * nrow * N;
-    for (int k0 = 0; k0 < nh; k0 += kSliceBatch) {
-        // rows of angles beyond nh (last batch) read as zero
-        for (int it = threadIdx.x + (nh - k0) * nj; it < kSliceBatch * nj; it += blockDim.x)
-            Xs[it] = make_float2(0.f, 0.f);
-        const int bi = k0 / kSliceBatch;
-        const int g0 = __ldg(A.goff + bi), ng = __ldg(A.goff + bi + 1) - g0;
-        for (int slot = threadIdx.x; slot < ng * 16; slot += blockDim.x) {
-            const unsigned ent = __ldg(A.gtab + (size_t)(g0 + (slot >> 4)) * 16 + (slot & 15));
-            if (ent == 0xFFFFu) continue;
-            const int kk = (int)(ent >> 7), j = (int)(ent & 127u);
-            const int k = k0 + kk;
-            const float jf = (float)j;
-            const float2 e = __ldg(A.cs + k);
-            // target y = -t N on the grid (t = (j/B) e, N = B), kept inside
-            // the stored half plane whatever the rounding
-            const float y1 = fminf(fmaxf(-(jf * e.x), -hN), hN);
-            const float y2 = fminf(fmaxf(-(jf * e.y), -hN), 0.f);
-            const float f1 = ceilf(y1 - 0.5f * (float)kSliceW);
-            const float f2 = ceilf(y2 - 0.5f * (float)kSliceW);
-            // offsets from the cell, exact: y - f is in (W/2 - 1, W/2]
-            const float x1 = (y1 - f1) - (float)(kSliceW / 2);
-            const float x2 = (y2 - f2) - (float)(kSliceW / 2);
-            float wx[kSliceW], wy[kSliceW];
+    float *outi = A.out + (size_t)gi * nrow * N;
+    // rows of angles beyond nh (last batch) read as zero
+    for (int it = threadIdx.x + (nh - k0) * nj; it < BATCH * nj; it += blockDim.x)
+        Xs[it] = make_float2(0.f, 0.f);
+    const int g0 = __ldg(A.goff + bi), ng = __ldg(A.goff + bi + 1) - g0;
+    for (int slot = threadIdx.x; slot < ng * 16; slot += blockDim.x) {
+        const unsigned ent = __ldg(A.gtab + (size_t)(g0 + (slot >> 4)) * 16 + (slot & 15));
+        if (ent == 0xFFFFu) continue;
+        const int kk = (int)(ent >> 8), j = (int)(ent & 255u);
+        const int k = k0 + kk;
+        const float jf = (float)j;
+        const float2 e = __ldg(A.cs + k);
+        // target y = -t N on the grid (t = (j/B) e, N = B), kept inside the
+        // stored half plane whatever the rounding
+        const float y1 = fminf(fmaxf(-(jf * e.x), -hN), hN);
+        const float y2 = fminf(fmaxf(-(jf * e.y), -hN), 0.f);
+        const float f1 = ceilf(y1 - 0.5f * (float)kSliceW);
+        const float f2 = ceilf(y2 - 0.5f * (float)kSliceW);
+        // offsets from the cell, exact: y - f is in (W/2 - 1, W/2]
+        const float x1 = (y1 - f1) - (float)(kSliceW / 2);
+        const float x2 = (y2 - f2) - (float)(kSliceW / 2);
+        float wx[kSliceW], wy[kSliceW];
+#pragma unroll
+        for (int a = 0; a < kSliceW; ++a) {
+            float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
+#pragma unroll
+            for (int d = kSliceDeg - 1; d >= 0; --d) {
+                px = fmaf(px, x1, A.coef.c[a][d]);
+                py = fmaf(py, x2, A.coef.c[a][d]);
+            }
+            wx[a] = px;
+            wy[a] = py;
+        }
+        const int i1 = (int)f1, i2 = (int)f2 - lo;
+        // left half: taps at increasing addresses; right half reversed
+        const bool left = i1 <= 0;
+        const float2 *g = G + i2 * S + (left ? i1 - lo : nleft + nright - i1);
+        const int da = left ? 1 : -1;
+        float tr = 0.f, ti = 0.f;
+#pragma unroll
+        for (int b = 0; b < kSliceW; ++b) {
+            float rr = 0.f, ri = 0.f;
 #pragma unroll
             for (int a = 0; a < kSliceW; ++a) {
-                float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
-#pragma unroll
-                for (int d = kSliceDeg - 1; d >= 0; --d) {
-                    px = fmaf(px, x1, A.coef.c[a][d]);
-                    py = fmaf(py, x2, A.coef.c[a][d]);
-                }
-                wx[a] = px;
-                wy[a] = py;
+                const float2 gv = g[b * S + a * da];
+                rr = fmaf(wx[a], gv.x, rr);
+                ri = fmaf(wx[a], gv.y, ri);
             }
-            const int i1 = (int)f1, i2 = (int)f2 - lo;
-            // left half: taps at increasing addresses; right half reversed
-            const bool left = i1 <= 0;
-            const float2 *g = G + i2 * S + (left ? i1 - lo : nleft + nright - i1);
-            const int da = left ? 1 : -1;
-            float tr = 0.f, ti = 0.f;
-#pragma unroll
-            for (int b = 0; b < kSliceW; ++b) {
-                float rr = 0.f, ri = 0.f;
-#pragma unroll
-                for (int a = 0; a < kSliceW; ++a) {
-                    const float2 gv = g[b * S + a * da];
-                    rr = fmaf(wx[a], gv.x, rr);
-                    ri = fmaf(wx[a], gv.y, ri);
-                }
-                tr = fmaf(wy[b], rr, tr);
-                ti = fmaf(wy[b], ri, ti);
-            }
-            // cell sinc factors and phase (host table, FP64)
-            const float2 fc = __ldg(A.fac + (size_t)k * nj + j);
-            Xs[kk * nj + j] = make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
+            tr = fmaf(wy[b], rr, tr);
+            ti = fmaf(wy[b], ri, ti);
         }
-        __syncthreads();
-        // D: warp w inverse-transforms the angles ka = 2w, kb = 2w + 1 of the
-        // batch as Y_j = X_a + i X_b, Y_{B-j} = conj X_a + i conj X_b
-        // (Y_0, Y_{B/2}: real parts), then writes both rows
-        const int ka = 2 * warp;
-        if (k0 + ka < nh) {
-            const float2 *Xa = Xs + ka * nj, *Xb = Xa + nj;
-            float2 v[M];
-#pragma unroll
-            for (int n1 = 0; n1 < M; ++n1) {
-                const int n = 32 * n1 + lane;
-                const int j = n <= N / 2 ? n : N - n;
-                const float2 a = Xa[j], b = Xb[j];
-                if (n == 0 || 2 * n == N) v[n1] = make_float2(a.x, b.x);
-                else if (n < N / 2) v[n1] = make_float2(a.x - b.y, a.y + b.x);
-                else v[n1] = make_float2(a.x + b.y, b.x - a.y);
-            }
-            __syncwarp();
-            warp_ifft<M>(v, tw, lane);
-            // stage the two rows in this warp's own sample rows (2 nj >= B + 2)
-            float *stw = reinterpret_cast<float *>(Xs + ka * nj);
-            const int kb = M * brev5(lane);
-#pragma unroll
-            for (int k1 = 0; k1 < M; ++k1) {
-                stw[k1 + kb] = v[k1].x * invB;
-                stw[N + k1 + kb] = v[k1].y * invB;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int k = k0 + ka + h2;
-                if (k >= nh) break;
-                float *o = outi + (size_t)k * N;
-                float *om = outi + (size_t)(nh + k) * N + (N - 1);
-                for (int b = lane; b < N; b += 32) {
-                    float val = stw[h2 * N + b];
-                    if (A.clip) val = fmaxf(val, 0.f);
-                    o[b] = val;
-                    if (A.full_n) om[-b] = val;
-                }
-            }
-        }
-        __syncthreads();
+        // cell sinc factors and phase (host table, FP64)
+        const float2 fc = __ldg(A.fac + (size_t)k * nj + j);
+        Xs[kk * nj + j] = make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
     }
+    __syncthreads();
+    // D: warp w inverse-transforms the angles ka = 2w, kb = 2w + 1 of the
+    // batch as Y_j = X_a + i X_b, Y_{B-j} = conj X_a + i conj X_b
+    // (Y_0, Y_{B/2}: real parts), then writes both rows
+    const int ka = 2 * warp;
+    if (k0 + ka < nh) {
+        const float2 *Xa = Xs + ka * nj, *Xb = Xa + nj;
+        float2 v[M];
+#pragma unroll
+        for (int n1 = 0; n1 < M; ++n1) {
+            const int n = 32 * n1 + lane;
+            const int j = n <= N / 2 ? n : N - n;
+            const float2 a = Xa[j], b = Xb[j];
+            if (n == 0 || 2 * n == N) v[n1] = make_float2(a.x, b.x);
+            else if (n < N / 2) v[n1] = make_float2(a.x - b.y, a.y + b.x);
+            else v[n1] = make_float2(a.x + b.y, b.x - a.y);
+        }
+        __syncwarp();
+        warp_ifft<M>(v, tw, lane);
+        // stage the two rows in this warp's own sample rows (2 nj >= B + 2)
+        float *stw = reinterpret_cast<float *>(Xs + ka * nj);
+        const int kb = M * brev5(lane);
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) {
+            stw[k1 + kb] = v[k1].x * invB;
+            stw[N + k1 + kb] = v[k1].y * invB;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int k = k0 + ka + h2;
+            if (k >= nh) break;
+            float *o = outi + (size_t)k * N;
+            float *om = outi + (size_t)(nh + k) * N + (N - 1);
+            for (int b = lane; b < N; b += 32) {
+                float val = stw[h2 * N + b];
+                if (A.clip) val = fmaxf(val, 0.f);
+                o[b] = val;
+                if (A.full_n) om[-b] = val;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// L <= 128: one CTA per image, the grid in shared memory.
+template <int M>
+__global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
+{
+    constexpr int N = 32 * M;
+    extern __shared__ float2 sms[];
+    const int nj = N / 2 + 1;
+    float2 *G = sms;                                        // [rows][S] grid
+    float2 *Xs = G + slice_rows(N) * slice_stride(N);       // [kSliceBatch][nj]
+    float2 *tw = Xs + kSliceBatch * nj;                     // [N]
+    __shared__ int s_bad, s_mass;
+    const int gi = A.img_off + blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_mass = 0;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
+    __syncthreads();
+    int bad = 0, mass = 0;
+    slice_grid<M>(A, image_of(A, gi), G, tw, warp, kSliceThreads / 32, lane, bad, mass);
+    if (bad) atomicOr(&s_bad, 1);
+    if (mass) atomicOr(&s_mass, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) A.status[gi] = (s_bad || !s_mass) ? 1 : 0;
+    for (int k0 = 0; k0 < A.nh; k0 += kSliceBatch)
+        slice_batch<M, kSliceBatch>(A, G, Xs, tw, gi, k0, k0 / kSliceBatch, warp, lane);
+}
+
+// 128 < L: the grid of image img_off + blockIdx.x into A.grid[blockIdx.x].
+template <int M>
+__global__ void __launch_bounds__(kBigThreads, 1) k_slice_grid(SliceArgs A)
+{
+    constexpr int N = 32 * M;
+    __shared__ float2 tw[N];
+    __shared__ int s_bad, s_mass;
+    const int gi = A.img_off + blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_mass = 0;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
+    __syncthreads();
+    float2 *G = A.grid + (size_t)blockIdx.x * slice_rows(N) * slice_stride(N);
+    int bad = 0, mass = 0;
+    slice_grid<M>(A, image_of(A, gi), G, tw, warp, kBigThreads / 32, lane, bad, mass);
+    if (bad) atomicOr(&s_bad, 1);
+    if (mass) atomicOr(&s_mass, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) A.status[gi] = (s_bad || !s_mass) ? 1 : 0;
+}
+
+// 128 < L: slice samples and rows of angle batch blockIdx.x of image
+// img_off + blockIdx.y from the grid A.grid[blockIdx.y].
+template <int M>
+__global__ void __launch_bounds__(kBigThreads, 1) k_slice_interp(SliceArgs A)
+{
+    constexpr int N = 32 * M;
+    extern __shared__ float2 sms[];
+    float2 *Xs = sms;                           // [kBigBatch][nj]
+    float2 *tw = Xs + kBigBatch * (N / 2 + 1);  // [N]
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
+    __syncthreads();
+    const float2 *G = A.grid + (size_t)blockIdx.y * slice_rows(N) * slice_stride(N);
+    slice_batch<M, kBigBatch>(A, G, Xs, tw, A.img_off + blockIdx.y, blockIdx.x * kBigBatch,
+                              blockIdx.x, threadIdx.x >> 5, threadIdx.x & 31);
 }
 
 template <int M>
-cudaError_t launch_m(const SliceArgs &a, int nb, size_t smem, cudaStream_t st)
+cudaError_t launch_small(const SliceArgs &a, int nb, cudaStream_t st)
 {
+    const size_t smem = slice_smem_bytes(32 * M);
     cudaError_t e = cudaFuncSetAttribute(k_project_slice<M>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -347,12 +422,41 @@ cudaError_t launch_m(const SliceArgs &a, int nb, size_t smem, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int M>
+cudaError_t launch_big(SliceArgs a, int nb, int chunk, cudaStream_t st)
+{
+    constexpr int N = 32 * M;
+    const int nbatch = (a.nh + kBigBatch - 1) / kBigBatch;
+    const size_t smem = sizeof(float2) * ((size_t)kBigBatch * (N / 2 + 1) + N);
+    cudaError_t e = cudaFuncSetAttribute(k_slice_interp<M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    for (int i0 = 0; i0 < nb; i0 += chunk) {
+        const int cnt = std::min(chunk, nb - i0);
+        a.img_off = i0;
+        k_slice_grid<M><<<cnt, kBigThreads, 0, st>>>(a);
+        k_slice_interp<M><<<dim3(nbatch, cnt), kBigThreads, smem, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 int slice_default_bins(int L, int min_bins)
 {
     const int need = std::max(min_bins, (3 * L + 1) / 2);  // >= the default bins and 1.5 L
-    return 32 * ((need + 31) / 32);
+    int m = (need + 31) / 32;
+    if (m > 6) m = m <= 8 ? 8 : (m <= 10 ? 10 : 12);  // grids in global memory: 256, 320, 384
+    return 32 * m;
+}
+
+bool slice_bins_supported(int L, int B)
+{
+    if (B % 32 || 2 * B < 3 * L) return false;
+    const int m = B / 32;
+    return L <= 128 ? (m >= 1 && m <= 6 && slice_smem_bytes(B) <= kSliceSmemMax)
+                    : (L <= 256 && (m == 8 || m == 10 || m == 12));
 }
 
 size_t slice_smem_bytes(int B)
@@ -361,18 +465,29 @@ size_t slice_smem_bytes(int B)
                              (size_t)kSliceBatch * (B / 2 + 1) + (size_t)B);
 }
 
+int slice_batch_of(int L) { return L <= 128 ? kSliceBatch : kBigBatch; }
+
+size_t slice_scratch_bytes(int L, int B, int nb)
+{
+    if (L <= 128) return 0;
+    return sizeof(float2) * (size_t)slice_rows(B) * slice_stride(B) *
+           (size_t)std::min(nb, kSliceChunk);
+}
+
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
                                  const uint16_t *gtab, const int *goff, const SliceCoef &coef,
-                                 const float2 *tw, int clip, float *out, int full_n,
-                                 int32_t *status, cudaStream_t st, const float *img2,
+                                 const float2 *tw, float2 *scratch, int clip, float *out,
+                                 int full_n, int32_t *status, cudaStream_t st, const float *img2,
                                  int nb_first)
 {
     if (nb <= 0) return cudaSuccess;
+    if (!slice_bins_supported(L, B)) return cudaErrorInvalidValue;
     SliceArgs a;
     a.img = img;
     a.img2 = img2 ? img2 : img;
     a.nb1 = (img2 && nb_first >= 0) ? nb_first : nb;
+    a.img_off = 0;
     a.L = L;
     a.srcL = srcL;
     a.nh = nh;
@@ -381,20 +496,29 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.gtab = gtab;
     a.goff = goff;
     a.tw = tw;
+    a.grid = scratch;
     a.clip = clip;
     a.full_n = full_n;
     a.cs = cs;
     a.psi_inv = psi_inv;
     a.out = out;
     a.status = status;
-    const size_t smem = slice_smem_bytes(B);
+    if (L > 128) {
+        if (!scratch) return cudaErrorInvalidValue;
+        switch (B / 32) {
+        case 8: return launch_big<8>(a, nb, kSliceChunk, st);
+        case 10: return launch_big<10>(a, nb, kSliceChunk, st);
+        case 12: return launch_big<12>(a, nb, kSliceChunk, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (B / 32) {
-    case 1: return launch_m<1>(a, nb, smem, st);
-    case 2: return launch_m<2>(a, nb, smem, st);
-    case 3: return launch_m<3>(a, nb, smem, st);
-    case 4: return launch_m<4>(a, nb, smem, st);
-    case 5: return launch_m<5>(a, nb, smem, st);
-    case 6: return launch_m<6>(a, nb, smem, st);
+    case 1: return launch_small<1>(a, nb, st);
+    case 2: return launch_small<2>(a, nb, st);
+    case 3: return launch_small<3>(a, nb, st);
+    case 4: return launch_small<4>(a, nb, st);
+    case 5: return launch_small<5>(a, nb, st);
+    case 6: return launch_small<6>(a, nb, st);
     default: return cudaErrorInvalidValue;
     }
 }

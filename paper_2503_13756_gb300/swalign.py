@@ -63,7 +63,10 @@ def bins_of(params: Params) -> int:
         # the slice projector's bins are its oversampled grid: a multiple of
         # 32 that is at least 1.5 L
         need = max(B, (3 * L + 1) // 2)
-        return 32 * ((need + 31) // 32)
+        m = (need + 31) // 32
+        if m > 6:  # grids in global memory: 256, 320 or 384 bins
+            m = 8 if m <= 8 else (10 if m <= 10 else 12)
+        return 32 * m
     if params.metric == METRIC["rfsw2"]:
         def smooth(m):
             for q in (2, 3, 5):

@@ -69,7 +69,10 @@ def ref_rows(img, n, B, clip):
 
 @pytest.mark.parametrize("L,n,metric", [(3, 4, "sw2"), (16, 8, "sw2"), (33, 20, "sw2"),
                                         (48, 60, "sw2"), (64, 36, "rfsw2"), (100, 24, "rfsw2"),
-                                        (128, 256, "sw2")])
+                                        (128, 256, "sw2"),
+                                        # grids in global memory (B = 256, 320, 384)
+                                        (129, 12, "sw2"), (160, 8, "rfsw2"), (192, 12, "sw2"),
+                                        (256, 8, "sw2")])
 def test_slice_rows_match_oracle(al, L, n, metric):
     rng = np.random.default_rng(L * 7 + n)
     imgs = blobs(rng, 2, L)
@@ -229,6 +232,46 @@ def test_slice_bank_with_half_size_queries_equals_batch(al):
     np.testing.assert_allclose(a["d2"], b["d2"], rtol=1e-9, atol=1e-12)
 
 
+def test_slice_global_grid_batch_on_gpu_rows(al):
+    # 128 < L: the grids of chunks of images in global scratch; more images
+    # than one chunk (256) so that the chunk loop runs twice
+    rng = np.random.default_rng(89)
+    L, n, M = 192, 24, 32
+    q = blobs(rng, 260, L)
+    t = blobs(rng, 3, L)
+    p = params(L, n, M)
+    assert swalign.bins_of(p) == 320
+    got = swalign.results_to_numpy(al.align_batch(q, t, p)).reshape(len(q), len(t))
+    for i in (0, 7, 255, 256, 259):
+        rows = al.project(np.stack([q[i], t[1]]), p).cpu().numpy().astype(np.float64)
+        Dref, Sref, Sc = curve_from_rows(rows[0], rows[1], 2.0 / L, M, 1)
+        gr = got[i, 1]
+        l = int(gr["best_l"])
+        assert gr["status"] == 0
+        assert abs(gr["d2"] - Dref[l]) <= d2_tol(Dref[l], Sc), i
+        np.testing.assert_allclose(gr["shift"], Sref[l], rtol=0, atol=1e-6)
+        lref = int(np.argmin(Dref))
+        assert check_argmin(l, lref, Dref, d2_tol(Dref[lref], Sc))
+
+
+def test_slice_bank_256_with_half_size_queries_equals_batch(al):
+    # the serving setting: a bank at 256^2 and queries at 128^2 upsampled 2 x 2
+    rng = np.random.default_rng(97)
+    L, n, M = 256, 36, 32
+    t = blobs(rng, 5, L)
+    qh = blobs(rng, 3, L // 2)
+    qu = np.ascontiguousarray(np.repeat(np.repeat(qh, 2, axis=1), 2, axis=2) * 0.25)
+    p = params(L, n, M)
+    bank = swalign.Bank(al, t, p)
+    try:
+        a = swalign.results_to_numpy(bank.align(qh, q_L=L // 2))
+    finally:
+        bank.close()
+    b = swalign.results_to_numpy(al.align_batch(qu, t, p))
+    np.testing.assert_array_equal(a["best_l"], b["best_l"])
+    np.testing.assert_allclose(a["d2"], b["d2"], rtol=1e-9, atol=1e-12)
+
+
 def test_slice_status_flags(al):
     rng = np.random.default_rng(79)
     L, n, M = 32, 24, 16
@@ -243,10 +286,13 @@ def test_slice_status_flags(al):
 
 
 def test_slice_rejections(al):
-    big = params(160, 16, 8)
+    big = params(300, 16, 8)
     with pytest.raises(swalign.SwError) as e:
-        al.project(np.zeros((1, 160, 160), np.float32), big)
-    assert e.value.status == 2  # SW_ERR_UNSUPPORTED: the half grid does not fit one CTA
+        al.project(np.zeros((1, 300, 300), np.float32), big)
+    assert e.value.status == 2  # SW_ERR_UNSUPPORTED: built for L <= 256
+    with pytest.raises(swalign.SwError) as e:  # above L = 128 only 256, 320 or 384 bins
+        al.project(np.zeros((1, 160, 160), np.float32), params(160, 16, 8, n_bins=288))
+    assert e.value.status == 1
     odd_bins = params(64, 16, 8, n_bins=94)  # not a multiple of 32 (the warp FFT's length)
     with pytest.raises(swalign.SwError) as e:
         al.project(np.zeros((1, 64, 64), np.float32), odd_bins)
