@@ -229,9 +229,10 @@ def serving_block(args, device):
     out = {"workload": "Poisson 200 req/s, 1-512 images per request (log-uniform), L=128 "
                        "(upsampled) or 256, bank of 1000 templates at 256x256, n=360, M=256, "
                        "best template per query",
+           "projector": PROJECTOR_NAMES[args.projector],
            "requests": args.serve_requests}
     for prec in ("bf16", "fp32"):
-        p = swalign.make_params(256, 360, 256, precision=prec)
+        p = swalign.make_params(256, 360, 256, precision=prec, projector=args.projector)
         eng = serving.ServingEngine(bank["templates"], p, n_slots=3, max_batch_images=512,
                                     device=device, autotune=not args.no_autotune)
         try:
@@ -259,7 +260,8 @@ def uneven_block(args, device):
 
     from paper_2503_13756_gb300 import synth, uneven
     batch = synth.uneven_batch()
-    g = uneven.UnevenGraph(uneven.buckets_from(batch, 256, "bf16", device), mode=0,
+    g = uneven.UnevenGraph(uneven.buckets_from(batch, 256, "bf16", device,
+                                               projector=args.projector), mode=0,
                            device=device, autotune=not args.no_autotune)
     try:
         st = g.stream
@@ -286,6 +288,7 @@ def uneven_block(args, device):
                   for k, d in g.stage_times().items()}
         return {"workload": "uneven 20,000 queries, L in {64,96,128,192,256}, 64 templates per L, "
                             "n=256, M=L, BF16 GEMM, one CUDA graph",
+                "projector": PROJECTOR_NAMES[args.projector],
                 "pairs": g.pairs, "ms_per_graph": ms_graph, "pairs_per_s": g.pairs / (ms_graph / 1e3),
                 "eager_ms": ms_eager, "kernels_per_graph": g.launches_per_replay,
                 "queries_per_L": {int(b.L): int(b.queries.shape[0]) for b in g.buckets},

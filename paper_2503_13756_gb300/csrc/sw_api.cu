@@ -749,6 +749,9 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
                                                      sl->coef, tb->tw, c->slice_scratch, clip,
                                                      out, full_n, status, st, img2, nb_first);
                 }));
+        // above L = 128: a grid and an interpolation kernel per chunk of images
+        if (p->L > 128 && nb > 0)
+            c->launches += 2 * ((nb + swk::kSliceChunk - 1) / swk::kSliceChunk) - 1;
         return SW_OK;
     }
     SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {

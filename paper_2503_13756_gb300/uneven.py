@@ -112,7 +112,8 @@ class UnevenGraph:
         self.al.close()
 
 
-def buckets_from(batch, n_theta: int = 256, precision: str = "bf16", device: int = 0):
+def buckets_from(batch, n_theta: int = 256, precision: str = "bf16", device: int = 0,
+                 projector: str = "splat"):
     """Device buckets from a host batch {L: {"queries", "templates"}} with
     M = L levels per size (the uneven-batch recipe)."""
     import torch
@@ -121,5 +122,6 @@ def buckets_from(batch, n_theta: int = 256, precision: str = "bf16", device: int
         d = batch[L]
         q = torch.as_tensor(d["queries"], dtype=torch.float32).to(f"cuda:{device}")
         t = torch.as_tensor(d["templates"], dtype=torch.float32).to(f"cuda:{device}")
-        out.append(Bucket(L, swalign.make_params(L, n_theta, L, precision=precision), q, t))
+        out.append(Bucket(L, swalign.make_params(L, n_theta, L, precision=precision,
+                                                 projector=projector), q, t))
     return out

@@ -79,6 +79,29 @@ def test_graph_replay_equals_eager_calls_and_oracle():
         g.close()
 
 
+def test_graph_with_the_slice_projector_equals_eager_calls():
+    # the Fourier-slice projector: L <= 128 in one launch, 192 and 256 with
+    # the grids in the context's scratch (two launches per chunk of images),
+    # reserved before the capture
+    batch = synth.uneven_batch(n_queries=120, n_templates_per_L=4, seed=11)
+    g = uneven.UnevenGraph(uneven.buckets_from(batch, N_THETA, "bf16", projector="slice"),
+                           mode=0)
+    try:
+        assert g.launches_per_replay == 5 * 5 + 2  # L = 192 and 256: grid + interpolation
+        for b in g.buckets:
+            b.out.zero_()
+        g.replay()
+        replay = g.results()
+        g.run_eager()
+        eager = g.results()
+        for L in batch:
+            assert np.all(replay[L]["status"] == 0)
+            np.testing.assert_array_equal(replay[L]["best_l"], eager[L]["best_l"])
+            np.testing.assert_array_equal(replay[L]["d2"], eager[L]["d2"])
+    finally:
+        g.close()
+
+
 def test_graph_best_template_mode():
     batch = synth.uneven_batch(n_queries=100, n_templates_per_L=5, seed=7)
     g = uneven.UnevenGraph(uneven.buckets_from(batch, N_THETA, "bf16"), mode=1)
