@@ -98,10 +98,12 @@ typedef enum {
                        /* at the bin centres by an inverse FFT over the bin      */
                        /* period B h.  Rows are clipped at zero except for       */
                        /* RFSW2, which splits the signed rows.  The default bin  */
-                       /* count is the smallest even 2/3/5-smooth count >= the   */
-                       /* default B; an explicit n_bins must be 2/3/5-smooth.    */
-                       /* One CTA holds the image's half grid in shared memory:  */
-                       /* L <= 128 (else SW_ERR_UNSUPPORTED).  Not for the       */
+                       /* count is the smallest multiple of 32 >= the default B  */
+                       /* and 1.5 L (it is also the grid length of the NUFFT);   */
+                       /* an explicit n_bins must be such a count too.           */
+                       /* L <= 256 (else SW_ERR_UNSUPPORTED); above L = 128 the  */
+                       /* bins are 256, 320 or 384 and the grids use scratch     */
+                       /* memory owned by the context.  Not for the              */
                        /* allocation-free call.                                  */
 } sw_projector;
 
