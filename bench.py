@@ -300,10 +300,11 @@ def uneven_block(args, device):
         torch.cuda.empty_cache()
 
 
-def configs_block(device):
+def configs_block(device, projector="slice"):
     """The other configurations of the method, each on the GPU (device time
     from CUDA events; single-pair latency also as host wall time) and the
-    FP64 oracle on a bounded sample (1 thread and all host threads):
+    FP64 oracle on a bounded sample (1 thread and all host threads), with the
+    given projector:
       single pair 64 x 64, n = 360, M = 128, all rotations + translation;
       one reference x 10,000 queries, 128 x 128, n = 512, M = 256;
       random dense U[0,1) images, L = n = M in {32, 64, 96, 128}, rotation only
@@ -313,7 +314,7 @@ def configs_block(device):
     import oracle
     from paper_2503_13756_gb300 import swalign, synth
     al = swalign.Aligner(device)
-    out = {}
+    out = {"projector": PROJECTOR_NAMES[projector]}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cores = os.cpu_count() or 1
 
@@ -338,15 +339,18 @@ def configs_block(device):
             ts.append(1e3 * (time.perf_counter() - t0))
         return float(np.median(ts))
 
+    proj = int(projector == "slice")
+
     def oracle_rate(q, t, n, M, translation, threads):
         t0 = time.perf_counter()
-        oracle.align_all_pairs(q, t, n, M, translation=translation, nthreads=threads)
+        oracle.align_all_pairs(q, t, n, M, translation=translation, nthreads=threads,
+                               projector=proj)
         return len(q) * len(t) / (time.perf_counter() - t0)
 
     # ---- single pair
     d = synth.single_pair()
     f, g = d["f"].astype(np.float32), d["g"].astype(np.float32)
-    p = swalign.make_params(64, 360, 128)
+    p = swalign.make_params(64, 360, 128, projector=projector)
     fd, gd = torch.from_numpy(f).cuda(device), torch.from_numpy(g).cuda(device)
     al.reserve(p, 1, 1)
     fn = lambda: al.align_all_rotations(fd, gd, p)
@@ -357,23 +361,24 @@ def configs_block(device):
     # ---- one reference x 10,000 queries
     d = synth.one_reference_batch()
     q, ref = d["queries"], d["reference"]
-    p = swalign.make_params(128, 512, 256)
+    p = swalign.make_params(128, 512, 256, projector=projector)
     qd, rd = torch.from_numpy(q).cuda(device), torch.from_numpy(ref).cuda(device)
     res = torch.empty((len(q), 40), dtype=torch.uint8, device=qd.device)
     al.autotune(p)
     al.reserve(p, len(q), 1)
     ms = dev_ms(lambda: al.align_batch(qd, rd, p, out=res), 5)
-    sub = q[:256].astype(np.float64)
+    nsub = 64 if proj else 256  # the oracle's slice sums take seconds per image
+    sub = q[:nsub].astype(np.float64)
     out["one_reference_10000_n512_M256"] = {
         "pairs_per_s": len(q) / (ms / 1e3), "ms_per_batch": ms,
         "oracle_pairs_per_s": oracle_rate(sub, ref.astype(np.float64), 512, 256, 1, cores),
-        "oracle_threads": cores, "oracle_sample": "first 256 queries"}
+        "oracle_threads": cores, "oracle_sample": f"first {nsub} queries"}
     del qd, res
     # ---- random dense, rotation only, L = n = M
     wa = {}
     for Lw in (32, 64, 96, 128):
         x = synth.random_dense(Lw, count=1024 + 64, seed=synth.SEED_BASE + 9 + Lw)
-        p = swalign.make_params(Lw, Lw, Lw, translation=0)
+        p = swalign.make_params(Lw, Lw, Lw, translation=0, projector=projector)
         xd = torch.from_numpy(x).cuda(device)
         one = lambda: al.align_all_rotations(xd[0], xd[1], p)
         res = torch.empty((1024 * 64, 40), dtype=torch.uint8, device=xd.device)
@@ -391,7 +396,7 @@ def configs_block(device):
     d = synth.many_to_many(n_queries=512, n_templates=64)
     qd = torch.from_numpy(d["queries"]).cuda(device)
     td = torch.from_numpy(d["templates"]).cuda(device)
-    p = swalign.make_params(128, 256, 128, metric="msw2")
+    p = swalign.make_params(128, 256, 128, metric="msw2", projector=projector)
     res = torch.empty((512 * 64, 40), dtype=torch.uint8, device=qd.device)
     al.reserve(p, 512, 64)
     al.profile(True)
@@ -681,7 +686,7 @@ def main():
     }
     print(json.dumps(line), flush=True)
     if args.configs and world == 1:
-        print(json.dumps({"configs": configs_block(local)}), flush=True)
+        print(json.dumps({"configs": configs_block(local, args.projector)}), flush=True)
 
 
 if __name__ == "__main__":
