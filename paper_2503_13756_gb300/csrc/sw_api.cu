@@ -260,7 +260,7 @@ struct ProfRec {
 struct Tune {
     int want = 0;  // target CTA count of the projection's angle split
     int spec = 0;  // signals per FFT batch of the spectra (4, 8, 16)
-    int dec = 0;   // signals per CTA of the decision (4, 8, 16)
+    int dec = 0;   // decision form: 1 register FFT, else signals per CTA (4, 8, 16)
     int plan = 0;  // FFT radix order (fft_plan variant)
 };
 
@@ -1702,8 +1702,9 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
     const int wants[3] = {456, 304, 912};
     const int widths_small[3] = {16, 8, 4}, widths_large[3] = {8, 4, 4};
     const int *specs = n <= 512 ? widths_small : widths_large;
-    const int dec_small[3] = {8, 16, 4}, dec_large[3] = {4, 8, 4};
-    const int *decs = n <= 512 ? dec_small : dec_large;
+    // decision: 1 = the register form where it exists, else shared-memory widths
+    const int dec_reg[3] = {1, 8, 16}, dec_small[3] = {8, 16, 4}, dec_large[3] = {4, 8, 4};
+    const int *decs = swk::decide_reg_ok(n) ? dec_reg : (n <= 512 ? dec_small : dec_large);
     TrialTimes t1[3];
     for (int i = 0; i < 3 && s == SW_OK; ++i) {
         Tune tu;

@@ -12,9 +12,17 @@
 // l* = argmin (lowest l on ties) is taken on FP32 values; the distance at l*
 // is formed in FP64.
 //
-// Design: one CTA per (query, 2*nsig templates); two real correlation
-// curves are packed in one complex inverse FFT (the curves are real, so the
-// spectrum of c_a + i c_b is C_a + i C_b extended by Hermitian symmetry).
+// Two real correlation curves are packed in one complex inverse FFT (the
+// curves are real, so the spectrum of c_a + i c_b is C_a + i C_b extended by
+// Hermitian symmetry).  Two forms:
+//  - register form (n = 64, 128, 256, 512): one CTA per (query, 16
+//    templates), the block of spectra staged in shared memory by cp.async,
+//    then one warp per curve pair: the length-n transform lives in the
+//    warp's registers (an in-lane radix-2 pass, twiddles, five shuffle
+//    stages), and the argmin is a warp reduction.  No block barrier after
+//    the staging.
+//  - shared-memory form (any n): one CTA per (query, 2*nsig templates), the
+//    mixed-radix Stockham FFT of the library over nsig signals.
 #include "sw_internal.cuh"
 #include "swalign.h"
 
@@ -58,6 +66,132 @@ __device__ __forceinline__ void centre_of(const double *ctr, int idx, int parts,
         ay = 0.5 * (c[1] + c[3]);
         dx = c[0] - c[2];
         dy = c[1] - c[3];
+    }
+}
+
+// Terms of the argmin key that depend on the rotation (FP32: they only rank
+// the rotations; the distance at l* is formed again in FP64).
+struct XtraTerms {
+    int tmode;         // 0 rotation only, 1 closed-form shift, 2 shift grid
+    bool rot_t;        // a shift term is present
+    float gstep, ginv, gk;
+    float hnm, qnm;    // (1/2 or 1) n M and n M / 4
+    float aix, aiy, dix, diy;
+};
+
+// The query's centre (aix, aiy, dix, diy) in FP32.
+template <int PARTS, bool XTRA>
+__device__ __forceinline__ XtraTerms xtra_terms(const DecideArgs &A, float aix, float aiy,
+                                                float dix, float diy)
+{
+    XtraTerms X;
+    X.tmode = !XTRA ? 1 : (!A.translation ? 0 : (A.grid_k > 0 ? 2 : 1));
+    X.rot_t = XTRA && X.tmode != 1;
+    X.gstep = A.gstep;
+    X.ginv = A.ginv;
+    X.gk = A.gk;
+    X.hnm = A.hnm;
+    X.qnm = A.qnm;
+    X.aix = aix;
+    X.aiy = aiy;
+    X.dix = dix;
+    X.diy = diy;
+    return X;
+}
+
+// Key k of one pair at alpha_l = (c, sn) plus rc |s - c(l)|^2, c(l) =
+// abar_i - R abar_j, s = 0 (rotation only) or the grid point nearest c(l),
+// and (two parts) |d_i - R d_j|^2 / 4 scaled by n M.  (ax, ay), (ex, ey):
+// the template's abar and d.
+template <int PARTS>
+__device__ __forceinline__ float xtra_key(float k, const XtraTerms &X, float c, float sn,
+                                          float ax, float ay, float ex, float ey)
+{
+    if (X.rot_t) {
+        float sx = X.aix - (c * ax - sn * ay), sy = X.aiy - (sn * ax + c * ay);
+        if (X.tmode == 2) {
+            sx -= fminf(fmaxf(rintf(sx * X.ginv), -X.gk), X.gk) * X.gstep;
+            sy -= fminf(fmaxf(rintf(sy * X.ginv), -X.gk), X.gk) * X.gstep;
+        }
+        k = fmaf(X.hnm, sx * sx + sy * sy, k);
+    }
+    if (PARTS == 2) {
+        const float sx = X.dix - (c * ex - sn * ey), sy = X.diy - (sn * ex + c * ey);
+        k = fmaf(X.qnm, sx * sx + sy * sy, k);
+    }
+    return k;
+}
+
+// FP64 distance and shift of a pair at rotation l from rval = n corr(l);
+// base = n |m_i - m_j|^2 + N_i + N_j.
+template <int PARTS>
+__device__ __forceinline__ double pair_distance(const DecideArgs &A, int l, float rval,
+                                                double base, int tmode, double aix, double aiy,
+                                                double dix, double diy, double ajx, double ajy,
+                                                double djx, double djy, double &sx, double &sy)
+{
+    const double corr = (double)rval * A.inv_n;
+    const double2 c = A.cs64[l];
+    sx = aix - (c.x * ajx - c.y * ajy);
+    sy = aiy - (c.y * ajx + c.x * ajy);
+    double d = (base - 2.0 * corr) * A.inv_nM;
+    if (PARTS == 2) {
+        const double ex = dix - (c.x * djx - c.y * djy);
+        const double ey = diy - (c.y * djx + c.x * djy);
+        d += 0.25 * (ex * ex + ey * ey);
+    }
+    restrict_shift(tmode, A.grid_k, A.grid_step, PARTS == 2 ? 1.0 : 0.5, sx, sy, d);
+    return d;
+}
+
+// The result of pair (i, j): rotation bl (>= n when every key was NaN),
+// rval = n corr(bl), delta = n |m_i - m_j|^2, bad_t: template j unusable.
+template <int PARTS>
+__device__ __forceinline__ void write_result(const DecideArgs &A, int i, int j, int bl,
+                                             float rval, float delta, int bad_t, int tmode,
+                                             double aix, double aiy, double dix, double diy)
+{
+    if (bl >= A.n) bl = 0;  // keep the index in range
+    const int st = A.st_q[i] ? 1 : (bad_t ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
+    sw_result r;
+    if (st) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+        r.best_l = -1;
+        r.status = st;
+        r.angle_rad = __int_as_float(0x7fc00000);
+        r.shift[0] = r.shift[1] = nan;
+        r.d2 = nan;
+    } else {
+        double ajx, ajy, djx, djy;
+        centre_of(A.ctr_t, j, PARTS, ajx, ajy, djx, djy);
+        const double base = (double)delta + A.norm_q[i] + A.norm_t[j];
+        double sx, sy;
+        r.d2 = pair_distance<PARTS>(A, bl, rval, base, tmode, aix, aiy, dix, diy, ajx, ajy, djx,
+                                    djy, sx, sy);
+        r.best_l = bl;
+        r.status = 0;
+        r.angle_rad = (float)(A.dalpha * bl);
+        r.shift[0] = sx;
+        r.shift[1] = sy;
+    }
+    r.reserved = 0.f;
+    reinterpret_cast<sw_result *>(A.out)[(size_t)i * A.Nt + j] = r;
+}
+
+// Point l of the full curve of pair (0, 0) (single-pair call).
+template <int PARTS>
+__device__ __forceinline__ void curve_point(const DecideArgs &A, int l, float rval, double base,
+                                            int st, int tmode, double aix, double aiy, double dix,
+                                            double diy, double ajx, double ajy, double djx,
+                                            double djy)
+{
+    double sx, sy;
+    const double d = pair_distance<PARTS>(A, l, rval, base, tmode, aix, aiy, dix, diy, ajx, ajy,
+                                          djx, djy, sx, sy);
+    A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
+    if (A.shifts) {
+        A.shifts[2 * l] = sx;
+        A.shifts[2 * l + 1] = sy;
     }
 }
 
@@ -148,24 +282,17 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
     // ---- argmin over l (FP32 keys, lowest l on ties).  Thread (s, lq) scans
     // l = lq, lq + LQ, ... for both pairs of signal s: a warp then reads 32
     // consecutive complex values (conflict-free).
-    // the distance's M is the levels per part (parts = 2: ramp-filtered)
-    const double nM = (double)n * (M / PARTS);
     double aix, aiy, dix, diy;
     centre_of(A.ctr_q, i, PARTS, aix, aiy, dix, diy);
+    const XtraTerms X = xtra_terms<PARTS, XTRA>(A, (float)aix, (float)aiy, (float)dix, (float)diy);
     const float invn = 1.f / (float)n;
     constexpr int LQ = kDecThreads / nsig;
     const int s = threadIdx.x % nsig, lq = threadIdx.x / nsig;
     float best0 = __int_as_float(0x7f800000), best1 = best0;
     int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
-    // rotation-dependent terms of the two pairs: rc |s - c|^2 with
-    // c = abar_i - R abar_j and s = 0 (rotation only) or the grid point
-    // nearest c (translation on a grid), and xc |d_i - R d_j|^2 (two parts)
-    const int tmode = !XTRA ? 1 : (!A.translation ? 0 : (A.grid_k > 0 ? 2 : 1));
-    const bool rot_t = XTRA && tmode != 1, x_t = PARTS == 2;
-    const float gstep = (float)A.grid_step, ginv = tmode == 2 ? (float)(1.0 / A.grid_step) : 0.f;
-    const float gk = (float)A.grid_k;
+    const bool x_t = PARTS == 2;
     float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ex0 = 0.f, ey0 = 0.f, ex1 = 0.f, ey1 = 0.f;
-    if (rot_t || x_t) {
+    if (X.rot_t || x_t) {
         const int ja = min(j0 + 2 * s, Nt - 1), jb = min(j0 + 2 * s + 1, Nt - 1);
         double x, y, u, v;
         centre_of(A.ctr_t, ja, PARTS, x, y, u, v);
@@ -173,36 +300,13 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
         centre_of(A.ctr_t, jb, PARTS, x, y, u, v);
         ax1 = (float)x, ay1 = (float)y, ex1 = (float)u, ey1 = (float)v;
     }
-    const float hnm = (PARTS == 2 ? 1.f : 0.5f) * (float)nM;
-    const float qnm = 0.25f * (float)nM;
     for (int l = lq; l < n; l += LQ) {
         const float2 z = R[l * nsig + s];
         float k0 = -2.f * z.x * invn, k1 = -2.f * z.y * invn;
-        if (rot_t || x_t) {
+        if (X.rot_t || x_t) {
             const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
-            const float c = w.x, sn = -w.y;
-            if (rot_t) {
-                float sx = (float)aix - (c * ax0 - sn * ay0), sy = (float)aiy - (sn * ax0 + c * ay0);
-                if (tmode == 2) {
-                    sx -= fminf(fmaxf(rintf(sx * ginv), -gk), gk) * gstep;
-                    sy -= fminf(fmaxf(rintf(sy * ginv), -gk), gk) * gstep;
-                }
-                k0 = fmaf(hnm, sx * sx + sy * sy, k0);
-                sx = (float)aix - (c * ax1 - sn * ay1);
-                sy = (float)aiy - (sn * ax1 + c * ay1);
-                if (tmode == 2) {
-                    sx -= fminf(fmaxf(rintf(sx * ginv), -gk), gk) * gstep;
-                    sy -= fminf(fmaxf(rintf(sy * ginv), -gk), gk) * gstep;
-                }
-                k1 = fmaf(hnm, sx * sx + sy * sy, k1);
-            }
-            if (x_t) {
-                float sx = (float)dix - (c * ex0 - sn * ey0), sy = (float)diy - (sn * ex0 + c * ey0);
-                k0 = fmaf(qnm, sx * sx + sy * sy, k0);
-                sx = (float)dix - (c * ex1 - sn * ey1);
-                sy = (float)diy - (sn * ex1 + c * ey1);
-                k1 = fmaf(qnm, sx * sx + sy * sy, k1);
-            }
+            k0 = xtra_key<PARTS>(k0, X, w.x, -w.y, ax0, ay0, ex0, ey0);
+            k1 = xtra_key<PARTS>(k1, X, w.x, -w.y, ax1, ay1, ex1, ey1);
         }
         if (k0 < best0) { best0 = k0; bl0 = l; }   // l increases: ties keep the lowest
         if (k1 < best1) { best1 = k1; bl1 = l; }
@@ -237,42 +341,9 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
                 const int l = red_l[w][pr];
                 if (k < bk || (k == bk && l < bl)) { bk = k; bl = l; }
             }
-            if (bl >= n) bl = 0;  // every key NaN (unusable input): keep the index in range
-            const int sg = pr >> 1, comp = pr & 1;
-            double ajx, ajy, djx, djy;
-            centre_of(A.ctr_t, j, PARTS, ajx, ajy, djx, djy);
-            const double base = (double)delta[pr] + A.norm_q[i] + A.norm_t[j];
-            const int st = A.st_q[i] ? 1 : (stt[pr] ? 2 : ((A.dev_err && *A.dev_err) ? 3 : 0));
-            sw_result r;
-            if (st) {
-                const double nan = __longlong_as_double(0x7ff8000000000000ULL);
-                r.best_l = -1;
-                r.status = st;
-                r.angle_rad = __int_as_float(0x7fc00000);
-                r.shift[0] = r.shift[1] = nan;
-                r.d2 = nan;
-            } else {
-                const float2 z = R[bl * nsig + sg];
-                const double corr = (double)(comp ? z.y : z.x) * A.inv_n;
-                const double2 c = A.cs64[bl];
-                double sx = aix - (c.x * ajx - c.y * ajy);
-                double sy = aiy - (c.y * ajx + c.x * ajy);
-                double d = (base - 2.0 * corr) * A.inv_nM;
-                if (x_t) {
-                    const double ex = dix - (c.x * djx - c.y * djy);
-                    const double ey = diy - (c.y * djx + c.x * djy);
-                    d += 0.25 * (ex * ex + ey * ey);
-                }
-                restrict_shift(tmode, A.grid_k, A.grid_step, PARTS == 2 ? 1.0 : 0.5, sx, sy, d);
-                r.best_l = bl;
-                r.status = 0;
-                r.angle_rad = (float)(A.dalpha * bl);
-                r.shift[0] = sx;
-                r.shift[1] = sy;
-                r.d2 = d;
-            }
-            r.reserved = 0.f;
-            reinterpret_cast<sw_result *>(A.out)[(size_t)i * Nt + j] = r;
+            const float2 z = R[(bl < n ? bl : 0) * nsig + (pr >> 1)];
+            write_result<PARTS>(A, i, j, bl, (pr & 1) ? z.y : z.x, delta[pr], stt[pr], X.tmode,
+                                aix, aiy, dix, diy);
         }
     }
     // ---- full curve of pair (0, 0) (single-pair call)
@@ -281,24 +352,286 @@ k_decide(DecideArgs A, FftPlan plan, const float2 *__restrict__ tw)
         centre_of(A.ctr_t, 0, PARTS, ajx, ajy, djx, djy);
         const double base = (double)delta[0] + A.norm_q[0] + A.norm_t[0];
         const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
-        for (int l = threadIdx.x; l < n; l += blockDim.x) {
-            const double corr = (double)R[l * nsig].x * A.inv_n;
-            const double2 c = A.cs64[l];
-            double sx = aix - (c.x * ajx - c.y * ajy);
-            double sy = aiy - (c.y * ajx + c.x * ajy);
-            double d = (base - 2.0 * corr) * A.inv_nM;
-            if (x_t) {
-                const double ex = dix - (c.x * djx - c.y * djy);
-                const double ey = diy - (c.y * djx + c.x * djy);
-                d += 0.25 * (ex * ex + ey * ey);
+        for (int l = threadIdx.x; l < n; l += blockDim.x)
+            curve_point<PARTS>(A, l, R[l * nsig].x, base, st, X.tmode, aix, aiy, dix, diy, ajx,
+                               ajy, djx, djy);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Register form.
+constexpr int kRegThreads = 256;   // 8 warps, one curve pair (two templates) each
+constexpr int kRegTemplates = 16;  // templates per CTA
+constexpr int kRegRow = 9;         // float4 per staged frequency: 16 complex + 16 bytes of pad
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+
+// Radix-2 decimation-in-time stages of span LEN, 2 LEN, ..., MW over a[] (bit-
+// reversed input): a[b + j] +- e^{+2 pi i j / LEN} a[b + j + LEN / 2].
+template <int MW, int LEN>
+__device__ __forceinline__ void lane_stages(float2 (&a)[MW], const float2 *__restrict__ tw)
+{
+    constexpr int n = 32 * MW, hl = LEN / 2;
+#pragma unroll
+    for (int b = 0; b < MW; b += LEN) {
+#pragma unroll
+        for (int j = 0; j < hl; ++j) {
+            float2 x = a[b + j + hl];
+            if (j == 0) {
+            } else if (4 * j == LEN) {
+                x = make_float2(-x.y, x.x);  // e^{+i pi / 2}
+            } else {
+                x = cmul(x, cconj(tw[j * (n / LEN)]));
             }
-            restrict_shift(tmode, A.grid_k, A.grid_step, PARTS == 2 ? 1.0 : 0.5, sx, sy, d);
-            A.curve[l] = st ? __longlong_as_double(0x7ff8000000000000ULL) : d;
-            if (A.shifts) {
-                A.shifts[2 * l] = sx;
-                A.shifts[2 * l + 1] = sy;
-            }
+            const float2 u = a[b + j];
+            a[b + j] = cadd(u, x);
+            a[b + j + hl] = csub(u, x);
         }
+    }
+    if constexpr (2 * LEN <= MW) lane_stages<MW, 2 * LEN>(a, tw);
+}
+
+// Unnormalised inverse DFT of length n = 32 MW (MW a power of two <= 16) held
+// by one warp, X(q) = sum_t x(t) e^{+2 pi i t q / n}.  In: v[t1] = x(32 t1 +
+// lane).  Out: v[k1] = X(k1 + MW brev5(lane)).  tw[q] = e^{-2 pi i q / n}.
+// With t = 32 t1 + lane and q = k1 + MW q2 the kernel factors into an MW-point
+// transform over t1 in each lane (radix 2, decimation in time), the twiddles
+// e^{+2 pi i lane k1 / n}, and a 32-point transform over the lanes (five
+// radix-2 decimation-in-frequency stages, outputs in bit-reversed lanes).
+template <int MW>
+__device__ __forceinline__ void reg_ifft(float2 (&v)[MW], const float2 *__restrict__ tw, int lane)
+{
+    constexpr int n = 32 * MW;
+    constexpr int LG = MW == 1 ? 0 : MW == 2 ? 1 : MW == 4 ? 2 : MW == 8 ? 3 : 4;
+    static_assert((1 << LG) == MW, "MW must be 1, 2, 4, 8 or 16");
+    float2 a[MW];
+#pragma unroll
+    for (int t = 0; t < MW; ++t) {
+        int r = 0;  // t with its LG bits reversed
+#pragma unroll
+        for (int b = 0; b < LG; ++b) r |= ((t >> b) & 1) << (LG - 1 - b);
+        a[r] = v[t];
+    }
+    lane_stages<MW, 2>(a, tw);
+#pragma unroll
+    for (int k1 = 1; k1 < MW; ++k1) a[k1] = cmul(a[k1], cconj(tw[lane * k1]));
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+        const float sg = up ? -1.f : 1.f;
+        // upper lane of a butterfly: (partner - mine) e^{+2 pi i (lane mod h) / (2h)}
+        const float2 w = (h > 1 && up) ? cconj(tw[(lane & (h - 1)) * (n / (2 * h))])
+                                       : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k1 = 0; k1 < MW; ++k1) {
+            const float px = __shfl_xor_sync(0xffffffffu, a[k1].x, h);
+            const float py = __shfl_xor_sync(0xffffffffu, a[k1].y, h);
+            const float2 d = make_float2(fmaf(sg, a[k1].x, px), fmaf(sg, a[k1].y, py));
+            a[k1] = h > 1 ? cmul(d, w) : d;
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < MW; ++k1) v[k1] = a[k1];
+}
+
+// Issue the copies of the block (query i, templates j0 .. j0 + 15) into buf
+// (the caller commits the cp.async group).  Templates past Nt are
+// zero-filled; even Nt keeps every row 16-byte aligned.
+template <int NH>
+__device__ __forceinline__ void stage_block(const DecideArgs &A, int i, int j0, float4 *buf,
+                                            int tid)
+{
+    const int Nq = A.Nq, Nt = A.Nt;
+    const size_t fs = (size_t)Nq * Nt;
+    const float2 *Ci = A.C + (size_t)i * Nt + j0;
+    if ((Nt & 1) == 0) {
+        for (int c = tid; c < NH * 8; c += kRegThreads) {
+            const int f = c >> 3, col = c & 7;
+            const int valid = min(max(Nt - (j0 + 2 * col), 0), 2);
+            const float2 *src = valid ? Ci + (size_t)f * fs + 2 * col : A.C;
+            cp_async16(buf + f * kRegRow + col, src, 8 * valid);
+        }
+    } else {
+        for (int c = tid; c < NH * 16; c += kRegThreads) {
+            const int f = c >> 4, col = c & 15;
+            const bool valid = j0 + col < Nt;
+            const float2 *src = valid ? Ci + (size_t)f * fs + col : A.C;
+            cp_async8(reinterpret_cast<float2 *>(buf + f * kRegRow) + col, src, valid ? 8 : 0);
+        }
+    }
+}
+
+// The staging buffer of n/2 rows, then the twiddles and the query's profile.
+size_t reg_smem_bytes(int n, int M)
+{
+    return sizeof(float4) * (size_t)(n / 2) * kRegRow + sizeof(float2) * (size_t)n +
+           sizeof(float) * (size_t)M;
+}
+
+// One CTA per (query i, templates j0 .. j0 + 15).
+template <int MW, int PARTS, bool XTRA>
+__global__ void __launch_bounds__(kRegThreads, MW <= 8 ? 4 : 2)
+k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
+{
+    constexpr int n = 32 * MW, nh = n / 2;
+    extern __shared__ float4 smr[];
+    float4 *sC = smr;                                             // [nh][kRegRow]
+    float2 *tws = reinterpret_cast<float2 *>(sC + nh * kRegRow);  // [n]
+    float *prof_i = reinterpret_cast<float *>(tws + n);           // [M]
+    __shared__ int stt[kRegTemplates];
+    __shared__ float4 ctr_f[kRegTemplates + 1];  // FP32 centres (abar, d): templates, then the query
+    __shared__ int res_l[kRegTemplates];         // per template: l*, n corr(l*), n |m_i - m_j|^2
+    __shared__ float res_v[kRegTemplates], res_d[kRegTemplates];
+    const int Nt = A.Nt, M = A.M;
+    const int i = blockIdx.x, j0 = blockIdx.y * kRegTemplates;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = warp;  // this warp's templates: j0 + 2s (real part), j0 + 2s + 1 (imaginary)
+
+    // ---- stage C(k', i, j0 .. j0 + 15), k' = 1..n/2 (row k' - 1)
+    stage_block<nh>(A, i, j0, sC, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int t = tid; t < n; t += kRegThreads) tws[t] = tw[t];
+    for (int p = tid; p < M; p += kRegThreads) prof_i[p] = A.prof_q[(size_t)i * M + p];
+    if (tid < kRegTemplates) {
+        const int j = j0 + tid;
+        stt[tid] = j < Nt ? A.st_t[j] : 1;
+    }
+    if ((XTRA || PARTS == 2) && tid <= kRegTemplates) {
+        // the keys' centres, converted once per CTA (not per warp)
+        double x, y, u, w;
+        if (tid < kRegTemplates) centre_of(A.ctr_t, min(j0 + tid, Nt - 1), PARTS, x, y, u, w);
+        else centre_of(A.ctr_q, i, PARTS, x, y, u, w);
+        ctr_f[tid] = make_float4((float)x, (float)y, (float)u, (float)w);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+
+    const int ja = j0 + 2 * s, jb = ja + 1;
+    // k' = 0 part: n |m_i - m_j|^2
+    float da = 0.f, db = 0.f;
+    if (ja < Nt) {
+        const float *pa = A.prof_t + (size_t)ja * M;
+        for (int p = lane; p < M; p += 32) {
+            const float d = prof_i[p] - __ldg(pa + p);
+            da = fmaf(d, d, da);
+        }
+    }
+    if (jb < Nt) {
+        const float *pb = A.prof_t + (size_t)jb * M;
+        for (int p = lane; p < M; p += 32) {
+            const float d = prof_i[p] - __ldg(pb + p);
+            db = fmaf(d, d, db);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        da += __shfl_xor_sync(0xffffffffu, da, off);
+        db += __shfl_xor_sync(0xffffffffu, db, off);
+    }
+    da *= (float)n;
+    db *= (float)n;
+
+    // Hermitian-extended spectrum Z(t) = C_a(t) + i C_b(t) (t < n/2),
+    // conj C_a(n - t) + i conj C_b(n - t) (t > n/2), real parts at n/2, 0
+    // at 0; unusable templates contribute zeros (their NaNs stay out of
+    // the partner)
+    const bool za = stt[2 * s] != 0, zb = stt[2 * s + 1] != 0;
+    float2 v[MW];
+#pragma unroll
+    for (int m = 0; m < MW; ++m) {
+        const int t = 32 * m + lane;
+        const int kf = m < MW / 2 ? t : n - t;
+        float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kf != 0) X = sC[(kf - 1) * kRegRow + s];
+        if (za) X.x = X.y = 0.f;
+        if (zb) X.z = X.w = 0.f;
+        if (m < MW / 2)
+            v[m] = make_float2(X.x - X.w, X.y + X.z);  // kf = 0 gives 0
+        else if (m == MW / 2 && lane == 0)
+            v[m] = make_float2(X.x, X.z);
+        else
+            v[m] = make_float2(X.x + X.w, X.z - X.y);
+    }
+    reg_ifft<MW>(v, tws, lane);  // v[k1] = n (corr_a + i corr_b) at l = k1 + MW brev5(lane)
+
+    // ---- argmin over l (FP32 keys, lowest l on ties), carrying n corr(l)
+    const bool x_t = PARTS == 2;
+    float4 cq = make_float4(0.f, 0.f, 0.f, 0.f), c0 = cq, c1 = cq;
+    if (XTRA || x_t) {
+        cq = ctr_f[kRegTemplates];
+        c0 = ctr_f[2 * s];
+        c1 = ctr_f[2 * s + 1];
+    }
+    const XtraTerms X = xtra_terms<PARTS, XTRA>(A, cq.x, cq.y, cq.z, cq.w);
+    const float invn = 1.f / (float)n;
+    const float qnan = __int_as_float(0x7fc00000);
+    float best0 = __int_as_float(0x7f800000), best1 = best0, rv0 = qnan, rv1 = qnan;
+    int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
+    const int lb = MW * brev5(lane);
+#pragma unroll
+    for (int k1 = 0; k1 < MW; ++k1) {
+        const int l = k1 + lb;
+        const float2 z = v[k1];
+        float k0 = -2.f * z.x * invn, kb = -2.f * z.y * invn;
+        if (X.rot_t || x_t) {
+            const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
+            k0 = xtra_key<PARTS>(k0, X, w.x, -w.y, c0.x, c0.y, c0.z, c0.w);
+            kb = xtra_key<PARTS>(kb, X, w.x, -w.y, c1.x, c1.y, c1.z, c1.w);
+        }
+        // l increases with k1 in a lane: ties keep the lowest
+        if (k0 < best0) { best0 = k0; bl0 = l; rv0 = z.x; }
+        if (kb < best1) { best1 = kb; bl1 = l; rv1 = z.y; }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float o0 = __shfl_xor_sync(0xffffffffu, best0, off);
+        const int q0 = __shfl_xor_sync(0xffffffffu, bl0, off);
+        const float r0 = __shfl_xor_sync(0xffffffffu, rv0, off);
+        const float o1 = __shfl_xor_sync(0xffffffffu, best1, off);
+        const int q1 = __shfl_xor_sync(0xffffffffu, bl1, off);
+        const float r1 = __shfl_xor_sync(0xffffffffu, rv1, off);
+        if (o0 < best0 || (o0 == best0 && q0 < bl0)) { best0 = o0; bl0 = q0; rv0 = r0; }
+        if (o1 < best1 || (o1 == best1 && q1 < bl1)) { best1 = o1; bl1 = q1; rv1 = r1; }
+    }
+    if (lane < 2) {
+        res_l[2 * s + lane] = lane ? bl1 : bl0;
+        res_v[2 * s + lane] = lane ? rv1 : rv0;
+        res_d[2 * s + lane] = lane ? db : da;
+    }
+    double aix, aiy, dix, diy;
+    // ---- full curve of pair (0, 0) (single-pair call)
+    if (A.curve && i == 0 && j0 == 0 && s == 0) {
+        centre_of(A.ctr_q, i, PARTS, aix, aiy, dix, diy);
+        double ajx, ajy, djx, djy;
+        centre_of(A.ctr_t, 0, PARTS, ajx, ajy, djx, djy);
+        const double base = (double)da + A.norm_q[0] + A.norm_t[0];
+        const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
+#pragma unroll
+        for (int k1 = 0; k1 < MW; ++k1)
+            curve_point<PARTS>(A, k1 + lb, v[k1].x, base, st, X.tmode, aix, aiy, dix, diy,
+                               ajx, ajy, djx, djy);
+    }
+    // every warp has posted its pairs
+    __syncthreads();
+    // ---- FP64 distance at l*: one lane per template, all in warp 0 (the
+    // FP64 pipe is narrow: its instructions are issued once per 16 pairs)
+    if (warp == 0 && lane < kRegTemplates && j0 + lane < Nt) {
+        centre_of(A.ctr_q, i, PARTS, aix, aiy, dix, diy);
+        write_result<PARTS>(A, i, j0 + lane, res_l[lane], res_v[lane], res_d[lane],
+                            stt[lane], X.tmode, aix, aiy, dix, diy);
     }
 }
 
@@ -350,6 +683,8 @@ __global__ void k_best_template(const sw_result *__restrict__ all, int Nq, int N
 
 }  // namespace
 
+bool decide_reg_ok(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+
 cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const float2 *tw,
                           cudaStream_t st, int nsig_req)
 {
@@ -360,9 +695,40 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
     a.inv_n = 1.0 / a.n;
     a.inv_nM = 1.0 / ((double)a.n * (a.M / a.parts));
     a.dalpha = 6.283185307179586 / a.n;
-    // 8 signals (16 pairs) per CTA keeps the shared footprint small enough
-    // for several CTAs per SM; 4 at n = 1024.  A requested width is taken
-    // when its buffers fit (2 n nsig complex values).
+    const double nM = (double)a.n * (a.M / a.parts);  // the levels per part
+    a.hnm = (a.parts == 2 ? 1.f : 0.5f) * (float)nM;
+    a.qnm = 0.25f * (float)nM;
+    a.gstep = (float)a.grid_step;
+    a.ginv = a.grid_k > 0 ? (float)(1.0 / a.grid_step) : 0.f;
+    a.gk = (float)a.grid_k;
+    if (decide_reg_ok(a.n) && (nsig_req == 0 || nsig_req == 1)) {
+        const size_t smem = reg_smem_bytes(a.n, a.M);
+        dim3 grid(a.Nq, (a.Nt + kRegTemplates - 1) / kRegTemplates);
+#define SW_REG_LAUNCH(MW, P, X)                                                                 \
+    do {                                                                                        \
+        cudaFuncSetAttribute(k_decide_reg<MW, P, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                        \
+        k_decide_reg<MW, P, X><<<grid, kRegThreads, smem, st>>>(a, tw);                         \
+    } while (0)
+#define SW_REG_FORMS(MW)                                                                        \
+    do {                                                                                        \
+        if (a.parts == 1 && a.translation && a.grid_k == 0) SW_REG_LAUNCH(MW, 1, false);       \
+        else if (a.parts == 1) SW_REG_LAUNCH(MW, 1, true);                                      \
+        else SW_REG_LAUNCH(MW, 2, true);                                                        \
+    } while (0)
+        switch (a.n) {
+        case 64: SW_REG_FORMS(2); break;
+        case 128: SW_REG_FORMS(4); break;
+        case 256: SW_REG_FORMS(8); break;
+        default: SW_REG_FORMS(16); break;
+        }
+#undef SW_REG_FORMS
+#undef SW_REG_LAUNCH
+        return cudaGetLastError();
+    }
+    // shared-memory form: 8 signals (16 pairs) per CTA keeps the shared
+    // footprint small enough for several CTAs per SM; 4 at n = 1024.  A
+    // requested width is taken when its buffers fit (2 n nsig complex values).
     int nsig = a.n <= 512 ? 8 : 4;
     if ((nsig_req == 4 || nsig_req == 8 || nsig_req == 16) && (size_t)a.n * nsig_req <= 8192)
         nsig = nsig_req;

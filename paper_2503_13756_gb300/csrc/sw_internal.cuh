@@ -81,6 +81,8 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// 5-bit bit reversal (lane order of the warp FFTs' outputs)
+__device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
 // multiply by -i (forward) or +i (inverse):  dir = -1 gives -i*a, +1 gives i*a
 __device__ __forceinline__ float2 cmul_i(float2 a, int dir)
 {
@@ -396,9 +398,18 @@ struct DecideArgs {
     double grid_step = 0.0;
     // filled by launch_decide: 1/n, 1/(nM), 2 pi/n (no FP64 divisions on the device)
     double inv_n, inv_nM, dalpha;
+    // FP32 constants of the argmin keys (filled by launch_decide; GB300 runs
+    // FP64 at a small fraction of FP32, so no key work is done in FP64):
+    // hnm = (1/2 or 1) n M', qnm = n M' / 4 with M' the levels per part,
+    // gstep, 1 / gstep (0 without a grid) and grid_k
+    float hnm, qnm, gstep, ginv, gk;
 };
+// nsig: 0 = default form, 1 = register form (n = 64, 128, 256, 512), 4, 8
+// or 16 = shared-memory form with that many signals per CTA.
 cudaError_t launch_decide(const DecideArgs &a, const FftPlan &plan, const float2 *tw,
                           cudaStream_t st, int nsig = 0);
+// n for which the register form of the decision exists (its default there)
+bool decide_reg_ok(int n);
 
 // Max-sliced W2 over rotations: q [Nq][n][M], t [Nt][n][M] uncentred
 // quantiles; with translation the columns are centred by ctr ([N][2]).

@@ -65,8 +65,6 @@ constexpr int kBigBatch = 32;        // angles per CTA of k_slice_interp
 static_assert(2 * (kSliceThreads / 32) == kSliceBatch, "one warp per angle pair of a batch");
 static_assert(2 * (kBigThreads / 32) == kBigBatch, "one warp per angle pair of a batch");
 
-__device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
-
 // x mod N for the small excursions of the grid indices (|x| < 2N).
 __device__ __forceinline__ int wrap_n(int x, int N)
 {

@@ -14,9 +14,11 @@
 //
 // Design (GB300): one CTA per image; levels are taken 2*nsig at a time, two
 // real levels packed into one complex signal, FFT'd by the shared-memory
-// Stockham FFT and unpacked by Hermitian symmetry.  Norms are accumulated
-// in FP64.  Optional BF16/FP16 copies feed the tensor-core GEMM, with their
-// norms taken from the rounded values so that self-distances cancel.
+// Stockham FFT and unpacked by Hermitian symmetry.  The batches are staged
+// by cp.async into two buffers, so that batch b + 1 is in flight while batch
+// b is transformed and written.  Norms are accumulated in double-float.
+// Optional BF16/FP16 copies feed the tensor-core GEMM, with their norms taken
+// from the rounded values so that self-distances cancel.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -26,6 +28,7 @@ namespace swk {
 namespace {
 
 constexpr int kSpecThreads = 256;
+constexpr size_t kSmemOptIn = 227 * 1024;  // dynamic shared memory a CTA may opt in to
 
 template <typename T>
 __device__ __forceinline__ T to_lp(float x);
@@ -113,6 +116,52 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
     }
 }
 
+__device__ __forceinline__ void cpa16(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa4(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+
+// Issue the copies of the level batch [p0, p0 + 2 nsig) of image qi into
+// buf: signal s of angle k is buf[k nsig + s] = (level p0 + 2s, p0 + 2s + 1);
+// levels past M are zero-filled.  With one part and M % 4 == 0 every angle's
+// slice is whole 16-byte chunks; otherwise one 4-byte copy per level.
+template <int nsig>
+__device__ __forceinline__ void stage_levels(const float *__restrict__ qi, int n, int M, int Mp,
+                                             int parts, int p0, float2 *buf)
+{
+    if (parts == 1 && (M & 3) == 0) {
+        constexpr int CH = nsig / 2;  // 16-byte chunks (4 levels) per angle
+        for (int c = threadIdx.x; c < n * CH; c += blockDim.x) {
+            const int k = c / CH, h = c % CH;
+            const int p = p0 + 4 * h;
+            const int valid = min(max(M - p, 0), 4);
+            const float *src = valid ? qi + (size_t)k * M + p : qi;
+            cpa16(buf + k * nsig + 2 * h, src, 4 * valid);
+        }
+    } else {
+        for (int c = threadIdx.x; c < n * 2 * nsig; c += blockDim.x) {
+            const int k = c / (2 * nsig), e = c % (2 * nsig);
+            const int p = p0 + e;
+            const float *src = qi;
+            if (p < M)
+                src = parts == 1 ? qi + (size_t)k * M + p
+                                 : qi + (size_t)(p / Mp) * n * Mp + (size_t)k * Mp + p % Mp;
+            cpa4(reinterpret_cast<float *>(buf + k * nsig) + e, src, p < M ? 4 : 0);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <typename T, int nsig>
 __global__ void __launch_bounds__(kSpecThreads)
 k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2 *__restrict__ tw,
@@ -123,51 +172,36 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     // [0, M/2) and [M/2, M) are the quantiles of the positive and negative
     // parts, stored as [parts][n][M/2], and each part is centred by its own
     // vector.
-    extern __shared__ float2 smc[];
-    float2 *b0 = smc;
-    float2 *b1 = b0 + n * nsig;
-    float2 *x1 = b1 + n * nsig;  // [M] Qhat(1, p) before centring
-    float2 *tws = x1 + M;        // [n] twiddles
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
+    extern __shared__ __align__(16) float2 smc[];
+    float2 *stage = smc;                 // [2][n nsig] level batches (cp.async)
+    float2 *scr = stage + 2 * n * nsig;  // [n nsig] the FFT's other buffer
+    float2 *x1 = scr + n * nsig;         // [M] Qhat(1, p) before centring
+    float2 *tws = x1 + M;                // [n] twiddles
     __shared__ double red[2][kSpecThreads / 32];
     __shared__ double s_c1[2][2];
     const int Mp = M / parts;  // levels per part
     const int img = blockIdx.x;
     const float *qi = q + (size_t)img * n * M;
+    stage_levels<nsig>(qi, n, M, Mp, parts, 0, stage);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     const int nh = n / 2;
     // norms in double-float (TwoSum-compensated FP32): FP64 arithmetic is
     // scarce on this part
     DF acc32 = {0.f, 0.f}, acc16 = {0.f, 0.f};
     const float invn = 1.f / (float)n;
 
-    for (int p0 = 0; p0 < M; p0 += 2 * nsig) {
-        // ---- load: signal s = levels (p0 + 2s, p0 + 2s + 1) as (re, im).
-        // Unrolled so that a thread's global loads are in flight together
-        // (the trip count is n nsig / blockDim, 16 at n = 256); an aligned
-        // level pair is one 8-byte load.
-#pragma unroll 8
-        for (int t = threadIdx.x; t < n * nsig; t += blockDim.x) {
-            const int k = t / nsig, s = t % nsig;
-            const int p = p0 + 2 * s;
-            float xr = 0.f, xi = 0.f;
-            if (parts == 1) {
-                if (p + 1 < M && !(M & 1)) {
-                    const float2 v = __ldg(reinterpret_cast<const float2 *>(qi + (size_t)k * M + p));
-                    xr = v.x;
-                    xi = v.y;
-                } else {
-                    if (p < M) xr = __ldg(qi + (size_t)k * M + p);
-                    if (p + 1 < M) xi = __ldg(qi + (size_t)k * M + p + 1);
-                }
-            } else {
-                if (p < M) xr = qi[(size_t)(p / Mp) * n * Mp + (size_t)k * Mp + p % Mp];
-                if (p + 1 < M)
-                    xi = qi[(size_t)((p + 1) / Mp) * n * Mp + (size_t)k * Mp + (p + 1) % Mp];
-            }
-            b0[t] = make_float2(xr, xi);
-        }
+    for (int p0 = 0, b = 0; p0 < M; p0 += 2 * nsig, ++b) {
+        // ---- batch b: levels (p0 + 2s, p0 + 2s + 1) as signal s (re, im).
+        // Stage batch b + 1 (an empty group at the end), then wait for b.
+        float2 *cur = stage + (b & 1) * n * nsig;
+        if (p0 + 2 * nsig < M)
+            stage_levels<nsig>(qi, n, M, Mp, parts, p0 + 2 * nsig,
+                               stage + ((b + 1) & 1) * n * nsig);
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();
-        const float2 *R = fft_smem<nsig, -1>(b0, b1, plan, tws);
+        const float2 *R = fft_smem<nsig, -1>(cur, scr, plan, tws);
         // ---- unpack two real spectra per signal, k' = 0..n/2
         for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
             const int kf = t / nsig, s = t % nsig;
@@ -293,13 +327,18 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
     int nsig = n <= 512 ? 16 : 8;
     if ((nsig_req == 4 || nsig_req == 8 || nsig_req == 16) && (size_t)n * nsig_req <= 8192)
         nsig = nsig_req;
-    const size_t smem = sizeof(float2) * ((size_t)2 * n * nsig + M + n);
+    // three batch buffers (two staged, one FFT scratch), within the 227 KB a
+    // CTA can hold
+    auto smem_of = [&](int ns) { return sizeof(float2) * ((size_t)3 * n * ns + M + n); };
+    while (nsig > 4 && smem_of(nsig) > kSmemOptIn) nsig /= 2;
+    const size_t smem = smem_of(nsig);
+    if (smem > kSmemOptIn) return cudaErrorInvalidValue;
     SpecOut o{spec32, fstride, lp_q, lpq_fstride, lp_t, lpt_fstride, Nq, tc_ldk(M),
               lp_kind != 0, lp_kind == 3};
 #define SW_SPEC_LAUNCH(T, NS)                                                                    \
     do {                                                                                        \
         cudaFuncSetAttribute(k_spectrum<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             200 * 1024);                                                       \
+                             (int)smem);                                                        \
         k_spectrum<T, NS><<<nb, kSpecThreads, smem, st>>>(q, n, M, plan, tw, o, prof, center,  \
                                                           norm32, norm16, parts);               \
     } while (0)

@@ -28,10 +28,11 @@ def blobs(rng, count, L):
 
 
 @pytest.mark.parametrize("metric", ["sw2", "rfsw2"])
-@pytest.mark.parametrize("K,step_q", [(2, 16), (6, 4), (1, 48)])
-def test_grid_batch_matches_oracle_brute_force(al, metric, K, step_q):
+# n = 64: the decision's register form (one warp per pair of curves)
+@pytest.mark.parametrize("K,step_q,n", [(2, 16, 24), (6, 4, 24), (1, 48, 24), (2, 16, 64)])
+def test_grid_batch_matches_oracle_brute_force(al, metric, K, step_q, n):
     rng = np.random.default_rng(K * 100 + step_q)
-    L, n, M = 40, 24, 16
+    L, M = 40, 16
     q, t = blobs(rng, 3, L), blobs(rng, 4, L)
     p = swalign.make_params(L, n, M, metric=metric, shift_grid=K, shift_step_q=step_q)
     B = swalign.bins_of(p)
@@ -56,9 +57,10 @@ def test_grid_batch_matches_oracle_brute_force(al, metric, K, step_q):
             # two tie: its distance is already within the bar above
 
 
-def test_grid_curve_matches_oracle(al):
+@pytest.mark.parametrize("n", [36, 64])
+def test_grid_curve_matches_oracle(al, n):
     rng = np.random.default_rng(3)
-    L, n, M = 48, 36, 24
+    L, M = 48, 24
     f, g = blobs(rng, 2, L)
     K, step_q = 3, 8
     step = step_q * (2.0 / L) / 16
