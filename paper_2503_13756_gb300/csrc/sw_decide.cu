@@ -447,6 +447,24 @@ __device__ __forceinline__ void reg_ifft(float2 (&v)[MW], const float2 *__restri
     for (int k1 = 0; k1 < MW; ++k1) v[k1] = a[k1];
 }
 
+// Integer image of a float that preserves its order, -0 taken as +0 and NaN
+// above everything.
+__device__ __forceinline__ int ordered_key(float x)
+{
+    x = x + 0.f;  // -0 -> +0 (equal keys must map to one integer)
+    const int i = __float_as_int(x);
+    return x != x ? 0x7fffffff : (i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// Warp-wide argmin: every lane offers (key, l); returns the lowest l among
+// the lanes holding the smallest key (a NaN key loses to any other).
+__device__ __forceinline__ int warp_argmin(float key, int l)
+{
+    const int k = ~ordered_key(key);  // order-reversing
+    const int kmax = __reduce_max_sync(0xffffffffu, k);
+    return (int)__reduce_min_sync(0xffffffffu, (unsigned)(k == kmax ? l : 0x7fffffff));
+}
+
 // Issue the copies of the block (query i, templates j0 .. j0 + 15) into buf
 // (the caller commits the cp.async group).  Templates past Nt are
 // zero-filled; even Nt keeps every row 16-byte aligned.
@@ -521,28 +539,22 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
 
     const int ja = j0 + 2 * s, jb = ja + 1;
     // k' = 0 part: n |m_i - m_j|^2
-    float da = 0.f, db = 0.f;
-    if (ja < Nt) {
-        const float *pa = A.prof_t + (size_t)ja * M;
-        for (int p = lane; p < M; p += 32) {
-            const float d = prof_i[p] - __ldg(pa + p);
-            da = fmaf(d, d, da);
+    // (half-warp h takes template ja + h)
+    float dsum = 0.f;
+    {
+        const int jh = lane < 16 ? ja : jb;
+        if (jh < Nt) {
+            const float *ph = A.prof_t + (size_t)jh * M;
+            for (int p = lane & 15; p < M; p += 16) {
+                const float d = prof_i[p] - __ldg(ph + p);
+                dsum = fmaf(d, d, dsum);
+            }
         }
-    }
-    if (jb < Nt) {
-        const float *pb = A.prof_t + (size_t)jb * M;
-        for (int p = lane; p < M; p += 32) {
-            const float d = prof_i[p] - __ldg(pb + p);
-            db = fmaf(d, d, db);
-        }
-    }
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        da += __shfl_xor_sync(0xffffffffu, da, off);
-        db += __shfl_xor_sync(0xffffffffu, db, off);
+        for (int off = 8; off; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
     }
-    da *= (float)n;
-    db *= (float)n;
+    const float da = __shfl_sync(0xffffffffu, dsum, 0) * (float)n;
+    const float db = __shfl_sync(0xffffffffu, dsum, 16) * (float)n;
 
     // Hermitian-extended spectrum Z(t) = C_a(t) + i C_b(t) (t < n/2),
     // conj C_a(n - t) + i conj C_b(n - t) (t > n/2), real parts at n/2, 0
@@ -576,36 +588,46 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
         c1 = ctr_f[2 * s + 1];
     }
     const XtraTerms X = xtra_terms<PARTS, XTRA>(A, cq.x, cq.y, cq.z, cq.w);
-    const float invn = 1.f / (float)n;
-    const float qnan = __int_as_float(0x7fc00000);
-    float best0 = __int_as_float(0x7f800000), best1 = best0, rv0 = qnan, rv1 = qnan;
-    int bl0 = 0x7fffffff, bl1 = 0x7fffffff;
+    // Per lane the lowest l of its best key (l grows with k1), then two warp
+    // reductions on order-preserving integer images of the keys: the best
+    // key, then the lowest l holding it.  NaN keys never win (unless all are).
+    float best0, best1, rv0, rv1;  // per lane: best key, and n corr at its l
+    int bl0, bl1;
     const int lb = MW * brev5(lane);
+    if (!X.rot_t && !x_t) {
+        // key = -2 corr(l) / n: n is a power of two, so the smallest key is
+        // exactly the largest n corr(l)
+        rv0 = rv1 = __int_as_float(0xff800000);  // -inf: NaN values never replace it
+        bl0 = bl1 = lb;
 #pragma unroll
-    for (int k1 = 0; k1 < MW; ++k1) {
-        const int l = k1 + lb;
-        const float2 z = v[k1];
-        float k0 = -2.f * z.x * invn, kb = -2.f * z.y * invn;
-        if (X.rot_t || x_t) {
-            const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
-            k0 = xtra_key<PARTS>(k0, X, w.x, -w.y, c0.x, c0.y, c0.z, c0.w);
-            kb = xtra_key<PARTS>(kb, X, w.x, -w.y, c1.x, c1.y, c1.z, c1.w);
+        for (int k1 = 0; k1 < MW; ++k1) {
+            if (v[k1].x > rv0) { rv0 = v[k1].x; bl0 = k1 + lb; }
+            if (v[k1].y > rv1) { rv1 = v[k1].y; bl1 = k1 + lb; }
         }
-        // l increases with k1 in a lane: ties keep the lowest
-        if (k0 < best0) { best0 = k0; bl0 = l; rv0 = z.x; }
-        if (kb < best1) { best1 = kb; bl1 = l; rv1 = z.y; }
-    }
+        best0 = -rv0;
+        best1 = -rv1;
+    } else {
+        const float invn = 1.f / (float)n;
+        best0 = best1 = __int_as_float(0x7f800000);
+        rv0 = v[0].x;
+        rv1 = v[0].y;
+        bl0 = bl1 = lb;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const float o0 = __shfl_xor_sync(0xffffffffu, best0, off);
-        const int q0 = __shfl_xor_sync(0xffffffffu, bl0, off);
-        const float r0 = __shfl_xor_sync(0xffffffffu, rv0, off);
-        const float o1 = __shfl_xor_sync(0xffffffffu, best1, off);
-        const int q1 = __shfl_xor_sync(0xffffffffu, bl1, off);
-        const float r1 = __shfl_xor_sync(0xffffffffu, rv1, off);
-        if (o0 < best0 || (o0 == best0 && q0 < bl0)) { best0 = o0; bl0 = q0; rv0 = r0; }
-        if (o1 < best1 || (o1 == best1 && q1 < bl1)) { best1 = o1; bl1 = q1; rv1 = r1; }
+        for (int k1 = 0; k1 < MW; ++k1) {
+            const int l = k1 + lb;
+            const float2 z = v[k1];
+            const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
+            const float k0 = xtra_key<PARTS>(-2.f * z.x * invn, X, w.x, -w.y, c0.x, c0.y, c0.z, c0.w);
+            const float kb = xtra_key<PARTS>(-2.f * z.y * invn, X, w.x, -w.y, c1.x, c1.y, c1.z, c1.w);
+            if (k0 < best0) { best0 = k0; bl0 = l; rv0 = z.x; }
+            if (kb < best1) { best1 = kb; bl1 = l; rv1 = z.y; }
+        }
     }
+    // the lane holding l* has l* as its own best: n corr(l*) comes from it
+    bl0 = warp_argmin(best0, bl0);
+    bl1 = warp_argmin(best1, bl1);
+    rv0 = __shfl_sync(0xffffffffu, rv0, brev5(bl0 / MW));
+    rv1 = __shfl_sync(0xffffffffu, rv1, brev5(bl1 / MW));
     if (lane < 2) {
         res_l[2 * s + lane] = lane ? bl1 : bl0;
         res_v[2 * s + lane] = lane ? rv1 : rv0;

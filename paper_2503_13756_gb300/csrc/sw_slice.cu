@@ -130,7 +130,23 @@ struct SliceArgs {
     float *out;
     int32_t *status;
     SliceCoef coef;         // tap weight polynomials (kernel parameter bank)
+    int pf_ahead;           // k_project_slice: CTA b prefetches image b + pf_ahead into L2
 };
+
+// Bulk prefetch of [p, p + bytes) into L2 (the 16-byte-aligned part), in
+// 32 KB requests.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes)
+{
+    size_t a = __cvta_generic_to_global(p);
+    size_t e = a + bytes;
+    a = (a + 15) & ~(size_t)15;
+    e &= ~(size_t)15;
+    while (a < e) {
+        const unsigned chunk = (unsigned)(e - a < 32768 ? e - a : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(chunk) : "memory");
+        a += chunk;
+    }
+}
 
 __device__ __forceinline__ const float *image_of(const SliceArgs &A, int gi)
 {
@@ -356,6 +372,10 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
     if (threadIdx.x == 0) {
         s_bad = 0;
         s_mass = 0;
+        // one CTA per SM: the image that starts about one CTA lifetime from
+        // now is pulled into L2, so that its phase-A loads hit there
+        if (A.pf_ahead > 0 && blockIdx.x + A.pf_ahead < gridDim.x)
+            prefetch_l2(image_of(A, gi + A.pf_ahead), sizeof(float) * A.srcL * A.srcL);
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
     __syncthreads();
@@ -410,12 +430,16 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_slice_interp(SliceArgs A)
 }
 
 template <int M>
-cudaError_t launch_small(const SliceArgs &a, int nb, cudaStream_t st)
+cudaError_t launch_small(SliceArgs a, int nb, cudaStream_t st)
 {
     const size_t smem = slice_smem_bytes(32 * M);
     cudaError_t e = cudaFuncSetAttribute(k_project_slice<M>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        a.pf_ahead = sms;  // resident CTAs: one per SM
     k_project_slice<M><<<nb, kSliceThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -486,6 +510,7 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.img2 = img2 ? img2 : img;
     a.nb1 = (img2 && nb_first >= 0) ? nb_first : nb;
     a.img_off = 0;
+    a.pf_ahead = 0;
     a.L = L;
     a.srcL = srcL;
     a.nh = nh;
