@@ -165,6 +165,9 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
     const int L = A.L, half = L / 2;
     const int rows = slice_rows(N), S = slice_stride(N), lo = slice_lo(N);
     const int nleft = slice_left(N), nright = slice_right(N);
+    // 8-byte pixel pairs: L even (every row starts 8-byte aligned, c is even)
+    // and the image itself 8-byte aligned
+    const bool pair8 = (L & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 7) == 0;
     // ---- A: one warp per column pair (c, c+1): FFT along r', kept rows
     for (int c = 2 * warp; c < L; c += 2 * nw) {
         float2 v[M];
@@ -176,7 +179,14 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
             v[n1] = make_float2(0.f, 0.f);
             if (r >= 0 && r < L) {
                 float x0, x1 = 0.f;
-                if (A.srcL == L) {
+                if (A.srcL == L && pair8) {
+                    // (c, c + 1) in one 8-byte load: each lane reads another
+                    // row, so every load instruction costs one L1 line request
+                    // per lane, and this halves them
+                    const float2 x = __ldg(reinterpret_cast<const float2 *>(src + (size_t)r * L + c));
+                    x0 = x.x;
+                    x1 = x.y;
+                } else if (A.srcL == L) {
                     x0 = __ldg(src + (size_t)r * L + c);
                     if (c + 1 < L) x1 = __ldg(src + (size_t)r * L + c + 1);
                 } else {  // 2 x 2 upsampling: columns c, c+1 share a source pixel (c even)
