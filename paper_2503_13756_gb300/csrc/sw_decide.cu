@@ -428,48 +428,9 @@ __device__ __forceinline__ void reg_ifft(float2 (&v)[MW], const float2 *__restri
     lane_stages<MW, 2>(a, tw);
 #pragma unroll
     for (int k1 = 1; k1 < MW; ++k1) a[k1] = cmul(a[k1], cconj(tw[lane * k1]));
-    // The lane stages treat every k1 alike: real and imaginary parts are held
-    // as packed pairs over k1 = 2q, 2q + 1, so that each FP32 pair operation
-    // (Blackwell's two-wide FMA) serves two transforms.
-    static_assert(MW % 2 == 0, "packed lane stages take k1 in pairs");
-    float2 re[MW / 2], im[MW / 2];
+    warp_lane_stages<MW>(a, tw, lane);
 #pragma unroll
-    for (int q = 0; q < MW / 2; ++q) {
-        re[q] = make_float2(a[2 * q].x, a[2 * q + 1].x);
-        im[q] = make_float2(a[2 * q].y, a[2 * q + 1].y);
-    }
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        const bool up = (lane & h) != 0;
-        const float sg = up ? -1.f : 1.f;
-        const float2 SG = make_float2(sg, sg);
-        // upper lane of a butterfly: (partner - mine) e^{+2 pi i (lane mod h) / (2h)}
-        const float2 w = (h > 1 && up) ? cconj(tw[(lane & (h - 1)) * (n / (2 * h))])
-                                       : make_float2(1.f, 0.f);
-        const float2 WX = make_float2(w.x, w.x), WY = make_float2(w.y, w.y);
-        const float2 NWY = make_float2(-w.y, -w.y);
-#pragma unroll
-        for (int q = 0; q < MW / 2; ++q) {
-            const float2 pr = make_float2(__shfl_xor_sync(0xffffffffu, re[q].x, h),
-                                          __shfl_xor_sync(0xffffffffu, re[q].y, h));
-            const float2 pi = make_float2(__shfl_xor_sync(0xffffffffu, im[q].x, h),
-                                          __shfl_xor_sync(0xffffffffu, im[q].y, h));
-            const float2 dr = __ffma2_rn(SG, re[q], pr);
-            const float2 di = __ffma2_rn(SG, im[q], pi);
-            if (h > 1) {
-                re[q] = __ffma2_rn(NWY, di, __fmul2_rn(WX, dr));  // dr wx - di wy
-                im[q] = __ffma2_rn(WY, dr, __fmul2_rn(WX, di));   // di wx + dr wy
-            } else {
-                re[q] = dr;
-                im[q] = di;
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < MW / 2; ++q) {
-        v[2 * q] = make_float2(re[q].x, im[q].x);
-        v[2 * q + 1] = make_float2(re[q].y, im[q].y);
-    }
+    for (int k1 = 0; k1 < MW; ++k1) v[k1] = a[k1];
 }
 
 // Integer image of a float that preserves its order, -0 taken as +0 and NaN

@@ -90,6 +90,66 @@ __device__ __forceinline__ float2 cmul_i(float2 a, int dir)
 }
 
 // ------------------------------------------------------------------------
+// The 32-point part of a warp-held inverse transform of length N = 32 M:
+// five radix-2 decimation-in-frequency stages over the lanes, applied alike
+// to the M values of every lane (outputs in bit-reversed lane order).  The
+// upper lane of a butterfly keeps (partner - mine) e^{+2 pi i (lane mod h) /
+// (2h)}, the lower one mine + partner; tw[q] = e^{-2 pi i q / N}.  Real and
+// imaginary parts go through as packed pairs over k1 = 2q, 2q + 1, so that
+// each two-wide FP32 operation of Blackwell serves two transforms (an odd M
+// leaves its last value to the scalar form).
+template <int M>
+__device__ __forceinline__ void warp_lane_stages(float2 (&a)[M], const float2 *__restrict__ tw,
+                                                 int lane)
+{
+    constexpr int N = 32 * M, P = M / 2;
+    float2 re[P > 0 ? P : 1], im[P > 0 ? P : 1];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        re[q] = make_float2(a[2 * q].x, a[2 * q + 1].x);
+        im[q] = make_float2(a[2 * q].y, a[2 * q + 1].y);
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+        const float sg = up ? -1.f : 1.f;
+        const float2 SG = make_float2(sg, sg);
+        const float2 w = (h > 1 && up) ? cconj(tw[(lane & (h - 1)) * (N / (2 * h))])
+                                       : make_float2(1.f, 0.f);
+        const float2 WX = make_float2(w.x, w.x), WY = make_float2(w.y, w.y);
+        const float2 NWY = make_float2(-w.y, -w.y);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float2 pr = make_float2(__shfl_xor_sync(0xffffffffu, re[q].x, h),
+                                          __shfl_xor_sync(0xffffffffu, re[q].y, h));
+            const float2 pi = make_float2(__shfl_xor_sync(0xffffffffu, im[q].x, h),
+                                          __shfl_xor_sync(0xffffffffu, im[q].y, h));
+            const float2 dr = __ffma2_rn(SG, re[q], pr);
+            const float2 di = __ffma2_rn(SG, im[q], pi);
+            if (h > 1) {
+                re[q] = __ffma2_rn(NWY, di, __fmul2_rn(WX, dr));  // dr wx - di wy
+                im[q] = __ffma2_rn(WY, dr, __fmul2_rn(WX, di));   // di wx + dr wy
+            } else {
+                re[q] = dr;
+                im[q] = di;
+            }
+        }
+        if (M % 2) {
+            float2 &y = a[M - 1];
+            const float px = __shfl_xor_sync(0xffffffffu, y.x, h);
+            const float py = __shfl_xor_sync(0xffffffffu, y.y, h);
+            const float2 d = make_float2(fmaf(sg, y.x, px), fmaf(sg, y.y, py));
+            y = h > 1 ? cmul(d, w) : d;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        a[2 * q] = make_float2(re[q].x, im[q].x);
+        a[2 * q + 1] = make_float2(re[q].y, im[q].y);
+    }
+}
+
+// ------------------------------------------------------------------------
 // Batched complex FFT of length n over NSIG signals held in shared memory
 // as buf[k * NSIG + s] (signal s, element k), Stockham self-sorting, mixed
 // radix 2/3/4/5/8.  DIR = -1: X(q) = sum_k x(k) e^{-2 pi i k q / n};

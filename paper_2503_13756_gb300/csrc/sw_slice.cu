@@ -95,20 +95,7 @@ __device__ __forceinline__ void warp_ifft(float2 (&v)[M], const float2 *__restri
         }
         y[k1] = k1 == 0 ? acc : cmul(acc, cconj(tw[lane * k1]));  // lane k1 < N
     }
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        const bool up = (lane & h) != 0;
-        const float2 w = up ? cconj(tw[(lane & (h - 1)) * (N / (2 * h))]) : make_float2(1.f, 0.f);
-        const float sg = up ? -1.f : 1.f;
-#pragma unroll
-        for (int k1 = 0; k1 < M; ++k1) {
-            const float px = __shfl_xor_sync(0xffffffffu, y[k1].x, h);
-            const float py = __shfl_xor_sync(0xffffffffu, y[k1].y, h);
-            // lower lane: mine + partner; upper lane: (partner - mine) w
-            const float2 d = make_float2(fmaf(sg, y[k1].x, px), fmaf(sg, y[k1].y, py));
-            y[k1] = cmul(d, w);
-        }
-    }
+    warp_lane_stages<M>(y, tw, lane);
 #pragma unroll
     for (int k1 = 0; k1 < M; ++k1) v[k1] = y[k1];
 }
