@@ -9,16 +9,38 @@
 // at tau = 0 (level p = 0 under the p/M rule) every t qualifies and Q is the
 // left end of the domain, e_0.
 //
-// Design (GB300): one warp per projection.  The CDF is a warp scan of
-// double-float partial sums (TwoSum-compensated FP32) kept in shared memory,
-// so that tau - F_{j-1} keeps ~48 bits even where it cancels; each lane then
-// binary-searches its levels.  No FP64 on this path.
+// Design (GB300): one warp per projection, four projections per warp, the next
+// one staged by cp.async while the current one is computed.  The CDF is a warp
+// scan of double-float partial sums (TwoSum-compensated FP32) kept in shared
+// memory, so that tau - F_{j-1} keeps ~48 bits even where it cancels; each
+// lane then binary-searches its levels.  No FP64 on this path.
 #include "sw_internal.cuh"
 
 namespace swk {
 namespace {
 
-constexpr int kQThreads = 256;  // 8 warps = 8 projections per block
+constexpr int kQThreads = 256;  // 8 warps
+constexpr int kQRows = 4;       // projections per warp: the next is staged while one is computed
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+
+// Issue the copies of projection k of image imgi into U (reversed for the
+// mirrored half: row k + n/2 of a half projection is row k read backwards).
+__device__ __forceinline__ void stage_row(float *U, const float *__restrict__ proj, int n, int B,
+                                          int half, int imgi, int k, int lane)
+{
+    const int nh = n / 2;
+    const bool mirror = half && k >= nh;
+    const float *row = half ? proj + ((size_t)imgi * nh + (mirror ? k - nh : k)) * B
+                            : proj + ((size_t)imgi * n + k) * B;
+    for (int b = lane; b < B; b += 32) cp_async4(U + b, mirror ? row + B - 1 - b : row + b);
+}
 
 __global__ void __launch_bounds__(kQThreads)
 k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int level_rule,
@@ -29,115 +51,117 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
     const int imgi = blockIdx.y;
-    const int k = blockIdx.x * nw + warp;
-    // per warp: U (B+1 floats, padded to even) then F (B+1 float2): every
-    // region and every F starts 8-byte aligned
+    const int nrows = mirror_out ? n / 2 : n;
+    const int k0 = (blockIdx.x * nw + warp) * kQRows;
+    if (k0 >= nrows) return;  // whole warp leaves; no block barrier below
+    const int kend = min(nrows, k0 + kQRows);
+    // per warp: two U buffers (B+1 floats, padded to even) then F (B+1
+    // float2) and the quantiles: every region and every F starts 8-byte aligned
     const int ue = (B + 1) + ((B + 1) & 1);
-    const int stride = ue + 2 * (B + 1) + M + (M & 1);
-    float *U = sm + warp * stride;                          // [B]
-    float2 *F = reinterpret_cast<float2 *>(U + ue);         // [B+1] (hi, lo)
-    float *qb = reinterpret_cast<float *>(F + (B + 1));     // [M] this projection's quantiles
-    if (k >= (mirror_out ? n / 2 : n)) return;  // whole warp leaves; no block barrier below
-    const int nh = n / 2;
-    const float *row;
-    bool mirror = false;
-    if (half) {
-        mirror = k >= nh;
-        row = proj + ((size_t)imgi * nh + (mirror ? k - nh : k)) * B;
-    } else {
-        row = proj + ((size_t)imgi * n + k) * B;
-    }
-#pragma unroll 4
-    for (int b = lane; b < B; b += 32) U[b] = mirror ? __ldg(row + B - 1 - b) : __ldg(row + b);
-    __syncwarp();
+    const int stride = 2 * ue + 2 * (B + 1) + M + (M & 1);
+    float *Ubuf = sm + warp * stride;                            // [2][ue]
+    float2 *F = reinterpret_cast<float2 *>(Ubuf + 2 * ue);       // [B+1] (hi, lo)
+    float *qb = reinterpret_cast<float *>(F + (B + 1));          // [M] this projection's quantiles
+    stage_row(Ubuf, proj, n, B, half, imgi, k0, lane);
+    asm volatile("cp.async.commit_group;" ::: "memory");
 
-    // ---- compensated prefix sums: lane owns bins [c0, c1)
-    const int C = (B + 31) / 32;
-    const int c0 = min(B, lane * C), c1 = min(B, c0 + C);
-    DF s = {0.f, 0.f};
-    for (int b = c0; b < c1; ++b) s = df_add(s, DF{U[b], 0.f});
-    // inclusive warp scan of the lane sums
-    DF inc = s;
+    for (int k = k0, r = 0; k < kend; ++k, ++r) {
+        if (k + 1 < kend) stage_row(Ubuf + ((r + 1) & 1) * ue, proj, n, B, half, imgi, k + 1, lane);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // projection k has landed
+        __syncwarp();
+        const float *U = Ubuf + (r & 1) * ue;
+
+        // ---- compensated prefix sums: lane owns bins [c0, c1)
+        const int C = (B + 31) / 32;
+        const int c0 = min(B, lane * C), c1 = min(B, c0 + C);
+        DF s = {0.f, 0.f};
+        for (int b = c0; b < c1; ++b) s = df_add(s, DF{U[b], 0.f});
+        // inclusive warp scan of the lane sums
+        DF inc = s;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        DF o;
-        o.hi = __shfl_up_sync(0xffffffffu, inc.hi, off);
-        o.lo = __shfl_up_sync(0xffffffffu, inc.lo, off);
-        if (lane >= off) inc = df_add(o, inc);
-    }
-    DF run;
-    run.hi = __shfl_up_sync(0xffffffffu, inc.hi, 1);
-    run.lo = __shfl_up_sync(0xffffffffu, inc.lo, 1);
-    if (lane == 0) {
-        run = {0.f, 0.f};
-        F[0] = make_float2(0.f, 0.f);
-    }
-    for (int b = c0; b < c1; ++b) {
-        run = df_add(run, DF{U[b], 0.f});
-        F[b + 1] = make_float2(run.hi, run.lo);
-    }
-    __syncwarp();
-    const DF total = {F[B].x, F[B].y};
-    float *qo = q + ((size_t)imgi * n + k) * M;
-    if (!(total.hi > 0.f) || !isfinite(total.hi)) {
-        for (int p = lane; p < M; p += 32) qo[p] = __int_as_float(0x7fc00000);
-        if (mirror_out) {
-            float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
-            for (int p = lane; p < M; p += 32) qm[p] = __int_as_float(0x7fc00000);
+        for (int off = 1; off < 32; off <<= 1) {
+            DF o;
+            o.hi = __shfl_up_sync(0xffffffffu, inc.hi, off);
+            o.lo = __shfl_up_sync(0xffffffffu, inc.lo, off);
+            if (lane >= off) inc = df_add(o, inc);
         }
-        if (lane == 0) atomicOr(status + (imgi >> status_shift), 1);
-        return;
-    }
-    const float dz = level_rule == 0 ? 2.f * M : (float)M;
-    const float inv_dz = 1.f / dz;
-    // lane owns levels [pb, pe): one binary search, then a forward walk (the
-    // levels increase, so j* never decreases)
-    const int P = (M + 31) / 32;
-    const int pb = min(M, lane * P), pe = min(M, pb + P);
-    int j = 1;
-    for (int p = pb; p < pe; ++p) {
-        // tau = z_p F_B with z_p = (2p+1)/(2M) or p/M, formed exactly
-        const float kz = level_rule == 0 ? 2.f * p + 1.f : (float)p;
-        float Q;
-        if (kz == 0.f) {
-            Q = -0.5f * (float)B * h;  // inf{t : F(t) >= 0}: the domain's left end e_0
-        } else {
-            const DF tau = df_scale_ratio(total, kz, dz, inv_dz);
-            if (p == pb || (level_rule == 1 && p == 1)) {
-                int lo = 1, hi = B;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    const float2 f = F[mid];
-                    if (df_ge(DF{f.x, f.y}, tau)) hi = mid;
-                    else lo = mid + 1;
-                }
-                j = lo;
-            } else {
-                while (j < B) {
-                    const float2 f = F[j];
-                    if (df_ge(DF{f.x, f.y}, tau)) break;
-                    ++j;
-                }
+        DF run;
+        run.hi = __shfl_up_sync(0xffffffffu, inc.hi, 1);
+        run.lo = __shfl_up_sync(0xffffffffu, inc.lo, 1);
+        if (lane == 0) {
+            run = {0.f, 0.f};
+            F[0] = make_float2(0.f, 0.f);
+        }
+        for (int b = c0; b < c1; ++b) {
+            run = df_add(run, DF{U[b], 0.f});
+            F[b + 1] = make_float2(run.hi, run.lo);
+        }
+        __syncwarp();
+        const DF total = {F[B].x, F[B].y};
+        float *qo = q + ((size_t)imgi * n + k) * M;
+        if (!(total.hi > 0.f) || !isfinite(total.hi)) {
+            for (int p = lane; p < M; p += 32) qo[p] = __int_as_float(0x7fc00000);
+            if (mirror_out) {
+                float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
+                for (int p = lane; p < M; p += 32) qm[p] = __int_as_float(0x7fc00000);
             }
-            const float2 fj = F[j - 1];
-            const float num = (tau.hi - fj.x) + (tau.lo - fj.y);
-            const float den = U[j - 1];
-            // the fraction only scales h: a fast divide (error ~2 ulp) is ample
-            float frac = den > 0.f ? __fdividef(num, den) : 0.f;
-            frac = fminf(fmaxf(frac, 0.f), 1.f);
-            const float ej = ((float)(j - 1) - 0.5f * (float)B) * h;
-            Q = fmaf(h, frac, ej);
+            if (lane == 0) atomicOr(status + (imgi >> status_shift), 1);
+        } else {
+            const float dz = level_rule == 0 ? 2.f * M : (float)M;
+            const float inv_dz = 1.f / dz;
+            // lane owns levels [pb, pe): one binary search, then a forward walk
+            // (the levels increase, so j* never decreases)
+            const int P = (M + 31) / 32;
+            const int pb = min(M, lane * P), pe = min(M, pb + P);
+            int j = 1;
+            for (int p = pb; p < pe; ++p) {
+                // tau = z_p F_B with z_p = (2p+1)/(2M) or p/M, formed exactly
+                const float kz = level_rule == 0 ? 2.f * p + 1.f : (float)p;
+                float Q;
+                if (kz == 0.f) {
+                    Q = -0.5f * (float)B * h;  // inf{t : F(t) >= 0}: the domain's left end e_0
+                } else {
+                    const DF tau = df_scale_ratio(total, kz, dz, inv_dz);
+                    if (p == pb || (level_rule == 1 && p == 1)) {
+                        int lo = 1, hi = B;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            const float2 f = F[mid];
+                            if (df_ge(DF{f.x, f.y}, tau)) hi = mid;
+                            else lo = mid + 1;
+                        }
+                        j = lo;
+                    } else {
+                        while (j < B) {
+                            const float2 f = F[j];
+                            if (df_ge(DF{f.x, f.y}, tau)) break;
+                            ++j;
+                        }
+                    }
+                    const float2 fj = F[j - 1];
+                    const float num = (tau.hi - fj.x) + (tau.lo - fj.y);
+                    const float den = U[j - 1];
+                    // the fraction only scales h: a fast divide (error ~2 ulp) is ample
+                    float frac = den > 0.f ? __fdividef(num, den) : 0.f;
+                    frac = fminf(fmaxf(frac, 0.f), 1.f);
+                    const float ej = ((float)(j - 1) - 0.5f * (float)B) * h;
+                    Q = fmaf(h, frac, ej);
+                }
+                qb[p] = Q;
+            }
+            __syncwarp();
+            for (int p = lane; p < M; p += 32) qo[p] = qb[p];
+            if (mirror_out) {
+                // theta + pi: the mirrored histogram has Q'(z) = -Q(1 - z), and
+                // with midpoint levels 1 - z_p = z_{M-1-p}
+                float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
+                for (int p = lane; p < M; p += 32) qm[p] = -qb[M - 1 - p];
+            }
         }
-        qb[p] = Q;
+        __syncwarp();  // U, F and qb are free for the next projection
     }
-    __syncwarp();
-    for (int p = lane; p < M; p += 32) qo[p] = qb[p];
-    if (mirror_out) {
-        // theta + pi: the mirrored histogram has Q'(z) = -Q(1 - z), and with
-        // midpoint levels 1 - z_p = z_{M-1-p}
-        float *qm = q + ((size_t)imgi * n + k + n / 2) * M;
-        for (int p = lane; p < M; p += 32) qm[p] = -qb[M - 1 - p];
-    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Centring vector and centred norm (public sw_quantiles outputs).  One block
@@ -210,13 +234,13 @@ cudaError_t launch_quantiles(const float *proj, int nb, int n, int B, int M, flo
     if (nb <= 0) return cudaSuccess;
     const int nw = kQThreads / 32;
     const int ue = (B + 1) + ((B + 1) & 1);
-    const size_t smem = sizeof(float) * (size_t)nw * (ue + 2 * (B + 1) + M + (M & 1));
+    const size_t smem = sizeof(float) * (size_t)nw * (2 * ue + 2 * (B + 1) + M + (M & 1));
     // with half projections and midpoint levels, angles k and k + n/2 come
     // from one quantile computation
     const int mirror = half && level_rule == 0;
     const int nang = mirror ? n / 2 : n;
     cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    dim3 grid((nang + nw - 1) / nw, nb);
+    dim3 grid((nang + nw * kQRows - 1) / (nw * kQRows), nb);
     k_quantiles<<<grid, kQThreads, smem, st>>>(proj, n, B, M, h, level_rule, half, mirror, q,
                                                 status, status_shift);
     return cudaGetLastError();
