@@ -17,14 +17,19 @@
 // TMA loads (128-byte swizzle, 3-D maps over frequency) into a 4-stage ring
 // of 64-wide K slices; warp 1 owns the 512-column TMEM allocation and one
 // lane issues tcgen05.mma (M=128, N=256, K=16) into one of two TMEM
-// accumulators; warps 2-5 drain the other accumulator with tcgen05.ld and
-// store FP32 rows to global memory, so the epilogue of one tile overlaps the
-// MMAs of the next.  Every mbarrier wait gives up after ~2 s of clock, sets
+// accumulators; warps 2-5 drain the other accumulator with tcgen05.ld, so
+// the epilogue of one tile overlaps the MMAs of the next.  With Nt even each
+// epilogue warp writes its 32 x 32 FP32 blocks into one of two 128-byte-
+// swizzled shared-memory buffers and one lane stores them with a TMA tensor
+// store (coalesced, clipped at the tensor's edges); odd Nt keeps per-lane
+// stores of each row.  Every mbarrier wait gives up after ~2 s of clock, sets
 // *err and lets the CTA run to its end, where TMEM is released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cstring>
 
 #include "sw_internal.cuh"
 
@@ -35,6 +40,7 @@ constexpr int BM = 128, BN = 256, BK = 64;       // tile; BK bf16 = 128 B rows
 constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * BK * 2;              // 16 KB
 constexpr int B_STAGE = BN * BK * 2;              // 32 KB
+constexpr int EPI_BUF = 32 * 32 * 4;              // 4 KB: 32 rows x 32 FP32, 128-byte swizzle
 constexpr int TC_THREADS = 192;                   // 6 warps
 constexpr int TMEM_COLS = 512;                    // two 256-column accumulators
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
@@ -80,6 +86,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         if (abort_flag && *abort_flag) return false;
         if (clock64() - t0 > WAIT_CYCLES) return false;
     }
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y,
+                                             int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -143,17 +159,19 @@ struct TcArgs {
     uint32_t idesc;
     float *C;                   // [nf][Nq][Nt2] fp32
     int *err;                   // set to 1 on a timed-out wait
+    int tma_store;              // C rows 16-byte aligned (Nt even): TMA stores through mapC
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-          TcArgs args)
+          const __grid_constant__ CUtensorMap mapC, TcArgs args)
 {
     extern __shared__ uint8_t dsm[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~static_cast<uintptr_t>(1023));
     uint8_t *sA = base;                       // STAGES x 16 KB
     uint8_t *sB = base + STAGES * A_STAGE;    // STAGES x 32 KB
+    uint8_t *sE = sB + STAGES * B_STAGE;      // [4 warps][2] x 4 KB epilogue blocks (1 KB aligned)
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
     __shared__ uint32_t tmem_base_s;
@@ -258,7 +276,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         // ------------------------------------------------------- epilogue
         const int q = warp & 3;                 // TMEM lane quarter of this warp
         const int row_in_tile = q * 32 + lane;
-        int lt = 0;
+        uint8_t *myE = sE + q * 2 * EPI_BUF;
+        int lt = 0, chunk = 0;
         for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x, ++lt) {
             const int nt = t % args.ntiles;
             const int mt = (t / args.ntiles) % args.mtiles;
@@ -275,26 +294,45 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * BN + c0, r);
-                if (i < args.Nq && c0 < ncols) {
-                    // rows are 2 Nt floats: 16-byte aligned only when Nt is even,
-                    // always 8-byte aligned (float2 per template)
-                    if (c0 + 32 <= ncols && (args.Nt2 & 3) == 0) {
-                        float4 *dst = reinterpret_cast<float4 *>(crow + c0);
+                if (args.tma_store) {
+                    // a box wholly past the tensor's edge holds nothing (warp-uniform)
+                    const int x = nt * BN + c0, y = mt * BM + q * 32;
+                    if (x >= args.Nt2 || y >= args.Nq) continue;
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * BN + c0, r);
+                    // the store issued two boxes ago read this buffer: it is done
+                    uint8_t *eb = myE + (chunk & 1) * EPI_BUF;
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    __syncwarp();
+                    // row `lane`, 16-byte chunk v at v ^ (row mod 8): the 128-byte
+                    // swizzle of the tensor map; a quarter-warp fills 8 distinct chunks
+                    float4 *rowp = reinterpret_cast<float4 *>(eb + lane * 128);
 #pragma unroll
-                        for (int v = 0; v < 8; ++v)
-                            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                                                 __uint_as_float(r[4 * v + 2]),
-                                                 __uint_as_float(r[4 * v + 3]));
-                    } else if (c0 + 32 <= ncols) {
-                        float2 *dst = reinterpret_cast<float2 *>(crow + c0);
+                    for (int v = 0; v < 8; ++v)
+                        rowp[v ^ (lane & 7)] =
+                            make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                        __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_3d(&mapC, eb, x, y, f);
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                    ++chunk;
+                } else {
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * BN + c0, r);
+                    if (i < args.Nq && c0 < ncols) {
+                        // rows are 2 Nt floats: 8-byte aligned (float2 per template)
+                        if (c0 + 32 <= ncols) {
+                            float2 *dst = reinterpret_cast<float2 *>(crow + c0);
 #pragma unroll
-                        for (int v = 0; v < 16; ++v)
-                            dst[v] = make_float2(__uint_as_float(r[2 * v]), __uint_as_float(r[2 * v + 1]));
-                    } else {
+                            for (int v = 0; v < 16; ++v)
+                                dst[v] = make_float2(__uint_as_float(r[2 * v]),
+                                                     __uint_as_float(r[2 * v + 1]));
+                        } else {
 #pragma unroll
-                        for (int v = 0; v < 32; ++v)
-                            if (c0 + v < ncols) crow[c0 + v] = __uint_as_float(r[v]);
+                            for (int v = 0; v < 32; ++v)
+                                if (c0 + v < ncols) crow[c0 + v] = __uint_as_float(r[v]);
+                        }
                     }
                 }
             }
@@ -302,6 +340,9 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[buf]);
         }
+        // every TMA store of this warp has completed before the CTA ends
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -323,6 +364,22 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     return fn;
+}
+
+// C as [nf][Nq][Nt2] FP32 in 32 x 32 boxes, 128-byte swizzle (Nt2 4 bytes a
+// multiple of 16: Nt even).
+bool make_map_c(CUtensorMap *m, float *C, uint64_t nt2, uint64_t nq, uint64_t nf)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {nt2, nq, nf};
+    const cuuint64_t strides[2] = {nt2 * 4, nt2 * 4 * nq};
+    const cuuint32_t box[3] = {32, 32, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 bool make_map(CUtensorMap *m, const void *base, int kind, uint64_t ldk, uint64_t rows,
@@ -370,11 +427,17 @@ cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M
               ((uint32_t)(BM >> 4) << 24);
     a.C = reinterpret_cast<float *>(C);
     a.err = err;
-    const size_t smem = (size_t)STAGES * (A_STAGE + B_STAGE) + 1024;
+    CUtensorMap mc;
+    std::memset(&mc, 0, sizeof(mc));
+    a.tma_store = (Nt % 2 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 &&
+                   make_map_c(&mc, a.C, (uint64_t)2 * Nt, (uint64_t)Nq, (uint64_t)nf))
+                      ? 1
+                      : 0;
+    const size_t smem = (size_t)STAGES * (A_STAGE + B_STAGE) + 4 * 2 * EPI_BUF + 1024;
     cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int tiles = nf * a.mtiles * a.ntiles;
     const int grid = tiles < num_sms ? tiles : num_sms;
-    k_corr_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, a);
+    k_corr_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, mc, a);
     return cudaGetLastError();
 }
 
