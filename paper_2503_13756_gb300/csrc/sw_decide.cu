@@ -487,7 +487,7 @@ size_t reg_smem_bytes(int n, int M)
 
 // One CTA per (query i, templates j0 .. j0 + 15).
 template <int MW, int PARTS, bool XTRA>
-__global__ void __launch_bounds__(kRegThreads, MW <= 8 ? 4 : 2)
+__global__ void __launch_bounds__(kRegThreads, MW <= 8 ? (XTRA || PARTS == 2 ? 4 : 6) : 2)
 k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
 {
     constexpr int n = 32 * MW, nh = n / 2;
