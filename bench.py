@@ -635,6 +635,16 @@ def main():
                 "algorithmic_bytes_per_launch": per_launch * (L * L * 4 + (N_THETA // 2) * Bs * 4),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)",
                 "binding_unit": "shared-memory pipe (tap loads) and instruction issue"}
+        # the binding unit: tap loads (8-byte complex, W x W per slice sample)
+        # against the shared-memory bandwidth (128 B per clock per SM)
+        tap_bytes = (N_THETA // 2) * (Bs // 2 + 1) * SLICE_W * SLICE_W * 8
+        smem_peak = SM_COUNT * 128 * peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL) * 1e6 / 1e12
+        smem_ach = args.steps * nimg * tap_bytes / (stages[dom][0] / 1e3) / 1e12
+        roof["shared_memory"] = {
+            "achieved": smem_ach, "peak": smem_peak, "unit": "TB/s", "frac": smem_ach / smem_peak,
+            "tap_bytes_per_image": tap_bytes,
+            "note": "tap loads only; the FFT exchanges and stores add the rest of the pipe's "
+                    "load (ncu: L1/shared 89% of peak)"}
     elif dom == "project":
         flops = args.steps * nimg * L * L * (N_THETA // 2) * PROJ_FLOPS_PER_CELL_ANGLE
         achieved = flops / (stages[dom][0] / 1e3) / 1e12
