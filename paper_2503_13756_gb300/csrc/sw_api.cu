@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -50,6 +52,8 @@ struct SliceTables {
     float2 *fac = nullptr;
     uint16_t *gtab = nullptr;  // target groups per angle batch (launch_project_slice)
     int *goff = nullptr;
+    uint32_t *ttab = nullptr;  // target groups per grid tile (L > 128)
+    int *toff = nullptr;
 };
 
 void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
@@ -569,51 +573,22 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
             fac[(size_t)k * nj + j] =
                 make_float2((float)(amp * std::cos(ph)), (float)(amp * std::sin(ph)));
         }
-    // Half-warp groups of the targets of every batch of kSliceBatch angles:
-    // within each half of the grid (taps at increasing or decreasing
-    // addresses), the targets are bucketed by first tap address mod 16 and
-    // group g takes the g-th target of every bucket, so the 16 lanes of a
-    // group read distinct banks at every tap.  Pooling the batch's angles
-    // keeps the buckets even.  Addresses follow the kernel's FP32 arithmetic.
-    // Half-warp groups of the targets of every batch of angles.  Grid in
-    // shared memory (L <= 128): within each half of the grid (taps at
-    // increasing or decreasing addresses) the targets are bucketed by first
-    // tap address mod 16 and group g takes the g-th of every bucket, so the 16
-    // lanes of a group read distinct banks at every tap; targets with the
-    // same first address (near the origin the angles of a batch meet) read
-    // the same words, which the hardware broadcasts, so such a class may fill
-    // several lanes.  Pooling the batch's angles keeps the buckets even.
-    // Addresses follow the kernel's FP32 arithmetic.  Grid in global memory:
-    // 16 consecutive targets of one ray per group (neighbouring taps share
-    // cache lines).
-    std::vector<uint16_t> gtab;
-    std::vector<int> goff(1, 0);
-    const int batch = swk::slice_batch_of(L);
-    for (int k0 = 0; k0 < nh; k0 += batch) {
-        const int k1 = std::min(nh, k0 + batch);
-        if (L > 128) {
-            for (int k = k0; k < k1; ++k)
-                for (int j0 = 0; j0 < nj; j0 += 16)
-                    for (int i = 0; i < 16; ++i)
-                        gtab.push_back(j0 + i < nj ? (uint16_t)((k - k0) * 256 + j0 + i)
-                                                   : (uint16_t)0xFFFF);
-            goff.push_back((int)(gtab.size() / 16));
-            continue;
-        }
-        // [half][residue] -> address classes, each a list of targets
-        std::map<int, std::vector<int>> cls[2][16];
-        for (int k = k0; k < k1; ++k)
-            for (int j = 0; j < nj; ++j) {
-                bool left;
-                const int base = swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N, &left);
-                cls[left ? 0 : 1][base & 15][base].push_back((k - k0) * 256 + j);
-            }
+    // Half-warp groups of targets.  The targets are bucketed by the bank of
+    // their first tap (address mod 16, within each half of the grid: taps at
+    // increasing or decreasing addresses) and group g takes the g-th of every
+    // bucket, so the 16 lanes of a group read distinct banks at every tap;
+    // targets with the same first address (near the origin the angles meet)
+    // read the same words, which the hardware broadcasts, so such a class may
+    // fill several lanes.  Addresses follow the kernel's FP32 arithmetic.
+    // classes: [half][residue] -> address -> entries; appends groups of 16.
+    auto group = [](auto &cls, auto &tab, auto idle) {
+        using E = typename std::remove_reference<decltype(tab)>::type::value_type;
         for (auto &half : cls) {
-            std::vector<std::vector<int>> q[16];  // per residue, largest class first
+            std::vector<std::vector<E>> q[16];  // per residue, largest class first
             for (int r = 0; r < 16; ++r) {
                 for (auto &kv : half[r]) q[r].push_back(kv.second);
                 std::stable_sort(q[r].begin(), q[r].end(),
-                                 [](const std::vector<int> &a, const std::vector<int> &b) {
+                                 [](const std::vector<E> &a, const std::vector<E> &b) {
                                      return a.size() > b.size();
                                  });
                 for (auto &v : q[r]) std::reverse(v.begin(), v.end());  // pop from the back
@@ -623,43 +598,96 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
                 int busy = 0;
                 for (int r = 0; r < 16; ++r) busy += head[r] < q[r].size();
                 if (!busy) break;
-                uint16_t lanes[16];
+                E lanes[16];
                 int used = 0;
                 for (int r = 0; r < 16; ++r) {
                     if (head[r] >= q[r].size()) continue;
                     --busy;  // residues after r that still wait keep one lane each
-                    std::vector<int> &v = q[r][head[r]];
+                    std::vector<E> &v = q[r][head[r]];
                     int take = std::min<int>((int)v.size(), 16 - used - busy);
                     take = std::max(take, 1);
                     for (int i = 0; i < take; ++i) {
-                        lanes[used++] = (uint16_t)v.back();
+                        lanes[used++] = v.back();
                         v.pop_back();
                     }
                     if (v.empty()) ++head[r];
                 }
-                for (int i = 0; i < 16; ++i) gtab.push_back(i < used ? lanes[i] : 0xFFFF);
+                for (int i = 0; i < 16; ++i) tab.push_back(i < used ? lanes[i] : idle);
             }
         }
-        goff.push_back((int)(gtab.size() / 16));
+    };
+    // L <= 128 (grid in shared memory): per batch of kSliceBatch angles, the
+    // batch's angles pooled so that the buckets stay even; entries kk 256 + j.
+    std::vector<uint16_t> gtab;
+    std::vector<int> goff(1, 0);
+    // L > 128 (grid in global memory, tiles in shared memory): per tile, the
+    // targets whose footprint starts in it; entries k << 16 | j; the bank is
+    // that of the first tap in the tile's copy (rows kSliceTileRS apart).
+    std::vector<uint32_t> ttab;
+    std::vector<int> toff(1, 0);
+    if (L <= 128) {
+        const int batch = swk::slice_batch_of(L);
+        for (int k0 = 0; k0 < nh; k0 += batch) {
+            const int k1 = std::min(nh, k0 + batch);
+            std::map<int, std::vector<uint16_t>> cls[2][16];
+            for (int k = k0; k < k1; ++k)
+                for (int j = 0; j < nj; ++j) {
+                    bool left;
+                    const int base =
+                        swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N, &left);
+                    cls[left ? 0 : 1][base & 15][base].push_back((uint16_t)((k - k0) * 256 + j));
+                }
+            group(cls, gtab, (uint16_t)0xFFFF);
+            goff.push_back((int)(gtab.size() / 16));
+        }
+    } else {
+        const int TY = swk::slice_tiles_y(t.N), TX = swk::slice_tiles_x(t.N);
+        std::vector<std::array<std::array<std::map<int, std::vector<uint32_t>>, 16>, 2>> cls(
+            (size_t)TY * TX);
+        for (int k = 0; k < nh; ++k)
+            for (int j = 0; j < nj; ++j) {
+                int row, col;
+                bool left;
+                swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, &row, &col, &left);
+                const int cmin = left ? col : col - (W - 1);
+                const int ty = row / swk::kSliceTile, tx = cmin / swk::kSliceTile;
+                const int local = (row - ty * swk::kSliceTile) * swk::kSliceTileRS +
+                                  (col - tx * swk::kSliceTile);
+                cls[(size_t)ty * TX + tx][left ? 0 : 1][local & 15][local].push_back(
+                    ((uint32_t)k << 16) | (uint32_t)j);
+            }
+        for (auto &tc : cls) {
+            group(tc, ttab, 0xFFFFFFFFu);
+            toff.push_back((int)(ttab.size() / 16));
+        }
     }
     SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
     SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));
     cudaError_t e = cudaMalloc(&t.fac, sizeof(float2) * fac.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(t.fac, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&t.gtab, sizeof(uint16_t) * gtab.size());
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !gtab.empty()) e = cudaMalloc(&t.gtab, sizeof(uint16_t) * gtab.size());
+    if (e == cudaSuccess && !gtab.empty())
         e = cudaMemcpy(t.gtab, gtab.data(), sizeof(uint16_t) * gtab.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&t.goff, sizeof(int) * goff.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(t.goff, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ttab.empty()) e = cudaMalloc(&t.ttab, sizeof(uint32_t) * ttab.size());
+    if (e == cudaSuccess && !ttab.empty())
+        e = cudaMemcpy(t.ttab, ttab.data(), sizeof(uint32_t) * ttab.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && L > 128) e = cudaMalloc(&t.toff, sizeof(int) * toff.size());
+    if (e == cudaSuccess && L > 128)
+        e = cudaMemcpy(t.toff, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(t.psi_inv);
         cudaFree(t.fac);
         cudaFree(t.gtab);
         cudaFree(t.goff);
+        cudaFree(t.ttab);
+        cudaFree(t.toff);
         return fail(c, SW_ERR_CUDA, "slice tables: %s", cudaGetErrorString(e));
     }
     c->slice_tables.push_back(t);
@@ -740,18 +768,19 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
         const Tables *tb;
         sw_status s;
         if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, B, &tb)) ||
-            (s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, B, nb))))
+            (s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, B, nb, nh))))
             return s;
         const int clip = p->metric != SW_METRIC_RFSW2;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                     return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
                                                      sl->psi_inv, sl->fac, sl->gtab, sl->goff,
-                                                     sl->coef, tb->tw, c->slice_scratch, clip,
-                                                     out, full_n, status, st, img2, nb_first);
+                                                     sl->ttab, sl->toff, sl->coef, tb->tw,
+                                                     c->slice_scratch, clip, out, full_n,
+                                                     status, st, img2, nb_first);
                 }));
-        // above L = 128: a grid and an interpolation kernel per chunk of images
+        // above L = 128: grid, tile and row kernels per chunk of images
         if (p->L > 128 && nb > 0)
-            c->launches += 2 * ((nb + swk::kSliceChunk - 1) / swk::kSliceChunk) - 1;
+            c->launches += 3 * ((nb + swk::kSliceChunk - 1) / swk::kSliceChunk) - 1;
         return SW_OK;
     }
     SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
@@ -863,6 +892,8 @@ void sw_destroy(sw_ctx *c)
         cudaFree(t.fac);
         cudaFree(t.gtab);
         cudaFree(t.goff);
+        cudaFree(t.ttab);
+        cudaFree(t.toff);
     }
     if (c->slice_scratch) cudaFree(c->slice_scratch);
     delete c;
@@ -930,7 +961,8 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
     if (p->projector == SW_PROJ_SLICE) {  // tables of the projector, built outside any capture
         const SliceTables *sl;
         if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, bins_of(p), &t)) ||
-            (s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, bins_of(p), Nq + Nt))))
+            (s = ensure_slice_scratch(
+                 c, swk::slice_scratch_bytes(p->L, bins_of(p), Nq + Nt, p->n_theta / 2))))
             return s;
     }
     return ensure_ws(c, batch_layout(p, Nq, Nt, lp_kind_of(p->gemm_precision), true).total);

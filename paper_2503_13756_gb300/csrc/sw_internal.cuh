@@ -318,20 +318,42 @@ __host__ __device__ inline int slice_stride(int N)
     const int S = slice_left(N) + slice_right(N);
     return S + (17 - S % 16) % 16;
 }
-// First grid address of the taps of target (j, theta) with e = (cos, sin)
-// of theta in FP32 on the grid N = B, exactly as the kernel forms it; *left
-// tells the half (taps at increasing addresses when set, decreasing
-// otherwise).
-__host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, bool *left)
+// Stored row and column of the first tap of target (j, theta) with e =
+// (cos, sin) of theta in FP32 on the grid N = B, exactly as the kernel forms
+// them; *left tells the half (taps at increasing columns when set, at
+// decreasing ones otherwise).
+__host__ __device__ inline void slice_tap_rc(int j, float ex, float ey, int N, int *row, int *col,
+                                             bool *left)
 {
     const float jf = (float)j, hN = 0.5f * (float)N;
     const float y1 = fminf(fmaxf(-(jf * ex), -hN), hN);
     const float y2 = fminf(fmaxf(-(jf * ey), -hN), 0.f);
     const int i1 = (int)ceilf(y1 - 0.5f * (float)kSliceW);
-    const int i2 = (int)ceilf(y2 - 0.5f * (float)kSliceW) - slice_lo(N);
+    *row = (int)ceilf(y2 - 0.5f * (float)kSliceW) - slice_lo(N);
     *left = i1 <= 0;
-    return i2 * slice_stride(N) +
-           (*left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1);
+    *col = *left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1;
+}
+// First grid address of the taps of target (j, theta) (see slice_tap_rc).
+__host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, bool *left)
+{
+    int row, col;
+    slice_tap_rc(j, ex, ey, N, &row, &col, left);
+    return row * slice_stride(N) + col;
+}
+// Tiles of the stored half grid for 128 < L: a target belongs to the tile
+// holding the top-left cell of its W x W footprint; a tile's shared-memory
+// copy is kSliceTileSpan square (the tile and a halo of W - 1), rows
+// kSliceTileRS apart (odd: the bank of a cell is (row + col) mod 16).
+constexpr int kSliceTile = 56;
+constexpr int kSliceTileSpan = kSliceTile + kSliceW - 1;  // 64
+constexpr int kSliceTileRS = kSliceTileSpan + 1;          // 65
+__host__ __device__ inline int slice_tiles_y(int N)
+{
+    return (slice_rows(N) - kSliceW) / kSliceTile + 1;
+}
+__host__ __device__ inline int slice_tiles_x(int N)
+{
+    return (slice_left(N) + slice_right(N) - kSliceW) / kSliceTile + 1;
 }
 
 // Band-limited projection through the Fourier slice theorem (see
@@ -352,8 +374,13 @@ __host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, 
 // addresses mod 16 (or equal ones), so its loads cost one pass.
 // L <= 128: the grid in shared memory (one CTA per image, kSliceBatch-angle
 // batches, targets grouped by bank).  128 < L <= 256: the grids of chunks of
-// kSliceChunk images in the caller's scratch (slice_scratch_bytes), 32-angle
-// batches (slice_batch_of), targets ordered along the rays.
+// kSliceChunk images in the caller's scratch (slice_scratch_bytes), then one
+// CTA per (tile, image) with the tile in shared memory writing the slice
+// samples to the scratch, then one CTA per (32-angle batch, image) for the
+// rows.  ttab/toff: the targets of tile t (slice_tiles_y x slice_tiles_x,
+// row-major) in half-warp groups toff[t] .. toff[t+1] of 16 entries
+// k << 16 | j or 0xFFFFFFFF, grouped by the bank of the first tap in the
+// tile's copy as above (left and right halves apart).
 constexpr int kSliceChunk = 256;
 constexpr size_t kSliceSmemMax = 227 * 1024 - 64;  // opt-in dynamic shared memory of a CTA
 // 32 ceil(max(min_bins, 1.5 L) / 32), rounded up to 256, 320 or 384 above 192
@@ -361,13 +388,15 @@ int slice_default_bins(int L, int min_bins);
 bool slice_bins_supported(int L, int B);
 size_t slice_smem_bytes(int B);
 int slice_batch_of(int L);
-size_t slice_scratch_bytes(int L, int B, int nb);
+// the grids and the slice samples of one chunk (nh angles): 0 for L <= 128
+size_t slice_scratch_bytes(int L, int B, int nb, int nh);
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
-                                 const uint16_t *gtab, const int *goff, const SliceCoef &coef,
-                                 const float2 *tw, float2 *scratch, int clip, float *out,
-                                 int full_n, int32_t *status, cudaStream_t st,
-                                 const float *img2 = nullptr, int nb_first = -1);
+                                 const uint16_t *gtab, const int *goff, const uint32_t *ttab,
+                                 const int *toff, const SliceCoef &coef, const float2 *tw,
+                                 float2 *scratch, int clip, float *out, int full_n,
+                                 int32_t *status, cudaStream_t st, const float *img2 = nullptr,
+                                 int nb_first = -1);
 
 // Quantiles.  proj: half ? [nb][nh][B] (angle k >= nh read mirrored)
 //                        : [nb][2nh][B].

@@ -82,7 +82,6 @@ __device__ __forceinline__ int wrap_n(int x, int N)
 template <int M>
 __device__ __forceinline__ void warp_ifft(float2 (&v)[M], const float2 *__restrict__ tw, int lane)
 {
-    constexpr int N = 32 * M;
     float2 y[M];
 #pragma unroll
     for (int k1 = 0; k1 < M; ++k1) {
@@ -114,6 +113,9 @@ struct SliceArgs {
     const int *goff;
     const float2 *tw;       // [B] e^{-2 pi i q / B}
     float2 *grid;           // global grids [chunk][rows][S] (128 < L only)
+    float2 *xs;             // global slice samples [chunk][nh][B/2 + 1] (128 < L only)
+    const uint32_t *ttab;   // target groups per tile (128 < L only)
+    const int *toff;
     float *out;
     int32_t *status;
     SliceCoef coef;         // tap weight polynomials (kernel parameter bank)
@@ -238,22 +240,78 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
     }
 }
 
-// Phases C and D for the angles [k0, k0 + BATCH) of image gi from the grid G
-// (shared or global memory); Xs [BATCH][B/2 + 1] and tw in shared memory;
-// BATCH / 2 warps.  Ends with a block barrier.
+// Weights, first tap and value of slice sample (k, j): the W x W taps of the
+// exponential-of-semicircle kernel around y = -(j / B) e_k N on the grid,
+// times the cell factor fac[k][j].  tap(row, col) returns the grid cell at a
+// stored row and column; the footprint is rows row0..row0+W-1 and columns
+// col0, col0 + da, ... (da = +1 on the left half, -1 on the right).
+template <int M>
+__device__ __forceinline__ void slice_target(const SliceArgs &A, int k, int j, int &row0,
+                                             int &col0, bool &left, float (&wx)[kSliceW],
+                                             float (&wy)[kSliceW])
+{
+    constexpr int N = 32 * M;
+    const float hN = 0.5f * (float)N;
+    const float jf = (float)j;
+    const float2 e = __ldg(A.cs + k);
+    // target y = -t N on the grid (t = (j/B) e, N = B), kept inside the
+    // stored half plane whatever the rounding
+    const float y1 = fminf(fmaxf(-(jf * e.x), -hN), hN);
+    const float y2 = fminf(fmaxf(-(jf * e.y), -hN), 0.f);
+    const float f1 = ceilf(y1 - 0.5f * (float)kSliceW);
+    const float f2 = ceilf(y2 - 0.5f * (float)kSliceW);
+    // offsets from the cell, exact: y - f is in (W/2 - 1, W/2]
+    const float x1 = (y1 - f1) - (float)(kSliceW / 2);
+    const float x2 = (y2 - f2) - (float)(kSliceW / 2);
+#pragma unroll
+    for (int a = 0; a < kSliceW; ++a) {
+        float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
+#pragma unroll
+        for (int d = kSliceDeg - 1; d >= 0; --d) {
+            px = fmaf(px, x1, A.coef.c[a][d]);
+            py = fmaf(py, x2, A.coef.c[a][d]);
+        }
+        wx[a] = px;
+        wy[a] = py;
+    }
+    const int i1 = (int)f1;
+    row0 = (int)f2 - slice_lo(N);
+    // left half: taps at increasing addresses; right half reversed
+    left = i1 <= 0;
+    col0 = left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1;
+}
+
+// sum_b wy[b] sum_a wx[a] g[b S + a da], complex, times fac
+__device__ __forceinline__ float2 slice_sum(const float2 *g, int S, int da,
+                                            const float (&wx)[kSliceW],
+                                            const float (&wy)[kSliceW], float2 fc)
+{
+    float tr = 0.f, ti = 0.f;
+#pragma unroll
+    for (int b = 0; b < kSliceW; ++b) {
+        float rr = 0.f, ri = 0.f;
+#pragma unroll
+        for (int a = 0; a < kSliceW; ++a) {
+            const float2 gv = g[b * S + a * da];
+            rr = fmaf(wx[a], gv.x, rr);
+            ri = fmaf(wx[a], gv.y, ri);
+        }
+        tr = fmaf(wy[b], rr, tr);
+        ti = fmaf(wy[b], ri, ti);
+    }
+    return make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
+}
+
+// Phase C for the angles [k0, k0 + BATCH) of the grid G (shared memory):
+// the slice samples into Xs [BATCH][B/2 + 1]; ends with a block barrier.
 template <int M, int BATCH>
-__device__ __forceinline__ void slice_batch(const SliceArgs &A, const float2 *G, float2 *Xs,
-                                            const float2 *tw, int gi, int k0, int bi, int warp,
-                                            int lane)
+__device__ __forceinline__ void slice_samples(const SliceArgs &A, const float2 *G, float2 *Xs,
+                                              int k0, int bi)
 {
     constexpr int N = 32 * M;
     const int nh = A.nh;
-    const int S = slice_stride(N), lo = slice_lo(N);
-    const int nleft = slice_left(N), nright = slice_right(N);
+    const int S = slice_stride(N);
     const int nj = N / 2 + 1;
-    const float hN = 0.5f * (float)N, invB = 1.f / (float)N;
-    const int nrow = A.full_n ? 2 * nh : nh;
-    float *outi = A.out + (size_t)gi * nrow * N;
     // rows of angles beyond nh (last batch) read as zero
     for (int it = threadIdx.x + (nh - k0) * nj; it < BATCH * nj; it += blockDim.x)
         Xs[it] = make_float2(0.f, 0.f);
@@ -263,52 +321,28 @@ __device__ __forceinline__ void slice_batch(const SliceArgs &A, const float2 *G,
         if (ent == 0xFFFFu) continue;
         const int kk = (int)(ent >> 8), j = (int)(ent & 255u);
         const int k = k0 + kk;
-        const float jf = (float)j;
-        const float2 e = __ldg(A.cs + k);
-        // target y = -t N on the grid (t = (j/B) e, N = B), kept inside the
-        // stored half plane whatever the rounding
-        const float y1 = fminf(fmaxf(-(jf * e.x), -hN), hN);
-        const float y2 = fminf(fmaxf(-(jf * e.y), -hN), 0.f);
-        const float f1 = ceilf(y1 - 0.5f * (float)kSliceW);
-        const float f2 = ceilf(y2 - 0.5f * (float)kSliceW);
-        // offsets from the cell, exact: y - f is in (W/2 - 1, W/2]
-        const float x1 = (y1 - f1) - (float)(kSliceW / 2);
-        const float x2 = (y2 - f2) - (float)(kSliceW / 2);
         float wx[kSliceW], wy[kSliceW];
-#pragma unroll
-        for (int a = 0; a < kSliceW; ++a) {
-            float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
-#pragma unroll
-            for (int d = kSliceDeg - 1; d >= 0; --d) {
-                px = fmaf(px, x1, A.coef.c[a][d]);
-                py = fmaf(py, x2, A.coef.c[a][d]);
-            }
-            wx[a] = px;
-            wy[a] = py;
-        }
-        const int i1 = (int)f1, i2 = (int)f2 - lo;
-        // left half: taps at increasing addresses; right half reversed
-        const bool left = i1 <= 0;
-        const float2 *g = G + i2 * S + (left ? i1 - lo : nleft + nright - i1);
-        const int da = left ? 1 : -1;
-        float tr = 0.f, ti = 0.f;
-#pragma unroll
-        for (int b = 0; b < kSliceW; ++b) {
-            float rr = 0.f, ri = 0.f;
-#pragma unroll
-            for (int a = 0; a < kSliceW; ++a) {
-                const float2 gv = g[b * S + a * da];
-                rr = fmaf(wx[a], gv.x, rr);
-                ri = fmaf(wx[a], gv.y, ri);
-            }
-            tr = fmaf(wy[b], rr, tr);
-            ti = fmaf(wy[b], ri, ti);
-        }
-        // cell sinc factors and phase (host table, FP64)
-        const float2 fc = __ldg(A.fac + (size_t)k * nj + j);
-        Xs[kk * nj + j] = make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
+        int row0, col0;
+        bool left;
+        slice_target<M>(A, k, j, row0, col0, left, wx, wy);
+        Xs[kk * nj + j] = slice_sum(G + row0 * S + col0, S, left ? 1 : -1, wx, wy,
+                                    __ldg(A.fac + (size_t)k * nj + j));
     }
     __syncthreads();
+}
+
+// Phase D for the angles [k0, k0 + BATCH) of image gi from the slice samples
+// Xs; tw in shared memory; BATCH / 2 warps.  Ends with a block barrier.
+template <int M, int BATCH>
+__device__ __forceinline__ void slice_rows_out(const SliceArgs &A, float2 *Xs, const float2 *tw,
+                                               int gi, int k0, int warp, int lane)
+{
+    constexpr int N = 32 * M;
+    const int nh = A.nh;
+    const int nj = N / 2 + 1;
+    const float invB = 1.f / (float)N;
+    const int nrow = A.full_n ? 2 * nh : nh;
+    float *outi = A.out + (size_t)gi * nrow * N;
     // D: warp w inverse-transforms the angles ka = 2w, kb = 2w + 1 of the
     // batch as Y_j = X_a + i X_b, Y_{B-j} = conj X_a + i conj X_b
     // (Y_0, Y_{B/2}: real parts), then writes both rows
@@ -382,8 +416,10 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
     if (mass) atomicOr(&s_mass, 1);
     __syncthreads();
     if (threadIdx.x == 0) A.status[gi] = (s_bad || !s_mass) ? 1 : 0;
-    for (int k0 = 0; k0 < A.nh; k0 += kSliceBatch)
-        slice_batch<M, kSliceBatch>(A, G, Xs, tw, gi, k0, k0 / kSliceBatch, warp, lane);
+    for (int k0 = 0; k0 < A.nh; k0 += kSliceBatch) {
+        slice_samples<M, kSliceBatch>(A, G, Xs, k0, k0 / kSliceBatch);
+        slice_rows_out<M, kSliceBatch>(A, Xs, tw, gi, k0, warp, lane);
+    }
 }
 
 // 128 < L: the grid of image img_off + blockIdx.x into A.grid[blockIdx.x].
@@ -410,20 +446,67 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_slice_grid(SliceArgs A)
     if (threadIdx.x == 0) A.status[gi] = (s_bad || !s_mass) ? 1 : 0;
 }
 
-// 128 < L: slice samples and rows of angle batch blockIdx.x of image
-// img_off + blockIdx.y from the grid A.grid[blockIdx.y].
+// 128 < L: the slice samples whose footprints start in tile blockIdx.x of
+// the grid A.grid[blockIdx.y], with the tile and its halo in shared memory,
+// into A.xs[blockIdx.y].
 template <int M>
-__global__ void __launch_bounds__(kBigThreads, 1) k_slice_interp(SliceArgs A)
+__global__ void __launch_bounds__(kBigThreads) k_slice_tile(SliceArgs A)
 {
     constexpr int N = 32 * M;
-    extern __shared__ float2 sms[];
-    float2 *Xs = sms;                           // [kBigBatch][nj]
-    float2 *tw = Xs + kBigBatch * (N / 2 + 1);  // [N]
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
+    constexpr int TS = kSliceTileSpan, RS = kSliceTileRS;
+    __shared__ float2 T[TS * RS];
+    const int rows = slice_rows(N), S = slice_stride(N), nj = N / 2 + 1;
+    const int tile = blockIdx.x;
+    const int r0 = (tile / slice_tiles_x(N)) * kSliceTile, c0 = (tile % slice_tiles_x(N)) * kSliceTile;
+    const int g0 = __ldg(A.toff + tile), ng = __ldg(A.toff + tile + 1) - g0;
+    if (ng == 0) return;  // no footprint starts here (whole CTA)
+    const float2 *G = A.grid + (size_t)blockIdx.y * rows * S;
+    float2 *X = A.xs + (size_t)blockIdx.y * A.nh * nj;
+    for (int idx = threadIdx.x; idx < TS * TS; idx += blockDim.x) {
+        const int r = idx / TS, c = idx % TS;
+        const int gr = r0 + r, gc = c0 + c;
+        T[r * RS + c] = (gr < rows && gc < S) ? G[(size_t)gr * S + gc] : make_float2(0.f, 0.f);
+    }
     __syncthreads();
-    const float2 *G = A.grid + (size_t)blockIdx.y * slice_rows(N) * slice_stride(N);
-    slice_batch<M, kBigBatch>(A, G, Xs, tw, A.img_off + blockIdx.y, blockIdx.x * kBigBatch,
-                              blockIdx.x, threadIdx.x >> 5, threadIdx.x & 31);
+    for (int slot = threadIdx.x; slot < ng * 16; slot += blockDim.x) {
+        const uint32_t ent = __ldg(A.ttab + (size_t)(g0 + (slot >> 4)) * 16 + (slot & 15));
+        if (ent == 0xFFFFFFFFu) continue;
+        const int k = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
+        float wx[kSliceW], wy[kSliceW];
+        int row0, col0;
+        bool left;
+        slice_target<M>(A, k, j, row0, col0, left, wx, wy);
+        const int da = left ? 1 : -1;
+        const int lr = row0 - r0, lc = col0 - c0;
+        const int cmin = left ? lc : lc - (kSliceW - 1);
+        const float2 fc = __ldg(A.fac + (size_t)k * nj + j);
+        // the host assigned the footprint to this tile; should the rounding
+        // ever place it elsewhere, the taps are read from the global grid
+        const bool inside = lr >= 0 && lr + kSliceW <= TS && cmin >= 0 && cmin + kSliceW <= TS;
+        X[(size_t)k * nj + j] = inside ? slice_sum(T + lr * RS + lc, RS, da, wx, wy, fc)
+                                       : slice_sum(G + (size_t)row0 * S + col0, S, da, wx, wy, fc);
+    }
+}
+
+// 128 < L: rows of angle batch blockIdx.x of image img_off + blockIdx.y from
+// the slice samples A.xs[blockIdx.y].
+template <int M>
+__global__ void __launch_bounds__(kBigThreads, 1) k_slice_rows(SliceArgs A)
+{
+    constexpr int N = 32 * M;
+    constexpr int nj = N / 2 + 1;
+    extern __shared__ float2 sms[];
+    float2 *Xs = sms;                   // [kBigBatch][nj]
+    float2 *tw = Xs + kBigBatch * nj;   // [N]
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
+    const int k0 = blockIdx.x * kBigBatch;
+    const float2 *X = A.xs + ((size_t)blockIdx.y * A.nh + k0) * nj;
+    const int valid = min(kBigBatch, A.nh - k0) * nj;
+    for (int it = threadIdx.x; it < kBigBatch * nj; it += blockDim.x)
+        Xs[it] = it < valid ? X[it] : make_float2(0.f, 0.f);
+    __syncthreads();
+    slice_rows_out<M, kBigBatch>(A, Xs, tw, A.img_off + blockIdx.y, k0, threadIdx.x >> 5,
+                                 threadIdx.x & 31);
 }
 
 template <int M>
@@ -446,15 +529,17 @@ cudaError_t launch_big(SliceArgs a, int nb, int chunk, cudaStream_t st)
 {
     constexpr int N = 32 * M;
     const int nbatch = (a.nh + kBigBatch - 1) / kBigBatch;
+    const int ntiles = slice_tiles_y(N) * slice_tiles_x(N);
     const size_t smem = sizeof(float2) * ((size_t)kBigBatch * (N / 2 + 1) + N);
-    cudaError_t e = cudaFuncSetAttribute(k_slice_interp<M>,
+    cudaError_t e = cudaFuncSetAttribute(k_slice_rows<M>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int i0 = 0; i0 < nb; i0 += chunk) {
         const int cnt = std::min(chunk, nb - i0);
         a.img_off = i0;
         k_slice_grid<M><<<cnt, kBigThreads, 0, st>>>(a);
-        k_slice_interp<M><<<dim3(nbatch, cnt), kBigThreads, smem, st>>>(a);
+        k_slice_tile<M><<<dim3(ntiles, cnt), kBigThreads, 0, st>>>(a);
+        k_slice_rows<M><<<dim3(nbatch, cnt), kBigThreads, smem, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -486,18 +571,19 @@ size_t slice_smem_bytes(int B)
 
 int slice_batch_of(int L) { return L <= 128 ? kSliceBatch : kBigBatch; }
 
-size_t slice_scratch_bytes(int L, int B, int nb)
+size_t slice_scratch_bytes(int L, int B, int nb, int nh)
 {
     if (L <= 128) return 0;
-    return sizeof(float2) * (size_t)slice_rows(B) * slice_stride(B) *
+    return sizeof(float2) * ((size_t)slice_rows(B) * slice_stride(B) + (size_t)nh * (B / 2 + 1)) *
            (size_t)std::min(nb, kSliceChunk);
 }
 
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
-                                 const uint16_t *gtab, const int *goff, const SliceCoef &coef,
-                                 const float2 *tw, float2 *scratch, int clip, float *out,
-                                 int full_n, int32_t *status, cudaStream_t st, const float *img2,
+                                 const uint16_t *gtab, const int *goff, const uint32_t *ttab,
+                                 const int *toff, const SliceCoef &coef, const float2 *tw,
+                                 float2 *scratch, int clip, float *out, int full_n,
+                                 int32_t *status, cudaStream_t st, const float *img2,
                                  int nb_first)
 {
     if (nb <= 0) return cudaSuccess;
@@ -517,6 +603,10 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.goff = goff;
     a.tw = tw;
     a.grid = scratch;
+    a.xs = scratch ? scratch + (size_t)slice_rows(B) * slice_stride(B) * std::min(nb, kSliceChunk)
+                   : nullptr;
+    a.ttab = ttab;
+    a.toff = toff;
     a.clip = clip;
     a.full_n = full_n;
     a.cs = cs;
@@ -524,7 +614,7 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.out = out;
     a.status = status;
     if (L > 128) {
-        if (!scratch) return cudaErrorInvalidValue;
+        if (!scratch || !ttab || !toff) return cudaErrorInvalidValue;
         switch (B / 32) {
         case 8: return launch_big<8>(a, nb, kSliceChunk, st);
         case 10: return launch_big<10>(a, nb, kSliceChunk, st);

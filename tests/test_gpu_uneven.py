@@ -87,7 +87,7 @@ def test_graph_with_the_slice_projector_equals_eager_calls():
     g = uneven.UnevenGraph(uneven.buckets_from(batch, N_THETA, "bf16", projector="slice"),
                            mode=0)
     try:
-        assert g.launches_per_replay == 5 * 5 + 2  # L = 192 and 256: grid + interpolation
+        assert g.launches_per_replay == 5 * 5 + 2 * 2  # L = 192 and 256: grid, tile and row kernels
         for b in g.buckets:
             b.out.zero_()
         g.replay()
