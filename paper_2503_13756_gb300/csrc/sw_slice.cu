@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
 
 // 128 < L: the grid of image img_off + blockIdx.x into A.grid[blockIdx.x].
 template <int M>
-__global__ void __launch_bounds__(kBigThreads, 1) k_slice_grid(SliceArgs A)
+__global__ void __launch_bounds__(kBigThreads, 2) k_slice_grid(SliceArgs A)
 {
     constexpr int N = 32 * M;
     __shared__ float2 tw[N];
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(kBigThreads) k_slice_tile(SliceArgs A)
 // 128 < L: rows of angle batch blockIdx.x of image img_off + blockIdx.y from
 // the slice samples A.xs[blockIdx.y].
 template <int M>
-__global__ void __launch_bounds__(kBigThreads, 1) k_slice_rows(SliceArgs A)
+__global__ void __launch_bounds__(kBigThreads, 2) k_slice_rows(SliceArgs A)
 {
     constexpr int N = 32 * M;
     constexpr int nj = N / 2 + 1;
