@@ -60,9 +60,9 @@ def slice_flops_per_image(Lc, n, B):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the slice projector kernel, from one ncu capture of its 1088-image launch
-# (1024 queries and 64 templates: 125,255,168 bytes); None once that kernel
+# (1024 queries and 64 templates: 125,067,264 bytes); None once that kernel
 # changes.
-SLICE_DRAM_BYTES_PER_IMAGE = 125255168 / 1088
+SLICE_DRAM_BYTES_PER_IMAGE = 125067264 / 1088
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the four-angle projection kernel, from one ncu capture of its 2112-image
 # launch (2048 queries and 64 templates in one launch: 277,210,112 bytes);
@@ -94,6 +94,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
+    ap.add_argument("--project-L", type=int, default=0,
+                    help="profiling runs only: time the projection of 512 synthetic images of "
+                         "this size (n = 256) and print one line")
     return ap.parse_args()
 
 
@@ -456,11 +459,41 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def project_only(args):
+    """Profiling aid: the projector alone on 512 blob-mixture images of side
+    --project-L (n = 256, M = 128), 2 warm-up and 5 timed calls."""
+    import torch
+
+    from paper_2503_13756_gb300 import swalign, synth
+    Lp = args.project_L
+    al = swalign.Aligner(0)
+    rng = np.random.default_rng(synth.SEED_BASE + 7)
+    imgs = np.ascontiguousarray(synth.render(synth.draw_mixtures(rng, 512, Lp, ncomp=(2, 4)), Lp),
+                                dtype=np.float32)
+    pa = swalign.make_params(Lp, N_THETA, M_LEVELS, projector=args.projector)
+    x = torch.from_numpy(imgs).cuda()
+    for _ in range(2):
+        al.project(x, pa)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        al.project(x, pa)
+    e1.record()
+    e1.synchronize()
+    us = e0.elapsed_time(e1) / 5 / 512 * 1e3
+    print(json.dumps({"profile": "projection only", "L": Lp, "projector": args.projector,
+                      "images": 512, "us_per_image": us}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.project_L:
+        project_only(args)
         return
     import torch
 
