@@ -205,20 +205,32 @@ __device__ __forceinline__ const float *image_of(const SliceArgs &A, int gi)
 
 // Phases A and B for one image into the grid G (shared or global memory),
 // by nw warps; returns the image's bad/mass flags of this thread.
+__device__ __forceinline__ void cp_async4z(float *dst, const float *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+
+// Phases A and B for one image into the grid G (shared or global memory),
+// by nw warps; returns the image's bad/mass flags of this thread.  stage
+// (shared memory, two bands of L x 33 floats, or null): with 16 warps and no
+// upsampling the image passes through it in 32-column bands by cp.async,
+// band b + 1 in flight while the warps transform band b (one column pair
+// each); otherwise each lane loads its pixels directly.
 template <int M>
 __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__restrict__ src,
                                            float2 *G, const float2 *tw, int warp, int nw,
-                                           int lane, int &bad, int &mass)
+                                           int lane, int &bad, int &mass, float *stage = nullptr)
 {
     constexpr int N = 32 * M;
     const int L = A.L, half = L / 2;
     const int rows = slice_rows(N), S = slice_stride(N), lo = slice_lo(N);
     const int nleft = slice_left(N), nright = slice_right(N);
-    // 8-byte pixel pairs: L even (every row starts 8-byte aligned, c is even)
-    // and the image itself 8-byte aligned
-    const bool pair8 = (L & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 7) == 0;
-    // ---- A: one warp per column pair (c, c+1): FFT along r', kept rows
-    for (int c = 2 * warp; c < L; c += 2 * nw) {
+    // ---- A: one warp per column pair (c, c+1): FFT along r', kept rows.
+    // fetch(r) gives the pixels (r, c) and (r, c + 1).
+    auto column_pair = [&](int c, auto fetch) {
         float2 v[M];
         const float pc0 = __ldg(A.psi_inv + c), pc1 = c + 1 < L ? __ldg(A.psi_inv + c + 1) : 0.f;
 #pragma unroll
@@ -227,34 +239,20 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
             const int r = (n < N / 2 ? n : n - N) + half;
             v[n1] = make_float2(0.f, 0.f);
             if (r >= 0 && r < L) {
-                float x0, x1 = 0.f;
-                if (A.srcL == L && pair8) {
-                    // (c, c + 1) in one 8-byte load: each lane reads another
-                    // row, so every load instruction costs one L1 line request
-                    // per lane, and this halves them
-                    const float2 x = __ldg(reinterpret_cast<const float2 *>(src + (size_t)r * L + c));
-                    x0 = x.x;
-                    x1 = x.y;
-                } else if (A.srcL == L) {
-                    x0 = __ldg(src + (size_t)r * L + c);
-                    if (c + 1 < L) x1 = __ldg(src + (size_t)r * L + c + 1);
-                } else {  // 2 x 2 upsampling: columns c, c+1 share a source pixel (c even)
-                    x0 = 0.25f * __ldg(src + (size_t)(r >> 1) * A.srcL + (c >> 1));
-                    if (c + 1 < L) x1 = x0;
-                }
-                if (!isfinite(x0)) {
+                float2 x = fetch(r);
+                if (!isfinite(x.x)) {
                     bad = 1;
-                    x0 = 0.f;
+                    x.x = 0.f;
                 }
-                if (!isfinite(x1)) {
+                if (!isfinite(x.y)) {
                     bad = 1;
-                    x1 = 0.f;
+                    x.y = 0.f;
                 }
-                x0 = fmaxf(x0, 0.f);
-                x1 = fmaxf(x1, 0.f);
-                mass |= (x0 > 0.f) | (x1 > 0.f);
+                x.x = fmaxf(x.x, 0.f);
+                x.y = fmaxf(x.y, 0.f);
+                mass |= (x.x > 0.f) | (x.y > 0.f);
                 const float pr = __ldg(A.psi_inv + r);
-                v[n1] = make_float2(x0 * pc0 * pr, x1 * pc1 * pr);
+                v[n1] = make_float2(x.x * pc0 * pr, x.y * pc1 * pr);
             }
         }
         warp_ifft<M>(v, tw, lane);
@@ -276,6 +274,53 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
                     G[i * S + c + 1] = make_float2(0.5f * (Z.y - Zc.y), -0.5f * (Z.x - Zc.x));
             }
         }
+    };
+    constexpr int BW = 32, RSB = BW + 1;  // band width; staged row stride (odd: rows on distinct banks)
+    if (stage != nullptr && A.srcL == L && 2 * nw == BW) {
+        const int nbands = (L + BW - 1) / BW;
+        auto issue = [&](int b, float *buf) {
+            const int cb = b * BW, w = min(BW, L - cb);
+            for (int idx = threadIdx.x; idx < L * BW; idx += blockDim.x) {
+                const int r = idx / BW, cc = idx % BW;
+                const bool ok = cc < w;
+                cp_async4z(buf + r * RSB + cc, ok ? src + (size_t)r * L + cb + cc : src, ok ? 4 : 0);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        issue(0, stage);
+        for (int b = 0; b < nbands; ++b) {
+            if (b + 1 < nbands) issue(b + 1, stage + ((b + 1) & 1) * L * RSB);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            __syncthreads();
+            const float *buf = stage + (b & 1) * L * RSB;
+            const int c = b * BW + 2 * warp;
+            if (c < L)
+                column_pair(c, [&](int r) {
+                    const float *row = buf + r * RSB + (c - b * BW);
+                    return make_float2(row[0], c + 1 < L ? row[1] : 0.f);
+                });
+            __syncthreads();  // the band's buffer is refilled two bands on
+        }
+    } else {
+        // 8-byte pixel pairs: L even (every row starts 8-byte aligned, c is
+        // even) and the image itself 8-byte aligned
+        const bool pair8 = (L & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 7) == 0;
+        for (int c = 2 * warp; c < L; c += 2 * nw)
+            column_pair(c, [&](int r) {
+                if (A.srcL == L && pair8) {
+                    // (c, c + 1) in one 8-byte load: each lane reads another
+                    // row, so every load instruction costs one L1 line request
+                    // per lane, and this halves them
+                    return __ldg(reinterpret_cast<const float2 *>(src + (size_t)r * L + c));
+                } else if (A.srcL == L) {
+                    return make_float2(__ldg(src + (size_t)r * L + c),
+                                       c + 1 < L ? __ldg(src + (size_t)r * L + c + 1) : 0.f);
+                }
+                // 2 x 2 upsampling: columns c, c+1 share a source pixel (c even)
+                const float x0 = 0.25f * __ldg(src + (size_t)(r >> 1) * A.srcL + (c >> 1));
+                return make_float2(x0, c + 1 < L ? x0 : 0.f);
+            });
     }
     __syncthreads();
     // ---- B: one warp per kept row: FFT along c', left and right columns
@@ -497,9 +542,11 @@ __global__ void __launch_bounds__(kBigThreads, 2) k_slice_grid(SliceArgs A)
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
     __syncthreads();
+    extern __shared__ float stg[];  // [2][L][33] image bands (not upsampled)
     float2 *G = A.grid + (size_t)blockIdx.x * slice_rows(N) * slice_stride(N);
     int bad = 0, mass = 0;
-    slice_grid<M>(A, image_of(A, gi), G, tw, warp, kBigThreads / 32, lane, bad, mass);
+    slice_grid<M>(A, image_of(A, gi), G, tw, warp, kBigThreads / 32, lane, bad, mass,
+                  A.srcL == A.L ? stg : nullptr);
     if (bad) atomicOr(&s_bad, 1);
     if (mass) atomicOr(&s_mass, 1);
     __syncthreads();
@@ -594,10 +641,15 @@ cudaError_t launch_big(SliceArgs a, int nb, int chunk, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(k_slice_rows<M>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // two 32-column bands of the image (rows 33 floats apart) when not upsampled
+    const size_t smem_grid = a.srcL == a.L ? sizeof(float) * 2 * (size_t)a.L * 33 : 0;
+    e = cudaFuncSetAttribute(k_slice_grid<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_grid);
+    if (e != cudaSuccess) return e;
     for (int i0 = 0; i0 < nb; i0 += chunk) {
         const int cnt = std::min(chunk, nb - i0);
         a.img_off = i0;
-        k_slice_grid<M><<<cnt, kBigThreads, 0, st>>>(a);
+        k_slice_grid<M><<<cnt, kBigThreads, smem_grid, st>>>(a);
         k_slice_tile<M><<<dim3(ntiles, cnt), kBigThreads, 0, st>>>(a);
         k_slice_rows<M><<<dim3(nbatch, cnt), kBigThreads, smem, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
