@@ -102,9 +102,9 @@ typedef enum {
                        /* and 1.5 L (it is also the grid length of the NUFFT);   */
                        /* an explicit n_bins must be such a count too.           */
                        /* L <= 256 (else SW_ERR_UNSUPPORTED); above L = 128 the  */
-                       /* bins are 256, 320 or 384 and the grids use scratch     */
-                       /* memory owned by the context.  Not for the              */
-                       /* allocation-free call.                                  */
+                       /* bins are 256, 320 or 384 and the grids and slice       */
+                       /* samples use scratch memory owned by the context.  Not  */
+                       /* for the allocation-free call.                          */
 } sw_projector;
 
 typedef struct {

@@ -362,8 +362,8 @@ __host__ __device__ inline int slice_tiles_x(int N)
 // M = 8, 10 or 12 for 128 < L <= 256), also the oversampled grid length; psi_inv [L] = 1 / Psi(c - floor(L/2)) with Psi
 // the Fourier transform of the spreading kernel; tw [B] = e^{-2 pi i q / B}.
 // clip = 1 writes max(row, 0).  For L <= 128, one CTA of 1024 threads per
-// image with slice_smem_bytes(B) of dynamic shared memory; above, two
-// launches per chunk of images with the grids in scratch.
+// image with slice_smem_bytes(B) of dynamic shared memory; above, three
+// launches per chunk of images with the grids and slice samples in scratch.
 // fac: [nh][B/2 + 1] sinc(pi t_1) sinc(pi t_2) (-1)^j e^{i pi j (1 - 2 delta (cos + sin)) / B}
 // with t = (j / B)(cos theta_k, sin theta_k), delta = 1/2 for even L, else 0.
 // gtab/goff: the targets (kk, j) of angle batch b (angles b batch + kk)

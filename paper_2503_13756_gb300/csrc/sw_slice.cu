@@ -46,10 +46,13 @@
 //    grid in shared memory (175 KB at L = 128); 64-angle batches; the
 //    targets grouped so that each tap load of a half-warp hits 16 distinct
 //    banks (one pass).
-//  - 128 < L <= 256 (k_slice_grid, then k_slice_interp): the grid of a chunk
-//    of images is built in a global scratch buffer (one CTA of 16 warps per
-//    image, phases A and B), then one CTA per (image, 32-angle batch) reads
-//    its taps through L1/L2, ordered along the rays for locality.
+//  - 128 < L <= 256 (k_slice_grid, k_slice_tile, k_slice_rows): the grid of
+//    a chunk of images is built in a global scratch buffer (one CTA of 16
+//    warps per image, phases A and B, the image staged in 32-column bands);
+//    phase C runs one CTA per (56 x 56 tile of the stored grid, image) with
+//    the tile and its halo in shared memory, the targets whose footprint
+//    starts in the tile grouped by bank, into a global sample buffer; phase D
+//    runs one CTA per (image, 32-angle batch).
 // With W = 9 and N / L >= 1.5 the rows are within ~3e-7 (relative l2) of the
 // exact band-limited projection, at the level of FP32 rounding.
 #include <algorithm>
@@ -61,7 +64,7 @@ namespace {
 
 constexpr int kSliceThreads = 1024;  // shared-memory grid: 32 warps
 constexpr int kBigThreads = 512;     // global grid: 16 warps (more registers per lane)
-constexpr int kBigBatch = 32;        // angles per CTA of k_slice_interp
+constexpr int kBigBatch = 32;        // angles per CTA of k_slice_rows
 static_assert(2 * (kSliceThreads / 32) == kSliceBatch, "one warp per angle pair of a batch");
 static_assert(2 * (kBigThreads / 32) == kBigBatch, "one warp per angle pair of a batch");
 
