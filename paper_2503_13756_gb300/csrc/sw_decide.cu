@@ -414,7 +414,6 @@ __device__ __forceinline__ void lane_stages(float2 (&a)[MW], const float2 *__res
 template <int MW>
 __device__ __forceinline__ void reg_ifft(float2 (&v)[MW], const float2 *__restrict__ tw, int lane)
 {
-    constexpr int n = 32 * MW;
     constexpr int LG = MW == 1 ? 0 : MW == 2 ? 1 : MW == 4 ? 2 : MW == 8 ? 3 : 4;
     static_assert((1 << LG) == MW, "MW must be 1, 2, 4, 8 or 16");
     float2 a[MW];
