@@ -56,13 +56,23 @@ struct SpecOut {
     int split;  // FP16 hi/lo split: rows of 3 segments
 };
 
+// Compensated (Kahan) sum of nonnegative terms, kept as (sum, -compensation):
+// the value is a.hi + a.lo, within about 2 ulp of the exact sum.
+__device__ __forceinline__ void kahan_add(DF &a, float x)
+{
+    const float y = x + a.lo;
+    const float t = a.hi + y;
+    a.lo = y - (t - a.hi);
+    a.hi = t;
+}
+
 // Writes Qhat(kf, p) (kf >= 1) for image img and adds its |.|^2 (weight w)
 // to acc32 (FP32 values) and acc16 (the low-precision values the GEMM sees).
 template <typename T>
 __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, int p, float2 X,
                                      float w, DF &acc32, DF &acc16)
 {
-    acc32 = df_add(acc32, DF{w * fmaf(X.x, X.x, X.y * X.y), 0.f});
+    kahan_add(acc32, w * fmaf(X.x, X.x, X.y * X.y));
     if (!o.lp) {
         float *row = o.spec32 + (size_t)(kf - 1) * o.fstride + (size_t)img * 2 * M;
         row[p] = X.x;
@@ -80,7 +90,7 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
                 : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
                       (size_t)img * row_len;
     if (!o.split) {
-        acc16 = df_add(acc16, DF{w * fmaf(rf, rf, imf * imf), 0.f});
+        kahan_add(acc16, w * fmaf(rf, rf, imf * imf));
         r[p] = re;
         r[M + p] = im;
         if (tmpl) {
@@ -113,6 +123,91 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
         r2[seg + M + p] = rel;
         r2[2 * seg + p] = nim;
         r2[2 * seg + M + p] = re;
+    }
+}
+
+template <typename T>
+struct Pair2;
+template <>
+struct Pair2<__half> {
+    using V = __half2;
+    static __device__ __forceinline__ V make(__half a, __half b) { return __halves2half2(a, b); }
+};
+template <>
+struct Pair2<__nv_bfloat16> {
+    using V = __nv_bfloat162;
+    static __device__ __forceinline__ V make(__nv_bfloat16 a, __nv_bfloat16 b)
+    {
+        return __halves2bfloat162(a, b);
+    }
+};
+
+// emit for the two levels pa (even) and pa + 1 of one frequency at once, M
+// even: every row segment then takes the pair as one 4-byte store (FP32
+// rows: one 8-byte store), the same values as two emit calls.
+template <typename T>
+__device__ __forceinline__ void emit2(const SpecOut &o, int img, int M, int kf, int pa, float2 Xa,
+                                      float2 Xb, float w, DF &acc32, DF &acc16)
+{
+    kahan_add(acc32, w * fmaf(Xa.x, Xa.x, Xa.y * Xa.y));
+    kahan_add(acc32, w * fmaf(Xb.x, Xb.x, Xb.y * Xb.y));
+    if (!o.lp) {
+        float *row = o.spec32 + (size_t)(kf - 1) * o.fstride + (size_t)img * 2 * M;
+        *reinterpret_cast<float2 *>(row + pa) = make_float2(Xa.x, Xb.x);
+        *reinterpret_cast<float2 *>(row + M + pa) = make_float2(Xa.y, Xb.y);
+        return;
+    }
+    using P = Pair2<T>;
+    using V = typename P::V;
+    const T rea = to_lp<T>(Xa.x), ima = to_lp<T>(Xa.y), reb = to_lp<T>(Xb.x), imb = to_lp<T>(Xb.y);
+    const float rfa = from_lp<T>(rea), imfa = from_lp<T>(ima);
+    const float rfb = from_lp<T>(reb), imfb = from_lp<T>(imb);
+    const bool tmpl = img >= o.Nq;
+    const int seg = o.ldk;
+    const int row_len = o.split ? 3 * seg : seg;
+    T *r = tmpl ? reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
+                      (size_t)(2 * (img - o.Nq)) * row_len
+                : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
+                      (size_t)img * row_len;
+    auto put = [](T *dst, V v) { *reinterpret_cast<V *>(dst) = v; };
+    const V re2 = P::make(rea, reb), im2 = P::make(ima, imb);
+    const V nim2 = P::make(to_lp<T>(-imfa), to_lp<T>(-imfb));
+    if (!o.split) {
+        kahan_add(acc16, w * fmaf(rfa, rfa, imfa * imfa));
+        kahan_add(acc16, w * fmaf(rfb, rfb, imfb * imfb));
+        put(r + pa, re2);
+        put(r + M + pa, im2);
+        if (tmpl) {
+            put(r + row_len + pa, nim2);  // row 2j+1: [ -im | re | 0 ]
+            put(r + row_len + M + pa, re2);
+        }
+        return;
+    }
+    // FP16 split: lo = x - hi, exact in FP32, rounded to FP16
+    const V rel2 = P::make(to_lp<T>(Xa.x - rfa), to_lp<T>(Xb.x - rfb));
+    const V iml2 = P::make(to_lp<T>(Xa.y - imfa), to_lp<T>(Xb.y - imfb));
+    if (!tmpl) {  // A' = [hi | hi | lo]
+        put(r + pa, re2);
+        put(r + M + pa, im2);
+        put(r + seg + pa, re2);
+        put(r + seg + M + pa, im2);
+        put(r + 2 * seg + pa, rel2);
+        put(r + 2 * seg + M + pa, iml2);
+    } else {      // B' = [hi | lo | hi], rows [re|im] and [-im|re]
+        const V nrel2 = P::make(to_lp<T>(-(Xa.y - imfa)), to_lp<T>(-(Xb.y - imfb)));
+        put(r + pa, re2);
+        put(r + M + pa, im2);
+        put(r + seg + pa, rel2);
+        put(r + seg + M + pa, iml2);
+        put(r + 2 * seg + pa, re2);
+        put(r + 2 * seg + M + pa, im2);
+        T *r2 = r + row_len;
+        put(r2 + pa, nim2);
+        put(r2 + M + pa, re2);
+        put(r2 + seg + pa, nrel2);
+        put(r2 + seg + M + pa, rel2);
+        put(r2 + 2 * seg + pa, nim2);
+        put(r2 + 2 * seg + M + pa, re2);
     }
 }
 
@@ -185,8 +280,8 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     stage_levels<nsig>(qi, n, M, Mp, parts, 0, stage);
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     const int nh = n / 2;
-    // norms in double-float (TwoSum-compensated FP32): FP64 arithmetic is
-    // scarce on this part
+    // norms as compensated (Kahan) FP32 sums: FP64 arithmetic is scarce on
+    // this part
     DF acc32 = {0.f, 0.f}, acc16 = {0.f, 0.f};
     const float invn = 1.f / (float)n;
 
@@ -212,6 +307,13 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
             const float2 dz = make_float2(0.5f * (Z.x - Zc.x), 0.5f * (Z.y - Zc.y));
             const float2 Xb = make_float2(dz.y, -dz.x);
             const int pa = p0 + 2 * s, pb = pa + 1;
+            if (kf >= 2 && (M & 1) == 0 && pb < M) {
+                // both levels at once (pa even, M even: 4-byte aligned pairs)
+                float2 A = Xa, Bv = Xb;
+                if (kf == nh) A.y = Bv.y = 0.f;  // Nyquist term of a real signal
+                emit2<T>(o, img, M, kf, pa, A, Bv, kf == nh ? 1.f : 2.f, acc32, acc16);
+                continue;
+            }
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
                 const int p = h2 ? pb : pa;
