@@ -158,7 +158,8 @@ int sw_default_bins(int L);
 /* Caps the workspace (bytes; 0 = no cap).  A call whose workspace would
  * exceed the cap returns SW_ERR_OOM without launching anything. */
 sw_status sw_set_workspace_limit(sw_ctx *ctx, size_t bytes);
-/* Workspace bytes that sw_align_batch needs for Nq x Nt pairs. */
+/* Workspace bytes that sw_align_batch needs for Nq x Nt pairs; 0 when p is
+ * NULL or fails the limits of sw_params, or when Nq or Nt is negative. */
 size_t sw_batch_workspace_bytes(const sw_params *p, int Nq, int Nt);
 /* Allocates the workspace for batches up to Nq x Nt now, so that later
  * calls of that size allocate nothing (and can be stream-captured). */

@@ -42,7 +42,7 @@ def make_params(L, n_theta, n_levels, n_bins=0, translation=1, level_rule=0,
                 projector="splat") -> Params:
     """shift_grid = K > 0 restricts the translation to the grid (i, j) * step,
     |i|, |j| <= K, step = shift_step_q / 16 pixel.  projector "splat" (linear
-    splat) or "slice" (band-limited Fourier-slice projection, L <= 128)."""
+    splat) or "slice" (band-limited Fourier-slice projection, L <= 256)."""
     prec = PREC[precision] if isinstance(precision, str) else int(precision)
     met = METRIC[metric] if isinstance(metric, str) else int(metric)
     proj = PROJECTOR[projector] if isinstance(projector, str) else int(projector)

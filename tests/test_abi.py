@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 import oracle
 from paper_2503_13756_gb300 import swalign
 
@@ -65,3 +67,18 @@ def test_workspace_size_is_host_computable():
     assert 0 < small < big
     bad = swalign.make_params(128, 257, 128)  # odd n is rejected
     assert lib.sw_batch_workspace_bytes(ctypes.byref(bad), 16, 8) == 0
+
+
+def test_without_a_device_the_product_path_fails_loudly():
+    """No CPU fallback: on a machine with no visible CUDA device the Python
+    context raises and sw_create returns an error with no context."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is visible")
+    with pytest.raises(RuntimeError):
+        swalign.Aligner(0)
+    lib = swalign.load()
+    h = ctypes.c_void_p(1)
+    assert lib.sw_create(0, ctypes.byref(h)) != 0
+    assert not h.value
+    assert lib.sw_create(0, None) == 1  # SW_ERR_INVALID_ARG
