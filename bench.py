@@ -421,7 +421,9 @@ def configs_block(device, projector="slice"):
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 CPU oracle, bounded sample per step."""
+    """Reference arm: the FP64 CPU oracle on a bounded sample per step: 16
+    queries x 16 templates of the workload's images (their transforms and
+    256 pair searches; about 2 s on 16 cores), a different block each step."""
     if rank != 0:
         return
     from paper_2503_13756_gb300 import synth
@@ -429,7 +431,7 @@ def run_reference(args, world, rank):
     oracle.build()
     data = synth.many_to_many(n_queries=64, n_templates=64)
     slice_proj = args.projector == "slice"
-    sq = st = 4 if slice_proj else 6
+    sq = st = 16
     cores = os.cpu_count() or 1
     times = []
     for k in range(args.warmup + args.steps):
@@ -488,10 +490,12 @@ def project_only(args):
 
 def main():
     args = parse()
-    world, rank, local = dist_setup()
     if args.impl == "reference":
-        run_reference(args, world, rank)
+        # rank 0 alone times the oracle; no collective, so no process group
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")),
+                      int(os.environ.get("RANK", "0")))
         return
+    world, rank, local = dist_setup()
     if args.project_L:
         project_only(args)
         return
