@@ -129,6 +129,23 @@ def test_quantiles_of_uniform_histogram_closed_form():
     assert Q1[0, 0] == -B / 2 * h  # z = 0: the left end of the domain
 
 
+@pytest.mark.parametrize("M", [1, 2, 7, 64, 257])
+def test_quantiles_invert_the_piecewise_linear_cdf(M):
+    """With every bin's mass positive, the CDF of Sec. 2.3 (cumulative sums at
+    the bin edges, linear inside a bin) is strictly increasing, so Q(z) is its
+    plain inverse: np.interp of z F_B over (F_j, e_j).  Both level rules; M = 1
+    under the midpoint rule is the median."""
+    rng = np.random.default_rng(M)
+    B, h = 37, 0.13
+    U = rng.uniform(0.05, 2.0, size=(5, B))
+    e = (np.arange(B + 1) - B / 2) * h
+    for rule, z in ((0, (np.arange(M) + 0.5) / M), (1, np.arange(M) / M)):
+        Q = oracle.quantiles(U, h, M, level_rule=rule)
+        for r in range(U.shape[0]):
+            F = np.concatenate([[0.0], np.cumsum(U[r])])
+            np.testing.assert_allclose(Q[r], np.interp(z * F[-1], F, e), rtol=0, atol=1e-12)
+
+
 def test_sampled_w2_of_two_uniforms_closed_form():
     # Q_a(z) = e_5 + 4hz, Q_b(z) = e_20 + 8hz: the difference is D - 4hz, whose
     # midpoint mean square is D^2 - 4hD + 16h^2 (4M^2-1)/(12M^2) and whose
