@@ -36,7 +36,7 @@ NQ, NT, L, N_THETA, M_LEVELS = 4096, 256, 128, 256, 128
 SM_COUNT, FP32_LANES, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
 B_BINS = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2   # default bin count at L = 128
 WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
-# algorithmic work per unit (stated in the design doc)
+# algorithmic work per unit of the projection (the roofline counts only these flops)
 PROJ_FLOPS_PER_CELL_ANGLE = 8           # s = <x, e> (FMA), frac, 1-t, two FMA accumulations
 SLICE_W = 9                              # spreading kernel taps per axis
 

@@ -1607,7 +1607,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
 // the FFT batch widths of the spectra and of the decision, and the FFT radix
 // order are chosen by timing candidates on a batch of random images with the
 // stage events of the profiler.  The stages are separate kernels, so each
-// stage's choice is taken from its own time; the radix order is judged by the
+// stage's choice is taken from its own time; the radix order is chosen on the time of the
 // spectra and decision together (both run the FFT).
 namespace {
 
