@@ -82,3 +82,15 @@ def test_without_a_device_the_product_path_fails_loudly():
     assert lib.sw_create(0, ctypes.byref(h)) != 0
     assert not h.value
     assert lib.sw_create(0, None) == 1  # SW_ERR_INVALID_ARG
+
+
+def test_build_targets_sm_103a_only_and_compiles_every_source():
+    from paper_2503_13756_gb300 import build as b
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "-lineinfo" in b.NVCC_FLAGS and "-O3" in b.NVCC_FLAGS
+    flags = " ".join(b.NVCC_FLAGS)
+    assert "march" not in flags and "sm_90" not in flags and "sm_100" not in flags
+    names = sorted(os.path.basename(s) for s in b.sources())
+    on_disk = sorted(f for f in os.listdir(b.CSRC) if f.endswith(".cu"))
+    assert names == on_disk and "sw_api.cu" in names
+    assert os.path.exists(b.build())
