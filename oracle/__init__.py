@@ -91,6 +91,9 @@ def _load():
             lib.orc_align_all_pairs.argtypes = [dp, ci, dp, ci, ci, ci, ci, ci, ci,
                                                 ci, ci, ci, ctypes.c_void_p]
             lib.orc_align_all_pairs.restype = ci
+            lib.orc_transform_images.argtypes = [dp, ci, ci, ci, ci, ci, ci, ci, ci, dp, dp,
+                                                 ctypes.POINTER(ctypes.c_int)]
+            lib.orc_transform_images.restype = ci
             lib.orc_ramp_filter.argtypes = [dp, ci, ci, dp]
             lib.orc_ramp_filter.restype = None
             lib.orc_rfsw_parts.argtypes = [dp, ci, ci, dp, dp]
@@ -241,6 +244,36 @@ def align_all_pairs(queries, templates, n: int, M: int, B: int | None = None,
     if not ok:
         raise MemoryError("oracle allocation failed")
     return out
+
+
+def transform_images(imgs, n: int, M: int, B: int | None = None, level_rule: int = 0,
+                     projector: int = 0, nthreads: int | None = None):
+    """The per-image steps of ``align_pair`` (prepare, project, quantiles,
+    centring vector) for every image, in parallel.  Returns (Q [N][n][M]
+    uncentred quantiles, A [N][2] centring vectors, ok [N] bool)."""
+    x = _f64(imgs)
+    N, L = x.shape[0], x.shape[-1]
+    B = bins_for(L, 0, projector) if B is None else int(B)
+    nthreads = os.cpu_count() or 1 if nthreads is None else int(nthreads)
+    Q = np.zeros((N, n, M), dtype=np.float64)
+    A = np.zeros((N, 2), dtype=np.float64)
+    ok = np.zeros(N, dtype=np.intc)
+    _load().orc_transform_images(_dp(x), N, L, int(n), int(M), B, int(level_rule),
+                                 int(projector), nthreads, _dp(Q), _dp(A),
+                                 ok.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return Q, A, ok.astype(bool)
+
+
+def shifts_of(af, ag, n: int) -> np.ndarray:
+    """s*(l) = a_f - R_{alpha_l} a_g for every l (the closed-form optimal
+    translation, derived from the shift lemma of App. B), [n][2]."""
+    ang = 2.0 * np.pi * np.arange(n) / n
+    c, s = np.cos(ang), np.sin(ang)
+    q = n // 4 if n % 4 == 0 else None
+    if q is not None:  # exact axis directions at quarter turns, as the oracle's table
+        for k, (cc, ss) in zip(range(0, n, q), ((1, 0), (0, 1), (-1, 0), (0, -1))):
+            c[k], s[k] = cc, ss
+    return np.stack([af[0] - (c * ag[0] - s * ag[1]), af[1] - (s * ag[0] + c * ag[1])], axis=1)
 
 
 # ---------------------------------------------------------------------------

@@ -540,6 +540,29 @@ static void orc_run(orc_job *job, void *(*fn)(void *), int nthreads)
     free(th);
 }
 
+/* The per-image transform of every image, in parallel: Q [nimg][n][M]
+ * receives the uncentred quantiles, A [nimg][2] the centring vectors and
+ * ok [nimg] 0 for an unusable image (the same steps as orc_align_pair:
+ * prepare, project, quantiles, centre).  Returns 0 on allocation failure. */
+int orc_transform_images(const double *imgs, int nimg, int L, int n, int M, int B,
+                         int level_rule, int projector, int nthreads, double *Q, double *A,
+                         int *ok)
+{
+    orc_cfg cfg = {L, n, M, B, level_rule, 0, projector};
+    orc_job job;
+    memset(&job, 0, sizeof(job));
+    job.cfg = &cfg;
+    job.imgs = imgs;
+    job.Q = Q;
+    job.A = A;
+    job.ok = ok;
+    job.nimg = nimg;
+    pthread_mutex_init(&job.mu, NULL);
+    orc_run(&job, orc_image_worker, nthreads);
+    pthread_mutex_destroy(&job.mu);
+    return 1;
+}
+
 /* All pairs (query i, template j): out[i*Nt + j] aligns template j onto
  * query i (query = reference f, template = g).  Queries are [Nq][L][L],
  * templates [Nt][L][L], both double.  Returns 0 on allocation failure. */

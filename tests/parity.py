@@ -27,14 +27,19 @@ REL_FP32 = 1e-5
 REL_LP = 1e-2
 
 
-def norm_scale(f, g, n, M, level_rule=0):
-    """S = (N_f + N_g) / (n M) from the oracle's centred quantiles."""
+def norm_scale(f, g, n, M, level_rule=0, projector=0):
+    """S = (N_f + N_g) / (n M) from the oracle's centred quantiles (projector
+    0: linear splat; 1: Fourier slice, rows clipped at zero)."""
     tot = 0.0
     for img in (f, g):
         F, mass = oracle.prepare(img)
         if mass <= 0:
             return np.nan
-        Q = oracle.quantiles(oracle.project(F, n), 2.0 / F.shape[0], M, level_rule)
+        if projector:
+            U = np.maximum(oracle.project_slice(F, n), 0.0)
+        else:
+            U = oracle.project(F, n)
+        Q = oracle.quantiles(U, 2.0 / F.shape[0], M, level_rule)
         _, Qc = oracle.center(Q)
         tot += float((Qc ** 2).sum())
     return tot / (n * M)

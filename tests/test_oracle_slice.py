@@ -143,3 +143,25 @@ def test_clipping_is_applied_for_sliced_w2_only():
     assert r0["status"] == 0 and r1["status"] == 0
     Qp = oracle.quantiles(np.maximum(U, 0.0), 2.0 / L, M)
     assert np.all(np.isfinite(Qp))
+
+
+@pytest.mark.parametrize("projector", [0, 1])
+def test_transform_images_are_the_steps_of_align_pair(projector):
+    # The batched per-image transform (used by the GPU tests to score many
+    # pairs cheaply) is the same prepare / project / quantile / centre chain
+    # as align_pair: its curve and shifts reproduce align_pair's exactly,
+    # and an unusable image is reported.
+    rng = np.random.default_rng(23 + projector)
+    L, n, M = 20, 12, 9
+    imgs = np.stack([random_image(rng, L) for _ in range(3)] + [np.zeros((L, L))])
+    Q, A, ok = oracle.transform_images(imgs, n, M, projector=projector, nthreads=2)
+    assert list(ok) == [True, True, True, False]
+    for i, j in ((0, 1), (2, 0)):
+        res, D, S = oracle.align_pair(imgs[i], imgs[j], n, M, projector=projector)
+        _, Qci = oracle.center(Q[i])
+        _, Qcj = oracle.center(Q[j])
+        np.testing.assert_array_equal(oracle.rotation_curve(Qci, Qcj), D)
+        np.testing.assert_allclose(oracle.shifts_of(A[i], A[j], n), S, rtol=0, atol=1e-15)
+        res0, D0, _ = oracle.align_pair(imgs[i], imgs[j], n, M, translation=0,
+                                        projector=projector)
+        np.testing.assert_array_equal(oracle.rotation_curve(Q[i], Q[j]), D0)
