@@ -254,15 +254,21 @@ sw_status sw_align_all_rotations(sw_ctx *ctx, const sw_params *p, const float *d
  * own pool, a latency-critical loop that cannot accept the device-wide
  * synchronisation of cudaMalloc/cudaFree, or a plugin whose host forbids
  * device allocations after start-up).  Same arguments and results as
- * sw_align_all_rotations, minus the context; the pair is scored in the FP32
- * path on the current device and the given stream.  It calls no cudaMalloc,
- * cudaFree or allocating library routine: every intermediate buffer and table
- * lives in one fixed 4 MiB device array inside the library, which every GPU
- * that loads the library holds until the process exits.
+ * sw_align_all_rotations, minus the context, for the sliced-W2 metric with
+ * the linear-splat projector only: metric RFSW2 or MSW2 and projector
+ * SW_PROJ_SLICE return SW_ERR_UNSUPPORTED.  The pair is scored in the FP32
+ * path (CUDA-core correlation) on the current device and the given stream.
+ * It calls no cudaMalloc, cudaFree or allocating library routine, and copies
+ * nothing from host memory: every intermediate buffer and the angle tables
+ * (computed by a kernel) live in one fixed 4 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.
  *   Limit: the per-pair intermediates, about 8 (n/2) B + 16 n M + 20 n
  *   bytes, must fit in 4 MiB (e.g. L <= 512 with n <= 512 and M <= 256);
- *   larger sizes return SW_ERR_OOM and launch nothing.  Invalid parameters or
- *   pointers return SW_ERR_INVALID_ARG.
+ *   larger sizes return SW_ERR_OOM and launch nothing.  Parameters that fail
+ *   the limits of sw_params return the status sw_align_all_rotations would
+ *   (SW_ERR_INVALID_ARG or SW_ERR_UNSUPPORTED); NULL or misaligned pointers
+ *   return SW_ERR_INVALID_ARG.  No message is kept (there is no context).
  *   The first call on a device looks up the array's device address (make it
  *   before any stream capture).  All calls on a device share the array and
  *   leave their intermediates in it; calls that overlap on the GPU (e.g. on

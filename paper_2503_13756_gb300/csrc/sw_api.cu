@@ -1461,20 +1461,49 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 struct NoAllocState {
     std::mutex mu;
     char *addr[kNoAllocMaxDevices] = {};
-    // host copies of the angle tables, per n
-    struct HostTables {
-        int n;
-        FftPlan plan;
-        std::vector<float2> cs, tw;
-        std::vector<double2> cs64;
-    };
-    std::deque<HostTables> tables;
+    // FFT plans (host values passed by kernel argument), per n
+    std::deque<std::pair<int, FftPlan>> plans;
 };
 
 NoAllocState &noalloc_state()
 {
     static NoAllocState s;
     return s;
+}
+
+// The angle tables of one call, computed on the device so that a call copies
+// nothing from host memory: cs[k] = (cos, sin) theta_k for k < n/2 (FP32),
+// cs64[k] for k < n (FP64), tw[k] = e^{-i theta_k} (FP32), theta_k = 2 pi k / n.
+// Each angle is reduced to the first octant by integer arithmetic and
+// rebuilt by the symmetries of the square, as the host tables of a context
+// are, so quarter turns give the exact axis vectors.  Thread 0 also clears
+// the decision's error word, the one scratch value that must start at zero.
+__global__ void k_noalloc_tables(int n, float2 *cs, double2 *cs64, float2 *tw, int *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) *err = 0;
+    if (k >= n) return;
+    const long long num = 8LL * k;  // angle = (num / n) pi / 4
+    const int oct = (int)(num / n);
+    const long long rem = num - (long long)oct * n;
+    const bool from_top = oct & 1;
+    double t = (double)rem / n * (M_PI / 4.0);
+    if (from_top) t = M_PI / 4.0 - t;
+    const double co = cos(t), si = sin(t);
+    double cc, ss;
+    switch (oct & 7) {
+    case 0: cc = co; ss = si; break;
+    case 1: cc = si; ss = co; break;
+    case 2: cc = -si; ss = co; break;
+    case 3: cc = -co; ss = si; break;
+    case 4: cc = -co; ss = -si; break;
+    case 5: cc = -si; ss = -co; break;
+    case 6: cc = si; ss = -co; break;
+    default: cc = co; ss = -si; break;
+    }
+    if (k < n / 2) cs[k] = make_float2((float)cc, (float)ss);
+    cs64[k] = make_double2(cc, ss);
+    tw[k] = make_float2((float)cc, (float)-ss);
 }
 
 }  // namespace
@@ -1484,7 +1513,8 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
                                                     double *d_shift, sw_result *d_best,
                                                     sw_stream_t stream)
 {
-    if (check_params(nullptr, p) != SW_OK) return SW_ERR_INVALID_ARG;
+    const sw_status sp = check_params(nullptr, p);
+    if (sp != SW_OK) return sp;
     if (p->metric != SW_METRIC_SW2 || p->projector != SW_PROJ_SPLAT)
         return SW_ERR_UNSUPPORTED;  // sliced W2 on the linear splat only
     if (!d_f || !d_g || !d_best || !aligned16(d_f) || !aligned16(d_g) || !aligned16(d_best) ||
@@ -1507,7 +1537,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
     if (dev < 0 || dev >= kNoAllocMaxDevices) return SW_ERR_UNSUPPORTED;
     NoAllocState &ns = noalloc_state();
     char *w = nullptr;
-    const NoAllocState::HostTables *ht = nullptr;
+    FftPlan plan{};
     {
         std::lock_guard<std::mutex> g(ns.mu);
         if (!ns.addr[dev]) {
@@ -1519,25 +1549,16 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
             ns.addr[dev] = static_cast<char *>(ptr);
         }
         w = ns.addr[dev];
-        for (const auto &t : ns.tables)
-            if (t.n == n) ht = &t;
-        if (!ht) {
-            NoAllocState::HostTables t;
-            t.n = n;
-            if (!fft_plan(n, t.plan)) return SW_ERR_INVALID_ARG;
-            std::vector<double> co, si;
-            angle_table(n, co, si);
-            t.cs.resize(nh);
-            t.tw.resize(n);
-            t.cs64.resize(n);
-            for (int k = 0; k < n; ++k) {
-                if (k < nh) t.cs[k] = make_float2((float)co[k], (float)si[k]);
-                t.cs64[k] = make_double2(co[k], si[k]);
-                t.tw[k] = make_float2((float)co[k], (float)-si[k]);
-            }
-            ns.tables.push_back(std::move(t));
-            ht = &ns.tables.back();
+        const FftPlan *found = nullptr;
+        for (const auto &e : ns.plans)
+            if (e.first == n) found = &e.second;
+        if (!found) {
+            FftPlan fp{};
+            if (!fft_plan(n, fp)) return SW_ERR_INVALID_ARG;
+            ns.plans.emplace_back(n, fp);
+            found = &ns.plans.back().second;
         }
+        plan = *found;
     }
     cudaStream_t st = (cudaStream_t)stream;
     float2 *cs = reinterpret_cast<float2 *>(w + o_cs);
@@ -1551,10 +1572,8 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
             return SW_ERR_CUDA;                    \
         }                                          \
     } while (0)
-    SW_NA(cudaMemcpyAsync(cs, ht->cs.data(), sizeof(float2) * nh, cudaMemcpyHostToDevice, st));
-    SW_NA(cudaMemcpyAsync(cs64, ht->cs64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, st));
-    SW_NA(cudaMemcpyAsync(tw, ht->tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, st));
-    SW_NA(cudaMemsetAsync(err, 0, sizeof(int), st));  // the only value that must start at zero
+    k_noalloc_tables<<<(n + 255) / 256, 256, 0, st>>>(n, cs, cs64, tw, err);
+    SW_NA(cudaGetLastError());
 
     int32_t *status = reinterpret_cast<int32_t *>(w + l.status);
     float *proj = reinterpret_cast<float *>(w + l.proj);
@@ -1571,7 +1590,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
                               status + 1, st));
     SW_NA(swk::launch_quantiles(proj, 2, n, B, M, 2.0f / (float)p->L, p->level_rule, 1, quant,
                                 status, st));
-    SW_NA(swk::launch_spectrum(quant, 2, n, M, ht->plan, tw, spec32, fstride, 0, nullptr, 0,
+    SW_NA(swk::launch_spectrum(quant, 2, n, M, plan, tw, spec32, fstride, 0, nullptr, 0,
                                nullptr, 0, 1, prof, center, norm32, norm16, st));
     SW_NA(swk::launch_corr_simt(spec32, fstride, spec32 + (size_t)2 * M, fstride, 1, 1, M, nh, C,
                                 st));
@@ -1597,7 +1616,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
     a.out = d_best;
     a.curve = d_D;
     a.shifts = d_shift;
-    SW_NA(swk::launch_decide(a, ht->plan, tw, st));
+    SW_NA(swk::launch_decide(a, plan, tw, st));
 #undef SW_NA
     return SW_OK;
 }
@@ -1612,7 +1631,7 @@ extern "C" sw_status sw_align_all_rotations_noalloc(const sw_params *p, const fl
 namespace {
 
 struct TrialTimes {
-    double proj = 1e30, spec = 1e30, dec = 1e30;
+    double proj = 1e30, spec = 1e30, dec = 1e30, corr = 1e30;
 };
 
 sw_status run_trial(sw_ctx *c, const sw_params *p, const Tune &tu, const float *dq, int Nq,

@@ -69,3 +69,24 @@ def test_noalloc_matches_allocating_entry_point_twice():
         assert st == swalign.SW_ERR_OOM
     finally:
         al.close()
+
+
+def test_noalloc_refuses_what_it_does_not_offer():
+    # the allocation-free call covers sliced W2 with the linear splat; other
+    # metrics and the Fourier-slice projector are refused before any launch,
+    # and parameters outside the limits give the status of the allocating call
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = swalign.load()
+    f = torch.zeros((32, 32), device="cuda")
+    out = torch.zeros((40,), dtype=torch.uint8, device="cuda")
+    cases = [(swalign.make_params(32, 16, 8, metric="msw2"), swalign.SW_ERR_UNSUPPORTED),
+             (swalign.make_params(32, 16, 8, metric="rfsw2"), swalign.SW_ERR_UNSUPPORTED),
+             (swalign.make_params(32, 16, 8, projector="slice"), swalign.SW_ERR_UNSUPPORTED),
+             (swalign.make_params(300, 16, 8, projector="slice"), swalign.SW_ERR_UNSUPPORTED),
+             (swalign.make_params(32, 15, 8), swalign.SW_ERR_INVALID_ARG)]
+    for p, want in cases:
+        st = lib.sw_align_all_rotations_noalloc(
+            ctypes.byref(p), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+            None, None, ctypes.c_void_p(out.data_ptr()), None)
+        assert st == want, (p.metric, p.projector, p.L, st)
