@@ -33,7 +33,7 @@ PROJECTOR_NAMES = {"slice": "Fourier slice: type-2 NUFFT of the cell image, band
                             "(Sec. 2.3)",
                    "splat": "pixel-driven linear splat"}
 NQ, NT, L, N_THETA, M_LEVELS = 4096, 256, 128, 256, 128
-SM_COUNT, FP32_LANES, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
+FP32_LANES, SM_MAX_MHZ_NOMINAL = 128, 2070.0   # FP32 lanes per SM; nominal max SM clock
 B_BINS = 2 * math.ceil((L - 1) / math.sqrt(2.0)) + 2   # default bin count at L = 128
 WORKLOAD = f"many-to-many {NQ}x{NT} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}"
 # algorithmic work per unit of the projection (the roofline counts only these flops)
@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--configs", action="store_true",
                     help="also time the single-pair, one-reference and random-dense "
                          "configurations (GPU and oracle) and print them as a second line")
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "rows"],
+                    help="N > 1: independent replicas of the workload (weak scaling) or one "
+                         "workload with its query rows split over the ranks (strong scaling)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
@@ -98,6 +101,21 @@ def parse():
                     help="profiling runs only: time the projection of 512 synthetic images of "
                          "this size (n = 256) and print one line")
     return ap.parse_args()
+
+
+def fp32_peak(device):
+    """FP32 FMA peak of the device: measured by the library's FFMA probe
+    (sw_measure_fp32_fma, at the clocks the GPU runs at), with the unit-count
+    figure (SMs x 128 lanes x 2 x max SM clock) beside it."""
+    import torch
+
+    from paper_2503_13756_gb300 import swalign
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peaks, _ = measured_peaks()
+    nominal = sms * FP32_LANES * 2 * peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL) * 1e6 / 1e12
+    tf, ms = swalign.measure_fp32_fma(device)
+    return {"tflops": tf, "unit_count_tflops": nominal, "sms": sms, "probe_ms": ms,
+            "source": "measured: FFMA probe (sw_measure_fp32_fma), best of 10 launches"}
 
 
 def measured_peaks():
@@ -166,6 +184,24 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of rank r's images in the replica (weak-scaling) mode: every
+    replica aligns its own workload, so no two ranks repeat each other's
+    pairs."""
+    from paper_2503_13756_gb300 import synth
+    return synth.SEED_BASE + 2 + 1000 * rank
+
+
+def row_block(nq: int, world: int, rank: int):
+    """Query rows [lo, hi) of rank r in the row-partition (strong-scaling)
+    mode: one fixed workload whose query rows are split as evenly as
+    possible, the templates replicated on every rank.  Pairs are independent,
+    so no rank needs another's data."""
+    base, extra = divmod(nq, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -202,24 +238,75 @@ def sum_over_ranks(x, world, device):
     return float(t.item())
 
 
-def cpu_baseline(data, projector="slice"):
-    """The FP64 oracle as it stands, on the host cores, on the first
-    sample_q x sample_t pairs of the workload (the oracle's slice projector
-    sums the slice samples directly, seconds per image, hence the smaller
-    sample)."""
+def sample_size(projector):
+    """Queries (and templates) of the oracle's sample: the first s x s pairs
+    of the workload (the oracle's slice projector sums the slice samples
+    directly, seconds per image, hence the smaller sample)."""
+    return 32 if projector == "slice" else 160
+
+
+def parity_of(gpu, ref, S, rel):
+    """Measured error of the GPU results against the oracle's on the same
+    pairs: plain relative error of d2 (no floor), absolute error in units of
+    S = (N_i + N_j) / (n M), the ratio to the test bar rel max(d2, 0.1 S),
+    rotation agreement and the largest shift error where the rotations agree."""
+    g, r = gpu.reshape(-1), ref.reshape(-1)
+    S = np.asarray(S, dtype=np.float64).reshape(-1)
+    err = np.abs(g["d2"] - r["d2"])
+    same = g["best_l"] == r["best_l"]
+    dl = np.abs((g["best_l"] - r["best_l"] + N_THETA // 2) % N_THETA - N_THETA // 2)
+    ds = np.abs(g["shift"] - r["shift"]).max(axis=1)
+    relerr = err / r["d2"]
+    return {"pairs": int(g.size), "argmin_same": float(same.mean()),
+            "argmin_within_1_bin": float((dl <= 1).mean()),
+            "max_rel_d2": float(relerr.max()), "median_rel_d2": float(np.median(relerr)),
+            "frac_rel_d2_above_1e-5": float((relerr > 1e-5).mean()),
+            "max_abs_d2_over_S": float((err / S).max()),
+            "worst_ratio_to_bar": float((err / (rel * np.maximum(r["d2"], 0.1 * S) + 1e-12)).max()),
+            "bar": f"{rel:g} max(d2, 0.1 S)",
+            "max_shift_err": float(ds[same].max()) if same.any() else None,
+            "min_d2_over_S": float((r["d2"] / S).min())}
+
+
+def cpu_baseline(data, projector="slice", gpu=None, norms=None):
+    """The FP64 oracle as it stands, on the host cores, on the first s x s
+    pairs of the workload (sample_size), timed.  With `gpu` ({name: (block
+    [s][s], source pairs [s])} of sw_result records from the timed runs) and
+    `norms` (the GPU's centred quantile norms of the sample's queries, their
+    templates and their source templates), the oracle's results on the same
+    pairs -- the timed block, and each sampled query with its own template
+    (well aligned: d2 / S ~ 1e-4) -- give the measured error per result."""
     import oracle
-    sample_q = sample_t = 32 if projector == "slice" else 160
-    q = data["queries"][:sample_q].astype(np.float64)
-    t = data["templates"][:sample_t].astype(np.float64)
+    s = sample_size(projector)
+    proj = int(projector == "slice")
+    q = data["queries"][:s].astype(np.float64)
+    t = data["templates"][:s].astype(np.float64)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.align_all_pairs(q, t, N_THETA, M_LEVELS, nthreads=cores,
-                           projector=int(projector == "slice"))
+    ref = oracle.align_all_pairs(q, t, N_THETA, M_LEVELS, nthreads=cores, projector=proj)
     dt = time.perf_counter() - t0
-    pairs = sample_q * sample_t
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample_q} queries x {sample_t} templates of the workload "
-                      f"({pairs} pairs, {dt:.1f} s)"}
+    pairs = s * s
+    out = {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {s} queries x {s} templates of the workload "
+                     f"({pairs} pairs, {dt:.1f} s)"}
+    parity = None
+    if gpu:
+        src = np.asarray(data["source"][:s])
+        ts = data["templates"][src].astype(np.float64)
+        ref_src = oracle.align_all_pairs(q, ts, N_THETA, M_LEVELS, nthreads=cores,
+                                         projector=proj)[np.arange(s), np.arange(s)]
+        nq_, nt_, ns_ = norms
+        S_blk = (nq_[:, None] + nt_[None, :]) / (N_THETA * M_LEVELS)
+        S_src = (nq_ + ns_) / (N_THETA * M_LEVELS)
+        parity = {"oracle": "FP64 oracle from the same FP32 images (independent code)",
+                  "block": f"first {s} queries x {s} templates ({pairs} pairs)",
+                  "source_pairs": f"the first {s} queries with their own templates "
+                                  "(well-aligned pairs)"}
+        for name, (blk, srcp) in gpu.items():
+            rel = 1e-2 if name in ("bf16", "fp16") else 1e-5
+            parity[name] = {"block": parity_of(blk, ref, S_blk, rel),
+                            "source_pairs": parity_of(srcp, ref_src, S_src, rel)}
+    return out, parity
 
 
 def serving_block(args, device):
@@ -245,8 +332,17 @@ def serving_block(args, device):
             reqs = serving.make_requests(pool, sched)
             st = eng.run(reqs, realtime=True)
             hits = float(np.mean(np.concatenate(
-                [r.results["reserved"].astype(int) == r.source for r in reqs])))
+                [r.results["template_index"].astype(int) == r.source for r in reqs])))
             st["source_template_found"] = hits
+            # saturation: the same requests offered all at once (load above
+            # capacity), so the slots never wait for arrivals; pairs/s is then
+            # the engine's capacity and latency is mostly queueing
+            eng.batches, eng.batch_sizes = 0, []
+            sat = eng.run(serving.make_requests(pool, sched), realtime=False)
+            st["saturation"] = {"pairs_per_s": sat["pairs_per_s"], "wall_s": sat["wall_s"],
+                                "latency_ms": sat["latency_ms"], "batches": sat["batches"],
+                                "mean_batch_images": sat["mean_batch_images"],
+                                "offered": "all requests at t = 0"}
             out[prec] = st
         finally:
             eng.close()
@@ -409,12 +505,13 @@ def configs_block(device, projector="slice"):
     al.profile(False)
     k_ms = st_m.get("decide", (0.0, 1))[0] / st_m.get("decide", (0.0, 1))[1]
     flops = 512 * 64 * 256 * 256 * 128 * 3  # subtract + fused multiply-add per term
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    fp = fp32_peak(device)
+    peak = fp["tflops"]
     out["max_sliced_512x64_n256_M128"] = {
         "pairs_per_s": 512 * 64 / (ms / 1e3), "ms_per_batch": ms,
         "k_msw": {"ms": k_ms, "achieved_tflops": flops / (k_ms / 1e3) / 1e12, "peak": peak,
                   "frac": flops / (k_ms / 1e3) / 1e12 / peak,
-                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}}
+                  "peak_source": fp["source"], "unit_count_peak": fp["unit_count_tflops"]}}
     al.close()
     torch.cuda.empty_cache()
     return out
@@ -505,8 +602,15 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    nq, nt = args.nq, args.nt
-    data = synth.many_to_many(n_queries=nq, n_templates=nt, seed=synth.SEED_BASE + 2 + 1000 * rank)
+    nq_all, nt = args.nq, args.nt
+    if args.partition == "rows":
+        # one workload on every rank; this rank aligns its block of query rows
+        data = synth.many_to_many(n_queries=nq_all, n_templates=nt, seed=rank_seed(0))
+        lo, hi = row_block(nq_all, world, rank)
+        data = dict(data, queries=data["queries"][lo:hi], source=data["source"][lo:hi])
+    else:
+        data = synth.many_to_many(n_queries=nq_all, n_templates=nt, seed=rank_seed(rank))
+    nq = len(data["queries"])
     pairs_per_rank = nq * nt
     al = swalign.Aligner(local)
     p = swalign.make_params(L, N_THETA, M_LEVELS, precision=args.precision, metric=args.metric,
@@ -518,6 +622,19 @@ def main():
     tune = None if args.no_autotune else list(al.autotune(p))
     al.reserve(p, nq, nt)
     stream = torch.cuda.current_stream()
+    fp32pk = fp32_peak(local)
+    # results of the oracle's sample (the first s x s pairs and the first s
+    # queries with their own templates), kept from every run of the sample's
+    # projector and distance for the measured error per result
+    s_par = min(sample_size(args.projector), nq, nt)
+    src_idx = torch.as_tensor(np.asarray(data["source"][:s_par]), device=dev)
+    gpu_sample = {}
+
+    def keep_sample(name):
+        o3 = out.view(nq, nt, 40)
+        gpu_sample[name] = (
+            swalign.results_to_numpy(o3[:s_par, :s_par].contiguous()).reshape(s_par, s_par),
+            swalign.results_to_numpy(o3[torch.arange(s_par, device=dev), src_idx].contiguous()))
 
     for _ in range(max(3, args.warmup)):
         al.align_batch(q_d, t_d, p, out=out)
@@ -545,6 +662,8 @@ def main():
     value = total_pairs / (ms_max / 1e3)
     res = swalign.results_to_numpy(out[:nt])
     assert np.all(res["status"] == 0)
+    if args.metric == "sw2":
+        keep_sample(args.precision)
 
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
     variants = {}
@@ -573,6 +692,8 @@ def main():
             al.profile(False)
             ms_v = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
             rv = swalign.results_to_numpy(out[:nt])
+            if metric == "sw2" and proj == args.projector:
+                keep_sample(prec)
             corr_ms = st_v.get("corr", (0.0, 1))[0] / args.steps
             # the ramp-filtered metric correlates both parts: K = 4M instead of 2M
             flops = (nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
@@ -580,8 +701,7 @@ def main():
             peaks_v, _ = measured_peaks()
             tf = flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else None
             simt = prec == "fp32_simt"
-            peak_v = (SM_COUNT * FP32_LANES * 2 * peaks_v.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL)
-                      * 1e6 / 1e12) if simt else peaks_v.get("bf16_tflops")
+            peak_v = fp32pk["tflops"] if simt else peaks_v.get("bf16_tflops")
             variants[name] = {
                 "metric": {"sw2": "sliced W2", "rfsw2": "ramp-filtered sliced W2"}[metric],
                 "projector": PROJECTOR_NAMES[proj],
@@ -589,7 +709,8 @@ def main():
                 "ms_per_step": ms_v, "status_ok": bool(np.all(rv["status"] == 0)),
                 "stages": {k: v[0] / args.steps for k, v in st_v.items()},
                 "corr": {"achieved": tf, "unit": "TFLOP/s", "peak": peak_v,
-                         "peak_kind": "FP32 FMA (unit counts)" if simt else "measured BF16 burst",
+                         "peak_kind": ("FP32 FMA, measured by the FFMA probe" if simt
+                                       else "measured BF16 burst"),
                          "frac": tf / peak_v if tf else None,
                          "algorithmic_flops_per_launch": flops},
             }
@@ -656,7 +777,9 @@ def main():
     per_stage = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                  for k, v in stages.items()}
     dom = max(stages, key=lambda k: stages[k][0])
-    alu_peak = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL) * 1e6 / 1e12
+    alu_peak = fp32pk["tflops"]
+    alu_src = (f"{fp32pk['source']}; unit counts: {fp32pk['sms']} SMs x 128 FP32 lanes x 2 x "
+               f"max SM clock = {fp32pk['unit_count_tflops']:.1f} TFLOP/s")
     if dom == "project" and args.projector == "slice":
         Bs = slice_bins(L)
         flops = args.steps * nimg * slice_flops_per_image(L, N_THETA, Bs)
@@ -670,12 +793,12 @@ def main():
                 "traffic_unit": "bytes per launch (average launch of the step)",
                 "algorithmic_flops_per_image": slice_flops_per_image(L, N_THETA, Bs),
                 "algorithmic_bytes_per_launch": per_launch * (L * L * 4 + (N_THETA // 2) * Bs * 4),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)",
+                "peak_source": alu_src,
                 "binding_unit": "shared-memory pipe (tap loads) and instruction issue"}
         # the binding unit: tap loads (8-byte complex, W x W per slice sample)
         # against the shared-memory bandwidth (128 B per clock per SM)
         tap_bytes = (N_THETA // 2) * (Bs // 2 + 1) * SLICE_W * SLICE_W * 8
-        smem_peak = SM_COUNT * 128 * peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL) * 1e6 / 1e12
+        smem_peak = fp32pk["sms"] * 128 * peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL) * 1e6 / 1e12
         smem_ach = args.steps * nimg * tap_bytes / (stages[dom][0] / 1e3) / 1e12
         roof["shared_memory"] = {
             "achieved": smem_ach, "peak": smem_peak, "unit": "TB/s", "frac": smem_ach / smem_peak,
@@ -692,28 +815,34 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (average launch of the step)",
                 "algorithmic_bytes_per_launch": per_launch * (L * L * 4 + (N_THETA // 2) * B_BINS * 4),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
+                "peak_source": alu_src}
     elif dom == "corr" and args.precision == "fp32_simt":
         flops = args.steps * nq * nt * (N_THETA // 2) * CORR_FLOPS_PER_PAIR_FREQ
         achieved = flops / (stages[dom][0] / 1e3) / 1e12
         roof = {"kernel": "k_corr_simt", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
+                "peak_source": alu_src}
     else:
         roof = {"kernel": dom, "bound": "unknown", "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
-    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(data, args.projector)
+    cpu, parity = None, None
+    if not (args.no_cpu_baseline or world > 1):
+        pn = swalign.make_params(L, N_THETA, M_LEVELS, projector=args.projector)
+        norm = [al.quantiles(al.project(x, pn), pn)[2].cpu().numpy() for x in
+                (q_d[:s_par], t_d[:s_par], t_d[src_idx])]
+        cpu, parity = cpu_baseline(data, args.projector, gpu_sample, norm)
     serve = None if (args.no_serving or world > 1) else serving_block(args, local)
     unev = None if (args.no_uneven or world > 1) else uneven_block(args, local)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True,
+        "scaling": "strong" if args.partition == "rows" else "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision.startswith("fp32") else args.precision,
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if (nq, nt) == (NQ, NT) else
-                   f"many-to-many {nq}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
-                   "Nq": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
+        "config": {"workload": WORKLOAD if (nq_all, nt) == (NQ, NT) else
+                   f"many-to-many {nq_all}x{nt} pairs, {L}x{L}, n={N_THETA}, M={M_LEVELS}",
+                   "Nq": nq_all, "Nq_per_rank": nq, "Nt": nt, "L": L, "n_theta": N_THETA,
                    "n_levels": M_LEVELS, "precision": args.precision, "translation": 1,
                    "projector": PROJECTOR_NAMES[args.projector],
                    "n_bins": swalign.bins_of(p),
@@ -724,10 +853,14 @@ def main():
                                    {"fp32": "tcgen05, 3-term FP16 split, FP32 accumulate",
                                     "bf16": "tcgen05 BF16", "fp16": "tcgen05 FP16",
                                     "fp32_simt": "CUDA-core FP32"}[args.precision]),
-                   "parallelism": f"{world} independent replicas (weak)",
+                   "parallelism": (f"query rows of one {nq_all}x{nt} workload split over {world} "
+                                   "ranks, templates replicated (strong)"
+                                   if args.partition == "rows" else
+                                   f"{world} independent replicas (weak)"),
                    "launch_shapes": tune,
                    "l2": "no flush: inputs (285 MB) and per-step workspace (>2 GB) exceed L2"},
-        "roofline": roof, "peaks": peak_src, "stages": per_stage, "cpu_baseline": cpu,
+        "roofline": roof, "peaks": peak_src, "fp32_peak": fp32pk, "stages": per_stage,
+        "cpu_baseline": cpu, "parity": parity,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
         "variants": variants, "serving": serve, "uneven": unev,
     }

@@ -139,7 +139,10 @@ typedef struct {
     int32_t status;   /* 0 ok, 1 reference/query unusable, 2 template unusable, */
                       /* 3 a bounded device wait gave up (results NaN)           */
     float angle_rad;  /* alpha* = 2 pi l* / n                                   */
-    float reserved;
+    int32_t template_index; /* j, the template (moving image) this result is  */
+                      /* for: the pair's j; in sw_align_batch / sw_bank_align   */
+                      /* mode 1 the best template (-1 when none is usable); 0   */
+                      /* for single-pair calls                                  */
     double shift[2];  /* s*: f ~ T_{s*} R_{alpha*} g; 0 when translation == 0   */
     double d2;        /* squared distance at (l*, s*), Eq. discrete_sw2         */
 } sw_result;          /* 40 bytes */
@@ -153,6 +156,28 @@ sw_status sw_create(int device, sw_ctx **out);
 void sw_destroy(sw_ctx *ctx);
 /* Message for the last failing call on ctx ("" if none).  Owned by ctx. */
 const char *sw_last_error(const sw_ctx *ctx);
+/* Limit, in SM clock cycles, of every wait of one pipeline role on another
+ * inside the tensor-core correlation kernel (not part of the method: it
+ * bounds the kernel's producer / consumer waits so that a stalled pipeline
+ * cannot hang the GPU).  0 = the default, about 4e9 cycles (~2 s).  A wait
+ * that runs out stops the kernel's remaining work after letting every copy
+ * and MMA already issued land; every result of that call then has status 3
+ * and NaN values, and later calls are unaffected.  Applies to later calls on
+ * ctx.  Negative values return SW_ERR_INVALID_ARG. */
+sw_status sw_set_wait_limit(sw_ctx *ctx, int64_t cycles);
+/* Test hook for that failure path (not part of the method): while enabled
+ * (enable != 0), every tensor-core correlation on ctx issues no operand
+ * copies, so its MMA role waits on a barrier that nothing completes, runs
+ * out at the wait limit and the call's results get status 3.  No fault and
+ * no hang: every wait stays bounded.  enable = 0 restores normal work. */
+sw_status sw_set_correlation_stall(sw_ctx *ctx, int enable);
+/* Measured FP32 FMA throughput of device `device` (not part of the method:
+ * the denominator of the benchmark's ALU-bound rooflines).  Runs a probe
+ * kernel of independent FFMA chains on every SM at the clocks the GPU runs at
+ * (it changes no setting), timed with CUDA events: *tflops receives the best
+ * of 10 timed launches (2 flops per FMA), *ms_per_launch (may be NULL) that
+ * launch's time.  Synchronous; allocates a small output buffer. */
+sw_status sw_measure_fp32_fma(int device, double *tflops, double *ms_per_launch);
 /* Default bin count for side L: 2 ceil((L-1)/sqrt 2) + 2. */
 int sw_default_bins(int L);
 /* Caps the workspace (bytes; 0 = no cap).  A call whose workspace would
@@ -203,27 +228,43 @@ int64_t sw_launch_count(const sw_ctx *ctx);
  *             most one radix-4 stage); bits 0-1 give the order (0: the
  *             power-of-two stages first, then 2, 3, 5; 1: 2, 3, 5 first;
  *             2: power-of-two first, then 5, 3, 2; 3: 5, 3, 2 first);
- *             a value of 0 in choice[0..2] means the built-in default.
+ *             a value of 0 in choice[0..2] means the built-in default;
+ *   choice[4] output tile width of the tensor-core correlation (columns of
+ *             the real-embedded product, two per template: 256 or 128) for
+ *             batches of at most 64 templates, where a 256-wide tile would
+ *             be half padding,
+ *   choice[5] the same for batches of more templates (0 = 256; both timed
+ *             on the trial images, for BF16 / FP16 / FP32 split only).
  * None of them changes what is computed; the FFT plan changes the
  * rounding only.  cache_path (may be NULL): a text file of lines
- * "swtune1 <device> L= n= M= B= prec= w s d r"; a matching line is used
+ * "swtune2 <device> L= n= M= B= prec= w s d r g1 g2"; a matching line is used
  * without timing, and a new result is appended.  Synchronous (waits for its
  * own work); allocates trial buffers for the duration of the call.  Banks
  * keep the choice in force when they were created.  Returns SW_ERR_OOM if the
  * trial buffers do not fit, SW_ERR_INVALID_ARG if the cache cannot be
  * written. */
 sw_status sw_autotune(sw_ctx *ctx, const sw_params *p, const char *cache_path);
-/* The choice in force for p on ctx (zeros before sw_autotune). */
+/* The choice in force for p on ctx (zeros before sw_autotune); choice holds
+ * 6 ints. */
 sw_status sw_autotune_get(const sw_ctx *ctx, const sw_params *p, int *choice);
 
 /* Radon projections (Eq. radon_transform, Sec. 2.1; Sec. 2.3 "Computation")
- * of nb images, discretised as a pixel-driven linear splat: the mass of each
- * cell goes to the two bins around s = <(x, y), theta_k>, split linearly.
- *   d_img  [nb][L][L] float32 (input)
- *   d_proj [nb][n][B] float32 (output); row k is the projection at theta_k,
- *          holding the clipped (not renormalised) mass of the image. */
+ * of nb images by the projector p->projector: the linear splat (the mass of
+ * each cell goes to the two bins around s = <(x, y), theta_k>, split
+ * linearly) or the Fourier slice (the band-limited projection of the cell
+ * image by a NUFFT, clipped at zero except for RFSW2; see sw_projector).
+ * Negative pixels are clipped to 0 first (Sec. 5.4's g+ rule).
+ *   d_img   [nb][L][L] float32 (input)
+ *   d_proj  [nb][n][B] float32 (output); row k is the projection at theta_k,
+ *           holding the clipped (not renormalised) mass of the image; rows
+ *           k >= n/2 are the mirrors of rows k - n/2
+ *   d_scale [nb] double (output, may be NULL; 8-byte aligned): 1 / m with
+ *           m = sum max(pixel, 0) summed in FP64, the factor that makes the
+ *           image a probability density (Sec. 1.1); NaN for an image with no
+ *           positive mass or a non-finite pixel.  d_scale[i] * d_proj[i] is
+ *           the projection of the normalised image. */
 sw_status sw_project(sw_ctx *ctx, const sw_params *p, const float *d_img, int nb,
-                     float *d_proj, sw_stream_t stream);
+                     float *d_proj, double *d_scale, sw_stream_t stream);
 
 /* Quantile functions of projections (Sec. 2.3: CDF by cumulative sum, ICDF
  * by linear interpolation; Eq. inv_cdf with the ">=" of App. A.1.1).
@@ -282,9 +323,9 @@ sw_status sw_align_all_rotations_noalloc(const sw_params *p, const float *d_f, c
  * runs as a batched GEMM in the precision p->gemm_precision.
  *   d_q_img [Nq][L][L] float32, d_t_img [Nt][L][L] float32
  *   mode 0: d_out [Nq][Nt] sw_result, every pair
- *   mode 1: d_out [Nq] sw_result, the best template per query (lowest index
- *           on ties); best_l etc. refer to that template, whose index is
- *           written to `reserved` as a float. */
+ *   mode 1: d_out [Nq] sw_result, the best template per query (least d^2,
+ *           lowest index on ties); best_l etc. refer to that template, whose
+ *           index is template_index. */
 sw_status sw_align_batch(sw_ctx *ctx, const sw_params *p, const float *d_q_img, int Nq,
                          const float *d_t_img, int Nt, int mode, sw_result *d_out,
                          sw_stream_t stream);

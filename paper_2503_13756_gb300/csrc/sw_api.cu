@@ -266,6 +266,15 @@ struct Tune {
     int spec = 0;  // signals per FFT batch of the spectra (4, 8, 16)
     int dec = 0;   // decision form: 1 register FFT, else signals per CTA (4, 8, 16)
     int plan = 0;  // FFT radix order (fft_plan variant)
+    // output tile width of the tensor-core correlation (columns of D, two per
+    // template; 128 or 256, 0 = 256) for batches of at most 64 templates
+    // (tile_s) and of more (tile_l)
+    int tile_s = 0, tile_l = 0;
+    int tile_for(int Nt) const
+    {
+        const int t = Nt <= 64 ? tile_s : tile_l;
+        return t == 128 ? 128 : 256;
+    }
 };
 
 struct TuneKey {
@@ -293,6 +302,8 @@ struct sw_ctx {
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<TuneKey, Tune>> tunes;
     const Tune *trial = nullptr;  // overrides the lookup (autotuning, banks)
+    long long wait_cycles = 0;    // tensor-core pipeline wait limit (0 = default)
+    int stall_corr = 0;           // test hook: tensor-core correlations issue no copies
 };
 
 struct sw_bank {
@@ -901,6 +912,23 @@ void sw_destroy(sw_ctx *c)
 
 const char *sw_last_error(const sw_ctx *c) { return c ? c->err.c_str() : ""; }
 
+sw_status sw_set_wait_limit(sw_ctx *c, int64_t cycles)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    if (cycles < 0) return fail(c, SW_ERR_INVALID_ARG, "cycles=%lld", (long long)cycles);
+    c->wait_cycles = (long long)cycles;
+    return SW_OK;
+}
+
+sw_status sw_set_correlation_stall(sw_ctx *c, int enable)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    c->stall_corr = enable ? 1 : 0;
+    return SW_OK;
+}
+
 sw_status sw_profile(sw_ctx *c, int enable)
 {
     if (!c) return SW_ERR_INVALID_ARG;
@@ -969,7 +997,7 @@ sw_status sw_reserve(sw_ctx *c, const sw_params *p, int Nq, int Nt)
 }
 
 sw_status sw_project(sw_ctx *c, const sw_params *p, const float *d_img, int nb, float *d_proj,
-                     sw_stream_t stream)
+                     double *d_scale, sw_stream_t stream)
 {
     if (!c) return SW_ERR_INVALID_ARG;
     c->err.clear();
@@ -979,12 +1007,17 @@ sw_status sw_project(sw_ctx *c, const sw_params *p, const float *d_img, int nb, 
     if (nb == 0) return SW_OK;
     if ((s = check_ptr(c, d_img, "d_img", true)) || (s = check_ptr(c, d_proj, "d_proj", true)))
         return s;
+    if ((uintptr_t)d_scale & 7u) return fail(c, SW_ERR_INVALID_ARG, "d_scale is not 8-byte aligned");
     if ((s = set_device(c))) return s;
     const Tables *t;
     if ((s = get_tables(c, p->n_theta, &t))) return s;
     const size_t need = align_up(4 * (size_t)nb);
     if ((s = ensure_ws(c, need))) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if (d_scale)
+        SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                    return swk::launch_image_scale(d_img, nb, p->L, d_scale, st);
+                }));
     return project_rows(c, p, t, d_img, p->L, nb, d_proj, 1, at<int32_t>(c->ws, 0), st);
 }
 
@@ -1116,7 +1149,8 @@ sw_status align_batch_impl(sw_ctx *c, const sw_params *p, const float *dq, int N
     if (lp) {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
                     return swk::launch_corr_tc(o.lp_q, o.lp_t, Nq, Nt, M, nh, kind, C, err,
-                                               c->num_sms, st);
+                                               c->num_sms, st, c->wait_cycles, c->stall_corr,
+                                               tu.tile_for(Nt));
                 }));
     } else {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
@@ -1380,7 +1414,8 @@ static sw_status bank_align_impl(sw_ctx *c, const sw_bank *bank, const float *d_
     if (lp) {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
                     return swk::launch_corr_tc(o.lp_q, bank->lp_t, Nq, Nt, M, nh, kind, C, err,
-                                               c->num_sms, st);
+                                               c->num_sms, st, c->wait_cycles, c->stall_corr,
+                                               bank->tune.tile_for(Nt));
                 }));
     } else {
         SW_CUDA(c, launch(c, SW_STAGE_CORR, st, [&] {
@@ -1443,7 +1478,9 @@ void sw_bank_destroy(sw_bank *bank)
 // device allocations after start-up.  For them this entry point runs the same
 // kernel sequence as sw_align_all_rotations with every intermediate buffer
 // and table carved from one file-scope device array of fixed size, and calls
-// no cudaMalloc, cudaFree or allocating library routine.
+// no cudaMalloc, cudaFree or allocating library routine.  The angle tables
+// are computed by a kernel into that array, so a call copies nothing from
+// host memory and does not wait on the host.
 //
 // The array is a __device__ variable: host code cannot use its name as a
 // device address, so its address is taken with cudaGetSymbolAddress, once per
@@ -1649,6 +1686,7 @@ sw_status run_trial(sw_ctx *c, const sw_params *p, const Tune &tu, const float *
         tt.proj = std::min(tt.proj, ms[SW_STAGE_PROJECT]);
         tt.spec = std::min(tt.spec, ms[SW_STAGE_SPECTRUM]);
         tt.dec = std::min(tt.dec, ms[SW_STAGE_DECIDE]);
+        tt.corr = std::min(tt.corr, ms[SW_STAGE_CORR]);
     }
     c->trial = nullptr;
     return s;
@@ -1679,7 +1717,7 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
     for (char &ch : dev)
         if (ch == ' ' || ch == '\t') ch = '_';
     char kb[256];
-    snprintf(kb, sizeof kb, "swtune1 %s L=%d n=%d M=%d B=%d prec=%d", dev.c_str(), p->L,
+    snprintf(kb, sizeof kb, "swtune2 %s L=%d n=%d M=%d B=%d prec=%d", dev.c_str(), p->L,
              p->n_theta, p->n_levels, bins_of(p), (int)p->gemm_precision);
     const std::string key = kb;
     const TuneKey tk = tune_key(p);
@@ -1701,8 +1739,9 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
                 continue;
             Tune tu;
             std::istringstream is(line.substr(key.size()));
-            if (is >> tu.want >> tu.spec >> tu.dec >> tu.plan && tu.want >= 0 && tu.spec >= 0 &&
-                tu.dec >= 0 && tu.plan >= 0 && tu.plan < kPlanVariants) {
+            if (is >> tu.want >> tu.spec >> tu.dec >> tu.plan >> tu.tile_s >> tu.tile_l &&
+                tu.want >= 0 && tu.spec >= 0 && tu.dec >= 0 && tu.plan >= 0 &&
+                tu.plan < kPlanVariants && tu.tile_s >= 0 && tu.tile_l >= 0) {
                 store(tu);
                 return SW_OK;
             }
@@ -1731,7 +1770,9 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
         if (st) cudaStreamDestroy(st);
     };
     if (cudaMalloc(&d_img, sizeof(float) * h.size()) != cudaSuccess ||
-        cudaMalloc(&d_out, sizeof(sw_result) * (size_t)Nq * Nt) != cudaSuccess ||
+        cudaMalloc(&d_out, sizeof(sw_result) * std::max<size_t>((size_t)Nq * Nt,
+                                                                 (nimg > 256 ? nimg - 256 : 0) * 256)) !=
+            cudaSuccess ||
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
@@ -1792,6 +1833,31 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
                 best.plan = v;
             }
         }
+        // the correlation's output tile on the tensor cores: 256 or 128
+        // columns, timed on the trial batch (64 templates) for the small
+        // class and on 256 templates (the rest of the trial images as
+        // queries) for the large class
+        if (kind != 0 && s == SW_OK) {
+            double tc[2][2] = {{1e30, 1e30}, {1e30, 1e30}};
+            const int tiles[2] = {256, 128};
+            const int Nt_l = 256, Nq_l = (int)nimg - Nt_l;
+            for (int cls = 0; cls < 2 && s == SW_OK; ++cls) {
+                if (cls == 1 && (Nq_l < 64 || (c->limit && batch_layout(p, Nq_l, Nt_l, kind, false)
+                                                               .total > c->limit)))
+                    break;  // too few trial images, or beyond the workspace limit: default
+                for (int v = 0; v < 2 && s == SW_OK; ++v) {
+                    Tune tu = best;
+                    tu.tile_s = tu.tile_l = tiles[v];
+                    TrialTimes tv;
+                    s = cls == 0 ? run_trial(c, p, tu, dq, Nq, dt, Nt, d_out, st, tv)
+                                 : run_trial(c, p, tu, d_img, Nq_l,
+                                             d_img + (size_t)Nq_l * L * L, Nt_l, d_out, st, tv);
+                    tc[cls][v] = tv.corr;
+                }
+            }
+            best.tile_s = tc[0][1] < tc[0][0] ? 128 : 256;
+            best.tile_l = tc[1][1] < tc[1][0] ? 128 : 256;
+        }
     }
     c->trial = nullptr;
     c->prof = was_prof;
@@ -1803,7 +1869,7 @@ sw_status sw_autotune(sw_ctx *c, const sw_params *p, const char *cache_path)
         std::ofstream f(cache_path, std::ios::app);
         if (!f) return fail(c, SW_ERR_INVALID_ARG, "cannot append to %s", cache_path);
         f << key << ' ' << best.want << ' ' << best.spec << ' ' << best.dec << ' ' << best.plan
-          << '\n';
+          << ' ' << best.tile_s << ' ' << best.tile_l << '\n';
     }
     return SW_OK;
 }
@@ -1820,6 +1886,8 @@ sw_status sw_autotune_get(const sw_ctx *c, const sw_params *p, int *choice)
     choice[1] = tu.spec;
     choice[2] = tu.dec;
     choice[3] = tu.plan;
+    choice[4] = tu.tile_s;
+    choice[5] = tu.tile_l;
     return SW_OK;
 }
 

@@ -13,17 +13,21 @@
 // Rows are K-major with K = ldk (2M rounded up to 64, zero padded).
 //
 // Design: persistent CTAs, one per SM, each walking output tiles of
-// 128 queries x 256 columns (128 templates) for one frequency.  Warp 0 issues
-// TMA loads (128-byte swizzle, 3-D maps over frequency) into a 4-stage ring
-// of 64-wide K slices; warp 1 owns the 512-column TMEM allocation and one
-// lane issues tcgen05.mma (M=128, N=256, K=16) into one of two TMEM
-// accumulators; warps 2-5 drain the other accumulator with tcgen05.ld, so
-// the epilogue of one tile overlaps the MMAs of the next.  With Nt even each
+// 128 queries x BN columns (BN / 2 templates) for one frequency; BN is 256 or
+// 128 (the autotuner's choice: 128 when fewer templates would leave half of a
+// 256-wide tile as padding).  Warp 0 issues TMA loads (128-byte swizzle, 3-D
+// maps over frequency) into a 4-stage ring of 64-wide K slices; warp 1 owns
+// the 2 BN-column TMEM allocation and one lane issues tcgen05.mma (M=128,
+// N=BN, K=16) into one of two TMEM accumulators; warps 2-5 drain the other
+// accumulator with tcgen05.ld, so the epilogue of one tile overlaps the MMAs
+// of the next.  With Nt even each
 // epilogue warp writes its 32 x 32 FP32 blocks into one of two 128-byte-
 // swizzled shared-memory buffers and one lane stores them with a TMA tensor
 // store (coalesced, clipped at the tensor's edges); odd Nt keeps per-lane
-// stores of each row.  Every mbarrier wait gives up after ~2 s of clock, sets
-// *err and lets the CTA run to its end, where TMEM is released.
+// stores of each row.  Every wait of one role on another gives up after a
+// limit (a kernel argument: ~2 s of clock by default), sets *err and stops
+// every role; the waits that let issued copies and MMAs land before the CTA
+// ends keep the long limit, so nothing is in flight when TMEM is released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -36,14 +40,14 @@
 namespace swk {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;       // tile; BK bf16 = 128 B rows
+constexpr int BM = 128, BK = 64;                  // tile rows; BK bf16 = 128 B rows
 constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * BK * 2;              // 16 KB
-constexpr int B_STAGE = BN * BK * 2;              // 32 KB
 constexpr int EPI_BUF = 32 * 32 * 4;              // 4 KB: 32 rows x 32 FP32, 128-byte swizzle
 constexpr int TC_THREADS = 192;                   // 6 warps
-constexpr int TMEM_COLS = 512;                    // two 256-column accumulators
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+template <int BN> constexpr int b_stage() { return BN * BK * 2; }  // 32 KB (BN 256), 16 KB
+template <int BN> constexpr int tmem_cols() { return 2 * BN; }     // two BN-column accumulators
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: default and drain limit
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -67,9 +71,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Waits for the phase of `parity` to complete; false after the time limit, or
+// Waits for the phase of `parity` to complete; false after `limit` cycles, or
 // as soon as another role has given up (abort_flag != NULL and set).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit = WAIT_CYCLES)
 {
     const uint32_t a = smem_u32(bar);
     const long long t0 = clock64();
@@ -84,7 +89,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
             : "memory");
         if (ok) return true;
         if (abort_flag && *abort_flag) return false;
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -159,13 +164,18 @@ struct TcArgs {
     uint32_t idesc;
     float *C;                   // [nf][Nq][Nt2] fp32
     int *err;                   // set to 1 on a timed-out wait
+    long long wait_cycles;      // limit of each wait of one role on another
+    int stall;                  // test hook: issue no copies (the consumers' waits run out)
     int tma_store;              // C rows 16-byte aligned (Nt even): TMA stores through mapC
 };
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const __grid_constant__ CUtensorMap mapC, TcArgs args)
 {
+    constexpr int B_STAGE = b_stage<BN>();
+    constexpr int TMEM_COLS = tmem_cols<BN>();
     extern __shared__ uint8_t dsm[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -214,14 +224,15 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         // ------------------------------------------------------------ TMA
         if (lane == 0) {
             int it = 0;
-            for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x) {
+            for (int t = blockIdx.x; t < num_tiles && !*abort_flag && !args.stall;
+                 t += gridDim.x) {
                 const int nt = t % args.ntiles;
                 const int mt = (t / args.ntiles) % args.mtiles;
                 const int f = t / (args.ntiles * args.mtiles);
                 for (int kb = 0; kb < args.kblocks; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t round = it / STAGES;
-                    if (!mbar_wait(&empty_bar[s], (round & 1) ^ 1, abort_flag)) {
+                    if (!mbar_wait(&empty_bar[s], (round & 1) ^ 1, abort_flag, args.wait_cycles)) {
                         give_up();
                         break;
                     }
@@ -243,7 +254,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x, ++lt) {
                 const int buf = lt & 1;
                 const uint32_t use = lt >> 1;
-                if (!mbar_wait(&tempty_bar[buf], (use & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(&tempty_bar[buf], (use & 1) ^ 1, abort_flag, args.wait_cycles)) {
                     give_up();
                     break;
                 }
@@ -252,7 +263,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 bool ok = true;
                 for (int kb = 0; kb < args.kblocks; ++kb, ++it) {
                     const int s = it % STAGES;
-                    if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, abort_flag)) {
+                    if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, abort_flag, args.wait_cycles)) {
                         give_up();
                         ok = false;
                         break;
@@ -283,7 +294,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const int mt = (t / args.ntiles) % args.mtiles;
             const int f = t / (args.ntiles * args.mtiles);
             const int buf = lt & 1;
-            if (!mbar_wait(&tfull_bar[buf], (lt >> 1) & 1, abort_flag)) {
+            if (!mbar_wait(&tfull_bar[buf], (lt >> 1) & 1, abort_flag, args.wait_cycles)) {
                 give_up();
                 break;
             }
@@ -399,15 +410,11 @@ bool make_map(CUtensorMap *m, const void *base, int kind, uint64_t ldk, uint64_t
     return r == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-int tc_ldk(int M) { return ((2 * M + BK - 1) / BK) * BK; }
-int lp_row_len(int M, int lp_kind) { return lp_kind == 3 ? 3 * tc_ldk(M) : tc_ldk(M); }
-
-cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
-                           int kind, float2 *C, int *err, int num_sms, cudaStream_t st)
+template <int BN>
+cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf, int kind,
+                        float2 *C, int *err, int num_sms, cudaStream_t st, long long wait_cycles,
+                        int stall)
 {
-    if (Nq <= 0 || Nt <= 0 || nf <= 0) return cudaSuccess;
     const int ldk = lp_row_len(M, kind);
     CUtensorMap ma, mb;
     if (!make_map(&ma, Xq, kind, ldk, (uint64_t)Nq, nf, BM) ||
@@ -427,18 +434,36 @@ cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M
               ((uint32_t)(BM >> 4) << 24);
     a.C = reinterpret_cast<float *>(C);
     a.err = err;
+    a.wait_cycles = wait_cycles > 0 ? wait_cycles : WAIT_CYCLES;
+    a.stall = stall;
     CUtensorMap mc;
     std::memset(&mc, 0, sizeof(mc));
     a.tma_store = (Nt % 2 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 &&
                    make_map_c(&mc, a.C, (uint64_t)2 * Nt, (uint64_t)Nq, (uint64_t)nf))
                       ? 1
                       : 0;
-    const size_t smem = (size_t)STAGES * (A_STAGE + B_STAGE) + 4 * 2 * EPI_BUF + 1024;
-    cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)STAGES * (A_STAGE + b_stage<BN>()) + 4 * 2 * EPI_BUF + 1024;
+    cudaFuncSetAttribute(k_corr_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int tiles = nf * a.mtiles * a.ntiles;
     const int grid = tiles < num_sms ? tiles : num_sms;
-    k_corr_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, mc, a);
+    k_corr_tc<BN><<<grid, TC_THREADS, smem, st>>>(ma, mb, mc, a);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_ldk(int M) { return ((2 * M + BK - 1) / BK) * BK; }
+int lp_row_len(int M, int lp_kind) { return lp_kind == 3 ? 3 * tc_ldk(M) : tc_ldk(M); }
+
+cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
+                           int kind, float2 *C, int *err, int num_sms, cudaStream_t st,
+                           long long wait_cycles, int stall, int tile_n)
+{
+    if (Nq <= 0 || Nt <= 0 || nf <= 0) return cudaSuccess;
+    if (tile_n == 128)
+        return launch_tile<128>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st, wait_cycles,
+                                stall);
+    return launch_tile<256>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st, wait_cycles, stall);
 }
 
 }  // namespace swk

@@ -174,7 +174,7 @@ __device__ __forceinline__ void write_result(const DecideArgs &A, int i, int j, 
         r.shift[0] = sx;
         r.shift[1] = sy;
     }
-    r.reserved = 0.f;
+    r.template_index = j;
     reinterpret_cast<sw_result *>(A.out)[(size_t)i * A.Nt + j] = r;
 }
 
@@ -677,12 +677,12 @@ __global__ void k_best_template(const sw_result *__restrict__ all, int Nq, int N
             r.best_l = -1;
             r.status = qbad || Nt == 0 ? 1 : 2;
             r.angle_rad = __int_as_float(0x7fc00000);
-            r.reserved = -1.f;
+            r.template_index = -1;
             r.shift[0] = r.shift[1] = nan;
             r.d2 = nan;
         } else {
             r = row[bj];
-            r.reserved = (float)bj;
+            r.template_index = bj;
         }
         out[warp] = r;
     }

@@ -289,6 +289,10 @@ __device__ __forceinline__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan 
 // cs: [nh] (cos, sin) of theta_k.  status: [nb], 1 for an unusable image.
 // With img2: images [0, nb_first) come from img and [nb_first, nb) from img2
 // (two batches in one launch).
+// scale[i] = 1 / sum max(img_i, 0) in FP64 (NaN for an image without positive
+// mass or with a non-finite pixel); img [nb][L][L].
+cudaError_t launch_image_scale(const float *img, int nb, int L, double *scale, cudaStream_t st);
+
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
                            const float2 *cs, float *out, int full_n, int32_t *status,
                            cudaStream_t st, int want_ctas = 0, const float *img2 = nullptr,
@@ -449,11 +453,16 @@ cudaError_t launch_corr_simt(const float *X, size_t xf, const float *Y, size_t y
 // Tensor-core correlation (tcgen05): the same product as launch_corr_simt for
 // BF16 (kind 1) or FP16 (kind 2) spectra in the padded K-major layout of
 // launch_spectrum: Xq [nf][Nq][ldk], Yt [nf][2Nt][ldk] (doubled template rows).
-// *err is set to 1 if a bounded wait gave up.
+// *err is set to 1 if a bounded wait gave up.  wait_cycles: limit of each
+// wait of one pipeline role on another, in SM clock cycles (0 = ~2 s).
+// stall (a test hook): the producer issues no copies, so the MMA role's
+// first wait runs out at the limit and *err is set.  tile_n: output tile
+// width (columns of D = 2 x templates), 256 or 128.
 int tc_ldk(int M);  // K row length: 2M rounded up to 64
 int lp_row_len(int M, int lp_kind);  // low-precision row length: ldk, or 3 ldk for the split
 cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
-                           int kind, float2 *C, int *err, int num_sms, cudaStream_t st);
+                           int kind, float2 *C, int *err, int num_sms, cudaStream_t st,
+                           long long wait_cycles = 0, int stall = 0, int tile_n = 256);
 // kind: 1 bf16, 2 fp16, 3 fp16 split (rows of lp_row_len(M, 3) elements)
 
 // Inverse angle FFT of the correlation spectra, argmin over the rotation

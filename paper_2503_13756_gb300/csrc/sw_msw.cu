@@ -180,7 +180,7 @@ __global__ void k_msw_decide(MswArgs A)
             shift_at(bl, r.shift[0], r.shift[1]);
             r.d2 = (double)best * invM;
         }
-        r.reserved = 0.f;
+        r.template_index = j;
         reinterpret_cast<sw_result *>(A.out)[warp] = r;
     }
     if (A.full && warp == 0) {

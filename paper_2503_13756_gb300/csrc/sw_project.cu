@@ -367,7 +367,57 @@ k_project4(const float *__restrict__ img, int L, int srcL, int n, int B, int per
     }
 }
 
+// Ingest (row a1 of the path): the clipped mass m = sum max(pixel, 0) of
+// each image in FP64 and its normalising scale 1 / m (Sec. 1.1: images are
+// probability densities; Sec. 5.4's g+ rule clips negatives).  One CTA per
+// image; NaN for an image with no positive mass or a non-finite pixel.
+constexpr int kScaleThreads = 256;
+
+__global__ void __launch_bounds__(kScaleThreads) k_image_scale(const float *__restrict__ img,
+                                                                int L, double *__restrict__ scale)
+{
+    const float *im = img + (size_t)blockIdx.x * L * L;
+    const int np = L * L;
+    double m = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < np; i += kScaleThreads) {
+        const float x = __ldg(im + i);
+        if (!isfinite(x)) bad = 1;
+        else if (x > 0.f) m += (double)x;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        m += __shfl_xor_sync(0xffffffffu, m, off);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+    }
+    __shared__ double sm[kScaleThreads / 32];
+    __shared__ int sb[kScaleThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sm[w] = m;
+        sb[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        int b = 0;
+        for (int i = 0; i < kScaleThreads / 32; ++i) {  // fixed order: reproducible
+            t += sm[i];
+            b |= sb[i];
+        }
+        scale[blockIdx.x] = (b || !(t > 0.0)) ? __longlong_as_double(0x7ff8000000000000ULL)
+                                               : 1.0 / t;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_image_scale(const float *img, int nb, int L, double *scale, cudaStream_t st)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_image_scale<<<nb, kScaleThreads, 0, st>>>(img, L, scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_project(const float *img, int nb, int L, int srcL, int nh, int B,
                            const float2 *cs, float *out, int full_n, int32_t *status,

@@ -20,7 +20,7 @@ SW_OK, SW_ERR_INVALID_ARG, SW_ERR_UNSUPPORTED, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_T
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2, "fp32_simt": 3}
 
 RESULT_DTYPE = np.dtype(
-    [("best_l", "<i4"), ("status", "<i4"), ("angle_rad", "<f4"), ("reserved", "<f4"),
+    [("best_l", "<i4"), ("status", "<i4"), ("angle_rad", "<f4"), ("template_index", "<i4"),
      ("shift", "<f8", (2,)), ("d2", "<f8")],
     align=True,
 )
@@ -93,7 +93,7 @@ EXPORTS = (
     "sw_align_all_rotations", "sw_align_batch", "sw_bank_create", "sw_bank_align",
     "sw_bank_size", "sw_bank_destroy", "sw_profile", "sw_profile_read", "sw_launch_count",
     "sw_align_all_rotations_noalloc", "sw_bank_workspace_bytes", "sw_autotune",
-    "sw_autotune_get",
+    "sw_autotune_get", "sw_set_wait_limit", "sw_set_correlation_stall", "sw_measure_fp32_fma",
 )
 STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best", "ramp")
 
@@ -113,7 +113,7 @@ def load(path: str | None = None):
                 "sw_set_workspace_limit": ([vp, ctypes.c_size_t], ci),
                 "sw_batch_workspace_bytes": ([P, ci, ci], ctypes.c_size_t),
                 "sw_reserve": ([vp, P, ci, ci], ci),
-                "sw_project": ([vp, P, vp, ci, vp, vp], ci),
+                "sw_project": ([vp, P, vp, ci, vp, vp, vp], ci),
                 "sw_quantiles": ([vp, P, vp, ci, vp, vp, vp, vp], ci),
                 "sw_align_all_rotations": ([vp, P, vp, vp, vp, vp, vp, vp], ci),
                 "sw_align_batch": ([vp, P, vp, ci, vp, ci, ci, vp, vp], ci),
@@ -129,6 +129,10 @@ def load(path: str | None = None):
                 "sw_bank_workspace_bytes": ([vp, ci, ci], ctypes.c_size_t),
                 "sw_autotune": ([vp, P, ctypes.c_char_p], ci),
                 "sw_autotune_get": ([vp, P, ctypes.POINTER(ci)], ci),
+                "sw_set_wait_limit": ([vp, ctypes.c_int64], ci),
+                "sw_set_correlation_stall": ([vp, ci], ci),
+                "sw_measure_fp32_fma": ([ci, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)], ci),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -191,13 +195,14 @@ class Aligner:
     def autotune(self, params: Params, cache_path: str | None = None):
         """Times candidate launch shapes for params and keeps the fastest
         (sw_autotune); returns the choice (projection CTA target, spectrum
-        width, decision width, FFT plan: radix order, radix-4 or radix-8 stages)."""
+        width, decision width, FFT plan: radix order, radix-4 or radix-8
+        stages, correlation tile width for <= 64 and for more templates)."""
         path = None if cache_path is None else str(cache_path).encode()
         self.call("sw_autotune", ctypes.byref(params), path)
         return self.tune_choice(params)
 
     def tune_choice(self, params: Params):
-        out = (ctypes.c_int * 4)()
+        out = (ctypes.c_int * 6)()
         self.call("sw_autotune_get", ctypes.byref(params), out)
         return tuple(int(v) for v in out)
 
@@ -217,21 +222,35 @@ class Aligner:
     def default_bins(self, L: int) -> int:
         return int(self.lib.sw_default_bins(int(L)))
 
+    def set_wait_limit(self, cycles: int):
+        """Limit (SM cycles) of the tensor-core pipeline's bounded waits;
+        0 restores the default (sw_set_wait_limit)."""
+        self.call("sw_set_wait_limit", ctypes.c_int64(int(cycles)))
+
+    def set_correlation_stall(self, enable: bool):
+        """Test hook: tensor-core correlations issue no copies while enabled,
+        so their bounded waits run out (sw_set_correlation_stall)."""
+        self.call("sw_set_correlation_stall", int(bool(enable)))
+
     def set_workspace_limit(self, nbytes: int):
         self.call("sw_set_workspace_limit", ctypes.c_size_t(int(nbytes)))
 
     def reserve(self, params: Params, Nq: int, Nt: int):
         self.call("sw_reserve", ctypes.byref(params), int(Nq), int(Nt))
 
-    def project(self, imgs, params: Params, out=None, stream=None):
+    def project(self, imgs, params: Params, out=None, stream=None, scale=False):
+        """Projection rows [nb][n][B]; with scale=True also the FP64 scales
+        1 / mass [nb] (NaN for an unusable image)."""
         import torch
         x = _f32(imgs, self.torch_device)
         nb = x.shape[0]
         B = bins_of(params)
         if out is None:
             out = torch.empty((nb, params.n_theta, B), dtype=torch.float32, device=x.device)
-        self.call("sw_project", ctypes.byref(params), _ptr(x), nb, _ptr(out), _stream(stream))
-        return out
+        sc = torch.empty((nb,), dtype=torch.float64, device=x.device) if scale else None
+        self.call("sw_project", ctypes.byref(params), _ptr(x), nb, _ptr(out), _ptr(sc),
+                  _stream(stream))
+        return (out, sc) if scale else out
 
     def quantiles(self, proj, params: Params, stream=None):
         import torch
@@ -309,6 +328,17 @@ class Bank:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_fma(device: int = 0):
+    """(TFLOP/s, ms per probe launch) of FP32 FMAs on the device
+    (sw_measure_fp32_fma)."""
+    lib = load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib.sw_measure_fp32_fma(int(device), ctypes.byref(tf), ctypes.byref(ms))
+    if st != SW_OK:
+        raise SwError(st, "sw_measure_fp32_fma failed")
+    return tf.value, ms.value
 
 
 def results_to_numpy(buf) -> np.ndarray:

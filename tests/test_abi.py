@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_result_struct_layout():
-    # sw_result: int32 best_l, int32 status, float angle, float reserved,
+    # sw_result: int32 best_l, int32 status, float angle, int32 template_index,
     # double shift[2], double d2 -> 40 bytes, d2 at offset 32
     assert swalign.RESULT_DTYPE.itemsize == 40
     assert swalign.RESULT_DTYPE.fields["d2"][1] == 32

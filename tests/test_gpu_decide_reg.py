@@ -97,7 +97,7 @@ def test_shared_memory_form_at_register_sizes(al, tmp_path, n, dec):
     B = p.n_bins or al.default_bins(p.L)
     cache = tmp_path / "tune.txt"
     for form in (dec, 1):
-        cache.write_text(f"swtune1 {dev} L={p.L} n={p.n_theta} M={p.n_levels} B={B} "
-                         f"prec={p.gemm_precision} 304 8 {form} 0\n")
+        cache.write_text(f"swtune2 {dev} L={p.L} n={p.n_theta} M={p.n_levels} B={B} "
+                         f"prec={p.gemm_precision} 304 8 {form} 0 0 0\n")
         assert al.autotune(p, cache)[2] == form
         compare_batch(al, q, t, n=n, M=M)

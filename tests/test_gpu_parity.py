@@ -56,6 +56,30 @@ def test_project_matches_oracle(al, L, n):
         np.testing.assert_allclose(got[i].sum(axis=1), ref.sum(axis=1), rtol=2e-6)
 
 
+@pytest.mark.parametrize("projector", ["splat", "slice"])
+def test_project_scale_is_the_inverse_clipped_mass(al, projector):
+    # ingest (a1): d_scale = 1 / sum max(pixel, 0) in FP64, NaN for an image
+    # with no positive mass or a non-finite pixel
+    rng = np.random.default_rng(77)
+    L, n = 48, 12
+    imgs = blobs(rng, 4, L)
+    imgs[1] -= 0.3 * imgs[1].max()
+    imgs[2] = -1.0
+    imgs[3, 5, 7] = np.inf
+    imgs = f32(imgs)
+    p = swalign.make_params(L, n, 8, projector=projector)
+    rows, scale = al.project(imgs, p, scale=True)
+    scale = scale.cpu().numpy()
+    for i in range(2):
+        _, mass = oracle.prepare(imgs[i].astype(np.float64))
+        assert scale[i] == pytest.approx(1.0 / mass, rel=1e-13)
+        if projector == "splat":  # the splat keeps the mass exactly (the slice's
+            # band-limited rows are clipped at zero, which adds the ringing's mass)
+            np.testing.assert_allclose(rows[i].cpu().numpy().astype(np.float64).sum(axis=1)
+                                       * scale[i], 1.0, rtol=2e-6)
+    assert np.isnan(scale[2]) and np.isnan(scale[3])
+
+
 # -------------------------------------------------------------- quantiles
 
 @pytest.mark.parametrize("level_rule", [0, 1])
@@ -202,7 +226,7 @@ def test_best_template_mode(al):
     best = swalign.results_to_numpy(al.align_batch(q, t, p, mode=1))
     for i in range(6):
         j = int(np.argmin(allr[i]["d2"]))
-        assert int(best[i]["reserved"]) == j
+        assert int(best[i]["template_index"]) == j
         assert best[i]["d2"] == allr[i, j]["d2"]
         assert best[i]["best_l"] == allr[i, j]["best_l"]
 
@@ -242,7 +266,7 @@ def test_invalid_arguments_are_rejected(al):
     out = torch.zeros((2, 8, p.n_bins or al.default_bins(16)), device="cuda")
     with pytest.raises(swalign.SwError) as e:  # misaligned image pointer
         al.call("sw_project", ctypes.byref(p), ctypes.c_void_p(buf.data_ptr() + 4), 2,
-                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(0))
+                ctypes.c_void_p(out.data_ptr()), None, ctypes.c_void_p(0))
     assert e.value.status == swalign.SW_ERR_INVALID_ARG
 
 
