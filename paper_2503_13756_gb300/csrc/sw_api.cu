@@ -629,6 +629,13 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     };
     // L <= 128 (grid in shared memory): per batch of kSliceBatch angles, the
     // batch's angles pooled so that the buckets stay even; entries kk 256 + j.
+    // Ray-adjacent targets (j, j + 1) of one half whose footprints start at
+    // most a row and a column apart form a pair entry (kSlicePairBit), bucketed
+    // by the first address of their union footprint and by the offsets of the
+    // two footprints in it (nine patterns, each a compile-time path of the
+    // kernel).  Each pattern's groups are padded to an even count, so both
+    // half-warps of a warp take one path; pairs come before the single
+    // targets.
     std::vector<uint16_t> gtab;
     std::vector<int> goff(1, 0);
     // L > 128 (grid in global memory, tiles in shared memory): per tile, the
@@ -640,14 +647,37 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
         const int batch = swk::slice_batch_of(L);
         for (int k0 = 0; k0 < nh; k0 += batch) {
             const int k1 = std::min(nh, k0 + batch);
-            std::map<int, std::vector<uint16_t>> cls[2][16];
+            std::map<int, std::vector<uint16_t>> cls[2][16], pcls[9][2][16];
+            const int S = swk::slice_stride(t.N);
             for (int k = k0; k < k1; ++k)
-                for (int j = 0; j < nj; ++j) {
-                    bool left;
-                    const int base =
-                        swk::slice_tap_base(j, (float)co[k], (float)si[k], t.N, &left);
-                    cls[left ? 0 : 1][base & 15][base].push_back((uint16_t)((k - k0) * 256 + j));
+                for (int j = 0; j < nj;) {
+                    int rA, cA, rB, cB;
+                    bool lA, lB;
+                    swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, &rA, &cA, &lA);
+                    const uint16_t ent = (uint16_t)((k - k0) * 256 + j);
+                    if (j + 1 < nj) {
+                        swk::slice_tap_rc(j + 1, (float)co[k], (float)si[k], t.N, &rB, &cB, &lB);
+                        if (lA == lB && std::abs(rA - rB) <= 1 && std::abs(cA - cB) <= 1) {
+                            const int r0 = std::min(rA, rB);
+                            const int c0 = lA ? std::min(cA, cB) : std::max(cA, cB);
+                            const int base = r0 * S + c0;
+                            const int pr = rA > rB ? 1 : (rB > rA ? 2 : 0);
+                            const int pc = cA != c0 ? 1 : (cB != c0 ? 2 : 0);
+                            pcls[pr * 3 + pc][lA ? 0 : 1][base & 15][base].push_back(
+                                (uint16_t)(ent | swk::kSlicePairBit));
+                            j += 2;
+                            continue;
+                        }
+                    }
+                    const int base = rA * S + cA;
+                    cls[lA ? 0 : 1][base & 15][base].push_back(ent);
+                    j += 1;
                 }
+            const size_t g_start = gtab.size() / 16;
+            for (auto &pc : pcls) {
+                group(pc, gtab, (uint16_t)0xFFFF);
+                if ((gtab.size() / 16 - g_start) & 1) gtab.insert(gtab.end(), 16, (uint16_t)0xFFFF);
+            }
             group(cls, gtab, (uint16_t)0xFFFF);
             goff.push_back((int)(gtab.size() / 16));
         }

@@ -310,6 +310,9 @@ struct SliceCoef {
 // Angles per batch of the slice projector's interpolation (two per warp in
 // the inverse FFTs).
 constexpr int kSliceBatch = 64;
+// Flag of a target-table entry (L <= 128) that stands for the ray-adjacent
+// pair (j, j + 1), interpolated together from their union footprint.
+constexpr unsigned kSlicePairBit = 0x4000u;
 // Grid geometry of the slice projector for an N-point oversampled grid (see
 // sw_slice.cu): lowest tap index, kept rows, left and right column counts
 // and the row stride (complex elements).
@@ -371,8 +374,10 @@ __host__ __device__ inline int slice_tiles_x(int N)
 // fac: [nh][B/2 + 1] sinc(pi t_1) sinc(pi t_2) (-1)^j e^{i pi j (1 - 2 delta (cos + sin)) / B}
 // with t = (j / B)(cos theta_k, sin theta_k), delta = 1/2 for even L, else 0.
 // gtab/goff: the targets (kk, j) of angle batch b (angles b batch + kk)
-// in half-warp groups of 16 lanes, entries kk * 256 + j (j <= B/2 <= 192) or
-// 0xFFFF (idle),
+// in half-warp groups of 16 lanes, entries kk * 256 + j (j <= B/2 <= 96),
+// with kSlicePairBit set for the pair (j, j + 1) of one half of the grid
+// whose footprints start at most one row and column apart, or 0xFFFF
+// (idle); pair groups come first and hold only pairs,
 // groups goff[b] .. goff[b+1]; every target of the batch appears once.  The
 // grouping only orders the work: each group's targets have distinct tap
 // addresses mod 16 (or equal ones), so its loads cost one pass.

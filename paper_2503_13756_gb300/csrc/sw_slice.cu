@@ -410,8 +410,99 @@ __device__ __forceinline__ float2 slice_sum(const float2 *g, int S, int da,
     return make_float2(fc.x * tr - fc.y * ti, fc.x * ti + fc.y * tr);
 }
 
+// Tap sums of two ray-adjacent slice samples A = (k, j) and B = (k, j + 1)
+// whose footprints start DRA / DRB rows and DCA / DCB columns into their
+// union box (each 0 or 1, one of each pair 0): every cell of the box is
+// loaded once and added to the sample(s) whose 9 x 9 footprint holds it.
+// The offsets are compile-time, so no weight is selected at run time.
+template <int DRA, int DRB, int DCA, int DCB>
+__device__ __forceinline__ void pair_taps(const float2 *__restrict__ g, int S, int da,
+                                          const float (&wxA)[kSliceW], const float (&wyA)[kSliceW],
+                                          const float (&wxB)[kSliceW], const float (&wyB)[kSliceW],
+                                          float2 &tA, float2 &tB)
+{
+    constexpr int W = kSliceW;
+    constexpr int NR = W + (DRA | DRB), NC = W + (DCA | DCB);
+    float tAr = 0.f, tAi = 0.f, tBr = 0.f, tBi = 0.f;
+#pragma unroll
+    for (int b = 0; b < NR; ++b) {
+        const bool rowA = b >= DRA && b < DRA + W, rowB = b >= DRB && b < DRB + W;
+        float sAr = 0.f, sAi = 0.f, sBr = 0.f, sBi = 0.f;
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const float2 gv = g[b * S + a * da];
+            if (rowA && a >= DCA && a < DCA + W) {
+                sAr = fmaf(wxA[a - DCA], gv.x, sAr);
+                sAi = fmaf(wxA[a - DCA], gv.y, sAi);
+            }
+            if (rowB && a >= DCB && a < DCB + W) {
+                sBr = fmaf(wxB[a - DCB], gv.x, sBr);
+                sBi = fmaf(wxB[a - DCB], gv.y, sBi);
+            }
+        }
+        if (rowA) {
+            tAr = fmaf(wyA[b - DRA], sAr, tAr);
+            tAi = fmaf(wyA[b - DRA], sAi, tAi);
+        }
+        if (rowB) {
+            tBr = fmaf(wyB[b - DRB], sBr, tBr);
+            tBi = fmaf(wyB[b - DRB], sBi, tBi);
+        }
+    }
+    tA = make_float2(tAr, tAi);
+    tB = make_float2(tBr, tBi);
+}
+
+// Two ray-adjacent slice samples (k, j) and (k, j + 1) of one half of the
+// grid, whose footprints start at most one row and one column apart (the
+// host pairs only such targets: consecutive samples on a ray are one grid
+// cell apart): their union box of at most 10 x 10 taps is read once for
+// both, against 162 reads for two separate samples.  The footprints' offsets
+// in the box select one of nine compile-time tap patterns; the host groups
+// the pairs so that every warp takes one pattern.
+template <int M>
+__device__ __forceinline__ void slice_pair(const SliceArgs &A, const float2 *G, int S, int k,
+                                           int j, float2 &outA, float2 &outB)
+{
+    constexpr int W = kSliceW;
+    float wxA[W], wyA[W], wxB[W], wyB[W];
+    int rA, cA, rB, cB;
+    bool lA, lB;
+    slice_target<M>(A, k, j, rA, cA, lA, wxA, wyA);
+    slice_target<M>(A, k, j + 1, rB, cB, lB, wxB, wyB);
+    const int da = lA ? 1 : -1;  // both in the same half (host-checked)
+    const int r0 = min(rA, rB);
+    const int c0 = lA ? min(cA, cB) : max(cA, cB);
+    // pattern: rows (A below B, B below A, level), columns likewise
+    const int pr = rA > rB ? 1 : (rB > rA ? 2 : 0);
+    const int pc = cA != c0 ? 1 : (cB != c0 ? 2 : 0);
+    const float2 *g = G + r0 * S + c0;
+    float2 tA, tB;
+#define SW_PAIR_CASE(PR, PC, DRA, DRB, DCA, DCB)                                          \
+    case PR * 3 + PC:                                                                      \
+        pair_taps<DRA, DRB, DCA, DCB>(g, S, da, wxA, wyA, wxB, wyB, tA, tB);              \
+        break;
+    switch (pr * 3 + pc) {
+        SW_PAIR_CASE(0, 0, 0, 0, 0, 0)
+        SW_PAIR_CASE(0, 1, 0, 0, 1, 0)
+        SW_PAIR_CASE(0, 2, 0, 0, 0, 1)
+        SW_PAIR_CASE(1, 0, 1, 0, 0, 0)
+        SW_PAIR_CASE(1, 1, 1, 0, 1, 0)
+        SW_PAIR_CASE(1, 2, 1, 0, 0, 1)
+        SW_PAIR_CASE(2, 0, 0, 1, 0, 0)
+        SW_PAIR_CASE(2, 1, 0, 1, 1, 0)
+        default: pair_taps<0, 1, 0, 1>(g, S, da, wxA, wyA, wxB, wyB, tA, tB); break;
+    }
+#undef SW_PAIR_CASE
+    const int nj = 16 * M + 1;
+    const float2 fa = __ldg(A.fac + (size_t)k * nj + j), fb = __ldg(A.fac + (size_t)k * nj + j + 1);
+    outA = make_float2(fa.x * tA.x - fa.y * tA.y, fa.x * tA.y + fa.y * tA.x);
+    outB = make_float2(fb.x * tB.x - fb.y * tB.y, fb.x * tB.y + fb.y * tB.x);
+}
+
 // Phase C for the angles [k0, k0 + BATCH) of the grid G (shared memory):
 // the slice samples into Xs [BATCH][B/2 + 1]; ends with a block barrier.
+// An entry with kSlicePairBit set computes the pair (j, j + 1).
 template <int M, int BATCH>
 __device__ __forceinline__ void slice_samples(const SliceArgs &A, const float2 *G, float2 *Xs,
                                               int k0, int bi)
@@ -427,8 +518,15 @@ __device__ __forceinline__ void slice_samples(const SliceArgs &A, const float2 *
     for (int slot = threadIdx.x; slot < ng * 16; slot += blockDim.x) {
         const unsigned ent = __ldg(A.gtab + (size_t)(g0 + (slot >> 4)) * 16 + (slot & 15));
         if (ent == 0xFFFFu) continue;
-        const int kk = (int)(ent >> 8), j = (int)(ent & 255u);
+        const int kk = (int)((ent >> 8) & 63u), j = (int)(ent & 255u);
         const int k = k0 + kk;
+        if (ent & kSlicePairBit) {
+            float2 xa, xb;
+            slice_pair<M>(A, G, S, k, j, xa, xb);
+            Xs[kk * nj + j] = xa;
+            Xs[kk * nj + j + 1] = xb;
+            continue;
+        }
         float wx[kSliceW], wy[kSliceW];
         int row0, col0;
         bool left;
