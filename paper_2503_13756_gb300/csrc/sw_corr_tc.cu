@@ -159,7 +159,10 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 struct TcArgs {
-    int Nq, Nt2, nf, kblocks;   // Nt2 = 2 Nt columns of D
+    int Nq, Nt2, nf, kblocks;   // Nt2 = 2 Nt columns of D; kblocks: K slices of the product
+    int segb;                   // K slices per operand segment (ldk / BK)
+    int split;                  // FP16 split: rows [hi | lo]; the three products hi hi, hi lo,
+                                // lo hi take A's segments 0, 0, 1 and B's 0, 1, 0
     int mtiles, ntiles;
     uint32_t idesc;
     float *C;                   // [nf][Nq][Nt2] fp32
@@ -236,9 +239,13 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         give_up();
                         break;
                     }
+                    // K slice kb of product term t: A's and B's segment for that term
+                    const int t = kb / args.segb, kk = kb - t * args.segb;
+                    const int xa = ((args.split && t == 2) ? args.segb + kk : kk) * BK;
+                    const int xb = ((args.split && t == 1) ? args.segb + kk : kk) * BK;
                     mbar_expect_tx(&full_bar[s], A_STAGE + B_STAGE);
-                    tma_load_3d(sA + s * A_STAGE, &mapA, &full_bar[s], kb * BK, mt * BM, f);
-                    tma_load_3d(sB + s * B_STAGE, &mapB, &full_bar[s], kb * BK, nt * BN, f);
+                    tma_load_3d(sA + s * A_STAGE, &mapA, &full_bar[s], xa, mt * BM, f);
+                    tma_load_3d(sB + s * B_STAGE, &mapB, &full_bar[s], xb, nt * BN, f);
                 }
             }
             // let every issued copy land before the CTA may exit (time-bounded
@@ -424,7 +431,9 @@ cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, i
     a.Nq = Nq;
     a.Nt2 = 2 * Nt;
     a.nf = nf;
-    a.kblocks = ldk / BK;
+    a.segb = tc_ldk(M) / BK;
+    a.split = kind == 3;
+    a.kblocks = a.split ? 3 * a.segb : a.segb;
     a.mtiles = (Nq + BM - 1) / BM;
     a.ntiles = (2 * Nt + BN - 1) / BN;
     // kind::f16 instruction descriptor: FP32 accumulator, A/B BF16 (1) or
@@ -453,7 +462,7 @@ cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, i
 }  // namespace
 
 int tc_ldk(int M) { return ((2 * M + BK - 1) / BK) * BK; }
-int lp_row_len(int M, int lp_kind) { return lp_kind == 3 ? 3 * tc_ldk(M) : tc_ldk(M); }
+int lp_row_len(int M, int lp_kind) { return lp_kind == 3 ? 2 * tc_ldk(M) : tc_ldk(M); }
 
 cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
                            int kind, float2 *C, int *err, int num_sms, cudaStream_t st,

@@ -436,9 +436,10 @@ cudaError_t launch_center_norm(const float *q, int nb, int n, int M, const doubl
 // lp_q[(k'-1)*lpq_fstride + img*ldk] = [re | im | 0], templates to the doubled
 // layout lp_t[(k'-1)*lpt_fstride + (2j)*ldk] = [re | im | 0] and
 // [(2j+1)*ldk] = [-im | re | 0], and norm16 from the rounded values.
-// lp_kind 3 writes the FP16 split x = hi + lo in rows of 3 ldk elements:
-// queries [hi | hi | lo], templates [hi | lo | hi] (of the same [re|im|0] and
-// [-im|re|0] rows), so that one GEMM over K = 3 ldk sums hi*hi + hi*lo + lo*hi.
+// lp_kind 3 writes the FP16 split x = hi + lo in rows of 2 ldk elements,
+// [hi | lo] (of the same [re|im|0] and [-im|re|0] rows): the correlation
+// runs one GEMM over K = 3 ldk, reading the segments (hi, hi), (hi, lo),
+// (lo, hi) of the two operands, so that it sums hi*hi + hi*lo + lo*hi.
 // With lp_kind != 0, spec32 is not written (may be NULL).
 // parts = 2 (ramp-filtered distance): M counts the levels of both parts,
 // q is [nb][2][n][M/2], each part is centred by its own vector and center
@@ -464,7 +465,7 @@ cudaError_t launch_corr_simt(const float *X, size_t xf, const float *Y, size_t y
 // first wait runs out at the limit and *err is set.  tile_n: output tile
 // width (columns of D = 2 x templates), 256 or 128.
 int tc_ldk(int M);  // K row length: 2M rounded up to 64
-int lp_row_len(int M, int lp_kind);  // low-precision row length: ldk, or 3 ldk for the split
+int lp_row_len(int M, int lp_kind);  // low-precision row length: ldk, or 2 ldk ([hi | lo]) for the split
 cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf,
                            int kind, float2 *C, int *err, int num_sms, cudaStream_t st,
                            long long wait_cycles = 0, int stall = 0, int tile_n = 256);

@@ -53,7 +53,7 @@ struct SpecOut {
     int Nq;
     int ldk;    // low-precision segment length (>= 2M, zero padded)
     int lp;     // write low-precision copies (queries to lp_q, templates to lp_t)
-    int split;  // FP16 hi/lo split: rows of 3 segments
+    int split;  // FP16 hi/lo split: rows of 2 segments [hi | lo]
 };
 
 // Compensated (Kahan) sum of nonnegative terms, kept as (sum, -compensation):
@@ -84,7 +84,7 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
     const T nim = to_lp<T>(-imf);
     const bool tmpl = img >= o.Nq;
     const int seg = o.ldk;                     // one [re|im|0] segment
-    const int row_len = o.split ? 3 * seg : seg;
+    const int row_len = o.split ? 2 * seg : seg;
     T *r = tmpl ? reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
                       (size_t)(2 * (img - o.Nq)) * row_len
                 : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
@@ -99,30 +99,20 @@ __device__ __forceinline__ void emit(const SpecOut &o, int img, int M, int kf, i
         }
         return;
     }
-    // FP16 split: lo = x - hi, exact in FP32, rounded to FP16
+    // FP16 split: lo = x - hi, exact in FP32, rounded to FP16; rows [hi | lo]
+    // (the correlation reads segments hi hi, hi lo, lo hi of its operands)
     const T rel = to_lp<T>(X.x - rf), iml = to_lp<T>(X.y - imf);
-    const T nrel = to_lp<T>(-(X.y - imf));
-    if (!tmpl) {  // A' = [hi | hi | lo]
-        r[p] = re;
-        r[M + p] = im;
-        r[seg + p] = re;
-        r[seg + M + p] = im;
-        r[2 * seg + p] = rel;
-        r[2 * seg + M + p] = iml;
-    } else {      // B' = [hi | lo | hi], rows [re|im] and [-im|re]
-        r[p] = re;
-        r[M + p] = im;
-        r[seg + p] = rel;
-        r[seg + M + p] = iml;
-        r[2 * seg + p] = re;
-        r[2 * seg + M + p] = im;
+    r[p] = re;
+    r[M + p] = im;
+    r[seg + p] = rel;
+    r[seg + M + p] = iml;
+    if (tmpl) {  // row 2j+1: [-im | re]
+        const T nrel = to_lp<T>(-(X.y - imf));
         T *r2 = r + row_len;
         r2[p] = nim;
         r2[M + p] = re;
         r2[seg + p] = nrel;
         r2[seg + M + p] = rel;
-        r2[2 * seg + p] = nim;
-        r2[2 * seg + M + p] = re;
     }
 }
 
@@ -164,7 +154,7 @@ __device__ __forceinline__ void emit2(const SpecOut &o, int img, int M, int kf, 
     const float rfb = from_lp<T>(reb), imfb = from_lp<T>(imb);
     const bool tmpl = img >= o.Nq;
     const int seg = o.ldk;
-    const int row_len = o.split ? 3 * seg : seg;
+    const int row_len = o.split ? 2 * seg : seg;
     T *r = tmpl ? reinterpret_cast<T *>(o.lp_t) + (size_t)(kf - 1) * o.lpt_fstride +
                       (size_t)(2 * (img - o.Nq)) * row_len
                 : reinterpret_cast<T *>(o.lp_q) + (size_t)(kf - 1) * o.lpq_fstride +
@@ -186,28 +176,17 @@ __device__ __forceinline__ void emit2(const SpecOut &o, int img, int M, int kf, 
     // FP16 split: lo = x - hi, exact in FP32, rounded to FP16
     const V rel2 = P::make(to_lp<T>(Xa.x - rfa), to_lp<T>(Xb.x - rfb));
     const V iml2 = P::make(to_lp<T>(Xa.y - imfa), to_lp<T>(Xb.y - imfb));
-    if (!tmpl) {  // A' = [hi | hi | lo]
-        put(r + pa, re2);
-        put(r + M + pa, im2);
-        put(r + seg + pa, re2);
-        put(r + seg + M + pa, im2);
-        put(r + 2 * seg + pa, rel2);
-        put(r + 2 * seg + M + pa, iml2);
-    } else {      // B' = [hi | lo | hi], rows [re|im] and [-im|re]
+    put(r + pa, re2);  // [hi | lo]
+    put(r + M + pa, im2);
+    put(r + seg + pa, rel2);
+    put(r + seg + M + pa, iml2);
+    if (tmpl) {  // row 2j+1: [-im | re]
         const V nrel2 = P::make(to_lp<T>(-(Xa.y - imfa)), to_lp<T>(-(Xb.y - imfb)));
-        put(r + pa, re2);
-        put(r + M + pa, im2);
-        put(r + seg + pa, rel2);
-        put(r + seg + M + pa, iml2);
-        put(r + 2 * seg + pa, re2);
-        put(r + 2 * seg + M + pa, im2);
         T *r2 = r + row_len;
         put(r2 + pa, nim2);
         put(r2 + M + pa, re2);
         put(r2 + seg + pa, nrel2);
         put(r2 + seg + M + pa, rel2);
-        put(r2 + 2 * seg + pa, nim2);
-        put(r2 + 2 * seg + M + pa, re2);
     }
 }
 
@@ -374,7 +353,7 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     if (o.lp && o.ldk > 2 * M) {
         const int pad = o.ldk - 2 * M;
         const bool tmpl = img >= o.Nq;
-        const int nseg = o.split ? 3 : 1;
+        const int nseg = o.split ? 2 : 1;
         const int row_len = nseg * o.ldk;
         const int rows = tmpl ? 2 : 1;
         const int per_f = rows * nseg * pad;
