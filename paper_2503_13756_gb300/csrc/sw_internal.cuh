@@ -390,7 +390,7 @@ __host__ __device__ inline int slice_tiles_x(int N)
 // row-major) in half-warp groups toff[t] .. toff[t+1] of 16 entries
 // k << 16 | j or 0xFFFFFFFF, grouped by the bank of the first tap in the
 // tile's copy as above (left and right halves apart).
-constexpr int kSliceChunk = 256;
+constexpr int kSliceChunk = 1024;
 constexpr size_t kSliceSmemMax = 227 * 1024 - 64;  // opt-in dynamic shared memory of a CTA
 // 32 ceil(max(min_bins, 1.5 L) / 32), rounded up to 256, 320 or 384 above 192
 int slice_default_bins(int L, int min_bins);

@@ -234,15 +234,15 @@ def test_slice_bank_with_half_size_queries_equals_batch(al):
 
 def test_slice_global_grid_batch_on_gpu_rows(al):
     # 128 < L: the grids of chunks of images in global scratch; more images
-    # than one chunk (256) so that the chunk loop runs twice
+    # than one chunk (1024) so that the chunk loop runs twice
     rng = np.random.default_rng(89)
     L, n, M = 192, 24, 32
-    q = blobs(rng, 260, L)
+    q = blobs(rng, 1030, L)
     t = blobs(rng, 3, L)
     p = params(L, n, M)
     assert swalign.bins_of(p) == 320
     got = swalign.results_to_numpy(al.align_batch(q, t, p)).reshape(len(q), len(t))
-    for i in (0, 7, 255, 256, 259):
+    for i in (0, 7, 1023, 1024, 1029):
         rows = al.project(np.stack([q[i], t[1]]), p).cpu().numpy().astype(np.float64)
         Dref, Sref, Sc = curve_from_rows(rows[0], rows[1], 2.0 / L, M, 1)
         gr = got[i, 1]
