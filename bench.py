@@ -275,7 +275,7 @@ def parity_of(gpu, ref, S, rel):
             "min_d2_over_S": float((r["d2"] / S).min())}
 
 
-def cpu_baseline(data, projector="slice", gpu=None, norms=None):
+def cpu_baseline(data, projector="slice", gpu=None, norms=None, s=None):
     """The FP64 oracle as it stands, on the host cores, on the first s x s
     pairs of the workload (sample_size), timed.  With `gpu` ({name: (block
     [s][s], source pairs [s])} of sw_result records from the timed runs) and
@@ -284,7 +284,8 @@ def cpu_baseline(data, projector="slice", gpu=None, norms=None):
     pairs -- the timed block, and each sampled query with its own template
     (well aligned: d2 / S ~ 1e-4) -- give the measured error per result."""
     import oracle
-    s = sample_size(projector)
+    if s is None:
+        s = min(sample_size(projector), len(data["queries"]), len(data["templates"]))
     proj = int(projector == "slice")
     q = data["queries"][:s].astype(np.float64)
     t = data["templates"][:s].astype(np.float64)
@@ -842,7 +843,7 @@ def main():
         pn = swalign.make_params(L, N_THETA, M_LEVELS, projector=args.projector)
         norm = [al.quantiles(al.project(x, pn), pn)[2].cpu().numpy() for x in
                 (q_d[:s_par], t_d[:s_par], t_d[src_idx])]
-        cpu, parity = cpu_baseline(data, args.projector, gpu_sample, norm)
+        cpu, parity = cpu_baseline(data, args.projector, gpu_sample, norm, s_par)
     serve = None if (args.no_serving or world > 1) else serving_block(args, local)
     unev = None if (args.no_uneven or world > 1) else uneven_block(args, local)
     line = {
