@@ -18,9 +18,13 @@
 // 256-wide tile as padding).  Warp 0 issues TMA loads (128-byte swizzle, 3-D
 // maps over frequency) into a 4-stage ring of 64-wide K slices; warp 1 owns
 // the 2 BN-column TMEM allocation and one lane issues tcgen05.mma (M=128,
-// N=BN, K=16) into one of two TMEM accumulators; warps 2-5 drain the other
-// accumulator with tcgen05.ld, so the epilogue of one tile overlaps the MMAs
-// of the next.  With Nt even each
+// N=BN, K=16) into one of two TMEM accumulators; the epilogue warps drain
+// the other accumulator with tcgen05.ld, so the epilogue of one tile
+// overlaps the MMAs of the next.  BF16 / FP16 (one K pass per tile) take
+// eight epilogue warps, two per TMEM lane quarter each draining half of the
+// tile's columns, with a 3-stage ring at BN = 256 to leave room for their
+// store buffers; the FP16 split (three K passes per tile, bound by its operand
+// loads) keeps four epilogue warps and a 4-stage ring.  With Nt even each
 // epilogue warp writes its 32 x 32 FP32 blocks into one of two 128-byte-
 // swizzled shared-memory buffers and one lane stores them with a TMA tensor
 // store (coalesced, clipped at the tensor's edges); odd Nt keeps per-lane
@@ -41,10 +45,12 @@ namespace swk {
 namespace {
 
 constexpr int BM = 128, BK = 64;                  // tile rows; BK bf16 = 128 B rows
-constexpr int STAGES = 4;
+constexpr int MAX_STAGES = 4;
 constexpr int A_STAGE = BM * BK * 2;              // 16 KB
 constexpr int EPI_BUF = 32 * 32 * 4;              // 4 KB: 32 rows x 32 FP32, 128-byte swizzle
-constexpr int TC_THREADS = 192;                   // 6 warps
+// EPW epilogue warps per TMEM lane quarter (1 or 2)
+template <int EPW> constexpr int tc_threads() { return 64 + 128 * EPW; }  // TMA, MMA, epilogue
+template <int BN, int EPW> constexpr int stages() { return (BN == 256 && EPW == 2) ? 3 : 4; }
 template <int BN> constexpr int b_stage() { return BN * BK * 2; }  // 32 KB (BN 256), 16 KB
 template <int BN> constexpr int tmem_cols() { return 2 * BN; }     // two BN-column accumulators
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: default and drain limit
@@ -172,20 +178,22 @@ struct TcArgs {
     int tma_store;              // C rows 16-byte aligned (Nt even): TMA stores through mapC
 };
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int BN, int EPW>
+__global__ void __launch_bounds__(tc_threads<EPW>(), 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const __grid_constant__ CUtensorMap mapC, TcArgs args)
 {
     constexpr int B_STAGE = b_stage<BN>();
     constexpr int TMEM_COLS = tmem_cols<BN>();
+    constexpr int STAGES = stages<BN, EPW>();
+    constexpr int EPI_WARPS = 4 * EPW;
     extern __shared__ uint8_t dsm[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~static_cast<uintptr_t>(1023));
     uint8_t *sA = base;                       // STAGES x 16 KB
     uint8_t *sB = base + STAGES * A_STAGE;    // STAGES x 32 KB
-    uint8_t *sE = sB + STAGES * B_STAGE;      // [4 warps][2] x 4 KB epilogue blocks (1 KB aligned)
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+    uint8_t *sE = sB + STAGES * B_STAGE;      // [EPI_WARPS][2] x 4 KB epilogue blocks (1 KB aligned)
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
@@ -200,7 +208,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull_bar[b], 1);
-            mbar_init(&tempty_bar[b], 4);  // one arrival per epilogue warp
+            mbar_init(&tempty_bar[b], EPI_WARPS);  // one arrival per epilogue warp
         }
         mbar_init(&done_bar, 1);
         abort_s = 0;
@@ -293,8 +301,10 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     } else {
         // ------------------------------------------------------- epilogue
         const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int ew = warp - 2;                // epilogue warp 0 .. EPI_WARPS - 1
+        const int cbeg = (ew / 4) * (BN / EPW); // this warp's share of the columns
         const int row_in_tile = q * 32 + lane;
-        uint8_t *myE = sE + q * 2 * EPI_BUF;
+        uint8_t *myE = sE + ew * 2 * EPI_BUF;
         int lt = 0, chunk = 0;
         for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x, ++lt) {
             const int nt = t % args.ntiles;
@@ -310,7 +320,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             float *crow = args.C + ((size_t)f * args.Nq + i) * args.Nt2 + (size_t)nt * BN;
             const int ncols = min(BN, args.Nt2 - nt * BN);
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = cbeg; c0 < cbeg + BN / EPW; c0 += 32) {
                 uint32_t r[32];
                 if (args.tma_store) {
                     // a box wholly past the tensor's edge holds nothing (warp-uniform)
@@ -417,7 +427,7 @@ bool make_map(CUtensorMap *m, const void *base, int kind, uint64_t ldk, uint64_t
     return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int EPW>
 cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf, int kind,
                         float2 *C, int *err, int num_sms, cudaStream_t st, long long wait_cycles,
                         int stall)
@@ -451,11 +461,13 @@ cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, i
                    make_map_c(&mc, a.C, (uint64_t)2 * Nt, (uint64_t)Nq, (uint64_t)nf))
                       ? 1
                       : 0;
-    const size_t smem = (size_t)STAGES * (A_STAGE + b_stage<BN>()) + 4 * 2 * EPI_BUF + 1024;
-    cudaFuncSetAttribute(k_corr_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem =
+        (size_t)stages<BN, EPW>() * (A_STAGE + b_stage<BN>()) + 4 * EPW * 2 * EPI_BUF + 1024;
+    cudaFuncSetAttribute(k_corr_tc<BN, EPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     const int tiles = nf * a.mtiles * a.ntiles;
     const int grid = tiles < num_sms ? tiles : num_sms;
-    k_corr_tc<BN><<<grid, TC_THREADS, smem, st>>>(ma, mb, mc, a);
+    k_corr_tc<BN, EPW><<<grid, tc_threads<EPW>(), smem, st>>>(ma, mb, mc, a);
     return cudaGetLastError();
 }
 
@@ -469,10 +481,17 @@ cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M
                            long long wait_cycles, int stall, int tile_n)
 {
     if (Nq <= 0 || Nt <= 0 || nf <= 0) return cudaSuccess;
-    if (tile_n == 128)
-        return launch_tile<128>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st, wait_cycles,
-                                stall);
-    return launch_tile<256>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st, wait_cycles, stall);
+    // the FP16 split (kind 3) is bound by its operand loads: four epilogue
+    // warps and a 4-stage ring; BF16 / FP16 drain with eight
+    if (kind == 3)
+        return tile_n == 128 ? launch_tile<128, 1>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms,
+                                                   st, wait_cycles, stall)
+                             : launch_tile<256, 1>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms,
+                                                   st, wait_cycles, stall);
+    return tile_n == 128 ? launch_tile<128, 2>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
+                                               wait_cycles, stall)
+                         : launch_tile<256, 2>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
+                                               wait_cycles, stall);
 }
 
 }  // namespace swk
