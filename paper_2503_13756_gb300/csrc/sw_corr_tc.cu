@@ -481,13 +481,12 @@ cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M
                            long long wait_cycles, int stall, int tile_n)
 {
     if (Nq <= 0 || Nt <= 0 || nf <= 0) return cudaSuccess;
-    // the FP16 split (kind 3) is bound by its operand loads: four epilogue
-    // warps and a 4-stage ring; BF16 / FP16 drain with eight
-    if (kind == 3)
-        return tile_n == 128 ? launch_tile<128, 1>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms,
-                                                   st, wait_cycles, stall)
-                             : launch_tile<256, 1>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms,
-                                                   st, wait_cycles, stall);
+    // the FP16 split (kind 3) is bound by its operand loads: at BN = 256 four
+    // epilogue warps keep the 4-stage ring; BF16 / FP16, and the split at
+    // BN = 128 (where eight fit beside four stages), drain with eight
+    if (kind == 3 && tile_n != 128)
+        return launch_tile<256, 1>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st, wait_cycles,
+                                   stall);
     return tile_n == 128 ? launch_tile<128, 2>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
                                                wait_cycles, stall)
                          : launch_tile<256, 2>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
