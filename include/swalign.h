@@ -266,6 +266,20 @@ sw_status sw_autotune_get(const sw_ctx *ctx, const sw_params *p, int *choice);
 sw_status sw_project(sw_ctx *ctx, const sw_params *p, const float *d_img, int nb,
                      float *d_proj, double *d_scale, sw_stream_t stream);
 
+/* Projections, as sw_project writes them for p, of nb images of side L/2
+ * upsampled 2 x 2 to L x L (each pixel split into the four cells of a 2 x 2
+ * block with a quarter of its value; the paper has no counterpart: it is the
+ * projection that sw_bank_align applies to queries of side L/2).  L even.
+ * With the Fourier slice above L = 128 the L/2 image's own grid is used
+ * (T_L(t) = (1 + e^{-2 pi i t_1})(1 + e^{-2 pi i t_2}) / 4 T_{L/2}(2 t), Sec. 2.3
+ * "Computation" applied to the L/2 image), so the rows equal those of the
+ * upsampled image to the NUFFT's accuracy, not bitwise.
+ *   d_img  [nb][L/2][L/2] float32 (input)
+ *   d_proj [nb][n][B] float32 (output), layout of sw_project
+ * Returns SW_ERR_INVALID_ARG for odd L. */
+sw_status sw_project_upsampled(sw_ctx *ctx, const sw_params *p, const float *d_img, int nb,
+                               float *d_proj, sw_stream_t stream);
+
 /* Quantile functions of projections (Sec. 2.3: CDF by cumulative sum, ICDF
  * by linear interpolation; Eq. inv_cdf with the ">=" of App. A.1.1).
  *   d_proj   [nb][n][B] float32 (input, as written by sw_project)

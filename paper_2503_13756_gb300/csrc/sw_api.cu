@@ -7,6 +7,7 @@
 #include <type_traits>
 #include <array>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -54,6 +55,13 @@ struct SliceTables {
     int *goff = nullptr;
     uint32_t *ttab = nullptr;  // target groups per grid tile (L > 128)
     int *toff = nullptr;
+    // images of side L/2 upsampled 2 x 2 (launch_project_slice_up; 128 < L)
+    float *up_psi_inv = nullptr;
+    float2 *up_fac = nullptr;
+    uint16_t *up_gtab = nullptr;
+    int *up_goff = nullptr;
+    float2 *up_tw = nullptr;
+    swk::SliceUpTables up() const { return {up_psi_inv, up_fac, up_gtab, up_goff, up_tw}; }
 };
 
 void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
@@ -638,25 +646,22 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     // targets.
     std::vector<uint16_t> gtab;
     std::vector<int> goff(1, 0);
-    // L > 128 (grid in global memory, tiles in shared memory): per tile, the
-    // targets whose footprint starts in it; entries k << 16 | j; the bank is
-    // that of the first tap in the tile's copy (rows kSliceTileRS apart).
-    std::vector<uint32_t> ttab;
-    std::vector<int> toff(1, 0);
-    if (L <= 128) {
-        const int batch = swk::slice_batch_of(L);
+    // tap_rc(k, j, &row, &col, &left): the first tap of target (k, j) on the
+    // N-point grid; nj targets per angle
+    auto batch_groups = [&](int batch, int N, int njt, auto tap_rc, std::vector<uint16_t> &tab,
+                            std::vector<int> &off) {
         for (int k0 = 0; k0 < nh; k0 += batch) {
             const int k1 = std::min(nh, k0 + batch);
             std::map<int, std::vector<uint16_t>> cls[2][16], pcls[9][2][16];
-            const int S = swk::slice_stride(t.N);
+            const int S = swk::slice_stride(N);
             for (int k = k0; k < k1; ++k)
-                for (int j = 0; j < nj;) {
+                for (int j = 0; j < njt;) {
                     int rA, cA, rB, cB;
                     bool lA, lB;
-                    swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, &rA, &cA, &lA);
+                    tap_rc(k, j, &rA, &cA, &lA);
                     const uint16_t ent = (uint16_t)((k - k0) * 256 + j);
-                    if (j + 1 < nj) {
-                        swk::slice_tap_rc(j + 1, (float)co[k], (float)si[k], t.N, &rB, &cB, &lB);
+                    if (j + 1 < njt) {
+                        tap_rc(k, j + 1, &rB, &cB, &lB);
                         if (lA == lB && std::abs(rA - rB) <= 1 && std::abs(cA - cB) <= 1) {
                             const int r0 = std::min(rA, rB);
                             const int c0 = lA ? std::min(cA, cB) : std::max(cA, cB);
@@ -673,14 +678,26 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
                     cls[lA ? 0 : 1][base & 15][base].push_back(ent);
                     j += 1;
                 }
-            const size_t g_start = gtab.size() / 16;
+            const size_t g_start = tab.size() / 16;
             for (auto &pc : pcls) {
-                group(pc, gtab, (uint16_t)0xFFFF);
-                if ((gtab.size() / 16 - g_start) & 1) gtab.insert(gtab.end(), 16, (uint16_t)0xFFFF);
+                group(pc, tab, (uint16_t)0xFFFF);
+                if ((tab.size() / 16 - g_start) & 1) tab.insert(tab.end(), 16, (uint16_t)0xFFFF);
             }
-            group(cls, gtab, (uint16_t)0xFFFF);
-            goff.push_back((int)(gtab.size() / 16));
+            group(cls, tab, (uint16_t)0xFFFF);
+            off.push_back((int)(tab.size() / 16));
         }
+    };
+    // L > 128 (grid in global memory, tiles in shared memory): per tile, the
+    // targets whose footprint starts in it; entries k << 16 | j; the bank is
+    // that of the first tap in the tile's copy (rows kSliceTileRS apart).
+    std::vector<uint32_t> ttab;
+    std::vector<int> toff(1, 0);
+    if (L <= 128) {
+        batch_groups(swk::slice_batch_of(L), t.N, nj,
+                     [&](int k, int j, int *r, int *cc, bool *l) {
+                         swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, r, cc, l);
+                     },
+                     gtab, goff);
     } else {
         const int TY = swk::slice_tiles_y(t.N), TX = swk::slice_tiles_x(t.N);
         std::vector<std::array<std::array<std::map<int, std::vector<uint32_t>>, 16>, 2>> cls(
@@ -702,6 +719,44 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
             toff.push_back((int)(ttab.size() / 16));
         }
     }
+    // Images of side L/2 upsampled 2 x 2 (128 < L): their own grid of
+    // Nu = B/2 points (same oversampling, so the same kernel shape), the
+    // factor (1 + e^{-2 pi i t_1}) (1 + e^{-2 pi i t_2}) / 4 folded into fac,
+    // and targets j <= Nu in kUpBatch-angle batches.
+    const bool up = swk::slice_up_supported(L, B);
+    const int Lu = L / 2, Nu = B / 2;
+    std::vector<float> upinv;
+    std::vector<float2> upfac, uptw;
+    std::vector<uint16_t> upgtab;
+    std::vector<int> upgoff(1, 0);
+    if (up) {
+        upinv.resize(Lu);
+        for (int cidx = 0; cidx < Lu; ++cidx)
+            upinv[cidx] = (float)(1.0 / slice_kernel_ft(cidx - Lu / 2, Nu, W, t.beta));
+        upfac.resize((size_t)nh * nj);
+        for (int k = 0; k < nh; ++k)
+            for (int j = 0; j < nj; ++j) {
+                const double t1 = (double)j / B * co[k], t2 = (double)j / B * si[k];
+                const std::complex<double> h1(1.0 + std::cos(2.0 * M_PI * t1),
+                                              -std::sin(2.0 * M_PI * t1));
+                const std::complex<double> h2(1.0 + std::cos(2.0 * M_PI * t2),
+                                              -std::sin(2.0 * M_PI * t2));
+                const double amp = sinc_pi(t1) * sinc_pi(t2) * ((j & 1) ? -1.0 : 1.0);
+                const double ph = M_PI * j * (1.0 - 2.0 * delta * (co[k] + si[k])) / B;
+                const std::complex<double> v =
+                    std::complex<double>(amp * std::cos(ph), amp * std::sin(ph)) * h1 * h2 * 0.25;
+                upfac[(size_t)k * nj + j] = make_float2((float)v.real(), (float)v.imag());
+            }
+        uptw.resize(Nu);
+        for (int q = 0; q < Nu; ++q)
+            uptw[q] = make_float2((float)std::cos(2.0 * M_PI * q / Nu),
+                                  (float)-std::sin(2.0 * M_PI * q / Nu));
+        batch_groups(swk::kUpBatch, Nu, nj,
+                     [&](int k, int j, int *r, int *cc, bool *l) {
+                         swk::slice_up_rc(j, (float)co[k], (float)si[k], Nu, r, cc, l);
+                     },
+                     upgtab, upgoff);
+    }
     SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
     SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));
     cudaError_t e = cudaMalloc(&t.fac, sizeof(float2) * fac.size());
@@ -721,6 +776,19 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     if (e == cudaSuccess && L > 128) e = cudaMalloc(&t.toff, sizeof(int) * toff.size());
     if (e == cudaSuccess && L > 128)
         e = cudaMemcpy(t.toff, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice);
+    auto upload = [&](auto **dst, const auto &v) {
+        if (e != cudaSuccess || v.empty()) return;
+        const size_t bytes = sizeof(v[0]) * v.size();
+        e = cudaMalloc(dst, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice);
+    };
+    if (up) {
+        upload(&t.up_psi_inv, upinv);
+        upload(&t.up_fac, upfac);
+        upload(&t.up_gtab, upgtab);
+        upload(&t.up_goff, upgoff);
+        upload(&t.up_tw, uptw);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(t.psi_inv);
@@ -729,6 +797,11 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
         cudaFree(t.goff);
         cudaFree(t.ttab);
         cudaFree(t.toff);
+        cudaFree(t.up_psi_inv);
+        cudaFree(t.up_fac);
+        cudaFree(t.up_gtab);
+        cudaFree(t.up_goff);
+        cudaFree(t.up_tw);
         return fail(c, SW_ERR_CUDA, "slice tables: %s", cudaGetErrorString(e));
     }
     c->slice_tables.push_back(t);
@@ -808,10 +881,18 @@ sw_status project_rows(sw_ctx *c, const sw_params *p, const Tables *t, const flo
         const SliceTables *sl;
         const Tables *tb;
         sw_status s;
-        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, B, &tb)) ||
-            (s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, B, nb, nh))))
-            return s;
+        if ((s = get_slice_tables(c, p, &sl)) || (s = get_tables(c, B, &tb))) return s;
         const int clip = p->metric != SW_METRIC_RFSW2;
+        if (2 * srcL == p->L && sl->up_gtab) {  // the L/2 image's own grid, one launch
+            SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
+                        return swk::launch_project_slice_up(img, nb, p->L, nh, B, t->cs,
+                                                            sl->up(), sl->coef, tb->tw, clip,
+                                                            out, full_n, status, st, img2,
+                                                            nb_first);
+                    }));
+            return SW_OK;
+        }
+        if ((s = ensure_slice_scratch(c, swk::slice_scratch_bytes(p->L, B, nb, nh)))) return s;
         SW_CUDA(c, launch(c, SW_STAGE_PROJECT, st, [&] {
                     return swk::launch_project_slice(img, nb, p->L, srcL, nh, B, t->cs,
                                                      sl->psi_inv, sl->fac, sl->gtab, sl->goff,
@@ -935,6 +1016,11 @@ void sw_destroy(sw_ctx *c)
         cudaFree(t.goff);
         cudaFree(t.ttab);
         cudaFree(t.toff);
+        cudaFree(t.up_psi_inv);
+        cudaFree(t.up_fac);
+        cudaFree(t.up_gtab);
+        cudaFree(t.up_goff);
+        cudaFree(t.up_tw);
     }
     if (c->slice_scratch) cudaFree(c->slice_scratch);
     delete c;
@@ -1049,6 +1135,26 @@ sw_status sw_project(sw_ctx *c, const sw_params *p, const float *d_img, int nb, 
                     return swk::launch_image_scale(d_img, nb, p->L, d_scale, st);
                 }));
     return project_rows(c, p, t, d_img, p->L, nb, d_proj, 1, at<int32_t>(c->ws, 0), st);
+}
+
+sw_status sw_project_upsampled(sw_ctx *c, const sw_params *p, const float *d_img, int nb,
+                               float *d_proj, sw_stream_t stream)
+{
+    if (!c) return SW_ERR_INVALID_ARG;
+    c->err.clear();
+    sw_status s = check_params(c, p);
+    if (s) return s;
+    if (p->L & 1) return fail(c, SW_ERR_INVALID_ARG, "L=%d is odd: no L/2 images", p->L);
+    if (nb < 0) return fail(c, SW_ERR_INVALID_ARG, "nb=%d", nb);
+    if (nb == 0) return SW_OK;
+    if ((s = check_ptr(c, d_img, "d_img", true)) || (s = check_ptr(c, d_proj, "d_proj", true)))
+        return s;
+    if ((s = set_device(c))) return s;
+    const Tables *t;
+    if ((s = get_tables(c, p->n_theta, &t))) return s;
+    if ((s = ensure_ws(c, align_up(4 * (size_t)nb)))) return s;
+    return project_rows(c, p, t, d_img, p->L / 2, nb, d_proj, 1, at<int32_t>(c->ws, 0),
+                        (cudaStream_t)stream);
 }
 
 sw_status sw_quantiles(sw_ctx *c, const sw_params *p, const float *d_proj, int nb, float *d_q,

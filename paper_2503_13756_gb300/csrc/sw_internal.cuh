@@ -347,6 +347,55 @@ __host__ __device__ inline int slice_tap_base(int j, float ex, float ey, int N, 
     slice_tap_rc(j, ex, ey, N, &row, &col, left);
     return row * slice_stride(N) + col;
 }
+// Images of side L/2 seen as L x L images of 2 x 2 blocks (each pixel split
+// into four cells of a quarter of its value): with c' = 2 c'' + u, u in {0, 1},
+//   T_L(t) = (1 + e^{-2 pi i t_1}) (1 + e^{-2 pi i t_2}) / 4 * T_{L/2}(2 t),
+// and T_{L/2} is 1-periodic, so the L/2 image's own grid of N = B/2 points
+// serves the rows of B bins: target (j, theta), j <= B/2 = N, sits at
+// y = -j e on that grid.  First tap (i1, i2) and offsets (x1, x2) of the
+// target on the stored half grid: y1 wrapped by N into the columns the
+// grid keeps; a row footprint below the kept rows wraps into the upper half
+// plane, where the target is folded through T(-s) = conj T(s) (*conj set:
+// taps reflected, i -> -i - (W - 1), offsets negated).  Integer wrapping
+// and folding keep host and kernel in step (both take the same FP32 steps
+// up to the cell).
+__host__ __device__ inline void slice_up_tap(int j, float ex, float ey, int N, int *i1, int *i2,
+                                             float *x1, float *x2, bool *conj)
+{
+    const float jf = (float)j, Nf = (float)N;
+    const float y1 = fminf(fmaxf(-(jf * ex), -Nf), Nf);
+    const float y2 = fminf(fmaxf(-(jf * ey), -Nf), 0.f);
+    const float f1 = ceilf(y1 - 0.5f * (float)kSliceW);
+    const float f2 = ceilf(y2 - 0.5f * (float)kSliceW);
+    *x1 = (y1 - f1) - (float)(kSliceW / 2);
+    *x2 = (y2 - f2) - (float)(kSliceW / 2);
+    int a = (int)f1, b = (int)f2;
+    const int lo = slice_lo(N), hi = N / 2 - kSliceW / 2;
+    if (a > hi) a -= N;
+    else if (a < lo) a += N;
+    *conj = b < lo;
+    if (*conj) {
+        b = -(b + N) - (kSliceW - 1);
+        a = -a - (kSliceW - 1);
+        *x1 = -*x1;
+        *x2 = -*x2;
+    }
+    *i1 = a;
+    *i2 = b;
+}
+// Stored row, column and half of the first tap of an upsampled-image target
+// (see slice_up_tap), as slice_tap_rc gives them for plain targets.
+__host__ __device__ inline void slice_up_rc(int j, float ex, float ey, int N, int *row, int *col,
+                                            bool *left)
+{
+    int i1, i2;
+    float x1, x2;
+    bool conj;
+    slice_up_tap(j, ex, ey, N, &i1, &i2, &x1, &x2, &conj);
+    *row = i2 - slice_lo(N);
+    *left = i1 <= 0;
+    *col = *left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1;
+}
 // Tiles of the stored half grid for 128 < L: a target belongs to the tile
 // holding the top-left cell of its W x W footprint; a tile's shared-memory
 // copy is kSliceTileSpan square (the tile and a halo of W - 1), rows
@@ -399,6 +448,35 @@ size_t slice_smem_bytes(int B);
 int slice_batch_of(int L);
 // the grids and the slice samples of one chunk (nh angles): 0 for L <= 128
 size_t slice_scratch_bytes(int L, int B, int nb, int nh);
+
+// Images of side L/2 upsampled 2 x 2 for 128 < L (see slice_up_tap): one CTA
+// of 1024 threads per image holds the L/2 image's grid of N = B/2 points
+// (the L <= 128 layout) and writes rows of B bins, kUpBatch angles per
+// batch.  Tables (device memory, built with the L x L problem's angles):
+//   psi_inv [L/2]  1 / Psi(c - L/4) on the N-point grid (same kernel shape:
+//                  the oversampling N / (L/2) = B / L is unchanged);
+//   fac [nh][N + 1] the L x L problem's fac times
+//                  (1 + e^{-2 pi i t_1}) (1 + e^{-2 pi i t_2}) / 4;
+//   gtab/goff      targets (kk, j), j <= N, per kUpBatch-angle batch as for
+//                  L <= 128 (pairs by slice_up_rc);
+//   tw [N]         e^{-2 pi i q / N} (the grid's FFTs).
+// tw_rows [B] e^{-2 pi i q / B} (the rows' inverse FFTs).  img: [nb][L/2][L/2].
+constexpr int kUpBatch = 32;
+struct SliceUpTables {
+    const float *psi_inv;
+    const float2 *fac;
+    const uint16_t *gtab;
+    const int *goff;
+    const float2 *tw;
+};
+// L even, 128 < L, B/2 a supported L/2 grid, shared memory within a CTA's
+size_t slice_up_smem_bytes(int B);
+bool slice_up_supported(int L, int B);
+cudaError_t launch_project_slice_up(const float *img, int nb, int L, int nh, int B,
+                                    const float2 *cs, const SliceUpTables &up,
+                                    const SliceCoef &coef, const float2 *tw_rows, int clip,
+                                    float *out, int full_n, int32_t *status, cudaStream_t st,
+                                    const float *img2 = nullptr, int nb_first = -1);
 cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int nh, int B,
                                  const float2 *cs, const float *psi_inv, const float2 *fac,
                                  const uint16_t *gtab, const int *goff, const uint32_t *ttab,

@@ -174,7 +174,8 @@ struct SliceArgs {
     const float2 *fac;      // [nh][B/2 + 1] sinc factors times phase
     const uint16_t *gtab;   // target groups per angle batch (see launch_project_slice)
     const int *goff;
-    const float2 *tw;       // [B] e^{-2 pi i q / B}
+    const float2 *tw;       // [B] e^{-2 pi i q / B} (upsampled path: [N], the grid's)
+    const float2 *tw2;      // upsampled path: [2 N] e^{-2 pi i q / (2 N)} (the rows')
     float2 *grid;           // global grids [chunk][rows][S] (128 < L only)
     float2 *xs;             // global slice samples [chunk][nh][B/2 + 1] (128 < L only)
     const uint32_t *ttab;   // target groups per tile (128 < L only)
@@ -348,6 +349,24 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
     }
 }
 
+// Tap weights along each axis from the target's offsets (x1, x2) from its
+// cell: the degree-8 polynomials of the kernel parameters.
+__device__ __forceinline__ void slice_weights(const SliceArgs &A, float x1, float x2,
+                                              float (&wx)[kSliceW], float (&wy)[kSliceW])
+{
+#pragma unroll
+    for (int a = 0; a < kSliceW; ++a) {
+        float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
+#pragma unroll
+        for (int d = kSliceDeg - 1; d >= 0; --d) {
+            px = fmaf(px, x1, A.coef.c[a][d]);
+            py = fmaf(py, x2, A.coef.c[a][d]);
+        }
+        wx[a] = px;
+        wy[a] = py;
+    }
+}
+
 // Weights, first tap and value of slice sample (k, j): the W x W taps of the
 // exponential-of-semicircle kernel around y = -(j / B) e_k N on the grid,
 // times the cell factor fac[k][j].  tap(row, col) returns the grid cell at a
@@ -371,22 +390,52 @@ __device__ __forceinline__ void slice_target(const SliceArgs &A, int k, int j, i
     // offsets from the cell, exact: y - f is in (W/2 - 1, W/2]
     const float x1 = (y1 - f1) - (float)(kSliceW / 2);
     const float x2 = (y2 - f2) - (float)(kSliceW / 2);
-#pragma unroll
-    for (int a = 0; a < kSliceW; ++a) {
-        float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
-#pragma unroll
-        for (int d = kSliceDeg - 1; d >= 0; --d) {
-            px = fmaf(px, x1, A.coef.c[a][d]);
-            py = fmaf(py, x2, A.coef.c[a][d]);
-        }
-        wx[a] = px;
-        wy[a] = py;
-    }
+    slice_weights(A, x1, x2, wx, wy);
     const int i1 = (int)f1;
     row0 = (int)f2 - slice_lo(N);
     // left half: taps at increasing addresses; right half reversed
     left = i1 <= 0;
     col0 = left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1;
+}
+
+// The same for a target of an image of side L/2 seen as L x L (grid of the
+// L/2 image, N = 32 M points; j <= N): the first tap wrapped and folded by
+// slice_up_tap; conj tells that the taps give conj T.
+template <int M>
+__device__ __forceinline__ void slice_target_up(const SliceArgs &A, int k, int j, int &row0,
+                                                int &col0, bool &left, bool &conj,
+                                                float (&wx)[kSliceW], float (&wy)[kSliceW])
+{
+    constexpr int N = 32 * M;
+    const float2 e = __ldg(A.cs + k);
+    int i1, i2;
+    float x1, x2;
+    slice_up_tap(j, e.x, e.y, N, &i1, &i2, &x1, &x2, &conj);
+    slice_weights(A, x1, x2, wx, wy);
+    row0 = i2 - slice_lo(N);
+    left = i1 <= 0;
+    col0 = left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1;
+}
+
+// Plain or upsampled-image target (see slice_target, slice_target_up).
+template <int M, bool UP>
+__device__ __forceinline__ void slice_target_any(const SliceArgs &A, int k, int j, int &row0,
+                                                 int &col0, bool &left, bool &conj,
+                                                 float (&wx)[kSliceW], float (&wy)[kSliceW])
+{
+    if constexpr (UP) {
+        slice_target_up<M>(A, k, j, row0, col0, left, conj, wx, wy);
+    } else {
+        conj = false;
+        slice_target<M>(A, k, j, row0, col0, left, wx, wy);
+    }
+}
+
+// fc * T, or fc * conj(T)
+__device__ __forceinline__ float2 slice_scale(float2 fc, float2 t, bool conj)
+{
+    if (conj) t.y = -t.y;
+    return make_float2(fc.x * t.x - fc.y * t.y, fc.x * t.y + fc.y * t.x);
 }
 
 // sum_b wy[b] sum_a wx[a] g[b S + a da], complex, times fac
@@ -460,16 +509,16 @@ __device__ __forceinline__ void pair_taps(const float2 *__restrict__ g, int S, i
 // both, against 162 reads for two separate samples.  The footprints' offsets
 // in the box select one of nine compile-time tap patterns; the host groups
 // the pairs so that every warp takes one pattern.
-template <int M>
+template <int M, bool UP>
 __device__ __forceinline__ void slice_pair(const SliceArgs &A, const float2 *G, int S, int k,
                                            int j, float2 &outA, float2 &outB)
 {
     constexpr int W = kSliceW;
     float wxA[W], wyA[W], wxB[W], wyB[W];
     int rA, cA, rB, cB;
-    bool lA, lB;
-    slice_target<M>(A, k, j, rA, cA, lA, wxA, wyA);
-    slice_target<M>(A, k, j + 1, rB, cB, lB, wxB, wyB);
+    bool lA, lB, zA, zB;
+    slice_target_any<M, UP>(A, k, j, rA, cA, lA, zA, wxA, wyA);
+    slice_target_any<M, UP>(A, k, j + 1, rB, cB, lB, zB, wxB, wyB);
     const int da = lA ? 1 : -1;  // both in the same half (host-checked)
     const int r0 = min(rA, rB);
     const int c0 = lA ? min(cA, cB) : max(cA, cB);
@@ -494,23 +543,25 @@ __device__ __forceinline__ void slice_pair(const SliceArgs &A, const float2 *G, 
         default: pair_taps<0, 1, 0, 1>(g, S, da, wxA, wyA, wxB, wyB, tA, tB); break;
     }
 #undef SW_PAIR_CASE
-    const int nj = 16 * M + 1;
+    const int nj = (UP ? 32 : 16) * M + 1;
     const float2 fa = __ldg(A.fac + (size_t)k * nj + j), fb = __ldg(A.fac + (size_t)k * nj + j + 1);
-    outA = make_float2(fa.x * tA.x - fa.y * tA.y, fa.x * tA.y + fa.y * tA.x);
-    outB = make_float2(fb.x * tB.x - fb.y * tB.y, fb.x * tB.y + fb.y * tB.x);
+    outA = slice_scale(fa, tA, zA);
+    outB = slice_scale(fb, tB, zB);
 }
 
 // Phase C for the angles [k0, k0 + BATCH) of the grid G (shared memory):
 // the slice samples into Xs [BATCH][B/2 + 1]; ends with a block barrier.
-// An entry with kSlicePairBit set computes the pair (j, j + 1).
-template <int M, int BATCH>
+// An entry with kSlicePairBit set computes the pair (j, j + 1).  UP: G is
+// the grid of an image of side L/2 (N = 32 M = B/2 points), the samples
+// j <= N those of its 2 x 2 upsampled image (slice_target_up).
+template <int M, int BATCH, bool UP = false>
 __device__ __forceinline__ void slice_samples(const SliceArgs &A, const float2 *G, float2 *Xs,
                                               int k0, int bi)
 {
     constexpr int N = 32 * M;
     const int nh = A.nh;
     const int S = slice_stride(N);
-    const int nj = N / 2 + 1;
+    const int nj = (UP ? N : N / 2) + 1;
     // rows of angles beyond nh (last batch) read as zero
     for (int it = threadIdx.x + (nh - k0) * nj; it < BATCH * nj; it += blockDim.x)
         Xs[it] = make_float2(0.f, 0.f);
@@ -522,17 +573,21 @@ __device__ __forceinline__ void slice_samples(const SliceArgs &A, const float2 *
         const int k = k0 + kk;
         if (ent & kSlicePairBit) {
             float2 xa, xb;
-            slice_pair<M>(A, G, S, k, j, xa, xb);
+            slice_pair<M, UP>(A, G, S, k, j, xa, xb);
             Xs[kk * nj + j] = xa;
             Xs[kk * nj + j + 1] = xb;
             continue;
         }
         float wx[kSliceW], wy[kSliceW];
         int row0, col0;
-        bool left;
-        slice_target<M>(A, k, j, row0, col0, left, wx, wy);
-        Xs[kk * nj + j] = slice_sum(G + row0 * S + col0, S, left ? 1 : -1, wx, wy,
-                                    __ldg(A.fac + (size_t)k * nj + j));
+        bool left, conj;
+        slice_target_any<M, UP>(A, k, j, row0, col0, left, conj, wx, wy);
+        float2 fc = __ldg(A.fac + (size_t)k * nj + j);
+        // fc conj(T) = conj(conj(fc) T)
+        if (conj) fc.y = -fc.y;
+        float2 x = slice_sum(G + row0 * S + col0, S, left ? 1 : -1, wx, wy, fc);
+        if (conj) x.y = -x.y;
+        Xs[kk * nj + j] = x;
     }
     __syncthreads();
 }
@@ -553,7 +608,7 @@ __device__ __forceinline__ void slice_rows_out(const SliceArgs &A, float2 *Xs, c
     // batch as Y_j = X_a + i X_b, Y_{B-j} = conj X_a + i conj X_b
     // (Y_0, Y_{B/2}: real parts), then writes both rows
     const int ka = 2 * warp;
-    if (k0 + ka < nh) {
+    if (ka < BATCH && k0 + ka < nh) {
         const float2 *Xa = Xs + ka * nj, *Xb = Xa + nj;
         float2 v[M];
 #pragma unroll
@@ -625,6 +680,44 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice(SliceArgs A)
     for (int k0 = 0; k0 < A.nh; k0 += kSliceBatch) {
         slice_samples<M, kSliceBatch>(A, G, Xs, k0, k0 / kSliceBatch);
         slice_rows_out<M, kSliceBatch>(A, Xs, tw, gi, k0, warp, lane);
+    }
+}
+
+// Images of side L/2 upsampled 2 x 2 (128 < L): one CTA per image with the
+// grid of the L/2 image (N = 32 MG = B/2 points, A.L = A.srcL = L/2) in
+// shared memory, the slice samples j <= N of the L x L image from it in
+// kUpBatch-angle batches (slice_samples<UP>), and rows of B = 2 N bins.
+template <int MG>
+__global__ void __launch_bounds__(kSliceThreads, 1) k_project_slice_up(SliceArgs A)
+{
+    constexpr int N = 32 * MG;
+    constexpr int nj = N + 1;
+    extern __shared__ float2 sms[];
+    float2 *G = sms;                                        // [rows][S] grid
+    float2 *Xs = G + slice_rows(N) * slice_stride(N);       // [kUpBatch][nj]
+    float2 *tw = Xs + kUpBatch * nj;                        // [N]
+    float2 *tw2 = tw + N;                                   // [2 N]
+    __shared__ int s_bad, s_mass;
+    const int gi = A.img_off + blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_mass = 0;
+        if (A.pf_ahead > 0 && blockIdx.x + A.pf_ahead < gridDim.x)
+            prefetch_l2(image_of(A, gi + A.pf_ahead), sizeof(float) * A.srcL * A.srcL);
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = A.tw[i];
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) tw2[i] = A.tw2[i];
+    __syncthreads();
+    int bad = 0, mass = 0;
+    slice_grid<MG>(A, image_of(A, gi), G, tw, warp, kSliceThreads / 32, lane, bad, mass);
+    if (bad) atomicOr(&s_bad, 1);
+    if (mass) atomicOr(&s_mass, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) A.status[gi] = (s_bad || !s_mass) ? 1 : 0;
+    for (int k0 = 0; k0 < A.nh; k0 += kUpBatch) {
+        slice_samples<MG, kUpBatch, true>(A, G, Xs, k0, k0 / kUpBatch);
+        slice_rows_out<2 * MG, kUpBatch>(A, Xs, tw2, gi, k0, warp, lane);
     }
 }
 
@@ -732,6 +825,21 @@ cudaError_t launch_small(SliceArgs a, int nb, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int MG>
+cudaError_t launch_up(SliceArgs a, int nb, cudaStream_t st)
+{
+    const size_t smem = slice_up_smem_bytes(64 * MG);
+    cudaError_t e = cudaFuncSetAttribute(k_project_slice_up<MG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        a.pf_ahead = sms;
+    k_project_slice_up<MG><<<nb, kSliceThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int M>
 cudaError_t launch_big(SliceArgs a, int nb, int chunk, cudaStream_t st)
 {
@@ -784,6 +892,19 @@ size_t slice_smem_bytes(int B)
 
 int slice_batch_of(int L) { return L <= 128 ? kSliceBatch : kBigBatch; }
 
+size_t slice_up_smem_bytes(int B)
+{
+    const int N = B / 2;
+    return sizeof(float2) * ((size_t)slice_rows(N) * slice_stride(N) +
+                             (size_t)kUpBatch * (N + 1) + 3 * (size_t)N);
+}
+
+bool slice_up_supported(int L, int B)
+{
+    return L > 128 && (L & 1) == 0 && slice_bins_supported(L, B) && (B / 2) % 32 == 0 &&
+           slice_bins_supported(L / 2, B / 2) && slice_up_smem_bytes(B) <= kSliceSmemMax;
+}
+
 size_t slice_scratch_bytes(int L, int B, int nb, int nh)
 {
     if (L <= 128) return 0;
@@ -815,6 +936,7 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     a.gtab = gtab;
     a.goff = goff;
     a.tw = tw;
+    a.tw2 = nullptr;
     a.grid = scratch;
     a.xs = scratch ? scratch + (size_t)slice_rows(B) * slice_stride(B) * std::min(nb, kSliceChunk)
                    : nullptr;
@@ -842,6 +964,49 @@ cudaError_t launch_project_slice(const float *img, int nb, int L, int srcL, int 
     case 4: return launch_small<4>(a, nb, st);
     case 5: return launch_small<5>(a, nb, st);
     case 6: return launch_small<6>(a, nb, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_project_slice_up(const float *img, int nb, int L, int nh, int B,
+                                    const float2 *cs, const SliceUpTables &up,
+                                    const SliceCoef &coef, const float2 *tw_rows, int clip,
+                                    float *out, int full_n, int32_t *status, cudaStream_t st,
+                                    const float *img2, int nb_first)
+{
+    if (nb <= 0) return cudaSuccess;
+    if (!slice_up_supported(L, B) || !up.psi_inv || !up.fac || !up.gtab || !up.goff || !up.tw ||
+        !tw_rows)
+        return cudaErrorInvalidValue;
+    SliceArgs a{};
+    a.img = img;
+    a.img2 = img2 ? img2 : img;
+    a.nb1 = (img2 && nb_first >= 0) ? nb_first : nb;
+    a.img_off = 0;
+    a.pf_ahead = 0;
+    a.L = L / 2;
+    a.srcL = L / 2;
+    a.nh = nh;
+    a.coef = coef;
+    a.fac = up.fac;
+    a.gtab = up.gtab;
+    a.goff = up.goff;
+    a.tw = up.tw;
+    a.tw2 = tw_rows;
+    a.grid = nullptr;
+    a.xs = nullptr;
+    a.ttab = nullptr;
+    a.toff = nullptr;
+    a.clip = clip;
+    a.full_n = full_n;
+    a.cs = cs;
+    a.psi_inv = up.psi_inv;
+    a.out = out;
+    a.status = status;
+    switch (B / 64) {
+    case 4: return launch_up<4>(a, nb, st);
+    case 5: return launch_up<5>(a, nb, st);
+    case 6: return launch_up<6>(a, nb, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -94,6 +94,7 @@ EXPORTS = (
     "sw_bank_size", "sw_bank_destroy", "sw_profile", "sw_profile_read", "sw_launch_count",
     "sw_align_all_rotations_noalloc", "sw_bank_workspace_bytes", "sw_autotune",
     "sw_autotune_get", "sw_set_wait_limit", "sw_set_correlation_stall", "sw_measure_fp32_fma",
+    "sw_project_upsampled",
 )
 STAGES = ("project", "quantile", "spectrum", "corr", "decide", "best", "ramp")
 
@@ -114,6 +115,7 @@ def load(path: str | None = None):
                 "sw_batch_workspace_bytes": ([P, ci, ci], ctypes.c_size_t),
                 "sw_reserve": ([vp, P, ci, ci], ci),
                 "sw_project": ([vp, P, vp, ci, vp, vp, vp], ci),
+                "sw_project_upsampled": ([vp, P, vp, ci, vp, vp], ci),
                 "sw_quantiles": ([vp, P, vp, ci, vp, vp, vp, vp], ci),
                 "sw_align_all_rotations": ([vp, P, vp, vp, vp, vp, vp, vp], ci),
                 "sw_align_batch": ([vp, P, vp, ci, vp, ci, ci, vp, vp], ci),
@@ -251,6 +253,21 @@ class Aligner:
         self.call("sw_project", ctypes.byref(params), _ptr(x), nb, _ptr(out), _ptr(sc),
                   _stream(stream))
         return (out, sc) if scale else out
+
+    def project_upsampled(self, imgs, params: Params, out=None, stream=None):
+        """Projection rows [nb][n][B] of images of side L/2 upsampled 2 x 2
+        (each pixel split into four cells of a quarter of its value)."""
+        import torch
+        x = _f32(imgs, self.torch_device)
+        nb = x.shape[0]
+        if x.shape[-1] * 2 != params.L:
+            raise ValueError(f"images of side {x.shape[-1]}: want L/2 = {params.L // 2}")
+        B = bins_of(params)
+        if out is None:
+            out = torch.empty((nb, params.n_theta, B), dtype=torch.float32, device=x.device)
+        self.call("sw_project_upsampled", ctypes.byref(params), _ptr(x), nb, _ptr(out),
+                  _stream(stream))
+        return out
 
     def quantiles(self, proj, params: Params, stream=None):
         import torch

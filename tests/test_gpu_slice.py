@@ -254,22 +254,85 @@ def test_slice_global_grid_batch_on_gpu_rows(al):
         assert check_argmin(l, lref, Dref, d2_tol(Dref[lref], Sc))
 
 
-def test_slice_bank_256_with_half_size_queries_equals_batch(al):
-    # the serving setting: a bank at 256^2 and queries at 128^2 upsampled 2 x 2
+def upsample2(x):
+    return np.ascontiguousarray(np.repeat(np.repeat(x, 2, axis=-2), 2, axis=-1) * 0.25)
+
+
+@pytest.mark.parametrize("L,n", [(160, 10), (192, 8), (256, 12), (256, 20)])
+def test_slice_upsampled_rows_match_oracle(al, L, n):
+    # images of side L/2 through their own grid of B/2 points (128 < L): the
+    # rows of the 2 x 2 upsampled image within the row bar, every target
+    # wrapped into the half grid's period and folded by T(-s) = conj T(s)
+    rng = np.random.default_rng(L * 3 + n)
+    qh = blobs(rng, 2, L // 2)
+    qh[1] -= 0.2 * qh[1].max()  # negative pixels are clipped to 0 on load
+    p = params(L, n, 8)
+    B = swalign.bins_of(p)
+    n0 = al.launch_count()
+    got = al.project_upsampled(qh, p).cpu().numpy().astype(np.float64)
+    assert al.launch_count() - n0 == 1  # one CTA per image on the L/2 grid
+    qu = upsample2(qh)
+    tol = row_tol(L, B)
+    plain = al.project(qu, p).cpu().numpy().astype(np.float64)
+    for i in range(len(qh)):
+        mass = np.maximum(qu[i].astype(np.float64), 0).sum()
+        ref = ref_rows(qu[i], n, B, clip=True) * mass
+        err = np.linalg.norm(got[i] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() <= tol, (i, err.max(), tol)
+        np.testing.assert_array_equal(got[i, n // 2:], got[i, :n // 2, ::-1])
+        assert got[i].min() >= 0.0
+        # the L x L grid's rows of the upsampled image: both within the bar
+        dif = np.linalg.norm(got[i] - plain[i], axis=1) / np.linalg.norm(ref, axis=1)
+        assert dif.max() <= 2 * tol
+
+
+def test_slice_upsampled_query_status(al):
+    # a query of side L/2 with no mass or with a non-finite pixel is unusable
+    rng = np.random.default_rng(98)
+    L, n, M = 256, 8, 8
+    t = blobs(rng, 2, L)
+    qh = blobs(rng, 3, L // 2)
+    qh[1] = 0.0
+    qh[2, 3, 3] = np.inf
+    bank = swalign.Bank(al, t, params(L, n, M))
+    try:
+        a = swalign.results_to_numpy(bank.align(qh, q_L=L // 2)).reshape(3, 2)
+    finally:
+        bank.close()
+    assert np.all(a[0]["status"] == 0) and np.all(np.isfinite(a[0]["d2"]))
+    assert np.all(a[1]["status"] == 1) and np.all(a[2]["status"] == 1)
+
+
+def test_slice_bank_256_with_half_size_queries(al):
+    # the serving setting: a bank at 256^2 and queries at 128^2 upsampled
+    # 2 x 2; the pipeline after the rows at the FP32 bar on the GPU's own rows
     rng = np.random.default_rng(97)
     L, n, M = 256, 36, 32
     t = blobs(rng, 5, L)
     qh = blobs(rng, 3, L // 2)
-    qu = np.ascontiguousarray(np.repeat(np.repeat(qh, 2, axis=1), 2, axis=2) * 0.25)
     p = params(L, n, M)
     bank = swalign.Bank(al, t, p)
     try:
-        a = swalign.results_to_numpy(bank.align(qh, q_L=L // 2))
+        a = swalign.results_to_numpy(bank.align(qh, q_L=L // 2)).reshape(3, 5)
+        best = swalign.results_to_numpy(bank.align(qh, q_L=L // 2, mode=1))
     finally:
         bank.close()
-    b = swalign.results_to_numpy(al.align_batch(qu, t, p))
-    np.testing.assert_array_equal(a["best_l"], b["best_l"])
-    np.testing.assert_allclose(a["d2"], b["d2"], rtol=1e-9, atol=1e-12)
+    rq = al.project_upsampled(qh, p).cpu().numpy().astype(np.float64)
+    rt = al.project(t, p).cpu().numpy().astype(np.float64)
+    for i in range(3):
+        dmin = []
+        for j in range(5):
+            Dref, Sref, Sc = curve_from_rows(rq[i], rt[j], 2.0 / L, M, 1)
+            gr = a[i, j]
+            l = int(gr["best_l"])
+            assert gr["status"] == 0 and gr["template_index"] == j
+            assert abs(gr["d2"] - Dref[l]) <= d2_tol(Dref[l], Sc), (i, j)
+            np.testing.assert_allclose(gr["shift"], Sref[l], rtol=0, atol=1e-6)
+            lref = int(np.argmin(Dref))
+            assert check_argmin(l, lref, Dref, d2_tol(Dref[lref], Sc))
+            dmin.append(gr["d2"])
+        assert best[i]["template_index"] == int(np.argmin(dmin))
+        assert best[i]["d2"] == min(dmin)
 
 
 def test_slice_status_flags(al):
