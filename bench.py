@@ -678,6 +678,64 @@ def main():
     if args.metric == "sw2":
         keep_sample(args.precision)
 
+    # ---- end to end: pinned host inputs -> device -> results back, per step.
+    # Every step copies its inputs in and its results out inside the timed
+    # region; two buffer sets let step k+1's upload and step k-1's download run
+    # on copy streams while step k computes (the order a serving loop uses).
+    # Measured right after the device-resident steps, before the variants
+    # heat the GPU, with its own clock samples.
+    e2e = None
+    if not args.no_e2e:
+        cs_in, cs_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        qb = [q_d, torch.empty_like(q_d)]
+        tb = [t_d, torch.empty_like(t_d)]
+        ob = [out, torch.empty_like(out)]
+        oh = [torch.empty((nq * nt, 40), dtype=torch.uint8).pin_memory() for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_comp = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+
+        def pipeline(nsteps):
+            for k in range(nsteps):
+                b = k % 2
+                with torch.cuda.stream(cs_in):
+                    if k >= 2:
+                        cs_in.wait_event(ev_comp[b])  # step k-2 has read these inputs
+                    qb[b].copy_(q_h, non_blocking=True)
+                    tb[b].copy_(t_h, non_blocking=True)
+                    ev_in[b].record(cs_in)
+                stream.wait_event(ev_in[b])
+                if k >= 2:
+                    stream.wait_event(ev_out[b])      # step k-2's results are out
+                al.align_batch(qb[b], tb[b], p, out=ob[b], stream=stream)
+                ev_comp[b].record(stream)
+                with torch.cuda.stream(cs_out):
+                    cs_out.wait_event(ev_comp[b])
+                    oh[b].copy_(ob[b], non_blocking=True)
+                    ev_out[b].record(cs_out)
+            return ev_out[(nsteps - 1) % 2]
+
+        pipeline(2)
+        torch.cuda.synchronize()
+        barrier(world)
+        with ClockSampler(local) as clk_e2e:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            cs_in.wait_stream(stream)
+            last = pipeline(args.steps)
+            cs_out.wait_event(last)
+            e1.record(cs_out)
+            e1.synchronize()
+        torch.cuda.synchronize()
+        assert torch.equal(oh[(args.steps - 1) % 2], ob[(args.steps - 1) % 2].cpu())
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        e2e = {"value": total_pairs / (ms_e2e / 1e3), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(q_h.numel() * 4 + t_h.numel() * 4),
+               "d2h_bytes_per_step": int(oh[0].numel()),
+               "pipeline": "inputs of step k+1 uploaded and results of step k-1 read back "
+                           "on copy streams while step k computes (two buffer sets)",
+               "clocks": clk_e2e.summary()}
+
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
     variants = {}
     if args.precision == "fp32" and args.metric == "sw2" and not args.no_variants:
@@ -728,59 +786,6 @@ def main():
                          "algorithmic_flops_per_launch": flops},
             }
         al.reserve(p, nq, nt)
-
-    # ---- end to end: pinned host inputs -> device -> results back, per step.
-    # Every step copies its inputs in and its results out inside the timed
-    # region; two buffer sets let step k+1's upload and step k-1's download run
-    # on copy streams while step k computes (the order a serving loop uses).
-    e2e = None
-    if not args.no_e2e:
-        cs_in, cs_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        qb = [q_d, torch.empty_like(q_d)]
-        tb = [t_d, torch.empty_like(t_d)]
-        ob = [out, torch.empty_like(out)]
-        oh = [torch.empty((nq * nt, 40), dtype=torch.uint8).pin_memory() for _ in range(2)]
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_comp = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-
-        def pipeline(nsteps):
-            for k in range(nsteps):
-                b = k % 2
-                with torch.cuda.stream(cs_in):
-                    if k >= 2:
-                        cs_in.wait_event(ev_comp[b])  # step k-2 has read these inputs
-                    qb[b].copy_(q_h, non_blocking=True)
-                    tb[b].copy_(t_h, non_blocking=True)
-                    ev_in[b].record(cs_in)
-                stream.wait_event(ev_in[b])
-                if k >= 2:
-                    stream.wait_event(ev_out[b])      # step k-2's results are out
-                al.align_batch(qb[b], tb[b], p, out=ob[b], stream=stream)
-                ev_comp[b].record(stream)
-                with torch.cuda.stream(cs_out):
-                    cs_out.wait_event(ev_comp[b])
-                    oh[b].copy_(ob[b], non_blocking=True)
-                    ev_out[b].record(cs_out)
-            return ev_out[(nsteps - 1) % 2]
-
-        pipeline(2)
-        torch.cuda.synchronize()
-        barrier(world)
-        e0.record(stream)
-        cs_in.wait_stream(stream)
-        last = pipeline(args.steps)
-        cs_out.wait_event(last)
-        e1.record(cs_out)
-        e1.synchronize()
-        torch.cuda.synchronize()
-        assert torch.equal(oh[(args.steps - 1) % 2], ob[(args.steps - 1) % 2].cpu())
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
-        e2e = {"value": total_pairs / (ms_e2e / 1e3), "unit": "pairs/s",
-               "h2d_bytes_per_step": int(q_h.numel() * 4 + t_h.numel() * 4),
-               "d2h_bytes_per_step": int(oh[0].numel()),
-               "pipeline": "inputs of step k+1 uploaded and results of step k-1 read back "
-                           "on copy streams while step k computes (two buffer sets)"}
 
     if rank != 0:
         return
