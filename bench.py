@@ -102,6 +102,8 @@ def parse():
                     help="serving: most images per batch (larger requests are split)")
     ap.add_argument("--serve-only", action="store_true",
                     help="profiling runs only: print the serving block alone")
+    ap.add_argument("--uneven-only", action="store_true",
+                    help="profiling runs only: print the uneven-batch block alone")
     ap.add_argument("--nq", type=int, default=NQ, help="queries (profiling runs only)")
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
     ap.add_argument("--project-L", type=int, default=0,
@@ -367,11 +369,15 @@ def uneven_block(args, device):
     eagerly for comparison."""
     import torch
 
+    import tempfile
+
     from paper_2503_13756_gb300 import synth, uneven
     batch = synth.uneven_batch()
+    # one tuning cache for both graphs below: the same launch shapes in each
+    tune_cache = os.path.join(tempfile.mkdtemp(prefix="swtune"), "tune.txt")
     g = uneven.UnevenGraph(uneven.buckets_from(batch, 256, "bf16", device,
                                                projector=args.projector), mode=0,
-                           device=device, autotune=not args.no_autotune)
+                           device=device, autotune=not args.no_autotune, cache_path=tune_cache)
     try:
         st = g.stream
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -395,10 +401,29 @@ def uneven_block(args, device):
         ok = all(bool(np.all(r["status"] == 0)) for r in res.values())
         stages = {int(k): {s_: round(v, 4) for s_, v in d.items()}
                   for k, d in g.stage_times().items()}
+        # the same sizes back to back on one stream (one branch), for comparison
+        gs = uneven.UnevenGraph(g.buckets, mode=0, device=device, concurrent=False,
+                                autotune=not args.no_autotune, cache_path=tune_cache)
+        try:
+            for _ in range(2):
+                gs.replay()
+            gs.stream.synchronize()
+            e0.record(gs.stream)
+            for _ in range(reps):
+                gs.replay()
+            e1.record(gs.stream)
+            e1.synchronize()
+            ms_seq = e0.elapsed_time(e1) / reps
+            same = all(np.array_equal(gs.results()[L]["d2"], res[L]["d2"]) for L in res)
+        finally:
+            gs.close()
         return {"workload": "uneven 20,000 queries, L in {64,96,128,192,256}, 64 templates per L, "
                             "n=256, M=L, BF16 GEMM, one CUDA graph",
                 "projector": PROJECTOR_NAMES[args.projector],
                 "pairs": g.pairs, "ms_per_graph": ms_graph, "pairs_per_s": g.pairs / (ms_graph / 1e3),
+                "graph": "one branch per size (own context and stream), forked and joined "
+                         "inside the graph",
+                "sequential_ms_per_graph": ms_seq, "sequential_results_identical": bool(same),
                 "eager_ms": ms_eager, "kernels_per_graph": g.launches_per_replay,
                 "queries_per_L": {int(b.L): int(b.queries.shape[0]) for b in g.buckets},
                 "stages_ms_per_L": stages,
@@ -608,6 +633,9 @@ def main():
         return
     if args.serve_only:
         print(json.dumps({"serving": serving_block(args, local)}), flush=True)
+        return
+    if args.uneven_only:
+        print(json.dumps({"uneven": uneven_block(args, local)}), flush=True)
         return
     import torch
 

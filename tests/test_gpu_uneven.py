@@ -51,9 +51,12 @@ def check_sampled(batch, res, picks_per_L, rng):
     assert near >= 0.95 * total, (near, total)
 
 
-def test_graph_replay_equals_eager_calls_and_oracle():
+@pytest.mark.parametrize("concurrent", [True, False])
+def test_graph_replay_equals_eager_calls_and_oracle(concurrent):
+    # concurrent: one branch (context and stream) per size inside the graph
     batch = synth.uneven_batch(n_queries=150, n_templates_per_L=6)
-    g = uneven.UnevenGraph(uneven.buckets_from(batch, N_THETA, "bf16"), mode=0)
+    g = uneven.UnevenGraph(uneven.buckets_from(batch, N_THETA, "bf16"), mode=0,
+                           concurrent=concurrent)
     try:
         assert g.launches_per_replay == 5 * 5  # five kernels per size, all in the graph
         for b in g.buckets:
