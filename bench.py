@@ -108,7 +108,11 @@ def parse():
     ap.add_argument("--nt", type=int, default=NT, help="templates (profiling runs only)")
     ap.add_argument("--project-L", type=int, default=0,
                     help="profiling runs only: time the projection of 512 synthetic images of "
-                         "this size (n = 256) and print one line")
+                         "this size and print one line")
+    ap.add_argument("--project-n", type=int, default=256,
+                    help="profiling runs only: angles of --project-L")
+    ap.add_argument("--project-half", action="store_true",
+                    help="profiling runs only: --project-L on images of side L/2 upsampled 2 x 2")
     return ap.parse_args()
 
 
@@ -595,7 +599,9 @@ def run_reference(args, world, rank):
 
 def project_only(args):
     """Profiling aid: the projector alone on 512 blob-mixture images of side
-    --project-L (n = 256, M = 128), 2 warm-up and 5 timed calls."""
+    --project-L (n = --project-n, M = 128), 2 warm-up and 5 timed calls.
+    With --project-half the images are summed 2 x 2 to side L/2 and projected
+    as their 2 x 2 upsampled L x L images (sw_project_upsampled)."""
     import torch
 
     from paper_2503_13756_gb300 import swalign, synth
@@ -604,19 +610,24 @@ def project_only(args):
     rng = np.random.default_rng(synth.SEED_BASE + 7)
     imgs = np.ascontiguousarray(synth.render(synth.draw_mixtures(rng, 512, Lp, ncomp=(2, 4)), Lp),
                                 dtype=np.float32)
-    pa = swalign.make_params(Lp, N_THETA, M_LEVELS, projector=args.projector)
+    if args.project_half:
+        imgs = np.ascontiguousarray(
+            imgs.reshape(512, Lp // 2, 2, Lp // 2, 2).sum(axis=(2, 4)), dtype=np.float32)
+    pa = swalign.make_params(Lp, args.project_n, M_LEVELS, projector=args.projector)
     x = torch.from_numpy(imgs).cuda()
+    run = al.project_upsampled if args.project_half else al.project
     for _ in range(2):
-        al.project(x, pa)
+        run(x, pa)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(5):
-        al.project(x, pa)
+        run(x, pa)
     e1.record()
     e1.synchronize()
     us = e0.elapsed_time(e1) / 5 / 512 * 1e3
-    print(json.dumps({"profile": "projection only", "L": Lp, "projector": args.projector,
+    print(json.dumps({"profile": "projection only", "L": Lp, "n": args.project_n,
+                      "half_size": bool(args.project_half), "projector": args.projector,
                       "images": 512, "us_per_image": us}), flush=True)
 
 
