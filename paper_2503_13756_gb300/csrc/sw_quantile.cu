@@ -20,6 +20,19 @@ namespace swk {
 namespace {
 
 constexpr int kQThreads = 256;  // 8 warps
+
+// a + b for double-floats of non-negative value (every partial sum of a
+// projection row): TwoSum of the leading parts, then the tails, then a
+// Fast2Sum renormalisation -- exact, since without cancellation the tail
+// sum is below an ulp and a half of the leading sum, which Fast2Sum needs.
+// The same (hi, lo) as df_add with its second TwoSum, in three fewer flops.
+__device__ __forceinline__ DF df_add_nonneg(DF a, DF b)
+{
+    const DF s = df_two_sum(a.hi, b.hi);
+    const float e = s.lo + (a.lo + b.lo);
+    const float hi = s.hi + e;
+    return {hi, e - (hi - s.hi)};
+}
 constexpr int kQRows = 4;       // projections per warp: the next is staged while one is computed
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src)
@@ -76,7 +89,7 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
         const int C = (B + 31) / 32;
         const int c0 = min(B, lane * C), c1 = min(B, c0 + C);
         DF s = {0.f, 0.f};
-        for (int b = c0; b < c1; ++b) s = df_add(s, DF{U[b], 0.f});
+        for (int b = c0; b < c1; ++b) s = df_add_nonneg(s, DF{U[b], 0.f});
         // inclusive warp scan of the lane sums
         DF inc = s;
 #pragma unroll
@@ -84,7 +97,7 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
             DF o;
             o.hi = __shfl_up_sync(0xffffffffu, inc.hi, off);
             o.lo = __shfl_up_sync(0xffffffffu, inc.lo, off);
-            if (lane >= off) inc = df_add(o, inc);
+            if (lane >= off) inc = df_add_nonneg(o, inc);
         }
         DF run;
         run.hi = __shfl_up_sync(0xffffffffu, inc.hi, 1);
@@ -94,7 +107,7 @@ k_quantiles(const float *__restrict__ proj, int n, int B, int M, float h, int le
             F[0] = make_float2(0.f, 0.f);
         }
         for (int b = c0; b < c1; ++b) {
-            run = df_add(run, DF{U[b], 0.f});
+            run = df_add_nonneg(run, DF{U[b], 0.f});
             F[b + 1] = make_float2(run.hi, run.lo);
         }
         __syncwarp();

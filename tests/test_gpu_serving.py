@@ -131,3 +131,33 @@ def test_serving_memory_admission_limits_batches():
         assert stats["mean_batch_images"] <= eng.max_batch
     finally:
         eng.close()
+
+
+def test_serving_256_bank_half_size_queries_alone_equal_the_mix():
+    # the serving setting's shapes: a bank at 256^2 with queries at 128^2
+    # (projected on their own grid) and at 256^2, batched by the engine across
+    # slots; every image is computed on its own, so a request's results in
+    # the mix are bitwise those of the request alone
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(16)
+    L, n, M = 256, 36, 32
+    bank = synth.serving_bank(n_templates=20, L=L, seed=rng)
+    pool = synth.serving_pool(bank, pool_size=24, seed=rng, max_shift_px=4, warp_amp_px=1.0)
+    sched = synth.serving_schedule(16, rate_hz=4000.0, max_images=24, Lb=L, seed=rng)
+    reqs = serving.make_requests(pool, sched)
+    assert {r.images.shape[-1] for r in reqs} == {L, L // 2}
+    p = swalign.make_params(L, n, M, precision="bf16", projector="slice")
+    eng = serving.ServingEngine(bank["templates"], p, n_slots=3, max_batch_images=32)
+    try:
+        eng.run(reqs, realtime=False)
+        for r in reqs:
+            alone = swalign.results_to_numpy(
+                eng.bank.align(r.images, q_L=r.images.shape[-1], mode=1))
+            assert np.all(alone["status"] == 0)
+            assert alone.tobytes() == r.results.tobytes()
+        hits = np.mean(np.concatenate(
+            [r.results["template_index"].astype(int) == r.source for r in reqs]))
+        assert hits > 0.9
+    finally:
+        eng.close()
