@@ -432,6 +432,99 @@ __device__ __forceinline__ void reg_ifft(float2 (&v)[MW], const float2 *__restri
     for (int k1 = 0; k1 < MW; ++k1) v[k1] = a[k1];
 }
 
+// Unnormalised inverse DFT of length n = 30 MW (MW even, at most 16) held by
+// lanes 0..29 of a warp, X(q) = sum_t x(t) e^{+2 pi i t q / n}.  In: v[t1] =
+// x(30 t1 + lane).  Out: v[k1] = X(k1 + MW q2(lane)), q2 = lane30_q(lane).
+// tw[q] = e^{-2 pi i q / n}.  Four-step as reg_ifft: an MW-point mixed-radix
+// DFT over t1 in each lane, the twiddles e^{+2 pi i lane k1 / n}, and a
+// 30-point transform over the lanes in three decimation-in-frequency stages
+// (radix 2 over lanes 15 apart, radix 3 over lanes 5 apart in each block of
+// 15, radix 5 over adjacent lanes in each block of 5): the lane u + S m of a
+// stage of radix r and span S keeps its own output digit m,
+//   z = e^{+2 pi i u m / (r S)} sum_j y(u + S j) e^{+2 pi i j m / r},
+// so lane m3 + 5 m2 + 15 m ends with the output q2 = m + 2 m2 + 6 m3.
+// Lanes 30 and 31 compute nothing of use (they read their own values).
+__device__ __forceinline__ int lane30_q(int lane)
+{
+    return lane / 15 + 2 * ((lane % 15) / 5) + 6 * (lane % 5);
+}
+__device__ __forceinline__ int lane30_of_q(int q)
+{
+    return (q / 6) + 5 * ((q / 2) % 3) + 15 * (q % 2);
+}
+// e^{+2 pi i x / r} from the n-point table (r divides n, 0 <= x < r)
+__device__ __forceinline__ float2 root_of(const float2 *tw, int x, int r, int n)
+{
+    return cconj(tw[x * (n / r)]);
+}
+template <int MW>
+__device__ __forceinline__ void reg_ifft30(float2 (&v)[MW], const float2 *__restrict__ tw, int lane)
+{
+    constexpr int n = 30 * MW;
+    lane_dft<MW, 30>(v, tw);
+    const int ln = lane < 30 ? lane : 0;
+#pragma unroll
+    for (int k1 = 1; k1 < MW; ++k1) v[k1] = cmul(v[k1], cconj(tw[ln * k1]));
+    // radix 2, span 15: lane u + 15 m
+    {
+        const int m = ln / 15, u = ln % 15;
+        const int src = lane < 30 ? (m ? lane - 15 : lane + 15) : lane;
+        const float2 w = root_of(tw, u * m, 30, n);
+#pragma unroll
+        for (int k1 = 0; k1 < MW; ++k1) {
+            const float2 o = make_float2(__shfl_sync(0xffffffffu, v[k1].x, src),
+                                         __shfl_sync(0xffffffffu, v[k1].y, src));
+            // m = 0: y0 + y1 (own + other); m = 1: y0 - y1 (other - own)
+            const float2 z = m ? csub(o, v[k1]) : cadd(v[k1], o);
+            v[k1] = m ? cmul(z, w) : z;
+        }
+    }
+    // radix 3, span 5, in blocks of 15: lane b + v + 5 m2
+    {
+        const int b = ln - ln % 15, u = ln % 15, m2 = u / 5, vv = u % 5;
+        const int s1 = lane < 30 ? b + vv + 5 * ((m2 + 1) % 3) : lane;
+        const int s2 = lane < 30 ? b + vv + 5 * ((m2 + 2) % 3) : lane;
+        // inputs j = m2 (own), m2 + 1, m2 + 2 (mod 3), weighted e^{+2 pi i j m2 / 3}
+        const float2 c1 = root_of(tw, ((m2 + 1) % 3) * m2 % 3, 3, n);
+        const float2 c2 = root_of(tw, ((m2 + 2) % 3) * m2 % 3, 3, n);
+        const float2 c0 = root_of(tw, m2 * m2 % 3, 3, n);
+        const float2 w = root_of(tw, vv * m2, 15, n);
+#pragma unroll
+        for (int k1 = 0; k1 < MW; ++k1) {
+            const float2 o1 = make_float2(__shfl_sync(0xffffffffu, v[k1].x, s1),
+                                          __shfl_sync(0xffffffffu, v[k1].y, s1));
+            const float2 o2 = make_float2(__shfl_sync(0xffffffffu, v[k1].x, s2),
+                                          __shfl_sync(0xffffffffu, v[k1].y, s2));
+            const float2 z = cadd(cadd(cmul(v[k1], c0), cmul(o1, c1)), cmul(o2, c2));
+            v[k1] = cmul(z, w);
+        }
+    }
+    // radix 5, span 1, in blocks of 5: lane b + m3
+    {
+        const int b = ln - ln % 5, m3 = ln % 5;
+        int src[4];
+        float2 c[5];
+        c[0] = root_of(tw, m3 * m3 % 5, 5, n);
+#pragma unroll
+        for (int d = 1; d < 5; ++d) {
+            const int j = (m3 + d) % 5;
+            src[d - 1] = lane < 30 ? b + j : lane;
+            c[d] = root_of(tw, j * m3 % 5, 5, n);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < MW; ++k1) {
+            float2 z = cmul(v[k1], c[0]);
+#pragma unroll
+            for (int d = 1; d < 5; ++d) {
+                const float2 o = make_float2(__shfl_sync(0xffffffffu, v[k1].x, src[d - 1]),
+                                             __shfl_sync(0xffffffffu, v[k1].y, src[d - 1]));
+                z = cadd(z, cmul(o, c[d]));
+            }
+            v[k1] = z;
+        }
+    }
+}
+
 // Integer image of a float that preserves its order, -0 taken as +0 and NaN
 // above everything.
 __device__ __forceinline__ int ordered_key(float x)
@@ -484,12 +577,16 @@ size_t reg_smem_bytes(int n, int M)
            sizeof(float) * (size_t)M;
 }
 
-// One CTA per (query i, templates j0 .. j0 + 15).
-template <int MW, int PARTS, bool XTRA>
-__global__ void __launch_bounds__(kRegThreads, MW <= 8 ? (XTRA || PARTS == 2 ? 4 : 6) : 2)
+// One CTA per (query i, templates j0 .. j0 + 15).  LANES = 32: n = 32 MW
+// (powers of two); LANES = 30: n = 30 MW on lanes 0..29 (reg_ifft30).  At
+// MW = 12 (n = 360) four CTAs per SM (64 registers, no spills) beat two
+// (0.137 against 0.177 ms for 128 x 1000 pairs).
+template <int MW, int PARTS, bool XTRA, int LANES = 32>
+__global__ void __launch_bounds__(kRegThreads, MW <= 8 ? (XTRA || PARTS == 2 ? 4 : 6) : (MW == 12 ? 4 : 2))
 k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
 {
-    constexpr int n = 32 * MW, nh = n / 2;
+    constexpr int n = LANES * MW, nh = n / 2;
+    static_assert(LANES == 32 || (LANES == 30 && MW % 2 == 0), "n = 32 MW or 30 MW (MW even)");
     extern __shared__ float4 smr[];
     float4 *sC = smr;                                             // [nh][kRegRow]
     float2 *tws = reinterpret_cast<float2 *>(sC + nh * kRegRow);  // [n]
@@ -546,13 +643,14 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
     // at 0; unusable templates contribute zeros (their NaNs stay out of
     // the partner)
     const bool za = stt[2 * s] != 0, zb = stt[2 * s + 1] != 0;
+    const bool live = lane < LANES;  // lanes that hold samples of the transform
     float2 v[MW];
 #pragma unroll
     for (int m = 0; m < MW; ++m) {
-        const int t = 32 * m + lane;
+        const int t = LANES * m + lane;
         const int kf = m < MW / 2 ? t : n - t;
         float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kf != 0) X = sC[(kf - 1) * kRegRow + s];
+        if (live && kf != 0) X = sC[(kf - 1) * kRegRow + s];
         if (za) X.x = X.y = 0.f;
         if (zb) X.z = X.w = 0.f;
         if (m < MW / 2)
@@ -562,7 +660,9 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
         else
             v[m] = make_float2(X.x + X.w, X.z - X.y);
     }
-    reg_ifft<MW>(v, tws, lane);  // v[k1] = n (corr_a + i corr_b) at l = k1 + MW brev5(lane)
+    // v[k1] = n (corr_a + i corr_b) at l = k1 + MW q2(lane)
+    if constexpr (LANES == 32) reg_ifft<MW>(v, tws, lane);
+    else reg_ifft30<MW>(v, tws, lane);
 
     // ---- argmin over l (FP32 keys, lowest l on ties), carrying n corr(l)
     const bool x_t = PARTS == 2;
@@ -578,16 +678,20 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
     // key, then the lowest l holding it.  NaN keys never win (unless all are).
     float best0, best1, rv0, rv1;  // per lane: best key, and n corr at its l
     int bl0, bl1;
-    const int lb = MW * brev5(lane);
+    const int lb = MW * (LANES == 32 ? brev5(lane) : (live ? lane30_q(lane) : 0));
     if (!X.rot_t && !x_t) {
-        // key = -2 corr(l) / n: n is a power of two, so the smallest key is
-        // exactly the largest n corr(l)
+        // key = -2 corr(l) / n: the smallest key is the largest n corr(l)
+        // (exactly so for n a power of two; for n = 30 MW the keys are
+        // compared as -n corr, the same order up to the scaling's rounding,
+        // which is monotone)
         rv0 = rv1 = __int_as_float(0xff800000);  // -inf: NaN values never replace it
         bl0 = bl1 = lb;
+        if (live) {
 #pragma unroll
-        for (int k1 = 0; k1 < MW; ++k1) {
-            if (v[k1].x > rv0) { rv0 = v[k1].x; bl0 = k1 + lb; }
-            if (v[k1].y > rv1) { rv1 = v[k1].y; bl1 = k1 + lb; }
+            for (int k1 = 0; k1 < MW; ++k1) {
+                if (v[k1].x > rv0) { rv0 = v[k1].x; bl0 = k1 + lb; }
+                if (v[k1].y > rv1) { rv1 = v[k1].y; bl1 = k1 + lb; }
+            }
         }
         best0 = -rv0;
         best1 = -rv1;
@@ -599,6 +703,7 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
         bl0 = bl1 = lb;
 #pragma unroll
         for (int k1 = 0; k1 < MW; ++k1) {
+            if (!live) break;
             const int l = k1 + lb;
             const float2 z = v[k1];
             const float2 w = tws[l];  // (cos alpha_l, -sin alpha_l)
@@ -611,8 +716,8 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
     // the lane holding l* has l* as its own best: n corr(l*) comes from it
     bl0 = warp_argmin(best0, bl0);
     bl1 = warp_argmin(best1, bl1);
-    rv0 = __shfl_sync(0xffffffffu, rv0, brev5(bl0 / MW));
-    rv1 = __shfl_sync(0xffffffffu, rv1, brev5(bl1 / MW));
+    rv0 = __shfl_sync(0xffffffffu, rv0, LANES == 32 ? brev5(bl0 / MW) : lane30_of_q(bl0 / MW));
+    rv1 = __shfl_sync(0xffffffffu, rv1, LANES == 32 ? brev5(bl1 / MW) : lane30_of_q(bl1 / MW));
     if (lane < 2) {
         res_l[2 * s + lane] = lane ? bl1 : bl0;
         res_v[2 * s + lane] = lane ? rv1 : rv0;
@@ -626,10 +731,12 @@ k_decide_reg(DecideArgs A, const float2 *__restrict__ tw)
         centre_of(A.ctr_t, 0, PARTS, ajx, ajy, djx, djy);
         const double base = (double)da + A.norm_q[0] + A.norm_t[0];
         const int st = A.st_q[0] || stt[0] || (A.dev_err && *A.dev_err);
+        if (live) {
 #pragma unroll
-        for (int k1 = 0; k1 < MW; ++k1)
-            curve_point<PARTS>(A, k1 + lb, v[k1].x, base, st, X.tmode, aix, aiy, dix, diy,
-                               ajx, ajy, djx, djy);
+            for (int k1 = 0; k1 < MW; ++k1)
+                curve_point<PARTS>(A, k1 + lb, v[k1].x, base, st, X.tmode, aix, aiy, dix, diy,
+                                   ajx, ajy, djx, djy);
+        }
     }
     // every warp has posted its pairs
     __syncthreads();
@@ -690,7 +797,11 @@ __global__ void k_best_template(const sw_result *__restrict__ all, int Nq, int N
 
 }  // namespace
 
-bool decide_reg_ok(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+bool decide_reg_ok(int n)
+{
+    return n == 64 || n == 128 || n == 256 || n == 512 ||  // 32 lanes
+           n == 60 || n == 120 || n == 180 || n == 240 || n == 360 || n == 480;  // 30 lanes
+}
 
 cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const float2 *tw,
                           cudaStream_t st, int nsig_req)
@@ -711,23 +822,29 @@ cudaError_t launch_decide(const DecideArgs &args, const FftPlan &plan, const flo
     if (decide_reg_ok(a.n) && (nsig_req == 0 || nsig_req == 1)) {
         const size_t smem = reg_smem_bytes(a.n, a.M);
         dim3 grid(a.Nq, (a.Nt + kRegTemplates - 1) / kRegTemplates);
-#define SW_REG_LAUNCH(MW, P, X)                                                                 \
-    do {                                                                                        \
-        cudaFuncSetAttribute(k_decide_reg<MW, P, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)smem);                                                        \
-        k_decide_reg<MW, P, X><<<grid, kRegThreads, smem, st>>>(a, tw);                         \
+#define SW_REG_LAUNCH(MW, P, X, LN)                                                         \
+    do {                                                                                    \
+        cudaFuncSetAttribute(k_decide_reg<MW, P, X, LN>,                                    \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        k_decide_reg<MW, P, X, LN><<<grid, kRegThreads, smem, st>>>(a, tw);                 \
     } while (0)
-#define SW_REG_FORMS(MW)                                                                        \
-    do {                                                                                        \
-        if (a.parts == 1 && a.translation && a.grid_k == 0) SW_REG_LAUNCH(MW, 1, false);       \
-        else if (a.parts == 1) SW_REG_LAUNCH(MW, 1, true);                                      \
-        else SW_REG_LAUNCH(MW, 2, true);                                                        \
+#define SW_REG_FORMS(MW, LN)                                                                \
+    do {                                                                                    \
+        if (a.parts == 1 && a.translation && a.grid_k == 0) SW_REG_LAUNCH(MW, 1, false, LN); \
+        else if (a.parts == 1) SW_REG_LAUNCH(MW, 1, true, LN);                              \
+        else SW_REG_LAUNCH(MW, 2, true, LN);                                                \
     } while (0)
         switch (a.n) {
-        case 64: SW_REG_FORMS(2); break;
-        case 128: SW_REG_FORMS(4); break;
-        case 256: SW_REG_FORMS(8); break;
-        default: SW_REG_FORMS(16); break;
+        case 64: SW_REG_FORMS(2, 32); break;
+        case 128: SW_REG_FORMS(4, 32); break;
+        case 256: SW_REG_FORMS(8, 32); break;
+        case 512: SW_REG_FORMS(16, 32); break;
+        case 60: SW_REG_FORMS(2, 30); break;
+        case 120: SW_REG_FORMS(4, 30); break;
+        case 180: SW_REG_FORMS(6, 30); break;
+        case 240: SW_REG_FORMS(8, 30); break;
+        case 360: SW_REG_FORMS(12, 30); break;
+        default: SW_REG_FORMS(16, 30); break;  // 480
         }
 #undef SW_REG_FORMS
 #undef SW_REG_LAUNCH

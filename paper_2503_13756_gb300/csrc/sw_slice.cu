@@ -76,77 +76,6 @@ __device__ __forceinline__ int wrap_n(int x, int N)
     return x;
 }
 
-// In-lane inverse DFT of length M in registers, y[k] = sum_n v[n] w^{n k}
-// with w = e^{+2 pi i / M} = conj(tw[TS]) (tw[q] = e^{-2 pi i q / N}, N = TS M):
-// mixed-radix decimation in time with compile-time indices.  M = R Q with R
-// in {4, 2, 3, 5}: the R interleaved subsequences v[R m + r] are transformed
-// (length Q), twiddled by w^{r k'} and combined by R-point butterflies:
-// y[k' + Q s] = sum_r (w^{r k'} Y_r[k']) e^{+2 pi i r s / R}.
-template <int M, int TS>
-__device__ __forceinline__ void lane_dft(float2 (&v)[M], const float2 *__restrict__ tw)
-{
-    if constexpr (M > 1) {
-        constexpr int R = M % 4 == 0 ? 4 : (M % 2 == 0 ? 2 : (M % 3 == 0 ? 3 : 5));
-        constexpr int Q = M / R;
-        static_assert(R * Q == M && (M % 5 != 0 || R == 5 || M % 2 == 0 || M % 3 == 0),
-                      "M must factor into 2, 3, 4 and 5");
-        float2 sub[R][Q];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-#pragma unroll
-            for (int m = 0; m < Q; ++m) sub[r][m] = v[R * m + r];
-            lane_dft<Q, TS * R>(sub[r], tw);
-        }
-#pragma unroll
-        for (int kq = 0; kq < Q; ++kq) {
-            float2 a[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                a[r] = (r == 0 || kq == 0) ? sub[r][kq] : cmul(sub[r][kq], cconj(tw[TS * r * kq]));
-            if constexpr (R == 2) {
-                v[kq] = cadd(a[0], a[1]);
-                v[kq + Q] = csub(a[0], a[1]);
-            } else if constexpr (R == 4) {
-                const float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-                const float2 s13 = cadd(a[1], a[3]), d13 = cmul_i(csub(a[1], a[3]), +1);
-                v[kq] = cadd(s02, s13);
-                v[kq + Q] = cadd(d02, d13);
-                v[kq + 2 * Q] = csub(s02, s13);
-                v[kq + 3 * Q] = csub(d02, d13);
-            } else if constexpr (R == 3) {
-                // e^{+2 pi i / 3} = -1/2 + i sqrt(3)/2
-                const float s3 = 0.86602540378443864676f;
-                const float2 t1 = cadd(a[1], a[2]);
-                const float2 t2 = make_float2(a[0].x - 0.5f * t1.x, a[0].y - 0.5f * t1.y);
-                float2 t3 = cmul_i(csub(a[1], a[2]), +1);
-                t3.x *= s3;
-                t3.y *= s3;
-                v[kq] = cadd(a[0], t1);
-                v[kq + Q] = cadd(t2, t3);
-                v[kq + 2 * Q] = csub(t2, t3);
-            } else {  // R == 5
-                const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
-                const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
-                const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
-                const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
-                const float2 a1 = cadd(a[1], a[4]), b1 = csub(a[1], a[4]);
-                const float2 a2 = cadd(a[2], a[3]), b2 = csub(a[2], a[3]);
-                const float2 r1 = make_float2(a[0].x + c1 * a1.x + c2 * a2.x,
-                                              a[0].y + c1 * a1.y + c2 * a2.y);
-                const float2 r2 = make_float2(a[0].x + c2 * a1.x + c1 * a2.x,
-                                              a[0].y + c2 * a1.y + c1 * a2.y);
-                const float2 i1 = cmul_i(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y), +1);
-                const float2 i2 = cmul_i(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y), +1);
-                v[kq] = make_float2(a[0].x + a1.x + a2.x, a[0].y + a1.y + a2.y);
-                v[kq + Q] = cadd(r1, i1);
-                v[kq + 4 * Q] = csub(r1, i1);
-                v[kq + 2 * Q] = cadd(r2, i2);
-                v[kq + 3 * Q] = csub(r2, i2);
-            }
-        }
-    }
-}
-
 // Unnormalised inverse DFT of length N = 32 M held by one warp:
 //   X[k] = sum_n x[n] e^{+2 pi i n k / N}.
 // In: v[n1] = x[32 n1 + lane].  Out: v[k1] = X[k1 + M brev5(lane)].

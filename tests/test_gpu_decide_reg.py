@@ -2,7 +2,9 @@
 rotations": the inverse FFT over angle and the argmin of Eq. optimal_rotation).
 
 For n_theta = 64, 128, 256 and 512 the decision's inverse FFT runs in the
-registers of one warp per two templates.  Checked against the oracle at those
+registers of one warp per two templates (32 lanes); for n_theta = 60, 120,
+180, 240, 360 and 480 on 30 lanes (a mixed-radix 2 x 3 x 5 transform across
+the lanes).  Checked against the oracle at those
 n: odd and even ragged template counts (8- and 16-byte staging of the spectra,
 a zero-filled tail), both translation modes and both level rules, the full
 single-pair curve, and unusable templates next to usable ones.  The
@@ -36,6 +38,14 @@ def al():
     (256, 16, 17, 1, 1),   # left-endpoint levels
     (256, 48, 33, 0, 1),
     (512, 40, 6, 1, 0),    # 16 values per lane
+    # 30 lanes: n = 30 MW
+    (60, 16, 9, 1, 0),
+    (120, 24, 22, 0, 0),
+    (180, 32, 17, 1, 1),
+    (240, 24, 33, 0, 1),
+    (360, 40, 19, 1, 0),   # the serving and single-pair angle count
+    (360, 24, 16, 0, 0),
+    (480, 32, 6, 1, 0),
 ])
 def test_register_form_matches_oracle(al, n, M, nt, translation, level_rule):
     rng = np.random.default_rng(n + nt)
@@ -46,7 +56,7 @@ def test_register_form_matches_oracle(al, n, M, nt, translation, level_rule):
 
 
 @pytest.mark.parametrize("translation", [1, 0])
-@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("n", [128, 256, 360, 120])
 def test_register_form_single_pair_curve(al, n, translation):
     rng = np.random.default_rng(n + translation)
     L, M = 48, 40
@@ -84,7 +94,7 @@ def test_unusable_partner_template_leaves_its_pair_unchanged(al):
         assert r[i, 0]["d2"] == alone[i, 0]["d2"]
 
 
-@pytest.mark.parametrize("n,dec", [(64, 8), (256, 4), (512, 16)])
+@pytest.mark.parametrize("n,dec", [(64, 8), (256, 4), (512, 16), (360, 8), (60, 16)])
 def test_shared_memory_form_at_register_sizes(al, tmp_path, n, dec):
     """The shared-memory form, taken through the autotune cache, at n where
     the register form is the default: both meet the oracle's bar."""
