@@ -23,8 +23,11 @@
 // overlaps the MMAs of the next.  BF16 / FP16 (one K pass per tile) take
 // eight epilogue warps, two per TMEM lane quarter each draining half of the
 // tile's columns, with a 3-stage ring at BN = 256 to leave room for their
-// store buffers; the FP16 split (three K passes per tile, bound by its operand
-// loads) keeps four epilogue warps and a 4-stage ring.  With Nt even each
+// store buffers.  The FP16 split (three products per tile) loads each K
+// slice's four operand segments (A hi, A lo, B hi, B lo) into one stage and
+// issues the three products' MMAs from it, so each segment is read once per
+// tile instead of the hi segments twice (a third fewer operand bytes; two
+// stages at BN = 256, three at 128), with four epilogue warps.  With Nt even each
 // epilogue warp writes its 32 x 32 FP32 blocks into one of two 128-byte-
 // swizzled shared-memory buffers and one lane stores them with a TMA tensor
 // store (coalesced, clipped at the tensor's edges); odd Nt keeps per-lane
@@ -50,7 +53,11 @@ constexpr int A_STAGE = BM * BK * 2;              // 16 KB
 constexpr int EPI_BUF = 32 * 32 * 4;              // 4 KB: 32 rows x 32 FP32, 128-byte swizzle
 // EPW epilogue warps per TMEM lane quarter (1 or 2)
 template <int EPW> constexpr int tc_threads() { return 64 + 128 * EPW; }  // TMA, MMA, epilogue
-template <int BN, int EPW> constexpr int stages() { return (BN == 256 && EPW == 2) ? 3 : 4; }
+template <int BN, int EPW, bool S4>
+constexpr int stages()
+{
+    return S4 ? (BN == 256 ? 2 : 3) : ((BN == 256 && EPW == 2) ? 3 : 4);
+}
 template <int BN> constexpr int b_stage() { return BN * BK * 2; }  // 32 KB (BN 256), 16 KB
 template <int BN> constexpr int tmem_cols() { return 2 * BN; }     // two BN-column accumulators
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: default and drain limit
@@ -178,21 +185,25 @@ struct TcArgs {
     int tma_store;              // C rows 16-byte aligned (Nt even): TMA stores through mapC
 };
 
-template <int BN, int EPW>
+// S4: the FP16 split with the four segments of a K slice in one stage
+// (args.kblocks = segb); otherwise one A and one B slice per stage.
+template <int BN, int EPW, bool S4>
 __global__ void __launch_bounds__(tc_threads<EPW>(), 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const __grid_constant__ CUtensorMap mapC, TcArgs args)
 {
     constexpr int B_STAGE = b_stage<BN>();
     constexpr int TMEM_COLS = tmem_cols<BN>();
-    constexpr int STAGES = stages<BN, EPW>();
+    constexpr int STAGES = stages<BN, EPW, S4>();
     constexpr int EPI_WARPS = 4 * EPW;
+    constexpr int A_ST = S4 ? 2 * A_STAGE : A_STAGE;  // one stage: [hi | lo] with S4
+    constexpr int B_ST = S4 ? 2 * B_STAGE : B_STAGE;
     extern __shared__ uint8_t dsm[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t *sA = base;                       // STAGES x 16 KB
-    uint8_t *sB = base + STAGES * A_STAGE;    // STAGES x 32 KB
-    uint8_t *sE = sB + STAGES * B_STAGE;      // [EPI_WARPS][2] x 4 KB epilogue blocks (1 KB aligned)
+    uint8_t *sA = base;                       // STAGES x A_ST
+    uint8_t *sB = base + STAGES * A_ST;       // STAGES x B_ST
+    uint8_t *sE = sB + STAGES * B_ST;         // [EPI_WARPS][2] x 4 KB epilogue blocks (1 KB aligned)
     __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
     __shared__ uint32_t tmem_base_s;
@@ -247,13 +258,23 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         give_up();
                         break;
                     }
-                    // K slice kb of product term t: A's and B's segment for that term
-                    const int t = kb / args.segb, kk = kb - t * args.segb;
-                    const int xa = ((args.split && t == 2) ? args.segb + kk : kk) * BK;
-                    const int xb = ((args.split && t == 1) ? args.segb + kk : kk) * BK;
-                    mbar_expect_tx(&full_bar[s], A_STAGE + B_STAGE);
-                    tma_load_3d(sA + s * A_STAGE, &mapA, &full_bar[s], xa, mt * BM, f);
-                    tma_load_3d(sB + s * B_STAGE, &mapB, &full_bar[s], xb, nt * BN, f);
+                    if constexpr (S4) {
+                        // K slice kb: A hi, A lo, B hi, B lo
+                        const int xh = kb * BK, xl = (args.segb + kb) * BK;
+                        mbar_expect_tx(&full_bar[s], A_ST + B_ST);
+                        tma_load_3d(sA + s * A_ST, &mapA, &full_bar[s], xh, mt * BM, f);
+                        tma_load_3d(sA + s * A_ST + A_STAGE, &mapA, &full_bar[s], xl, mt * BM, f);
+                        tma_load_3d(sB + s * B_ST, &mapB, &full_bar[s], xh, nt * BN, f);
+                        tma_load_3d(sB + s * B_ST + B_STAGE, &mapB, &full_bar[s], xl, nt * BN, f);
+                    } else {
+                        // K slice kb of product term t: A's and B's segment for that term
+                        const int t = kb / args.segb, kk = kb - t * args.segb;
+                        const int xa = ((args.split && t == 2) ? args.segb + kk : kk) * BK;
+                        const int xb = ((args.split && t == 1) ? args.segb + kk : kk) * BK;
+                        mbar_expect_tx(&full_bar[s], A_STAGE + B_STAGE);
+                        tma_load_3d(sA + s * A_STAGE, &mapA, &full_bar[s], xa, mt * BM, f);
+                        tma_load_3d(sB + s * B_STAGE, &mapB, &full_bar[s], xb, nt * BN, f);
+                    }
                 }
             }
             // let every issued copy land before the CTA may exit (time-bounded
@@ -284,11 +305,28 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t da = smem_desc_sw128(sA + s * A_STAGE);
-                    const uint64_t db = smem_desc_sw128(sB + s * B_STAGE);
+                    if constexpr (S4) {
+                        // hi hi, hi lo, lo hi from the stage's four segments
+                        const uint64_t ah = smem_desc_sw128(sA + s * A_ST);
+                        const uint64_t al = smem_desc_sw128(sA + s * A_ST + A_STAGE);
+                        const uint64_t bh = smem_desc_sw128(sB + s * B_ST);
+                        const uint64_t bl = smem_desc_sw128(sB + s * B_ST + B_STAGE);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)  // +32 bytes along K per step
-                        mma_f16(d, da + 2 * kk, db + 2 * kk, args.idesc, (kb | kk) != 0);
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_f16(d, ah + 2 * kk, bh + 2 * kk, args.idesc, (kb | kk) != 0);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_f16(d, ah + 2 * kk, bl + 2 * kk, args.idesc, true);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_f16(d, al + 2 * kk, bh + 2 * kk, args.idesc, true);
+                    } else {
+                        const uint64_t da = smem_desc_sw128(sA + s * A_STAGE);
+                        const uint64_t db = smem_desc_sw128(sB + s * B_STAGE);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)  // +32 bytes along K per step
+                            mma_f16(d, da + 2 * kk, db + 2 * kk, args.idesc, (kb | kk) != 0);
+                    }
                     mma_commit(&empty_bar[s]);  // stage free once these MMAs finish
                 }
                 if (!ok) break;
@@ -427,7 +465,7 @@ bool make_map(CUtensorMap *m, const void *base, int kind, uint64_t ldk, uint64_t
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, int EPW>
+template <int BN, int EPW, bool S4 = false>
 cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, int nf, int kind,
                         float2 *C, int *err, int num_sms, cudaStream_t st, long long wait_cycles,
                         int stall)
@@ -443,7 +481,7 @@ cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, i
     a.nf = nf;
     a.segb = tc_ldk(M) / BK;
     a.split = kind == 3;
-    a.kblocks = a.split ? 3 * a.segb : a.segb;
+    a.kblocks = (a.split && !S4) ? 3 * a.segb : a.segb;
     a.mtiles = (Nq + BM - 1) / BM;
     a.ntiles = (2 * Nt + BN - 1) / BN;
     // kind::f16 instruction descriptor: FP32 accumulator, A/B BF16 (1) or
@@ -461,13 +499,14 @@ cudaError_t launch_tile(const void *Xq, const void *Yt, int Nq, int Nt, int M, i
                    make_map_c(&mc, a.C, (uint64_t)2 * Nt, (uint64_t)Nq, (uint64_t)nf))
                       ? 1
                       : 0;
-    const size_t smem =
-        (size_t)stages<BN, EPW>() * (A_STAGE + b_stage<BN>()) + 4 * EPW * 2 * EPI_BUF + 1024;
-    cudaFuncSetAttribute(k_corr_tc<BN, EPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int per = S4 ? 2 : 1;  // segments of each operand per stage
+    const size_t smem = (size_t)stages<BN, EPW, S4>() * per * (A_STAGE + b_stage<BN>()) +
+                        4 * EPW * 2 * EPI_BUF + 1024;
+    cudaFuncSetAttribute(k_corr_tc<BN, EPW, S4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     const int tiles = nf * a.mtiles * a.ntiles;
     const int grid = tiles < num_sms ? tiles : num_sms;
-    k_corr_tc<BN, EPW><<<grid, tc_threads<EPW>(), smem, st>>>(ma, mb, mc, a);
+    k_corr_tc<BN, EPW, S4><<<grid, tc_threads<EPW>(), smem, st>>>(ma, mb, mc, a);
     return cudaGetLastError();
 }
 
@@ -481,12 +520,14 @@ cudaError_t launch_corr_tc(const void *Xq, const void *Yt, int Nq, int Nt, int M
                            long long wait_cycles, int stall, int tile_n)
 {
     if (Nq <= 0 || Nt <= 0 || nf <= 0) return cudaSuccess;
-    // the FP16 split (kind 3) is bound by its operand loads: at BN = 256 four
-    // epilogue warps keep the 4-stage ring; BF16 / FP16, and the split at
-    // BN = 128 (where eight fit beside four stages), drain with eight
-    if (kind == 3 && tile_n != 128)
-        return launch_tile<256, 1>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st, wait_cycles,
-                                   stall);
+    // the FP16 split (kind 3): four segments per stage, four epilogue warps;
+    // BF16 / FP16 drain with eight
+    if (kind == 3)
+        return tile_n == 128
+                   ? launch_tile<128, 1, true>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
+                                               wait_cycles, stall)
+                   : launch_tile<256, 1, true>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
+                                               wait_cycles, stall);
     return tile_n == 128 ? launch_tile<128, 2>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
                                                wait_cycles, stall)
                          : launch_tile<256, 2>(Xq, Yt, Nq, Nt, M, nf, kind, C, err, num_sms, st,
