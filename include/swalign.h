@@ -221,7 +221,8 @@ int64_t sw_launch_count(const sw_ctx *ctx);
  *   choice[0] target CTA count of the projection's split over angles,
  *   choice[1] signals per FFT batch of the angle spectra (4, 8 or 16),
  *   choice[2] form of the decision's inverse FFT: 1 = one warp per pair of
- *             curves, in registers (n_theta = 64, 128, 256 or 512 only),
+ *             curves, in registers (n_theta = 64, 128, 256 or 512 on 32
+ *             lanes; 60, 120, 180, 240, 360 or 480 on 30 lanes),
  *             4, 8 or 16 = that many signals per CTA in shared memory,
  *   choice[3] FFT plan, 0..7: bit 2 clear takes the power-of-two part of
  *             the length in radix-4 stages, set in radix-8 stages (with at
