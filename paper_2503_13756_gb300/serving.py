@@ -27,6 +27,7 @@ neighbouring pair's values enter the rounding.
 from __future__ import annotations
 
 import collections
+import gc
 import threading
 import time
 from dataclasses import dataclass, field
@@ -198,7 +199,19 @@ class ServingEngine:
     # ----------------------------------------------------------------- run
     def run(self, requests, realtime: bool = True):
         """Feeds the requests at their arrival times (realtime) or all at
-        once, serves them, and returns summary statistics."""
+        once, serves them, and returns summary statistics.  The interpreter's
+        cyclic garbage collector is paused while the loop runs (reference
+        counting still frees every object; a collection pass over a large heap
+        would stall the loop for milliseconds) and restored on return."""
+        was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, realtime)
+        finally:
+            if was_enabled:
+                gc.enable()
+
+    def _run(self, requests, realtime):
         for r in requests:
             r.results = np.zeros(len(r.images), dtype=swalign.RESULT_DTYPE)
             r.remaining = len(r.images)
