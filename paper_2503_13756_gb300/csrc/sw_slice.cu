@@ -784,6 +784,10 @@ cudaError_t launch_big(SliceArgs a, int nb, int chunk, cudaStream_t st)
     e = cudaFuncSetAttribute(k_slice_grid<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_grid);
     if (e != cudaSuccess) return e;
+    // chunks of equal size (at most `chunk`): no small last chunk whose
+    // launches would leave most SMs idle
+    const int nchunks = (nb + chunk - 1) / chunk;
+    chunk = (nb + nchunks - 1) / nchunks;
     for (int i0 = 0; i0 < nb; i0 += chunk) {
         const int cnt = std::min(chunk, nb - i0);
         a.img_off = i0;
