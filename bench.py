@@ -756,6 +756,26 @@ def main():
 
         pipeline(2)
         torch.cuda.synchronize()
+        # the host link's rate on this machine: one upload of a step's inputs and
+        # one download of its results alone (the pipeline hides them behind
+        # the compute only while they take less than a step)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cs_in):
+            h0.record(cs_in)
+            for _ in range(3):
+                qb[1].copy_(q_h, non_blocking=True)
+                tb[1].copy_(t_h, non_blocking=True)
+            h1.record(cs_in)
+        h1.synchronize()
+        h2d_ms = h0.elapsed_time(h1) / 3
+        with torch.cuda.stream(cs_out):
+            h0.record(cs_out)
+            for _ in range(3):
+                oh[1].copy_(ob[1], non_blocking=True)
+            h1.record(cs_out)
+        h1.synchronize()
+        d2h_ms = h0.elapsed_time(h1) / 3
+        torch.cuda.synchronize()
         barrier(world)
         with ClockSampler(local) as clk_e2e:
             torch.cuda.synchronize()
@@ -773,6 +793,8 @@ def main():
                "d2h_bytes_per_step": int(oh[0].numel()),
                "pipeline": "inputs of step k+1 uploaded and results of step k-1 read back "
                            "on copy streams while step k computes (two buffer sets)",
+               "h2d_ms_alone": h2d_ms, "d2h_ms_alone": d2h_ms,
+               "h2d_gbs_alone": (q_h.numel() + t_h.numel()) * 4 / (h2d_ms / 1e3) / 1e9,
                "clocks": clk_e2e.summary()}
 
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
