@@ -396,3 +396,16 @@ def test_slice_many_to_many_full_size_sampled(al):
     ref = ref_rows(q[i], n, B, clip=True) * np.maximum(q[i].astype(np.float64), 0).sum()
     err = np.linalg.norm(rows - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() <= row_tol(L, B)
+
+
+def test_project_upsampled_rejects_odd_L(al):
+    import ctypes
+    p = params(65, 8, 8)
+    x = torch.zeros((2, 32, 32), dtype=torch.float32, device="cuda")
+    out = torch.empty((2, 8, swalign.bins_of(p)), dtype=torch.float32, device="cuda")
+    with pytest.raises(swalign.SwError) as e:
+        al.call("sw_project_upsampled", ctypes.byref(p), ctypes.c_void_p(x.data_ptr()), 2,
+                ctypes.c_void_p(out.data_ptr()), None)
+    assert e.value.status == 1 and "odd" in str(e.value)
+    with pytest.raises(ValueError):
+        al.project_upsampled(torch.zeros((2, 30, 30), device="cuda"), params(64, 8, 8))
