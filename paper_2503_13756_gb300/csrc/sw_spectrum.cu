@@ -247,16 +247,19 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     // parts, stored as [parts][n][M/2], and each part is centred by its own
     // vector.
     extern __shared__ __align__(16) float2 smc[];
-    float2 *stage = smc;                 // [2][n nsig] level batches (cp.async)
-    float2 *scr = stage + 2 * n * nsig;  // [n nsig] the FFT's other buffer
-    float2 *x1 = scr + n * nsig;         // [M] Qhat(1, p) before centring
+    // two batch buffers: the staged input of the FFT and its other buffer;
+    // once a batch's transform is done, the buffer it did not end in takes
+    // the next batch's copies while the unpack reads the result
+    float2 *bufA = smc;                  // [n nsig]
+    float2 *bufB = bufA + n * nsig;      // [n nsig]
+    float2 *x1 = bufB + n * nsig;        // [M] Qhat(1, p) before centring
     float2 *tws = x1 + M;                // [n] twiddles
     __shared__ double red[2][kSpecThreads / 32];
     __shared__ double s_c1[2][2];
     const int Mp = M / parts;  // levels per part
     const int img = blockIdx.x;
     const float *qi = q + (size_t)img * n * M;
-    stage_levels<nsig>(qi, n, M, Mp, parts, 0, stage);
+    stage_levels<nsig>(qi, n, M, Mp, parts, 0, bufA);
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     const int nh = n / 2;
     // norms as compensated (Kahan) FP32 sums: FP64 arithmetic is scarce on
@@ -264,18 +267,18 @@ k_spectrum(const float *__restrict__ q, int n, int M, FftPlan plan, const float2
     DF acc32 = {0.f, 0.f}, acc16 = {0.f, 0.f};
     const float invn = 1.f / (float)n;
 
-    for (int p0 = 0, b = 0; p0 < M; p0 += 2 * nsig, ++b) {
-        // ---- batch b: levels (p0 + 2s, p0 + 2s + 1) as signal s (re, im).
-        // Stage batch b + 1 (an empty group at the end), then wait for b.
-        float2 *cur = stage + (b & 1) * n * nsig;
-        if (p0 + 2 * nsig < M)
-            stage_levels<nsig>(qi, n, M, Mp, parts, p0 + 2 * nsig,
-                               stage + ((b + 1) & 1) * n * nsig);
-        else
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
+    float2 *cur = bufA, *oth = bufB;
+    for (int p0 = 0; p0 < M; p0 += 2 * nsig) {
+        // ---- batch: levels (p0 + 2s, p0 + 2s + 1) as signal s (re, im)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        const float2 *R = fft_smem<nsig, -1>(cur, scr, plan, tws);
+        float2 *R = fft_smem<nsig, -1>(cur, oth, plan, tws);
+        // the next batch goes to the buffer the transform did not end in
+        // (fft_smem ends with a block barrier: both buffers' readers are done)
+        float2 *nxt = R == cur ? oth : cur;
+        if (p0 + 2 * nsig < M) stage_levels<nsig>(qi, n, M, Mp, parts, p0 + 2 * nsig, nxt);
+        cur = nxt;
+        oth = R;
         // ---- unpack two real spectra per signal, k' = 0..n/2
         for (int t = threadIdx.x; t < (nh + 1) * nsig; t += blockDim.x) {
             const int kf = t / nsig, s = t % nsig;
@@ -408,9 +411,9 @@ cudaError_t launch_spectrum(const float *q, int nb, int n, int M, const FftPlan 
     int nsig = n <= 512 ? 16 : 8;
     if ((nsig_req == 4 || nsig_req == 8 || nsig_req == 16) && (size_t)n * nsig_req <= 8192)
         nsig = nsig_req;
-    // three batch buffers (two staged, one FFT scratch), within the 227 KB a
-    // CTA can hold
-    auto smem_of = [&](int ns) { return sizeof(float2) * ((size_t)3 * n * ns + M + n); };
+    // two batch buffers (the staged input and the FFT's other buffer),
+    // within the 227 KB a CTA can hold
+    auto smem_of = [&](int ns) { return sizeof(float2) * ((size_t)2 * n * ns + M + n); };
     while (nsig > 4 && smem_of(nsig) > kSmemOptIn) nsig /= 2;
     const size_t smem = smem_of(nsig);
     if (smem > kSmemOptIn) return cudaErrorInvalidValue;
