@@ -734,24 +734,34 @@ def main():
         ev_comp = [torch.cuda.Event() for _ in range(2)]
         ev_out = [torch.cuda.Event() for _ in range(2)]
 
-        def pipeline(nsteps):
+        def pipeline(nsteps, spans=None):
+            # spans: optional list that receives, per step, timing events around
+            # the upload, the compute and the download as they ran in the pipeline
             for k in range(nsteps):
                 b = k % 2
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if spans is not None else None
                 with torch.cuda.stream(cs_in):
                     if k >= 2:
                         cs_in.wait_event(ev_comp[b])  # step k-2 has read these inputs
+                    if ev: ev[0].record(cs_in)
                     qb[b].copy_(q_h, non_blocking=True)
                     tb[b].copy_(t_h, non_blocking=True)
                     ev_in[b].record(cs_in)
+                    if ev: ev[1].record(cs_in)
                 stream.wait_event(ev_in[b])
                 if k >= 2:
                     stream.wait_event(ev_out[b])      # step k-2's results are out
+                if ev: ev[2].record(stream)
                 al.align_batch(qb[b], tb[b], p, out=ob[b], stream=stream)
                 ev_comp[b].record(stream)
+                if ev: ev[3].record(stream)
                 with torch.cuda.stream(cs_out):
                     cs_out.wait_event(ev_comp[b])
+                    if ev: ev[4].record(cs_out)
                     oh[b].copy_(ob[b], non_blocking=True)
                     ev_out[b].record(cs_out)
+                    if ev: ev[5].record(cs_out)
+                if ev: spans.append(ev)
             return ev_out[(nsteps - 1) % 2]
 
         pipeline(2)
@@ -788,6 +798,18 @@ def main():
         torch.cuda.synchronize()
         assert torch.equal(oh[(args.steps - 1) % 2], ob[(args.steps - 1) % 2].cpu())
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        # one more pass of the same pipeline, outside the timed region, with
+        # events around each copy and each compute: how long they took while
+        # overlapped (a copy that slows under the compute, or a compute that
+        # slows under the copies, shows here)
+        spans = []
+        pipeline(args.steps, spans)
+        torch.cuda.synchronize()
+        med = lambda xs: float(np.median(xs))
+        in_pipe = {"h2d_ms": med([e[0].elapsed_time(e[1]) for e in spans]),
+                   "compute_ms": med([e[2].elapsed_time(e[3]) for e in spans]),
+                   "d2h_ms": med([e[4].elapsed_time(e[5]) for e in spans]),
+                   "step_ms": med([a[3].elapsed_time(b[3]) for a, b in zip(spans, spans[1:])])}
         e2e = {"value": total_pairs / (ms_e2e / 1e3), "unit": "pairs/s",
                "h2d_bytes_per_step": int(q_h.numel() * 4 + t_h.numel() * 4),
                "d2h_bytes_per_step": int(oh[0].numel()),
@@ -795,6 +817,7 @@ def main():
                            "on copy streams while step k computes (two buffer sets)",
                "h2d_ms_alone": h2d_ms, "d2h_ms_alone": d2h_ms,
                "h2d_gbs_alone": (q_h.numel() + t_h.numel()) * 4 / (h2d_ms / 1e3) / 1e9,
+               "in_pipeline_median": in_pipe,
                "clocks": clk_e2e.summary()}
 
     # ---- the same workload with the tensor-core correlation (BF16 / FP16)
