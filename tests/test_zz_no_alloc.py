@@ -71,6 +71,53 @@ def test_noalloc_matches_allocating_entry_point_twice():
         al.close()
 
 
+def test_noalloc_call_replays_from_a_cuda_graph():
+    # after a first call (which looks up the fixed array's address), a call
+    # captured into a CUDA graph replays with the same results: it copies
+    # nothing from host memory (its angle tables come from a kernel inside
+    # the graph) and allocates nothing
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = swalign.load()
+    rng = np.random.default_rng(77)
+    L, n, M = 64, 360, 128
+    mix = synth.draw_mixtures(rng, 2, L, ncomp=(2, 4))
+    imgs = synth.render(mix, L, beta=[0.0, 2.3], shift=[[0, 0], [1, -2]])
+    f = torch.from_numpy(imgs[0]).cuda()
+    g = torch.from_numpy(imgs[1]).cuda()
+    p = swalign.make_params(L, n, M, translation=1)
+    D0, S0, r0 = _call_noalloc(lib, p, f, g)
+    Sc = norm_scale(imgs[0].astype(np.float64), imgs[1].astype(np.float64), n, M)
+
+    D = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    S = torch.full((n, 2), float("nan"), dtype=torch.float64, device="cuda")
+    best = torch.zeros((40,), dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        st = lib.sw_align_all_rotations_noalloc(
+            ctypes.byref(p), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+            ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(S.data_ptr()),
+            ctypes.c_void_p(best.data_ptr()), ctypes.c_void_p(side.cuda_stream))
+    assert st == swalign.SW_OK, st
+    torch.cuda.synchronize()
+    for _ in range(2):
+        D.fill_(float("nan"))
+        S.fill_(float("nan"))
+        best.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        Dn, Sn = D.cpu().numpy(), S.cpu().numpy()
+        r = swalign.results_to_numpy(best)[0]
+        assert np.all(np.isfinite(Dn)) and np.all(np.isfinite(Sn))
+        assert np.all(np.abs(Dn - D0) <= d2_tol(D0, Sc))
+        np.testing.assert_allclose(Sn, S0, rtol=0, atol=1e-9)
+        assert r["status"] == r0["status"] == 0
+        assert r["best_l"] == r0["best_l"]
+    del graph
+
+
 def test_noalloc_refuses_what_it_does_not_offer():
     # the allocation-free call covers sliced W2 with the linear splat; other
     # metrics and the Fourier-slice projector are refused before any launch,
