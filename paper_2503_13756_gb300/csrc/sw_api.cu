@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "sw_internal.cuh"
+#include "sw_slice_plan.h"
 #include "swalign.h"
 
 using swk::FftPlan;
@@ -63,39 +64,6 @@ struct SliceTables {
     float2 *up_tw = nullptr;
     swk::SliceUpTables up() const { return {up_psi_inv, up_fac, up_gtab, up_goff, up_tw}; }
 };
-
-void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
-{
-    c.assign(n, 0.0);
-    s.assign(n, 0.0);
-    for (int k = 0; k < n; ++k) {
-        // reduce 8k/n to the first octant
-        long long num = 8LL * k;  // angle = (num / n) * (pi / 4)
-        int oct = (int)(num / n);
-        long long rem = num - (long long)oct * n;  // angle = (oct + rem/n) pi/4
-        double cc, ss;
-        auto base = [&](long long r, bool from_top, double &co, double &si) {
-            // t in [0, pi/4]
-            double t = (double)r / n * (M_PI / 4.0);
-            if (from_top) t = M_PI / 4.0 - t;
-            co = std::cos(t);
-            si = std::sin(t);
-        };
-        double co, si;
-        switch (oct & 7) {
-        case 0: base(rem, false, co, si); cc = co; ss = si; break;
-        case 1: base(rem, true, co, si); cc = si; ss = co; break;
-        case 2: base(rem, false, co, si); cc = -si; ss = co; break;
-        case 3: base(rem, true, co, si); cc = -co; ss = si; break;
-        case 4: base(rem, false, co, si); cc = -co; ss = -si; break;
-        case 5: base(rem, true, co, si); cc = -si; ss = -co; break;
-        case 6: base(rem, false, co, si); cc = si; ss = -co; break;
-        default: base(rem, true, co, si); cc = co; ss = -si; break;
-        }
-        c[k] = cc;
-        s[k] = ss;
-    }
-}
 
 // Mixed-radix plan of length n.  The radix order is free (any order is a
 // valid Stockham factorisation; only the rounding and the speed change).
@@ -486,7 +454,7 @@ sw_status get_tables(sw_ctx *c, int n, const Tables **out, int variant = 0)
     if (!fft_plan(n, t.plan, variant))
         return fail(c, SW_ERR_INVALID_ARG, "no FFT plan for n=%d", n);
     std::vector<double> co, si;
-    angle_table(n, co, si);
+    swk::angle_table(n, co, si);
     std::vector<float2> cs(n), tw(n);
     std::vector<double2> cs64(n);
     for (int k = 0; k < n; ++k) {
@@ -581,7 +549,7 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     const int nh = n / 2, nj = B / 2 + 1;
     const double delta = (L & 1) ? 0.0 : 0.5;
     std::vector<double> co, si;
-    angle_table(n, co, si);
+    swk::angle_table(n, co, si);
     std::vector<float2> fac((size_t)nh * nj);
     auto sinc_pi = [](double x) { return x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x); };
     for (int k = 0; k < nh; ++k)
@@ -592,170 +560,22 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
             fac[(size_t)k * nj + j] =
                 make_float2((float)(amp * std::cos(ph)), (float)(amp * std::sin(ph)));
         }
-    // Half-warp groups of targets.  The targets are bucketed by the bank of
-    // their first tap (address mod 16, within each half of the grid: taps at
-    // increasing or decreasing addresses) and group g takes the g-th of every
-    // bucket, so the 16 lanes of a group read distinct banks at every tap;
-    // targets with the same first address (near the origin the angles meet)
-    // read the same words, which the hardware broadcasts, so such a class may
-    // fill several lanes.  Addresses follow the kernel's FP32 arithmetic.
-    // classes: [half][residue] -> address -> entries; appends groups of 16.
-    auto group = [](auto &cls, auto &tab, auto idle) {
-        using E = typename std::remove_reference<decltype(tab)>::type::value_type;
-        for (auto &half : cls) {
-            std::vector<std::vector<E>> q[16];  // per residue, largest class first
-            for (int r = 0; r < 16; ++r) {
-                for (auto &kv : half[r]) q[r].push_back(kv.second);
-                std::stable_sort(q[r].begin(), q[r].end(),
-                                 [](const std::vector<E> &a, const std::vector<E> &b) {
-                                     return a.size() > b.size();
-                                 });
-                for (auto &v : q[r]) std::reverse(v.begin(), v.end());  // pop from the back
-            }
-            size_t head[16] = {};
-            for (;;) {
-                int busy = 0;
-                for (int r = 0; r < 16; ++r) busy += head[r] < q[r].size();
-                if (!busy) break;
-                E lanes[16];
-                int used = 0;
-                for (int r = 0; r < 16; ++r) {
-                    if (head[r] >= q[r].size()) continue;
-                    --busy;  // residues after r that still wait keep one lane each
-                    std::vector<E> &v = q[r][head[r]];
-                    int take = std::min<int>((int)v.size(), 16 - used - busy);
-                    take = std::max(take, 1);
-                    for (int i = 0; i < take; ++i) {
-                        lanes[used++] = v.back();
-                        v.pop_back();
-                    }
-                    if (v.empty()) ++head[r];
-                }
-                for (int i = 0; i < 16; ++i) tab.push_back(i < used ? lanes[i] : idle);
-            }
-        }
-    };
-    // L <= 128 (grid in shared memory): per batch of kSliceBatch angles, the
-    // batch's angles pooled so that the buckets stay even; entries kk 256 + j.
-    // Ray-adjacent targets (j, j + 1) of one half whose footprints start at
-    // most a row and a column apart form a pair entry (kSlicePairBit), bucketed
-    // by the first address of their union footprint and by the offsets of the
-    // two footprints in it (nine patterns, each a compile-time path of the
-    // kernel).  Each pattern's groups are padded to an even count, so both
-    // half-warps of a warp take one path; pairs come before the single
-    // targets.
+    // Half-warp groups of targets (sw_slice_plan.h): for L <= 128 (grid in
+    // shared memory) per batch of slice_batch_of(L) angles, with ray-adjacent
+    // pairs; addresses follow the kernel's FP32 arithmetic.
     std::vector<uint16_t> gtab;
     std::vector<int> goff(1, 0);
-    // tap_rc(k, j, &row, &col, &left): the first tap of target (k, j) on the
-    // N-point grid; nj targets per angle
-    // Which ray-adjacent samples form the pairs is a free choice: each ray is
-    // cut into kPairSegs segments, and a segment either pairs from its first
-    // sample or leaves that sample alone and pairs from the next.  The choice
-    // moves pairs between the classes and bank residues, and a class needs as
-    // many half-warp groups as its fullest residue holds entries, so a local
-    // search picks, ray by ray, the segment phases that lower the sum over
-    // classes of the fullest residue (a host replay at n = 256, B = 192: the
-    // pair groups 74% -> 85% full, 12% fewer of them).
-    constexpr int kPairSegs = 4;
-    struct PairEnt {
-        int cls;       // pattern * 2 + half for a pair; 18 + half for a single target
-        int base;      // first stored address of the footprint (union for a pair)
-        uint16_t ent;  // table entry
-    };
-    auto batch_groups = [&](int batch, int N, int njt, auto tap_rc, std::vector<uint16_t> &tab,
-                            std::vector<int> &off) {
-        const int S = swk::slice_stride(N);
-        // the entries of ray k (batch row kk) with segment phases `mask`
-        auto ray_entries = [&](int k, int kk, int mask, std::vector<PairEnt> &out) {
-            out.clear();
-            int seg = 0;
-            for (int j = 0; j < njt;) {
-                while (seg + 1 < kPairSegs && j >= (seg + 1) * njt / kPairSegs) ++seg;
-                int rA, cA, rB, cB;
-                bool lA, lB;
-                tap_rc(k, j, &rA, &cA, &lA);
-                const uint16_t ent = (uint16_t)(kk * 256 + j);
-                const bool alone = ((mask >> seg) & 1) && j == seg * njt / kPairSegs;
-                if (!alone && j + 1 < njt) {
-                    tap_rc(k, j + 1, &rB, &cB, &lB);
-                    if (lA == lB && std::abs(rA - rB) <= 1 && std::abs(cA - cB) <= 1) {
-                        const int r0 = std::min(rA, rB);
-                        const int c0 = lA ? std::min(cA, cB) : std::max(cA, cB);
-                        const int pr = rA > rB ? 1 : (rB > rA ? 2 : 0);
-                        const int pc = cA != c0 ? 1 : (cB != c0 ? 2 : 0);
-                        out.push_back({(pr * 3 + pc) * 2 + (lA ? 0 : 1), r0 * S + c0,
-                                       (uint16_t)(ent | swk::kSlicePairBit)});
-                        j += 2;
-                        continue;
-                    }
-                }
-                out.push_back({18 + (lA ? 0 : 1), rA * S + cA, ent});
-                j += 1;
-            }
-        };
-        for (int k0 = 0; k0 < nh; k0 += batch) {
-            const int k1 = std::min(nh, k0 + batch), nk = k1 - k0;
-            constexpr int NOPT = 1 << kPairSegs;
-            std::vector<std::array<std::vector<PairEnt>, NOPT>> opt(nk);
-            for (int kk = 0; kk < nk; ++kk)
-                for (int o = 0; o < NOPT; ++o) ray_entries(k0 + kk, kk, o, opt[kk][o]);
-            int cnt[20][16] = {};
-            auto add = [&](const std::vector<PairEnt> &v, int d) {
-                for (const PairEnt &e : v) cnt[e.cls][e.base & 15] += d;
-            };
-            auto cost = [&]() {
-                int c = 0;
-                for (int q = 0; q < 20; ++q) c += *std::max_element(cnt[q], cnt[q] + 16);
-                return c;
-            };
-            std::vector<int> mask(nk, 0);
-            for (int kk = 0; kk < nk; ++kk) add(opt[kk][0], 1);
-            int best = cost();
-            for (int pass = 0; pass < 6; ++pass) {
-                bool moved = false;
-                for (int kk = 0; kk < nk; ++kk)
-                    for (int o = 0; o < NOPT; ++o) {
-                        if (o == mask[kk]) continue;
-                        add(opt[kk][mask[kk]], -1);
-                        add(opt[kk][o], 1);
-                        const int c = cost();
-                        if (c < best) {
-                            best = c;
-                            mask[kk] = o;
-                            moved = true;
-                        } else {
-                            add(opt[kk][o], -1);
-                            add(opt[kk][mask[kk]], 1);
-                        }
-                    }
-                if (!moved) break;
-            }
-            std::map<int, std::vector<uint16_t>> cls[2][16], pcls[9][2][16];
-            for (int kk = 0; kk < nk; ++kk)
-                for (const PairEnt &e : opt[kk][mask[kk]]) {
-                    if (e.cls < 18) pcls[e.cls / 2][e.cls % 2][e.base & 15][e.base].push_back(e.ent);
-                    else cls[e.cls - 18][e.base & 15][e.base].push_back(e.ent);
-                }
-            const size_t g_start = tab.size() / 16;
-            for (auto &pc : pcls) {
-                group(pc, tab, (uint16_t)0xFFFF);
-                if ((tab.size() / 16 - g_start) & 1) tab.insert(tab.end(), 16, (uint16_t)0xFFFF);
-            }
-            group(cls, tab, (uint16_t)0xFFFF);
-            off.push_back((int)(tab.size() / 16));
-        }
-    };
     // L > 128 (grid in global memory, tiles in shared memory): per tile, the
     // targets whose footprint starts in it; entries k << 16 | j; the bank is
     // that of the first tap in the tile's copy (rows kSliceTileRS apart).
     std::vector<uint32_t> ttab;
     std::vector<int> toff(1, 0);
     if (L <= 128) {
-        batch_groups(swk::slice_batch_of(L), t.N, nj,
-                     [&](int k, int j, int *r, int *cc, bool *l) {
-                         swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, r, cc, l);
-                     },
-                     gtab, goff);
+        swk::slice_pair_groups(swk::slice_batch_of(L), nh, t.N, nj,
+                               [&](int k, int j, int *r, int *cc, bool *l) {
+                                   swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, r, cc, l);
+                               },
+                               gtab, goff);
     } else {
         const int TY = swk::slice_tiles_y(t.N), TX = swk::slice_tiles_x(t.N);
         std::vector<std::array<std::array<std::map<int, std::vector<uint32_t>>, 16>, 2>> cls(
@@ -773,7 +593,7 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
                     ((uint32_t)k << 16) | (uint32_t)j);
             }
         for (auto &tc : cls) {
-            group(tc, ttab, 0xFFFFFFFFu);
+            swk::slice_half_warp_groups(tc, ttab, 0xFFFFFFFFu);
             toff.push_back((int)(ttab.size() / 16));
         }
     }
@@ -809,11 +629,11 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
         for (int q = 0; q < Nu; ++q)
             uptw[q] = make_float2((float)std::cos(2.0 * M_PI * q / Nu),
                                   (float)-std::sin(2.0 * M_PI * q / Nu));
-        batch_groups(swk::kUpBatch, Nu, nj,
-                     [&](int k, int j, int *r, int *cc, bool *l) {
-                         swk::slice_up_rc(j, (float)co[k], (float)si[k], Nu, r, cc, l);
-                     },
-                     upgtab, upgoff);
+        swk::slice_pair_groups(swk::kUpBatch, nh, Nu, nj,
+                               [&](int k, int j, int *r, int *cc, bool *l) {
+                                   swk::slice_up_rc(j, (float)co[k], (float)si[k], Nu, r, cc, l);
+                               },
+                               upgtab, upgoff);
     }
     SW_CUDA(c, cudaMalloc(&t.psi_inv, sizeof(float) * L));
     SW_CUDA(c, cudaMemcpy(t.psi_inv, pinv.data(), sizeof(float) * L, cudaMemcpyHostToDevice));

@@ -1,0 +1,154 @@
+// Host check of the Fourier-slice projector's target tables (sw_slice_plan.h)
+// for the grid-in-shared-memory kernels: plain grids (L <= 128, N = B) and
+// the half-size images' own grids (N = B/2).  For every configuration:
+//   - every target (k, j), k < n/2, j <= B/2, is in the table exactly once
+//     (a pair entry stands for j and j + 1), inside its own batch;
+//   - every pair is what the kernel assumes without checking: j + 1 is a
+//     target, and both first taps lie in one half of the grid at most a row
+//     and a column apart (recomputed here from the kernel's geometry);
+//   - the groups are whole half-warps of one pattern and one half of the
+//     grid, the two half-warps of a warp take one pattern path (the kernel's
+//     compile-time case; the half is a run-time direction), and the entries
+//     of a half-warp start on distinct shared-memory banks (address mod 16)
+//     unless they start on the same word;
+//   - the pair groups of the benchmark's grid (n = 256, B = 192) are at least
+//     80% full (the balanced pairing's purpose).
+// Prints "ok" and the fill figures, or the first failure (exit status 1).
+// Host code only: no device is used.
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "sw_slice_plan.h"
+
+using namespace swk;
+
+struct Config {
+    int n, B;
+    bool up;  // half-size images: grid of N = B/2 points, targets by slice_up_rc
+};
+
+static int fail(const Config &c, const char *what, int a = -1, int b = -1)
+{
+    std::printf("FAIL n=%d B=%d up=%d: %s (%d, %d)\n", c.n, c.B, (int)c.up, what, a, b);
+    return 1;
+}
+
+static int check(const Config &c, double *pair_fill)
+{
+    const int nh = c.n / 2, nj = c.B / 2 + 1;
+    const int N = c.up ? c.B / 2 : c.B;
+    const int batch = c.up ? kUpBatch : kSliceBatch;
+    const int S = slice_stride(N);
+    std::vector<double> co, si;
+    angle_table(c.n, co, si);
+    auto tap_rc = [&](int k, int j, int *r, int *cc, bool *l) {
+        if (c.up) slice_up_rc(j, (float)co[k], (float)si[k], N, r, cc, l);
+        else slice_tap_rc(j, (float)co[k], (float)si[k], N, r, cc, l);
+    };
+    std::vector<uint16_t> tab;
+    std::vector<int> off(1, 0);
+    slice_pair_groups(batch, nh, N, nj, tap_rc, tab, off);
+
+    const int nbatch = (nh + batch - 1) / batch;
+    if ((int)off.size() != nbatch + 1) return fail(c, "batch count", (int)off.size(), nbatch);
+    if (tab.size() != 16 * (size_t)off.back()) return fail(c, "table size", (int)tab.size(), off.back());
+    std::vector<int> seen((size_t)nh * nj, 0);
+    long pair_lanes = 0, pair_entries = 0;
+    for (int b = 0; b < nbatch; ++b) {
+        if (off[b + 1] < off[b]) return fail(c, "group offsets decrease", b);
+        const int k0 = b * batch;
+        // warps are two consecutive groups counted from the batch's first group
+        for (int g = off[b]; g < off[b + 1]; ++g) {
+            const bool first_half = ((g - off[b]) & 1) == 0;
+            int bases[16], n_used = 0, pattern = -1;
+            bool any_pair = false;
+            for (int i = 0; i < 16; ++i) {
+                const uint16_t ent = tab[(size_t)g * 16 + i];
+                if (ent == 0xFFFFu) continue;
+                const bool pair = (ent & kSlicePairBit) != 0;
+                const int kk = (ent >> 8) & 63, j = ent & 255;
+                const int k = k0 + kk;
+                if (kk >= batch || k >= nh) return fail(c, "angle outside the batch", k, b);
+                if (j >= nj || (pair && j + 1 >= nj)) return fail(c, "frequency index", k, j);
+                int rA, cA, rB, cB;
+                bool lA, lB;
+                tap_rc(k, j, &rA, &cA, &lA);
+                int base = rA * S + cA;
+                if (pair) {
+                    tap_rc(k, j + 1, &rB, &cB, &lB);
+                    if (lA != lB) return fail(c, "pair across the halves", k, j);
+                    if (std::abs(rA - rB) > 1 || std::abs(cA - cB) > 1)
+                        return fail(c, "pair footprints more than a cell apart", k, j);
+                    const int r0 = std::min(rA, rB);
+                    const int c0 = lA ? std::min(cA, cB) : std::max(cA, cB);
+                    base = r0 * S + c0;
+                    const int pr = rA > rB ? 1 : (rB > rA ? 2 : 0);
+                    const int pc = cA != c0 ? 1 : (cB != c0 ? 2 : 0);
+                    const int pat = (pr * 3 + pc) * 2 + (lA ? 0 : 1);
+                    if (pattern >= 0 && pat != pattern) return fail(c, "two patterns in one group", g, pat);
+                    pattern = pat;
+                    any_pair = true;
+                    ++seen[(size_t)k * nj + j + 1];
+                    ++pair_entries;
+                }
+                ++seen[(size_t)k * nj + j];
+                bases[n_used++] = base;
+            }
+            // distinct banks within the half-warp, unless the same word
+            for (int a = 0; a < n_used; ++a)
+                for (int d = a + 1; d < n_used; ++d)
+                    if ((bases[a] & 15) == (bases[d] & 15) && bases[a] != bases[d])
+                        return fail(c, "bank conflict in a half-warp", g, bases[a] & 15);
+            if (any_pair) {
+                pair_lanes += 16;
+                // the partner half-warp of the same warp takes the same path
+                const int h = first_half ? g + 1 : g - 1;
+                if (h < off[b] || h >= off[b + 1]) return fail(c, "pair group without a partner", g);
+                for (int i = 0; i < 16; ++i) {
+                    const uint16_t ent = tab[(size_t)h * 16 + i];
+                    if (ent == 0xFFFFu) continue;
+                    if (!(ent & kSlicePairBit)) return fail(c, "pair and single targets in one warp", g);
+                    const int kk = (ent >> 8) & 63, j = ent & 255, k = k0 + kk;
+                    int rA, cA, rB, cB;
+                    bool lA, lB;
+                    tap_rc(k, j, &rA, &cA, &lA);
+                    tap_rc(k, j + 1, &rB, &cB, &lB);
+                    const int r0 = std::min(rA, rB);
+                    const int c0 = lA ? std::min(cA, cB) : std::max(cA, cB);
+                    const int pr = rA > rB ? 1 : (rB > rA ? 2 : 0);
+                    const int pc = cA != c0 ? 1 : (cB != c0 ? 2 : 0);
+                    // the path is the pattern; the half is a run-time direction
+                    if (pr * 3 + pc != pattern / 2) return fail(c, "two patterns in one warp", g, h);
+                }
+            }
+        }
+    }
+    for (int k = 0; k < nh; ++k)
+        for (int j = 0; j < nj; ++j)
+            if (seen[(size_t)k * nj + j] != 1)
+                return fail(c, "target not covered exactly once", k, j);
+    *pair_fill = pair_lanes ? (double)pair_entries / (double)pair_lanes : 0.0;
+    return 0;
+}
+
+int main()
+{
+    const Config cases[] = {
+        {256, 192, false}, {360, 192, false}, {1024, 192, false}, {4, 192, false},
+        {256, 96, false},  {60, 96, false},   {20, 64, false},    {512, 32, false},
+        {120, 160, false}, {360, 384, true},  {256, 384, true},   {512, 320, true},
+        {60, 256, true},   {1000, 384, true},
+    };
+    for (const Config &c : cases) {
+        double fill = 0.0;
+        if (check(c, &fill)) return 1;
+        if (c.n == 256 && c.B == 192 && !c.up && fill < 0.80) {
+            std::printf("FAIL n=256 B=192: pair groups %.3f full, below 0.80\n", fill);
+            return 1;
+        }
+        std::printf("n=%d B=%d up=%d pair fill %.3f\n", c.n, c.B, (int)c.up, fill);
+    }
+    std::printf("ok\n");
+    return 0;
+}
