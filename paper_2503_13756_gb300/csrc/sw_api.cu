@@ -577,25 +577,7 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
                                },
                                gtab, goff);
     } else {
-        const int TY = swk::slice_tiles_y(t.N), TX = swk::slice_tiles_x(t.N);
-        std::vector<std::array<std::array<std::map<int, std::vector<uint32_t>>, 16>, 2>> cls(
-            (size_t)TY * TX);
-        for (int k = 0; k < nh; ++k)
-            for (int j = 0; j < nj; ++j) {
-                int row, col;
-                bool left;
-                swk::slice_tap_rc(j, (float)co[k], (float)si[k], t.N, &row, &col, &left);
-                const int cmin = left ? col : col - (W - 1);
-                const int ty = row / swk::kSliceTile, tx = cmin / swk::kSliceTile;
-                const int local = (row - ty * swk::kSliceTile) * swk::kSliceTileRS +
-                                  (col - tx * swk::kSliceTile);
-                cls[(size_t)ty * TX + tx][left ? 0 : 1][local & 15][local].push_back(
-                    ((uint32_t)k << 16) | (uint32_t)j);
-            }
-        for (auto &tc : cls) {
-            swk::slice_half_warp_groups(tc, ttab, 0xFFFFFFFFu);
-            toff.push_back((int)(ttab.size() / 16));
-        }
+        swk::slice_tile_groups(nh, t.N, nj, co, si, ttab, toff);
     }
     // Images of side L/2 upsampled 2 x 2 (128 < L): their own grid of
     // Nu = B/2 points (same oversampling, so the same kernel shape), the

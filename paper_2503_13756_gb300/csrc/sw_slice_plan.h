@@ -219,4 +219,35 @@ void slice_pair_groups(int batch, int nh, int N, int njt, TapRC tap_rc, std::vec
     }
 }
 
+// Target table of the tiled kernels (128 < L, grid in global memory): per
+// tile t of slice_tiles_y(N) x slice_tiles_x(N), the half-warp groups of the
+// targets whose footprint starts in it (entries k << 16 | j, k < nh, j < nj),
+// tab holding the entries and off[t] the first group of tile t (off gains one
+// element per tile).  The bank of an entry is that of its first tap in the
+// tile's shared-memory copy (rows kSliceTileRS apart).  co, si: the angle
+// table (angle_table).
+inline void slice_tile_groups(int nh, int N, int nj, const std::vector<double> &co,
+                              const std::vector<double> &si, std::vector<uint32_t> &tab,
+                              std::vector<int> &off)
+{
+    const int TY = slice_tiles_y(N), TX = slice_tiles_x(N);
+    std::vector<std::array<std::array<std::map<int, std::vector<uint32_t>>, 16>, 2>> cls(
+        (size_t)TY * TX);
+    for (int k = 0; k < nh; ++k)
+        for (int j = 0; j < nj; ++j) {
+            int row, col;
+            bool left;
+            slice_tap_rc(j, (float)co[k], (float)si[k], N, &row, &col, &left);
+            const int cmin = left ? col : col - (kSliceW - 1);
+            const int ty = row / kSliceTile, tx = cmin / kSliceTile;
+            const int local = (row - ty * kSliceTile) * kSliceTileRS + (col - tx * kSliceTile);
+            cls[(size_t)ty * TX + tx][left ? 0 : 1][local & 15][local].push_back(
+                ((uint32_t)k << 16) | (uint32_t)j);
+        }
+    for (auto &tc : cls) {
+        slice_half_warp_groups(tc, tab, 0xFFFFFFFFu);
+        off.push_back((int)(tab.size() / 16));
+    }
+}
+
 }  // namespace swk

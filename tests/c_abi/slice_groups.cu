@@ -1,6 +1,8 @@
-// Host check of the Fourier-slice projector's target tables (sw_slice_plan.h)
-// for the grid-in-shared-memory kernels: plain grids (L <= 128, N = B) and
-// the half-size images' own grids (N = B/2).  For every configuration:
+// Host check of the Fourier-slice projector's target tables (sw_slice_plan.h).
+// The tiled kernels' tables (128 < L): every target once, in the tile where
+// its footprint starts, distinct banks per half-warp.  The tables of the
+// grid-in-shared-memory kernels, for plain grids (L <= 128, N = B) and the
+// half-size images' own grids (N = B/2):
 //   - every target (k, j), k < n/2, j <= B/2, is in the table exactly once
 //     (a pair entry stands for j and j + 1), inside its own batch;
 //   - every pair is what the kernel assumes without checking: j + 1 is a
@@ -132,8 +134,58 @@ static int check(const Config &c, double *pair_fill)
     return 0;
 }
 
+// The tiled kernels' table (128 < L, grid N = B in global memory): every
+// target once, in the tile its footprint starts in, and the entries of a
+// half-warp on distinct banks of the tile's copy unless on the same word.
+static int check_tiles(int n, int B)
+{
+    const Config c{n, B, false};
+    const int nh = n / 2, nj = B / 2 + 1, N = B;
+    const int TY = slice_tiles_y(N), TX = slice_tiles_x(N);
+    std::vector<double> co, si;
+    angle_table(n, co, si);
+    std::vector<uint32_t> tab;
+    std::vector<int> off(1, 0);
+    slice_tile_groups(nh, N, nj, co, si, tab, off);
+    if ((int)off.size() != TY * TX + 1) return fail(c, "tile count", (int)off.size(), TY * TX);
+    if (tab.size() != 16 * (size_t)off.back()) return fail(c, "tile table size", (int)tab.size());
+    std::vector<int> seen((size_t)nh * nj, 0);
+    for (int t = 0; t < TY * TX; ++t) {
+        if (off[t + 1] < off[t]) return fail(c, "tile offsets decrease", t);
+        for (int g = off[t]; g < off[t + 1]; ++g) {
+            int locs[16], n_used = 0;
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t ent = tab[(size_t)g * 16 + i];
+                if (ent == 0xFFFFFFFFu) continue;
+                const int k = (int)(ent >> 16), j = (int)(ent & 0xFFFFu);
+                if (k >= nh || j >= nj) return fail(c, "tile entry out of range", k, j);
+                int row, col;
+                bool left;
+                slice_tap_rc(j, (float)co[k], (float)si[k], N, &row, &col, &left);
+                const int cmin = left ? col : col - (kSliceW - 1);
+                const int ty = row / kSliceTile, tx = cmin / kSliceTile;
+                if (ty * TX + tx != t) return fail(c, "target in another tile's table", k, j);
+                locs[n_used++] = (row - ty * kSliceTile) * kSliceTileRS + (col - tx * kSliceTile);
+                ++seen[(size_t)k * nj + j];
+            }
+            for (int a = 0; a < n_used; ++a)
+                for (int d = a + 1; d < n_used; ++d)
+                    if ((locs[a] & 15) == (locs[d] & 15) && locs[a] != locs[d])
+                        return fail(c, "bank conflict in a tile's half-warp", g, locs[a] & 15);
+        }
+    }
+    for (int k = 0; k < nh; ++k)
+        for (int j = 0; j < nj; ++j)
+            if (seen[(size_t)k * nj + j] != 1)
+                return fail(c, "tile target not covered exactly once", k, j);
+    return 0;
+}
+
 int main()
 {
+    for (int n : {4, 60, 256, 360, 1000})
+        for (int B : {256, 320, 384})
+            if (check_tiles(n, B)) return 1;
     const Config cases[] = {
         {256, 192, false}, {360, 192, false}, {1024, 192, false}, {4, 192, false},
         {256, 96, false},  {60, 96, false},   {20, 64, false},    {512, 32, false},
