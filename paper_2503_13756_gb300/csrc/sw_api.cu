@@ -473,57 +473,6 @@ sw_status get_tables(sw_ctx *c, int n, const Tables **out, int variant = 0)
     return SW_OK;
 }
 
-// Psi(k) = integral over |u| <= W/2 of psi(u) cos(2 pi k u / N) du.  With
-// u = (W/2) sin(phi) the square root becomes cos(phi) and the integrand
-// W/2 exp(beta (cos phi - 1)) cos(pi k W sin(phi) / N) cos(phi) is smooth on
-// [-pi/2, pi/2]; composite Simpson with 2048 panels in FP64.
-double slice_kernel_ft(int k, int N, int W, double beta)
-{
-    const int m = 2048;
-    const double a = 0.5 * M_PI, hstep = a / m;  // integrate 2 x [0, pi/2]
-    double acc = 0.0;
-    for (int i = 0; i <= m; ++i) {
-        const double ph = i * hstep;
-        const double f = std::exp(beta * (std::cos(ph) - 1.0)) *
-                         std::cos(M_PI * k * W * std::sin(ph) / N) * std::cos(ph);
-        acc += f * (i == 0 || i == m ? 1.0 : (i & 1) ? 4.0 : 2.0);
-    }
-    return 2.0 * (0.5 * W) * acc * hstep / 3.0;
-}
-
-// Tap weights as polynomials in the target's offset x in (-1/2, 1/2]: for
-// tap a, psi(x + W/2 - a) interpolated at the W Chebyshev points of
-// [-1/2, 1/2] (degree W - 1 = kSliceDeg), monomial coefficients by Gaussian
-// elimination in FP64.  Error below 1e-8 for the kernel shapes used here.
-void slice_fit_weights(double beta, swk::SliceCoef &out)
-{
-    constexpr int W = swk::kSliceW, D = swk::kSliceDeg + 1;
-    static_assert(D == W, "one interpolation node per coefficient");
-    for (int a = 0; a < W; ++a) {
-        double A[D][D + 1];
-        for (int k = 0; k < D; ++k) {
-            const double x = 0.5 * std::cos(M_PI * (k + 0.5) / D);
-            const double u = x + W / 2 - a, z = 2.0 * u / W;
-            const double arg = 1.0 - z * z;
-            double xp = 1.0;
-            for (int d = 0; d < D; ++d, xp *= x) A[k][d] = xp;
-            A[k][D] = arg >= 0.0 ? std::exp(beta * (std::sqrt(arg) - 1.0)) : 0.0;
-        }
-        for (int col = 0; col < D; ++col) {  // elimination with partial pivoting
-            int piv = col;
-            for (int r = col + 1; r < D; ++r)
-                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
-            for (int q = 0; q <= D; ++q) std::swap(A[col][q], A[piv][q]);
-            for (int r = 0; r < D; ++r) {
-                if (r == col) continue;
-                const double f = A[r][col] / A[col][col];
-                for (int q = col; q <= D; ++q) A[r][q] -= f * A[col][q];
-            }
-        }
-        for (int d = 0; d < D; ++d) out.c[a][d] = (float)(A[d][D] / A[d][d]);
-    }
-}
-
 sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **out)
 {
     const int L = p->L, n = p->n_theta, B = bins_of(p);
@@ -541,10 +490,10 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     // shape for the oversampling sigma = N / L: beta = 0.97 pi (1 - 1/(2 sigma)) W
     const double sigma = (double)t.N / L;
     t.beta = 0.97 * M_PI * (1.0 - 0.5 / sigma) * W;
-    slice_fit_weights(t.beta, t.coef);
+    swk::slice_fit_weights(t.beta, t.coef);
     std::vector<float> pinv(L);
     for (int cidx = 0; cidx < L; ++cidx)
-        pinv[cidx] = (float)(1.0 / slice_kernel_ft(cidx - L / 2, t.N, W, t.beta));
+        pinv[cidx] = (float)(1.0 / swk::slice_kernel_ft(cidx - L / 2, t.N, W, t.beta));
     // per (angle, frequency): sinc(pi t1) sinc(pi t2) (-1)^j e^{i pi j (1 - 2 delta (c + s)) / B}
     const int nh = n / 2, nj = B / 2 + 1;
     const double delta = (L & 1) ? 0.0 : 0.5;
@@ -592,7 +541,7 @@ sw_status get_slice_tables(sw_ctx *c, const sw_params *p, const SliceTables **ou
     if (up) {
         upinv.resize(Lu);
         for (int cidx = 0; cidx < Lu; ++cidx)
-            upinv[cidx] = (float)(1.0 / slice_kernel_ft(cidx - Lu / 2, Nu, W, t.beta));
+            upinv[cidx] = (float)(1.0 / swk::slice_kernel_ft(cidx - Lu / 2, Nu, W, t.beta));
         upfac.resize((size_t)nh * nj);
         for (int k = 0; k < nh; ++k)
             for (int j = 0; j < nj; ++j) {

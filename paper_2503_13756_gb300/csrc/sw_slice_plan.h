@@ -6,8 +6,10 @@
 // banks at every tap, and, for L <= 128 and for half-size images, ray-adjacent
 // samples (j, j + 1) travel as one pair entry over their union footprint.
 // These functions build the tables on the host from the same FP32 geometry
-// the kernels use (slice_tap_rc, slice_up_rc).  Host code only, so that tests
-// can build and check the tables without a device.
+// the kernels use (slice_tap_rc, slice_up_rc), beside the host-side numbers
+// of the spreading kernel (its Fourier transform, its tap-weight
+// polynomials).  Host code only, so that tests can build and check them
+// without a device.
 #pragma once
 
 #include <algorithm>
@@ -55,6 +57,60 @@ inline void angle_table(int n, std::vector<double> &c, std::vector<double> &s)
         }
         c[k] = cc;
         s[k] = ss;
+    }
+}
+
+// The spreading kernel psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)) on
+// |u| <= W/2 (exponential of semicircle), its Fourier transform for the
+// deapodisation and its tap weights as polynomials in the target's offset.
+// Psi(k) = integral over |u| <= W/2 of psi(u) cos(2 pi k u / N) du.  With
+// u = (W/2) sin(phi) the square root becomes cos(phi) and the integrand
+// W/2 exp(beta (cos phi - 1)) cos(pi k W sin(phi) / N) cos(phi) is smooth on
+// [-pi/2, pi/2]; composite Simpson with 2048 panels in FP64.
+inline double slice_kernel_ft(int k, int N, int W, double beta)
+{
+    const int m = 2048;
+    const double a = 0.5 * M_PI, hstep = a / m;  // integrate 2 x [0, pi/2]
+    double acc = 0.0;
+    for (int i = 0; i <= m; ++i) {
+        const double ph = i * hstep;
+        const double f = std::exp(beta * (std::cos(ph) - 1.0)) *
+                         std::cos(M_PI * k * W * std::sin(ph) / N) * std::cos(ph);
+        acc += f * (i == 0 || i == m ? 1.0 : (i & 1) ? 4.0 : 2.0);
+    }
+    return 2.0 * (0.5 * W) * acc * hstep / 3.0;
+}
+
+// Tap weights as polynomials in the target's offset x in (-1/2, 1/2]: for
+// tap a, psi(x + W/2 - a) interpolated at the W Chebyshev points of
+// [-1/2, 1/2] (degree W - 1 = kSliceDeg), monomial coefficients by Gaussian
+// elimination in FP64.  Error below 1e-8 for the kernel shapes used here.
+inline void slice_fit_weights(double beta, SliceCoef &out)
+{
+    constexpr int W = kSliceW, D = kSliceDeg + 1;
+    static_assert(D == W, "one interpolation node per coefficient");
+    for (int a = 0; a < W; ++a) {
+        double A[D][D + 1];
+        for (int k = 0; k < D; ++k) {
+            const double x = 0.5 * std::cos(M_PI * (k + 0.5) / D);
+            const double u = x + W / 2 - a, z = 2.0 * u / W;
+            const double arg = 1.0 - z * z;
+            double xp = 1.0;
+            for (int d = 0; d < D; ++d, xp *= x) A[k][d] = xp;
+            A[k][D] = arg >= 0.0 ? std::exp(beta * (std::sqrt(arg) - 1.0)) : 0.0;
+        }
+        for (int col = 0; col < D; ++col) {  // elimination with partial pivoting
+            int piv = col;
+            for (int r = col + 1; r < D; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            for (int q = 0; q <= D; ++q) std::swap(A[col][q], A[piv][q]);
+            for (int r = 0; r < D; ++r) {
+                if (r == col) continue;
+                const double f = A[r][col] / A[col][col];
+                for (int q = col; q <= D; ++q) A[r][q] -= f * A[col][q];
+            }
+        }
+        for (int d = 0; d < D; ++d) out.c[a][d] = (float)(A[d][D] / A[d][d]);
     }
 }
 

@@ -8,8 +8,11 @@ grid period (T(-s) = conj T(s) when folded); and a second program
 (tests/c_abi/slice_groups.cu) builds the interpolation's target tables with
 the library's host code (sw_slice_plan.h) and checks that every target is
 covered exactly once, that every pair entry is one the kernel can take
-without a check, and the half-warp grouping the kernel's speed relies on.
-Host code only: no device."""
+without a check, and the half-warp grouping the kernel's speed relies on;
+a third (tests/c_abi/slice_kernel.cu) checks the spreading kernel's host-side
+numbers (tap-weight polynomials, Fourier transform) against FP64 references
+and the accuracy of a 1-D type-2 NUFFT made of them.  Host code only: no
+device."""
 import os
 import shutil
 import subprocess
@@ -44,4 +47,11 @@ def test_every_tap_inside_the_stored_grid(tmp_path):
 
 def test_target_tables_cover_every_target_once(tmp_path):
     out = _build_and_run(tmp_path, "slice_groups")
+    assert out.rstrip().endswith("ok"), out
+
+
+def test_spreading_kernel_numbers_and_nufft_accuracy(tmp_path):
+    # tap-weight polynomials against the kernel, its Fourier transform against
+    # quadrature, and a 1-D type-2 NUFFT of these parts against the direct sum
+    out = _build_and_run(tmp_path, "slice_kernel")
     assert out.rstrip().endswith("ok"), out
