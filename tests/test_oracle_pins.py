@@ -250,8 +250,8 @@ def test_quarter_and_half_turn_images_align_exactly(translation):
 
 
 def test_rotation_by_grid_multiple_on_analytic_projections():
-    # North star: zero distance and the exact shift when an image is compared
-    # with itself rotated by a multiple of 2 pi / n.  Done on analytic
+    # Zero distance and the exact shift when an image is compared with itself
+    # rotated by a multiple of 2 pi / n.  Done on analytic
     # projections, where rotating the mixture is exact.
     rng = np.random.default_rng(8)
     n, M, B, h = 40, 32, 182, 2 / 128
