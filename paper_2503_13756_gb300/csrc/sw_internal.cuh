@@ -379,6 +379,33 @@ constexpr int kSliceDeg = 8;
 struct SliceCoef {
     float c[kSliceW][kSliceDeg + 1];
 };
+// The W tap weights at offset x: w[a] = sum_d c[a][d] x^d.  psi is even, so
+// tap W-1-a at x is tap a at -x (c[W-1-a][d] = (-1)^d c[a][d]); a mirrored
+// pair shares the even and odd parts of the polynomial in x^2,
+// w = E(x^2) +- x O(x^2), and the middle tap is E alone: 41 FMAs per axis
+// instead of 72 for nine Horner chains in x.  Reads rows 0..W/2 only.
+__host__ __device__ __forceinline__ void slice_tap_weights(const SliceCoef &cf, float x,
+                                                           float (&w)[kSliceW])
+{
+    static_assert(kSliceW % 2 == 1 && kSliceDeg % 2 == 0, "odd tap count, even degree");
+    constexpr int H = kSliceW / 2;
+    const float s = x * x;
+#pragma unroll
+    for (int a = 0; a <= H; ++a) {
+        float e = cf.c[a][kSliceDeg];
+#pragma unroll
+        for (int d = kSliceDeg - 2; d >= 0; d -= 2) e = fmaf(e, s, cf.c[a][d]);
+        if (a == H) {
+            w[a] = e;
+        } else {
+            float o = cf.c[a][kSliceDeg - 1];
+#pragma unroll
+            for (int d = kSliceDeg - 3; d >= 1; d -= 2) o = fmaf(o, s, cf.c[a][d]);
+            w[a] = fmaf(x, o, e);
+            w[kSliceW - 1 - a] = fmaf(-x, o, e);
+        }
+    }
+}
 // Angles per batch of the slice projector's interpolation (two per warp in
 // the inverse FFTs).
 constexpr int kSliceBatch = 64;

@@ -283,6 +283,17 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
 __device__ __forceinline__ void slice_weights(const SliceArgs &A, float x1, float x2,
                                               float (&wx)[kSliceW], float (&wy)[kSliceW])
 {
+    slice_tap_weights(A.coef, x1, wx);
+    slice_tap_weights(A.coef, x2, wy);
+}
+
+// The same weights by one Horner chain in x per tap, from every row of the
+// (mirror-symmetric) coefficient table: 72 FMAs per axis, but fewer values
+// live at once, which the upsampled-image kernel needs to stay within its
+// registers.
+__device__ __forceinline__ void slice_weights_horner(const SliceArgs &A, float x1, float x2,
+                                                     float (&wx)[kSliceW], float (&wy)[kSliceW])
+{
 #pragma unroll
     for (int a = 0; a < kSliceW; ++a) {
         float px = A.coef.c[a][kSliceDeg], py = A.coef.c[a][kSliceDeg];
@@ -340,7 +351,7 @@ __device__ __forceinline__ void slice_target_up(const SliceArgs &A, int k, int j
     int i1, i2;
     float x1, x2;
     slice_up_tap(j, e.x, e.y, N, &i1, &i2, &x1, &x2, &conj);
-    slice_weights(A, x1, x2, wx, wy);
+    slice_weights_horner(A, x1, x2, wx, wy);
     row0 = i2 - slice_lo(N);
     left = i1 <= 0;
     col0 = left ? i1 - slice_lo(N) : slice_left(N) + slice_right(N) - i1;

@@ -85,11 +85,15 @@ inline double slice_kernel_ft(int k, int N, int W, double beta)
 // tap a, psi(x + W/2 - a) interpolated at the W Chebyshev points of
 // [-1/2, 1/2] (degree W - 1 = kSliceDeg), monomial coefficients by Gaussian
 // elimination in FP64.  Error below 1e-8 for the kernel shapes used here.
+// The nodes are symmetric and psi is even, so the interpolant of tap W-1-a
+// is that of tap a at -x: taps 0..W/2 are fitted, the others mirrored
+// (c[W-1-a][d] = (-1)^d c[a][d]) and the middle tap's odd terms are zero,
+// which is the form slice_tap_weights evaluates.
 inline void slice_fit_weights(double beta, SliceCoef &out)
 {
     constexpr int W = kSliceW, D = kSliceDeg + 1;
     static_assert(D == W, "one interpolation node per coefficient");
-    for (int a = 0; a < W; ++a) {
+    for (int a = 0; a <= W / 2; ++a) {
         double A[D][D + 1];
         for (int k = 0; k < D; ++k) {
             const double x = 0.5 * std::cos(M_PI * (k + 0.5) / D);
@@ -112,6 +116,9 @@ inline void slice_fit_weights(double beta, SliceCoef &out)
         }
         for (int d = 0; d < D; ++d) out.c[a][d] = (float)(A[d][D] / A[d][d]);
     }
+    for (int d = 1; d < D; d += 2) out.c[W / 2][d] = 0.f;
+    for (int a = W / 2 + 1; a < W; ++a)
+        for (int d = 0; d < D; ++d) out.c[a][d] = (d & 1) ? -out.c[W - 1 - a][d] : out.c[W - 1 - a][d];
 }
 
 // Half-warp groups from classes of targets.  cls[half][residue] maps a first

@@ -2,9 +2,11 @@
 // (sw_slice_plan.h) against independent FP64 references, for the kernel
 // shapes beta = 0.97 pi (1 - 1/(2 sigma)) W of the oversampling factors
 // sigma = N / L the library uses (1.5 to 3):
-//   1. the tap-weight polynomials (FP32 coefficients, evaluated in FP32 as
-//      the kernels do) against psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)) at
-//      u = x + W/2 - a (W/2 = 4) over offsets x in [-1/2, 1/2];
+//   1. the tap-weight polynomials (FP32 coefficients, evaluated in FP32 by
+//      the kernels' own slice_tap_weights) against psi(u) = exp(beta (sqrt(1
+//      - (2u/W)^2) - 1)) at u = x + W/2 - a (W/2 = 4) over offsets x in
+//      [-1/2, 1/2], and every row of the coefficient table (the mirrored taps
+//      included) by Horner against that evaluation;
 //   2. the kernel's Fourier transform Psi(k) against a midpoint rule in u;
 //   3. a one-dimensional type-2 NUFFT made of exactly these parts (divide by
 //      Psi, N-point DFT, W taps of the polynomial weights) against the direct
@@ -31,8 +33,17 @@ static double psi(double u, double beta)
 
 static double beta_of(double sigma) { return 0.97 * M_PI * (1.0 - 0.5 / sigma) * kSliceW; }
 
-// FP32 Horner of the FP32 coefficients, as slice_weights evaluates them
+// Tap a's weight as the kernels evaluate it (slice_tap_weights: FP32, the
+// mirrored taps from the even and odd parts in x^2)
 static float weight_fp32(const SliceCoef &cf, int a, float x)
+{
+    float w[kSliceW];
+    slice_tap_weights(cf, x, w);
+    return w[a];
+}
+
+// FP32 Horner in x of tap a's row of the coefficient table
+static float horner_fp32(const SliceCoef &cf, int a, float x)
 {
     float p = cf.c[a][kSliceDeg];
     for (int d = kSliceDeg - 1; d >= 0; --d) p = std::fmaf(p, x, cf.c[a][d]);
@@ -42,8 +53,9 @@ static float weight_fp32(const SliceCoef &cf, int a, float x)
 int main()
 {
     const int W = kSliceW;
-    // 1. tap weights
-    double worst_w = 0.0;
+    // 1. tap weights, and the table rows (mirrored taps included) against
+    //    the evaluation the kernels use
+    double worst_w = 0.0, worst_rows = 0.0;
     for (double sigma : {1.5, 1.6, 2.0, 3.0}) {
         const double beta = beta_of(sigma);
         SliceCoef cf;
@@ -53,7 +65,13 @@ int main()
                 const float x = (float)(-0.5 + i / 4000.0);
                 const double err = std::fabs((double)weight_fp32(cf, a, x) - psi((double)x + W / 2 - a, beta));
                 worst_w = std::fmax(worst_w, err);
+                worst_rows = std::fmax(worst_rows, std::fabs((double)horner_fp32(cf, a, x) -
+                                                             (double)weight_fp32(cf, a, x)));
             }
+    }
+    if (!(worst_rows < 2e-7)) {
+        std::printf("FAIL coefficient rows: max |Horner(row a) - tap a| = %.3e\n", worst_rows);
+        return 1;
     }
     // psi peaks at 1; FP32 evaluation of a degree-8 polynomial with
     // coefficients of a few units leaves a few 1e-7
@@ -144,7 +162,7 @@ int main()
         std::printf("FAIL NUFFT: relative l2 error %.3e\n", worst_nufft);
         return 1;
     }
-    std::printf("tap weights %.3e, kernel transform %.3e, NUFFT %.3e\nok\n", worst_w, worst_ft,
-                worst_nufft);
+    std::printf("tap weights %.3e (table rows %.3e), kernel transform %.3e, NUFFT %.3e\nok\n", worst_w,
+                worst_rows, worst_ft, worst_nufft);
     return 0;
 }
