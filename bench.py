@@ -60,8 +60,8 @@ def slice_flops_per_image(Lc, n, B):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the slice projector kernel, from one ncu capture of a 512-image launch
-# (73,154,048 bytes); None once that kernel changes.
-SLICE_DRAM_BYTES_PER_IMAGE = 73154048 / 512
+# (33,824,768 + 40,143,104 bytes); None once that kernel changes.
+SLICE_DRAM_BYTES_PER_IMAGE = 73967872 / 512
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128 x 128 image
 # of the four-angle projection kernel, from one ncu capture of its 2112-image
 # launch (2048 queries and 64 templates in one launch: 277,210,112 bytes);
