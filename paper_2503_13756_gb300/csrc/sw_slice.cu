@@ -35,7 +35,9 @@
 //     psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)); the W weights along each
 //     axis are degree-8 polynomials in the target's offset from its grid
 //     cell (fitted on the host in FP64 within 1e-8 of psi; coefficients in
-//     the kernel parameters), and the cell's sinc factors and the phase come
+//     the kernel parameters; psi is even, so the mirrored taps a and W-1-a
+//     share the even and odd parts of one polynomial in the offset squared),
+//     and the cell's sinc factors and the phase come
 //     from a host table per (angle, frequency).  The targets of an angle batch
 //     run in host-ordered half-warp groups.
 //  D. one warp per pair of angles (X_a + i X_b, both Hermitian): B-point
@@ -279,7 +281,8 @@ __device__ __forceinline__ void slice_grid(const SliceArgs &A, const float *__re
 }
 
 // Tap weights along each axis from the target's offsets (x1, x2) from its
-// cell: the degree-8 polynomials of the kernel parameters.
+// cell: the degree-8 polynomials of the kernel parameters, evaluated per
+// mirrored pair of taps (slice_tap_weights).
 __device__ __forceinline__ void slice_weights(const SliceArgs &A, float x1, float x2,
                                               float (&wx)[kSliceW], float (&wy)[kSliceW])
 {
