@@ -379,6 +379,12 @@ constexpr int kSliceDeg = 8;
 struct SliceCoef {
     float c[kSliceW][kSliceDeg + 1];
 };
+// "#pragma unroll" in the device pass only (host compilers do not know it).
+#ifdef __CUDA_ARCH__
+#define SW_DEVICE_UNROLL _Pragma("unroll")
+#else
+#define SW_DEVICE_UNROLL
+#endif
 // The W tap weights at offset x: w[a] = sum_d c[a][d] x^d.  psi is even, so
 // tap W-1-a at x is tap a at -x (c[W-1-a][d] = (-1)^d c[a][d]); a mirrored
 // pair shares the even and odd parts of the polynomial in x^2,
@@ -390,16 +396,16 @@ __host__ __device__ __forceinline__ void slice_tap_weights(const SliceCoef &cf, 
     static_assert(kSliceW % 2 == 1 && kSliceDeg % 2 == 0, "odd tap count, even degree");
     constexpr int H = kSliceW / 2;
     const float s = x * x;
-#pragma unroll
+SW_DEVICE_UNROLL
     for (int a = 0; a <= H; ++a) {
         float e = cf.c[a][kSliceDeg];
-#pragma unroll
+SW_DEVICE_UNROLL
         for (int d = kSliceDeg - 2; d >= 0; d -= 2) e = fmaf(e, s, cf.c[a][d]);
         if (a == H) {
             w[a] = e;
         } else {
             float o = cf.c[a][kSliceDeg - 1];
-#pragma unroll
+SW_DEVICE_UNROLL
             for (int d = kSliceDeg - 3; d >= 1; d -= 2) o = fmaf(o, s, cf.c[a][d]);
             w[a] = fmaf(x, o, e);
             w[kSliceW - 1 - a] = fmaf(-x, o, e);
